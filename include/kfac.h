@@ -1,0 +1,186 @@
+/*
+ * kfac.h - C ABI of the GB300 (sm_103a) randomized K-FAC library.
+ *
+ * The library implements the data-parallel hot path of randomized K-FAC
+ * (C. O. Puiu, "Randomized K-FACs: Speeding up K-FAC with Randomized Numerical
+ * Linear Algebra", arXiv 2206.15397):
+ *   - the exponentially averaged (EA) Kronecker-factor update (Alg. 1, the
+ *     forward- and backward-factor EA lines; closed form Eq. (6));
+ *   - the randomized low-rank eigendecomposition of a factor (Alg. 3, SREVD,
+ *     with the power iterations of Sec. 2.2): Gaussian sketch, power
+ *     iterations, orthonormalisation, projected eigenproblem C = Q^T F Q, lift;
+ *   - the damped low-rank preconditioner apply (Alg. 4, the M and S lines,
+ *     with the low-rank inverse of Eq. (13); Alg. 5 feeds it U~).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are dense, row-major, FP32, with a leading dimension (ld, in
+ *     elements, >= the column count). Every matrix pointer is DEVICE memory of
+ *     the context's device, owned by the caller; the library never frees or
+ *     retains it after the call's work has completed on the stream.
+ *   - Calls are stream-ordered and asynchronous on the context's stream.
+ *     Argument errors are detected on the host and returned synchronously
+ *     before anything is enqueued. Numerical conditions met on the device
+ *     (Cholesky breakdown, non-convergence, non-finite values) are recorded in
+ *     a device status word and returned by kfac_get_status().
+ *   - The library owns one workspace per context (device memory it allocates
+ *     itself and grows on demand; kfac_reserve() pre-sizes it, which a caller
+ *     that captures calls into a CUDA graph must do first).
+ *   - A context is not thread-safe: one host thread at a time.
+ *   - No call aborts, traps or prints.
+ */
+#ifndef KFAC_H_
+#define KFAC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KFAC_API __attribute__((visibility("default")))
+#else
+#define KFAC_API
+#endif
+
+typedef enum {
+  KFAC_OK = 0,
+  KFAC_ERR_INVALID_ARG = 1,  /* bad size, null pointer, ld too small, ...      */
+  KFAC_ERR_CUDA = 2,         /* a CUDA runtime call failed                      */
+  KFAC_ERR_OOM = 3,          /* workspace allocation failed                     */
+  KFAC_ERR_CHOLESKY = 4,     /* Gram Cholesky broke down even after shifting    */
+  KFAC_ERR_NOCONVERGE = 5,   /* Jacobi sweep limit reached                      */
+  KFAC_ERR_NONFINITE = 6,    /* NaN/Inf met in an input or an intermediate      */
+  KFAC_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up              */
+  KFAC_ERR_UNSUPPORTED = 8   /* valid request this build does not implement     */
+} kfac_status;
+
+/* Arithmetic of the large GEMMs (EA SYRK, sketch / power / projection, apply).
+ * The orthonormalisation and the eigensolve keep their own precision (FP32
+ * tensor/SIMT products with FP64 Cholesky and FP64 eigen-refinement) in every
+ * mode. */
+typedef enum {
+  KFAC_PREC_FP32 = 0,  /* FP32-accurate products (3xTF32 split on tensor cores)  */
+  KFAC_PREC_TF32 = 1,  /* single-pass TF32 tensor-core products, FP32 accumulate */
+  KFAC_PREC_BF16 = 2   /* BF16 operands on tensor cores, FP32 accumulate         */
+} kfac_precision;
+
+/* Device status bits accumulated since the last kfac_get_status(). */
+enum {
+  KFAC_FLAG_CHOL_SHIFTED = 1 << 0,   /* a Gram Cholesky needed an extra diagonal shift  */
+  KFAC_FLAG_CHOL_FAILED = 1 << 1,    /* ... and still broke down                       */
+  KFAC_FLAG_EIG_NOCONV = 1 << 2,     /* Jacobi hit its sweep cap                       */
+  KFAC_FLAG_NONFINITE = 1 << 3,      /* NaN/Inf seen                                   */
+  KFAC_FLAG_EIG_SHIFTED = 1 << 4,    /* eigensolver needed a larger PD shift           */
+  KFAC_FLAG_TIMEOUT = 1 << 5         /* a bounded device wait expired                  */
+};
+
+typedef struct kfac_ctx kfac_ctx;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+KFAC_API int kfac_version(void);
+
+/* Static, human-readable name of a status code. Never NULL. */
+KFAC_API const char* kfac_status_string(kfac_status st);
+
+/* Create a context bound to CUDA device `device` and stream `stream` (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream). *out
+ * receives an opaque handle owned by the caller (free with kfac_destroy). */
+KFAC_API kfac_status kfac_create(kfac_ctx** out, int device, void* stream);
+
+/* Synchronise the context's stream and release its workspace and handle. */
+KFAC_API kfac_status kfac_destroy(kfac_ctx* ctx);
+
+/* Re-bind the context to another stream of the same device. */
+KFAC_API kfac_status kfac_set_stream(kfac_ctx* ctx, void* stream);
+
+/* Pre-size the workspace for calls with factor dimension <= d_max, sketch
+ * width k = rank + oversample <= k_max and preconditioned matrices of at most
+ * mn_max elements (0 = none). Needed before graph capture; optional otherwise. */
+KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t mn_max);
+
+/* EA K-factor update, Alg. 1 (forward / backward factor EA lines):
+ *     F <- rho * F + (1 - rho) / n * X X^T
+ * X: d x n batch matrix (one column per sample, row stride ldx >= n).
+ * F: d x d symmetric factor, in/out (row stride ldf >= d); both triangles are
+ *    written, and the result is exactly symmetric.
+ * prec selects the product arithmetic (FP32 / TF32 / BF16 operands).
+ * The 1/n normalisation reads Alg. 1's A A^T as the batch mean. */
+KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X, int ldx, float rho,
+                                    kfac_precision prec, float* F, int ldf);
+
+/* Randomized low-rank eigendecomposition + damping coefficients of one
+ * symmetric PSD factor F (d x d), Alg. 3 with power iterations (Sec. 2.2):
+ *     Y = F Omega; Q = orth(Y); repeat power_iters times: Q = orth(F Q);
+ *     C = Q^T F Q; C = P diag(L) P^T (descending); U = Q P[:, :r]; D = L[:r];
+ *     coef_i = 1/(max(D_i, 0) + lambda) - 1/lambda            (Eq. (13))
+ * k = rank + oversample columns are sketched; r = min(rank, d) are returned.
+ * When k >= d the factor is diagonalised directly (Q = I).
+ * omega: d x k Gaussian test matrix (row stride ldo >= k), caller-drawn (the
+ *        library draws no random numbers). Ignored when k >= d (may be NULL).
+ * U: d x r output (row stride ldu >= r); D, coef: r outputs.
+ * F must hold the full symmetric matrix (both triangles are read; F is not
+ * modified). power_iters counts extra products F Q, each followed by a fresh
+ * orthonormalisation, so the basis spans F^(power_iters + 1) Omega. */
+KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
+                                      int power_iters, float lambda, const float* omega, int ldo,
+                                      kfac_precision prec, float* U, int ldu, float* D, float* coef);
+
+/* Damped Kronecker preconditioner apply, Alg. 4 (M and S lines) with Eq. (13):
+ *     M = J U_a diag(coef_a) U_a^T + J / lambda
+ *     S = U_g diag(coef_g) U_g^T M + M / lambda
+ * i.e. S = (U_g D_g U_g^T + lambda I)^-1 J (U_a D_a U_a^T + lambda I)^-1.
+ * J: d_g x d_a gradient matrix Mat(g) (row stride ldj >= d_a; bias gradient in
+ *    the last column when the layer has a bias).
+ * U_a: d_a x r_a (ld_ua >= r_a), coef_a: r_a; U_g: d_g x r_g (ld_ug >= r_g),
+ * coef_g: r_g. r_a or r_g may be 0. lambda must equal the value given to
+ * kfac_rsvd_invert. S: d_g x d_a output (lds >= d_a); S must not alias J. */
+KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const float* J, int ldj,
+                                       const float* U_a, int ld_ua, const float* coef_a, int r_a,
+                                       const float* U_g, int ld_ug, const float* coef_g, int r_g,
+                                       float lambda, kfac_precision prec, float* S, int lds);
+
+/* Synchronise the context's stream, return KFAC_OK or the most severe device
+ * condition recorded since the last call, store the raw KFAC_FLAG_* bits in
+ * *flags (may be NULL) and clear them. */
+KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags);
+
+/* Tunables (defaults in brackets). Returns KFAC_ERR_INVALID_ARG for an unknown
+ * option or an out-of-range value. */
+typedef enum {
+  KFAC_OPT_CHOLQR_PASSES = 0,   /* CholeskyQR passes per orthonormalisation [3], 1..6     */
+  KFAC_OPT_CHOLQR_SHIFT = 1,    /* first-pass diagonal shift, relative to trace(G) [1e-6] */
+  KFAC_OPT_EIG_REFINE = 2,      /* FP64 eigen-refinement steps after FP32 Jacobi [1], 0..3 */
+  KFAC_OPT_EIG_MAX_SWEEPS = 3,  /* Jacobi sweep cap [40]                                  */
+  KFAC_OPT_EIG_TOL = 4          /* Jacobi pair-orthogonality threshold [4e-7]            */
+} kfac_option;
+
+KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double value);
+
+/* Per-stage device timing (CUDA events recorded on the context stream around
+ * every kernel group; off by default). kfac_profile_enable(ctx, 1) starts
+ * recording and clears the totals. kfac_profile_read() synchronises the stream,
+ * and for i < min(max_stages, KFAC_NUM_STAGES) stores the stage name (static
+ * string), the summed device milliseconds and the number of timed launches,
+ * sets *n_stages to the number of stages written, and clears the totals. */
+#define KFAC_NUM_STAGES 15
+KFAC_API kfac_status kfac_profile_enable(kfac_ctx* ctx, int on);
+KFAC_API kfac_status kfac_profile_read(kfac_ctx* ctx, const char** names, double* total_ms, int* launches,
+                                       int max_stages, int* n_stages);
+
+/* Number of kernels this library has launched in the process so far (all
+ * contexts). Used to count device work inside a timed region. */
+KFAC_API uint64_t kfac_kernel_launch_count(void);
+
+/* Device-side counters of the context, read after synchronising its stream and
+ * then cleared: out[0] = Jacobi sweeps performed, out[1] = Jacobi solves,
+ * out[2] = Gram Cholesky factorisations, out[3] = extra Cholesky shift attempts.
+ * n = number of entries of out (at most 4 are written). */
+KFAC_API kfac_status kfac_stats_read(kfac_ctx* ctx, int64_t* out, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KFAC_H_ */

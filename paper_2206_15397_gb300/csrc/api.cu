@@ -1,0 +1,559 @@
+// C ABI of libkfac: context, workspace, argument checks and the orchestration
+// of the kernels that make up each entry point.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm.cuh"
+
+namespace {
+enum Stage {
+  ST_EA, ST_TRANSPOSE, ST_SKETCH, ST_GRAM, ST_CHOL, ST_TRSM, ST_PROJ, ST_EIG, ST_REFINE, ST_SELECT, ST_LIFT,
+  ST_APPLY_T, ST_APPLY_M, ST_APPLY_T2, ST_APPLY_S, ST_COUNT
+};
+const char* const kStageNames[ST_COUNT] = {
+    "ea_syrk", "omega_transpose", "sketch_gemm", "cholqr_gram", "cholqr_chol", "cholqr_trsm", "projection_gram",
+    "eig_jacobi", "eig_refine", "eig_select", "lift_gemm", "apply_T", "apply_M", "apply_T2", "apply_S"};
+static_assert(ST_COUNT == KFAC_NUM_STAGES, "stage table");
+
+// CUDA-event pairs recorded around each kernel group when profiling is on.
+struct Profiler {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[ST_COUNT];
+  size_t used[ST_COUNT] = {};
+  ~Profiler() {
+    for (auto& v : ev)
+      for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+  }
+};
+}  // namespace
+
+struct kfac_ctx {
+  Profiler prof;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* dflags = nullptr;  // device status word
+  unsigned long long* dstats = nullptr;  // STAT_COUNT device counters
+  // options
+  int cholqr_passes = 3;
+  double cholqr_shift = 1e-6;
+  int eig_refine = 1;
+  int eig_max_sweeps = 40;
+  double eig_tol = 2e-6;
+};
+
+namespace {
+
+using namespace kfac;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Bump allocator over the context workspace (256-byte aligned slices).
+struct Bump {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+kfac_status ensure_ws(kfac_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return KFAC_OK;
+  if (ctx->ws) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = std::max(bytes, size_t(1) << 20);
+  if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    return KFAC_ERR_OOM;
+  }
+  ctx->ws_bytes = want;
+  return KFAC_OK;
+}
+
+template <typename T>
+T* at(kfac_ctx* ctx, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ctx->ws) + off);
+}
+
+Round to_round(kfac_precision p) {
+  return p == KFAC_PREC_BF16 ? Round::BF16 : (p == KFAC_PREC_TF32 ? Round::TF32 : Round::None);
+}
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return KFAC_ERR_CUDA;   \
+  } while (0)
+
+inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// Records a start event now and an end event when the scope closes.
+struct StageScope {
+  kfac_ctx* c;
+  int st;
+  long long idx = -1;
+  StageScope(kfac_ctx* ctx, int stage) : c(ctx), st(stage) {
+    Profiler& p = c->prof;
+    if (!p.on) return;
+    if (p.used[st] == p.ev[st].size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+      p.ev[st].push_back({a, b});
+    }
+    idx = (long long)p.used[st]++;
+    cudaEventRecord(p.ev[st][idx].first, c->stream);
+  }
+  ~StageScope() {
+    if (idx >= 0) cudaEventRecord(c->prof.ev[st][idx].second, c->stream);
+  }
+};
+#define STAGE(ctx, st) StageScope stage_scope_##st(ctx, st)
+
+// ---- invert ------------------------------------------------------------------
+
+struct InvertLayout {
+  size_t om, y, q, part, g, l32, c, x, lam, work, jac, p32, total;
+  long long dp;
+  int nsplit, kchunk;
+};
+
+InvertLayout invert_layout(int d, int k, int r) {
+  InvertLayout L = {};
+  Bump b;
+  if (k >= d) {  // exact path
+    int n = d;
+    L.c = b.take<double>((size_t)n * n);
+    L.x = b.take<double>((size_t)n * n);
+    L.lam = b.take<double>(n);
+    L.work = b.take<double>(5 * (size_t)n * n);
+    L.jac = b.take<float>((size_t)n * n);
+    L.total = b.off;
+    return L;
+  }
+  L.dp = round_up(d, 4);
+  L.nsplit = (int)std::min<long long>(16, std::max<long long>(1, d / 512));
+  L.kchunk = (int)round_up((d + L.nsplit - 1) / L.nsplit, 16);
+  L.nsplit = (d + L.kchunk - 1) / L.kchunk;
+  L.om = b.take<float>((size_t)k * L.dp);
+  L.y = b.take<float>((size_t)k * L.dp);
+  L.q = b.take<float>((size_t)k * L.dp);
+  L.part = b.take<float>((size_t)L.nsplit * k * k);
+  L.g = b.take<double>((size_t)k * k);
+  L.l32 = b.take<float>((size_t)k * k);
+  L.c = b.take<double>((size_t)k * k);
+  L.x = b.take<double>((size_t)k * k);
+  L.lam = b.take<double>(k);
+  L.work = b.take<double>(5 * (size_t)k * k);
+  L.jac = b.take<float>((size_t)k * k);
+  L.p32 = b.take<float>((size_t)k * r);
+  L.total = b.off;
+  return L;
+}
+
+// Gram-type product out = A A'^T (k x k, K = d) for two k x d row-major
+// operands, split over K with FP32 partials reduced (and symmetrised) in FP64.
+kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const float* Bm, long long ld, int k,
+                     int d, kfac_precision prec, double* out, int stage) {
+  GemmDesc<float> g = {};
+  g.M = k; g.N = k; g.K = d;
+  g.A = A; g.sam = ld; g.sak = 1;
+  g.B = Bm; g.sbn = ld; g.sbk = 1;
+  g.D = at<float>(ctx, L.part); g.ldd = k;
+  g.alpha = 1.0f;
+  g.zsplit = L.nsplit; g.kchunk = L.kchunk; g.zstride = (long long)k * k;
+  StageScope sc(ctx, stage);
+  CK(gemm_f32(g, prec, ctx->stream));
+  CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, 1, ctx->dflags, ctx->stream));
+  return KFAC_OK;
+}
+
+// Yt_out (k x d) = Xt (k x d) F: the sketch / power / projection product. F is
+// symmetric, so B(n, kk) = F[n][kk] reads F row-major.
+kfac_status sketch_product(kfac_ctx* ctx, const float* Xt, long long ldx, const float* F, int ldf, int k, int d,
+                           kfac_precision prec, float* out, long long ldo) {
+  GemmDesc<float> g = {};
+  g.M = k; g.N = d; g.K = d;
+  g.A = Xt; g.sam = ldx; g.sak = 1;
+  g.B = F; g.sbn = ldf; g.sbk = 1;
+  g.D = out; g.ldd = ldo;
+  g.alpha = 1.0f; g.zsplit = 1;
+  STAGE(ctx, ST_SKETCH);
+  CK(gemm_f32(g, prec, ctx->stream));
+  return KFAC_OK;
+}
+
+kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, float*& other, int k, int d) {
+  for (int pass = 0; pass < ctx->cholqr_passes; ++pass) {
+    kfac_status st = gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM);
+    if (st != KFAC_OK) return st;
+    {
+      STAGE(ctx, ST_CHOL);
+      CK(chol_f64_cluster(at<double>(ctx, L.g), k, pass == 0 ? ctx->cholqr_shift : 0.0, at<float>(ctx, L.l32),
+                          ctx->dflags, ctx->dstats, ctx->stream));
+    }
+    {
+      STAGE(ctx, ST_TRSM);
+      CK(trsm_lower_f32(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, ctx->stream));
+    }
+    std::swap(cur, other);
+  }
+  return KFAC_OK;
+}
+
+kfac_status eigensolve(kfac_ctx* ctx, const double* C, int n, double* X, double* lam, double* work, float* jac) {
+  {
+    STAGE(ctx, ST_EIG);
+    CK(eig_onesided_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, X, lam, jac, ctx->dflags,
+                        ctx->dstats, ctx->stream));
+  }
+  STAGE(ctx, ST_REFINE);
+  for (int it = 0; it < ctx->eig_refine; ++it) CK(eig_refine_f64(C, n, X, lam, work, ctx->dflags, ctx->stream));
+  return KFAC_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+KFAC_API int kfac_version(void) { return 100; }
+
+KFAC_API const char* kfac_status_string(kfac_status st) {
+  switch (st) {
+    case KFAC_OK: return "KFAC_OK";
+    case KFAC_ERR_INVALID_ARG: return "KFAC_ERR_INVALID_ARG";
+    case KFAC_ERR_CUDA: return "KFAC_ERR_CUDA";
+    case KFAC_ERR_OOM: return "KFAC_ERR_OOM";
+    case KFAC_ERR_CHOLESKY: return "KFAC_ERR_CHOLESKY";
+    case KFAC_ERR_NOCONVERGE: return "KFAC_ERR_NOCONVERGE";
+    case KFAC_ERR_NONFINITE: return "KFAC_ERR_NONFINITE";
+    case KFAC_ERR_TIMEOUT: return "KFAC_ERR_TIMEOUT";
+    case KFAC_ERR_UNSUPPORTED: return "KFAC_ERR_UNSUPPORTED";
+  }
+  return "KFAC_ERR_UNKNOWN";
+}
+
+KFAC_API kfac_status kfac_create(kfac_ctx** out, int device, void* stream) {
+  if (!out) return KFAC_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return KFAC_ERR_CUDA; }
+  if (device < 0 || device >= ndev) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  if (!g.ok) return KFAC_ERR_CUDA;
+  kfac_ctx* ctx = new (std::nothrow) kfac_ctx();
+  if (!ctx) return KFAC_ERR_OOM;
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  if (cudaMalloc(&ctx->dflags, 64) != cudaSuccess) {
+    delete ctx;
+    return KFAC_ERR_OOM;
+  }
+  ctx->dstats = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->dflags) + 32);
+  if (cudaMemset(ctx->dflags, 0, 64) != cudaSuccess) {
+    cudaFree(ctx->dflags);
+    delete ctx;
+    return KFAC_ERR_CUDA;
+  }
+  *out = ctx;
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_destroy(kfac_ctx* ctx) {
+  if (!ctx) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->dflags) cudaFree(ctx->dflags);
+  delete ctx;
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_set_stream(kfac_ctx* ctx, void* stream) {
+  if (!ctx) return KFAC_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
+  if (!ctx) return KFAC_ERR_INVALID_ARG;
+  switch (opt) {
+    case KFAC_OPT_CHOLQR_PASSES:
+      if (v < 1 || v > 6) return KFAC_ERR_INVALID_ARG;
+      ctx->cholqr_passes = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_CHOLQR_SHIFT:
+      if (!(v >= 0 && v < 1)) return KFAC_ERR_INVALID_ARG;
+      ctx->cholqr_shift = v;
+      return KFAC_OK;
+    case KFAC_OPT_EIG_REFINE:
+      if (v < 0 || v > 3) return KFAC_ERR_INVALID_ARG;
+      ctx->eig_refine = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_EIG_MAX_SWEEPS:
+      if (v < 1 || v > 1000) return KFAC_ERR_INVALID_ARG;
+      ctx->eig_max_sweeps = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_EIG_TOL:
+      if (!(v > 0 && v < 1)) return KFAC_ERR_INVALID_ARG;
+      ctx->eig_tol = v;
+      return KFAC_OK;
+  }
+  return KFAC_ERR_INVALID_ARG;
+}
+
+KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t mn_max) {
+  if (!ctx || d_max < 0 || k_max < 0 || mn_max < 0) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  size_t need = 0;
+  if (d_max > 0 && k_max > 0) {
+    InvertLayout a = invert_layout(d_max, std::min(k_max, d_max - 1 > 0 ? d_max - 1 : 1), k_max);
+    InvertLayout b = invert_layout(std::min(d_max, k_max), k_max, k_max);
+    need = std::max(a.total, b.total);
+  }
+  if (mn_max > 0) {
+    size_t p = (size_t)mn_max * sizeof(float) + 2 * (size_t)d_max * std::max(k_max, 1) * sizeof(float) + 4096;
+    need = std::max(need, p);
+  }
+  return ensure_ws(ctx, need);
+}
+
+KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags) {
+  if (!ctx) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, ctx->dflags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    return KFAC_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  if (cudaMemsetAsync(ctx->dflags, 0, sizeof(int), ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  if (flags) *flags = h;
+  if (h & KFAC_FLAG_NONFINITE) return KFAC_ERR_NONFINITE;
+  if (h & KFAC_FLAG_CHOL_FAILED) return KFAC_ERR_CHOLESKY;
+  if (h & KFAC_FLAG_EIG_NOCONV) return KFAC_ERR_NOCONVERGE;
+  if (h & KFAC_FLAG_TIMEOUT) return KFAC_ERR_TIMEOUT;
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X, int ldx, float rho,
+                                    kfac_precision prec, float* F, int ldf) {
+  if (!ctx || d < 0 || n < 0 || ldf < d || (d > 0 && !F) || (n > 0 && (!X || ldx < n))) return KFAC_ERR_INVALID_ARG;
+  if (!(rho >= 0.0f && rho <= 1.0f) || prec < KFAC_PREC_FP32 || prec > KFAC_PREC_BF16) return KFAC_ERR_INVALID_ARG;
+  if (d == 0) return KFAC_OK;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  STAGE(ctx, ST_EA);
+  return ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf) == cudaSuccess ? KFAC_OK : KFAC_ERR_CUDA;
+}
+
+KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
+                                      int power_iters, float lambda, const float* omega, int ldo,
+                                      kfac_precision prec, float* U, int ldu, float* D, float* coef) {
+  if (!ctx || d <= 0 || !F || ldf < d || rank <= 0 || oversample < 0 || power_iters < 0 || power_iters > 64)
+    return KFAC_ERR_INVALID_ARG;
+  if (!(lambda > 0.0f) || prec < KFAC_PREC_FP32 || prec > KFAC_PREC_BF16) return KFAC_ERR_INVALID_ARG;
+  const int r = std::min(rank, d);
+  const long long kl = (long long)rank + oversample;
+  if (kl > 4096) return KFAC_ERR_UNSUPPORTED;
+  const int k = (int)kl;
+  if (!U || ldu < r || !D || !coef) return KFAC_ERR_INVALID_ARG;
+  const bool exact = k >= d;
+  if (!exact && (!omega || ldo < k)) return KFAC_ERR_INVALID_ARG;
+  if (exact && d > 4096) return KFAC_ERR_UNSUPPORTED;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  InvertLayout L = invert_layout(d, k, r);
+  kfac_status st = ensure_ws(ctx, L.total);
+  if (st != KFAC_OK) return st;
+  cudaStream_t s = ctx->stream;
+
+  if (exact) {  // nothing to sketch: diagonalise F itself (Q = I)
+    double* C = at<double>(ctx, L.c);
+    CK(convert_f32_to_f64(F, ldf, d, d, C, d, ctx->dflags, s));
+    st = eigensolve(ctx, C, d, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
+                    at<float>(ctx, L.jac));
+    if (st != KFAC_OK) return st;
+    STAGE(ctx, ST_SELECT);
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), d, r, lambda, nullptr, D, coef, U, ldu, s));
+    return KFAC_OK;
+  }
+
+  // Omega^T (k x d) so that every sketch product reads K-contiguous rows.
+  float* Om = at<float>(ctx, L.om);
+  float* cur = at<float>(ctx, L.y);
+  float* other = at<float>(ctx, L.q);
+  {
+    STAGE(ctx, ST_TRANSPOSE);
+    CK(transpose_f32(omega, ldo, d, k, Om, L.dp, s));
+  }
+  st = sketch_product(ctx, Om, L.dp, F, ldf, k, d, prec, cur, L.dp);  // Y^T = Omega^T F
+  if (st != KFAC_OK) return st;
+  for (int it = 0;; ++it) {
+    st = orthonormalise(ctx, L, cur, other, k, d);  // Q^T in cur
+    if (st != KFAC_OK) return st;
+    if (it == power_iters) break;
+    st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, prec, other, L.dp);  // Y^T = Q^T F
+    if (st != KFAC_OK) return st;
+    std::swap(cur, other);
+  }
+  // Projection C = Q^T F Q = Q^T (F Q): Z^T = Q^T F into `other`, then C = Q^T Z.
+  st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, prec, other, L.dp);
+  if (st != KFAC_OK) return st;
+  double* C = at<double>(ctx, L.c);
+  st = gram_f64(ctx, L, cur, other, L.dp, k, d, KFAC_PREC_FP32, C, ST_PROJ);
+  if (st != KFAC_OK) return st;
+  st = eigensolve(ctx, C, k, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
+                  at<float>(ctx, L.jac));
+  if (st != KFAC_OK) return st;
+  float* P32 = at<float>(ctx, L.p32);
+  {
+    STAGE(ctx, ST_SELECT);
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, lambda, P32, D, coef, nullptr, 0, s));
+  }
+  // Lift: U (d x r) = Q P[:, :r] = (Q^T)^T P32.
+  GemmDesc<float> g = {};
+  g.M = d; g.N = r; g.K = k;
+  g.A = cur; g.sam = 1; g.sak = L.dp;
+  g.B = P32; g.sbn = 1; g.sbk = r;
+  g.D = U; g.ldd = ldu;
+  g.alpha = 1.0f; g.zsplit = 1;
+  STAGE(ctx, ST_LIFT);
+  CK(gemm_f32(g, KFAC_PREC_FP32, s));
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const float* J, int ldj,
+                                       const float* U_a, int ld_ua, const float* coef_a, int r_a,
+                                       const float* U_g, int ld_ug, const float* coef_g, int r_g,
+                                       float lambda, kfac_precision prec, float* S, int lds) {
+  if (!ctx || d_g < 0 || d_a < 0 || r_a < 0 || r_g < 0 || r_a > d_a || r_g > d_g) return KFAC_ERR_INVALID_ARG;
+  if (!(lambda > 0.0f) || prec < KFAC_PREC_FP32 || prec > KFAC_PREC_BF16) return KFAC_ERR_INVALID_ARG;
+  if ((long long)d_g * d_a == 0) return KFAC_OK;
+  if (!J || ldj < d_a || !S || lds < d_a || S == J) return KFAC_ERR_INVALID_ARG;
+  if (r_a > 0 && (!U_a || ld_ua < r_a || !coef_a)) return KFAC_ERR_INVALID_ARG;
+  if (r_g > 0 && (!U_g || ld_ug < r_g || !coef_g)) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  Bump b;
+  size_t oT = b.take<float>((size_t)d_g * std::max(r_a, 1));
+  size_t oM = b.take<float>((size_t)d_g * d_a);
+  size_t oT2 = b.take<float>((size_t)std::max(r_g, 1) * d_a);
+  kfac_status st = ensure_ws(ctx, b.off);
+  if (st != KFAC_OK) return st;
+  float* T = at<float>(ctx, oT);
+  float* M = at<float>(ctx, oM);
+  float* T2 = at<float>(ctx, oT2);
+  cudaStream_t s = ctx->stream;
+  const float inv_lam = 1.0f / lambda;
+  if (r_a > 0) {  // T = J U_a diag(c_a)
+    STAGE(ctx, ST_APPLY_T);
+    GemmDesc<float> g = {};
+    g.M = d_g; g.N = r_a; g.K = d_a;
+    g.A = J; g.sam = ldj; g.sak = 1;
+    g.B = U_a; g.sbn = 1; g.sbk = ld_ua;
+    g.D = T; g.ldd = r_a;
+    g.alpha = 1.0f; g.colscale = coef_a; g.zsplit = 1;
+    CK(gemm_f32(g, prec, s));
+  }
+  {  // M = T U_a^T + J / lambda
+    STAGE(ctx, ST_APPLY_M);
+    GemmDesc<float> g = {};
+    g.M = d_g; g.N = d_a; g.K = r_a;
+    g.A = T; g.sam = r_a > 0 ? r_a : 1; g.sak = 1;
+    g.B = U_a; g.sbn = ld_ua; g.sbk = 1;
+    g.D = M; g.ldd = d_a;
+    g.alpha = 1.0f; g.beta = inv_lam; g.C0 = J; g.ldc = ldj; g.zsplit = 1;
+    CK(gemm_f32(g, prec, s));
+  }
+  if (r_g > 0) {  // T2 = diag(c_g) U_g^T M
+    STAGE(ctx, ST_APPLY_T2);
+    GemmDesc<float> g = {};
+    g.M = r_g; g.N = d_a; g.K = d_g;
+    g.A = U_g; g.sam = 1; g.sak = ld_ug;
+    g.B = M; g.sbn = 1; g.sbk = d_a;
+    g.D = T2; g.ldd = d_a;
+    g.alpha = 1.0f; g.rowscale = coef_g; g.zsplit = 1;
+    CK(gemm_f32(g, prec, s));
+  }
+  {  // S = U_g T2 + M / lambda
+    STAGE(ctx, ST_APPLY_S);
+    GemmDesc<float> g = {};
+    g.M = d_g; g.N = d_a; g.K = r_g;
+    g.A = U_g; g.sam = ld_ug > 0 ? ld_ug : 1; g.sak = 1;
+    g.B = T2; g.sbn = 1; g.sbk = d_a;
+    g.D = S; g.ldd = lds;
+    g.alpha = 1.0f; g.beta = inv_lam; g.C0 = M; g.ldc = d_a; g.zsplit = 1;
+    CK(gemm_f32(g, prec, s));
+  }
+  return KFAC_OK;
+}
+
+KFAC_API uint64_t kfac_kernel_launch_count(void) { return (uint64_t)launch_count(); }
+
+KFAC_API kfac_status kfac_stats_read(kfac_ctx* ctx, int64_t* out, int n) {
+  if (!ctx || n < 0 || (n > 0 && !out)) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  unsigned long long h[STAT_COUNT] = {};
+  if (cudaMemcpyAsync(h, ctx->dstats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    return KFAC_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  if (cudaMemsetAsync(ctx->dstats, 0, sizeof(h), ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  for (int i = 0; i < n && i < STAT_COUNT; ++i) out[i] = (int64_t)h[i];
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_profile_enable(kfac_ctx* ctx, int on) {
+  if (!ctx) return KFAC_ERR_INVALID_ARG;
+  ctx->prof.on = on != 0;
+  for (auto& u : ctx->prof.used) u = 0;
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_profile_read(kfac_ctx* ctx, const char** names, double* total_ms, int* launches,
+                                       int max_stages, int* n_stages) {
+  if (!ctx || max_stages < 0) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  int n = std::min(max_stages, (int)ST_COUNT);
+  for (int i = 0; i < ST_COUNT; ++i) {
+    double tot = 0.0;
+    for (size_t j = 0; j < ctx->prof.used[i]; ++j) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, ctx->prof.ev[i][j].first, ctx->prof.ev[i][j].second) == cudaSuccess) tot += ms;
+    }
+    if (i < n) {
+      if (names) names[i] = kStageNames[i];
+      if (total_ms) total_ms[i] = tot;
+      if (launches) launches[i] = (int)ctx->prof.used[i];
+    }
+    ctx->prof.used[i] = 0;
+  }
+  if (n_stages) *n_stages = n;
+  return KFAC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations shared by the CUDA translation units of libkfac.
+// Row-major storage everywhere; "ld" is the row stride in elements.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kfac.h"
+
+namespace kfac {
+
+// Largest dynamic shared memory a kernel here requests: the 227 KB opt-in limit
+// minus 1 KB kept for static shared variables.
+constexpr int kSmemOptin = 227 * 1024 - 1024;
+
+// Process-wide count of kernel launches issued by this library.
+void note_launch(unsigned n = 1);
+unsigned long long launch_count();
+
+// Device-side counters (see kfac_stats_read): sweeps, solves, Cholesky, retries.
+enum { STAT_SWEEPS = 0, STAT_EIG_SOLVES = 1, STAT_CHOL = 2, STAT_CHOL_RETRY = 3, STAT_COUNT = 4 };
+
+// Device-side status word: kernels OR KFAC_FLAG_* bits into it.
+__device__ __forceinline__ void raise_flag(int* flags, int bit) {
+  if (flags) atomicOr(flags, bit);
+}
+
+enum class Round { None = 0, TF32 = 1, BF16 = 2 };
+
+// Operand rounding applied by the SIMT fallback so that its numerics follow the
+// selected tensor-core precision (TF32 keeps the top 10 mantissa bits, BF16 rounds
+// to nearest even at 7 mantissa bits).
+__device__ __forceinline__ float round_operand(float x, Round r) {
+  if (r == Round::TF32) return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  if (r == Round::BF16) {
+    unsigned u = __float_as_uint(x);
+    if ((u & 0x7F800000u) == 0x7F800000u) return x;  // Inf/NaN unchanged
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return __uint_as_float(u & 0xFFFF0000u);
+  }
+  return x;
+}
+
+// Generic strided GEMM description: D[m, n] = alpha * rowscale[m] * colscale[n] *
+// sum_k A(m, k) B(n, k) + beta * C0[m, n], with A(m, k) = A[m*sam + k*sak] and
+// B(n, k) = B[n*sbn + k*sbk]. When zsplit > 1 the K range is cut into zsplit
+// chunks and chunk z writes its raw partial sums to D + z*zstride (alpha, scales,
+// beta ignored); a reduction kernel combines them.
+template <typename T>
+struct GemmDesc {
+  int M, N, K;
+  const T* A;
+  long long sam, sak;
+  const T* B;
+  long long sbn, sbk;
+  T* D;
+  long long ldd;
+  const T* C0;
+  long long ldc;
+  T alpha, beta;
+  const T* rowscale;
+  const T* colscale;
+  int zsplit;
+  int kchunk;
+  long long zstride;
+};
+
+// ---- launchers (host) --------------------------------------------------------
+cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s);
+cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s);
+// out[i, j] = sum_z part[z][i, j] in FP64 (n x n), optionally symmetrised as
+// (S + S^T) / 2. part has row stride ldp and z stride zstride.
+cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out,
+                              int ldo, int symmetrize, int* flags, cudaStream_t s);
+cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, float* out, long long ldo,
+                          cudaStream_t s);
+cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int cols, double* out, long long ldo,
+                               int* flags, cudaStream_t s);
+
+// FP64 Cholesky of (G + shift I) on a thread-block cluster; writes the lower
+// factor L as FP32 (k x k row-major, upper part zero). shift = shift_rel *
+// trace(G); on breakdown the shift grows (bounded retries) and flags record it.
+cudaError_t chol_f64_cluster(const double* G, int k, double shift_rel, float* L32, int* flags,
+                             unsigned long long* stats, cudaStream_t s);
+
+// Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
+cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
+                           cudaStream_t s);
+
+// One-CTA FP32 one-sided Jacobi on chol(C + s I): writes X (k x k FP64, column j
+// = unit eigenvector) and lam (k, unsorted). gscratch: k*k floats used when the
+// working matrix does not fit in shared memory.
+cudaError_t eig_onesided_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
+                             double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s);
+
+// One FP64 refinement step (Ogita-Aishima) of eigenpairs (X, lam) of C.
+// Workspace: 5 k*k doubles. X and lam are updated in place.
+cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, double* work, int* flags,
+                           cudaStream_t s);
+
+// Sort eigenpairs descending (stable by index), emit the r leading ones:
+// P32 (k x r FP32, columns = eigenvectors), D and coef (FP32, Eq. (13)), and
+// optionally Uout (k x r into a strided FP32 matrix, for the k >= d path).
+cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* P32, float* D,
+                       float* coef, float* Uout, long long ldu, cudaStream_t s);
+
+}  // namespace kfac

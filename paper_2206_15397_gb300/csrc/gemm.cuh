@@ -1,0 +1,16 @@
+// GEMM-shaped steps of the hot path and their dispatch.
+#pragma once
+#include "common.cuh"
+
+namespace kfac {
+
+// D = alpha * rowscale * colscale * A B^T + beta * C0 in FP32 storage with the
+// product arithmetic of `prec`. Dispatches to the tensor-core kernels where the
+// shape and layout qualify, else to the SIMT kernel.
+cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t s);
+
+// F <- rho F + (1 - rho)/n X X^T (Alg. 1 EA lines), exactly symmetric result.
+cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,
+                    int ldf);
+
+}  // namespace kfac

@@ -1,0 +1,181 @@
+// SIMT kernels: strided GEMM (FP32 with optional operand rounding, FP64),
+// split-K reduction to FP64, transpose and widening copies.
+#include "common.cuh"
+
+namespace kfac {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+// 64x64 output tile per CTA, 16x16 threads, each thread owns a 4x4 grid of
+// outputs strided by 16 so that stores of consecutive threads are consecutive.
+template <typename T, Round R>
+__global__ void __launch_bounds__(NT) k_gemm_simt(GemmDesc<T> g) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int it = 0; it < (BM * BK) / NT; ++it) {
+      int e = tid + it * NT, mm, kk;
+      if (g.sak == 1) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
+      int m = bm + mm, k = k0 + kk;
+      T v = T(0);
+      if (m < g.M && k < kend) v = g.A[(long long)m * g.sam + (long long)k * g.sak];
+      if constexpr (sizeof(T) == 4) v = round_operand(v, R);
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int it = 0; it < (BN * BK) / NT; ++it) {
+      int e = tid + it * NT, nn, kk;
+      if (g.sbk == 1) { nn = e / BK; kk = e % BK; } else { nn = e % BN; kk = e / BN; }
+      int n = bn + nn, k = k0 + kk;
+      T v = T(0);
+      if (n < g.N && k < kend) v = g.B[(long long)n * g.sbn + (long long)k * g.sbk];
+      if constexpr (sizeof(T) == 4) v = round_operand(v, R);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int m = bm + ty + 16 * i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int n = bn + tx + 16 * j;
+      if (n >= g.N) continue;
+      if (g.zsplit > 1) {
+        g.D[blockIdx.z * g.zstride + (long long)m * g.ldd + n] = acc[i][j];
+      } else {
+        T v = acc[i][j] * g.alpha;
+        if (g.rowscale) v *= g.rowscale[m];
+        if (g.colscale) v *= g.colscale[n];
+        if (g.beta != T(0)) v = fma(g.beta, g.C0[(long long)m * g.ldc + n], v);
+        g.D[(long long)m * g.ldd + n] = v;
+      }
+    }
+  }
+}
+
+template <typename T, Round R>
+cudaError_t launch_gemm(const GemmDesc<T>& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  GemmDesc<T> d = g;
+  if (d.zsplit < 1) d.zsplit = 1;
+  if (d.zsplit == 1) d.kchunk = d.K > 0 ? d.K : 1;
+  dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, d.zsplit);
+  k_gemm_simt<T, R><<<grid, NT, 0, s>>>(d);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
+                                double* __restrict__ out, int ldo, int symmetrize, int* flags) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  int i = (int)(idx / n), j = (int)(idx % n);
+  double s = 0.0;
+  for (int z = 0; z < nsplit; ++z) s += (double)part[z * zstride + (long long)i * ldp + j];
+  if (symmetrize) {
+    double t = 0.0;
+    for (int z = 0; z < nsplit; ++z) t += (double)part[z * zstride + (long long)j * ldp + i];
+    s = 0.5 * (s + t);
+  }
+  if (!isfinite(s)) raise_flag(flags, KFAC_FLAG_NONFINITE);
+  out[(long long)i * ldo + j] = s;
+}
+
+__global__ void k_transpose(const float* __restrict__ in, long long ldi, int rows, int cols, float* __restrict__ out,
+                            long long ldo) {
+  __shared__ float tile[32][33];
+  int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    int r = r0 + y, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[y][threadIdx.x] = in[(long long)r * ldi + c];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    int c = c0 + y, r = r0 + threadIdx.x;  // out[c][r] = in[r][c]
+    if (r < rows && c < cols) out[(long long)c * ldo + r] = tile[threadIdx.x][y];
+  }
+}
+
+__global__ void k_convert(const float* __restrict__ in, long long ldi, int rows, int cols, double* __restrict__ out,
+                          long long ldo, int* flags) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)rows * cols) return;
+  int r = (int)(idx / cols), c = (int)(idx % cols);
+  float v = in[(long long)r * ldi + c];
+  if (!isfinite(v)) raise_flag(flags, KFAC_FLAG_NONFINITE);
+  out[(long long)r * ldo + c] = (double)v;
+}
+
+}  // namespace
+
+static unsigned long long g_launches = 0;
+void note_launch(unsigned n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s) {
+  switch (rnd) {
+    case Round::TF32: return launch_gemm<float, Round::TF32>(g, s);
+    case Round::BF16: return launch_gemm<float, Round::BF16>(g, s);
+    default: return launch_gemm<float, Round::None>(g, s);
+  }
+}
+
+cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s) { return launch_gemm<double, Round::None>(g, s); }
+
+cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out, int ldo,
+                              int symmetrize, int* flags, cudaStream_t s) {
+  long long tot = (long long)n * n;
+  if (tot == 0) return cudaSuccess;
+  k_reduce_splitk<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, zstride, n, ldp, out, ldo, symmetrize,
+                                                                  flags);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, float* out, long long ldo,
+                          cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, ldi, rows, cols, out, ldo);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int cols, double* out, long long ldo,
+                               int* flags, cudaStream_t s) {
+  long long tot = (long long)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  k_convert<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(in, ldi, rows, cols, out, ldo, flags);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace kfac

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of libkfac (include/kfac.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA library.
+PyTorch supplies device memory and streams. The functions carry the C names and
+take CUDA float32 tensors whose rows are contiguous (stride(1) == 1); the row
+stride becomes the C leading dimension. There is no CPU fallback: without the
+compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libkfac.so")
+_lib = None
+
+PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
+OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_sweeps": 3, "eig_tol": 4}
+FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
+
+
+class KfacError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libkfac.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise KfacError(f"{_LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i, f, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_int64
+        L.kfac_version.restype = i
+        L.kfac_status_string.argtypes = [i]
+        L.kfac_status_string.restype = ctypes.c_char_p
+        L.kfac_create.argtypes = [ctypes.POINTER(vp), i, vp]
+        L.kfac_destroy.argtypes = [vp]
+        L.kfac_set_stream.argtypes = [vp, vp]
+        L.kfac_reserve.argtypes = [vp, i, i, i64]
+        L.kfac_set_option.argtypes = [vp, i, d]
+        L.kfac_get_status.argtypes = [vp, ctypes.POINTER(i)]
+        L.kfac_ea_update.argtypes = [vp, i, i, vp, i, f, i, vp, i]
+        L.kfac_rsvd_invert.argtypes = [vp, i, vp, i, i, i, i, f, vp, i, i, vp, i, vp, vp]
+        L.kfac_precondition.argtypes = [vp, i, i, vp, i, vp, i, vp, i, vp, i, vp, i, f, i, vp, i]
+        L.kfac_profile_enable.argtypes = [vp, i]
+        L.kfac_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d), ctypes.POINTER(i), i,
+                                        ctypes.POINTER(i)]
+        L.kfac_kernel_launch_count.restype = ctypes.c_uint64
+        L.kfac_stats_read.argtypes = [vp, ctypes.POINTER(i64), i]
+        for name in ("kfac_create", "kfac_destroy", "kfac_set_stream", "kfac_reserve", "kfac_set_option",
+                     "kfac_get_status", "kfac_ea_update", "kfac_rsvd_invert", "kfac_precondition",
+                     "kfac_profile_enable", "kfac_profile_read", "kfac_stats_read"):
+            getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise KfacError(f"{what}: {lib().kfac_status_string(st).decode()}")
+
+
+def _mat(t: torch.Tensor, name: str, rows: int | None = None, cols: int | None = None):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float32 or t.dim() != 2:
+        raise KfacError(f"{name} must be a 2-D CUDA float32 tensor")
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise KfacError(f"{name} rows must be contiguous")
+    if (rows is not None and t.shape[0] != rows) or (cols is not None and t.shape[1] != cols):
+        raise KfacError(f"{name} has shape {tuple(t.shape)}, expected ({rows}, {cols})")
+    return ctypes.c_void_p(t.data_ptr()), max(t.stride(0), t.shape[1], 1)
+
+
+def _vec(t: torch.Tensor, name: str, n: int):
+    if t.device.type != "cuda" or t.dtype != torch.float32 or t.dim() != 1 or t.shape[0] != n or (n > 1 and t.stride(0) != 1):
+        raise KfacError(f"{name} must be a contiguous CUDA float32 vector of length {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns a kfac_ctx (workspace + status word) bound to one device and stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = torch.device("cuda", device)
+        torch.cuda.init()
+        self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check(lib().kfac_create(ctypes.byref(h), device, ctypes.c_void_p(self._stream.cuda_stream)), "kfac_create")
+        self.handle = h
+
+    @property
+    def stream(self) -> torch.cuda.Stream:
+        return self._stream
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        _check(lib().kfac_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)), "kfac_set_stream")
+        self._stream = stream
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().kfac_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def kfac_set_option(ctx: Context, name: str, value: float):
+    _check(lib().kfac_set_option(ctx.handle, OPTIONS[name], float(value)), f"kfac_set_option({name})")
+
+
+def kfac_reserve(ctx: Context, d_max: int, k_max: int, mn_max: int = 0):
+    _check(lib().kfac_reserve(ctx.handle, int(d_max), int(k_max), int(mn_max)), "kfac_reserve")
+
+
+def kfac_get_status(ctx: Context):
+    """Synchronise the context stream; return (status code, list of raised flag names)."""
+    f = ctypes.c_int(0)
+    st = lib().kfac_get_status(ctx.handle, ctypes.byref(f))
+    return st, [n for b, n in FLAGS.items() if f.value & b]
+
+
+def kfac_ea_update(ctx: Context, X: torch.Tensor, F: torch.Tensor, rho: float, prec: str = "fp32"):
+    """F <- rho F + (1 - rho)/n X X^T in place; X is (d, n)."""
+    d, n = X.shape
+    px, ldx = _mat(X, "X", d, n)
+    pf, ldf = _mat(F, "F", d, d)
+    _check(lib().kfac_ea_update(ctx.handle, d, n, px, ldx, float(rho), PRECISION[prec], pf, ldf), "kfac_ea_update")
+    return F
+
+
+def kfac_rsvd_invert(ctx: Context, F: torch.Tensor, rank: int, oversample: int, power_iters: int, lam: float,
+                     omega: torch.Tensor | None, prec: str = "fp32", out=None):
+    """Randomized low-rank eigendecomposition of F and the damping coefficients.
+    Returns (U (d x r), D (r), coef (r)) with r = min(rank, d)."""
+    d = F.shape[0]
+    r = min(rank, d)
+    pf, ldf = _mat(F, "F", d, d)
+    k = rank + oversample
+    if omega is not None:
+        po, ldo = _mat(omega, "omega", d, k)
+    else:
+        po, ldo = ctypes.c_void_p(0), max(k, 1)
+    if out is None:
+        U = torch.empty((d, r), device=F.device, dtype=torch.float32)
+        D = torch.empty((r,), device=F.device, dtype=torch.float32)
+        coef = torch.empty((r,), device=F.device, dtype=torch.float32)
+    else:
+        U, D, coef = out
+    pu, ldu = _mat(U, "U", d, r)
+    _check(lib().kfac_rsvd_invert(ctx.handle, d, pf, ldf, int(rank), int(oversample), int(power_iters), float(lam),
+                                  po, ldo, PRECISION[prec], pu, ldu, _vec(D, "D", r), _vec(coef, "coef", r)),
+           "kfac_rsvd_invert")
+    return U, D, coef
+
+
+def kfac_precondition(ctx: Context, J: torch.Tensor, U_a: torch.Tensor, coef_a: torch.Tensor, U_g: torch.Tensor,
+                      coef_g: torch.Tensor, lam: float, prec: str = "fp32", out: torch.Tensor | None = None):
+    """S = (U_g D_g U_g^T + lam I)^-1 J (U_a D_a U_a^T + lam I)^-1 through Eq. (13) coefficients."""
+    dg, da = J.shape
+    ra, rg = U_a.shape[1], U_g.shape[1]
+    pj, ldj = _mat(J, "J", dg, da)
+    pua, ldua = _mat(U_a, "U_a", da, ra)
+    pug, ldug = _mat(U_g, "U_g", dg, rg)
+    S = torch.empty_like(J) if out is None else out
+    ps, lds = _mat(S, "S", dg, da)
+    _check(lib().kfac_precondition(ctx.handle, dg, da, pj, ldj, pua, ldua, _vec(coef_a, "coef_a", ra), ra,
+                                   pug, ldug, _vec(coef_g, "coef_g", rg), rg, float(lam), PRECISION[prec], ps, lds),
+           "kfac_precondition")
+    return S
+
+
+def kfac_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().kfac_profile_enable(ctx.handle, int(bool(on))), "kfac_profile_enable")
+
+
+def kfac_profile_read(ctx: Context) -> dict:
+    """{stage name: (device ms summed over timed launches, launch count)}; clears the totals."""
+    n = 32
+    names = (ctypes.c_char_p * n)()
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    got = ctypes.c_int(0)
+    _check(lib().kfac_profile_read(ctx.handle, names, ms, cnt, n, ctypes.byref(got)), "kfac_profile_read")
+    return {names[i].decode(): (ms[i], cnt[i]) for i in range(got.value)}
+
+
+def kfac_kernel_launch_count() -> int:
+    return int(lib().kfac_kernel_launch_count())
+
+
+def kfac_stats_read(ctx: Context) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    _check(lib().kfac_stats_read(ctx.handle, out, 4), "kfac_stats_read")
+    return {"jacobi_sweeps": out[0], "jacobi_solves": out[1], "cholesky": out[2], "cholesky_retries": out[3]}
