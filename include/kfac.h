@@ -53,7 +53,8 @@ typedef enum {
   KFAC_ERR_NOCONVERGE = 5,   /* Jacobi sweep limit reached                      */
   KFAC_ERR_NONFINITE = 6,    /* NaN/Inf met in an input or an intermediate      */
   KFAC_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up              */
-  KFAC_ERR_UNSUPPORTED = 8   /* valid request this build does not implement     */
+  KFAC_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement     */
+  KFAC_ERR_TOO_LARGE = 9     /* request exceeds a fixed-size static scratch area */
 } kfac_status;
 
 /* Arithmetic of the large GEMMs (EA SYRK, sketch / power / projection, apply).
@@ -140,6 +141,37 @@ KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const fl
                                        const float* U_a, int ld_ua, const float* coef_a, int r_a,
                                        const float* U_g, int ld_ug, const float* coef_g, int r_g,
                                        float lambda, kfac_precision prec, float* S, int lds);
+
+/* Allocation-free variant of kfac_precondition (the paper has no counterpart:
+ * this is a deployment interface). It is for callers that cannot allocate GPU
+ * memory at call time: code that runs while a CUDA graph is being captured,
+ * runtimes that hand out all device memory up front through their own pool,
+ * or processes whose allocator is locked. It needs no kfac_ctx (creating one
+ * allocates) and never calls cudaMalloc, cudaFree or any allocating library
+ * routine.
+ *
+ * Same inputs, output and arithmetic as kfac_precondition, on `stream` (a
+ * cudaStream_t as void*; NULL = legacy default stream) of the CURRENT device.
+ * The caller's S doubles as the staging area of M. The two thin intermediates
+ * T = J U_a diag(coef_a) (d_g x r_a) and T2 = diag(coef_g) U_g^T M
+ * (r_g x d_a) take turns in a static device array of KFAC_NOALLOC_SCRATCH_FLOATS
+ * floats (8 MiB) that every GPU loading this library holds until the process
+ * exits. Requests with max(d_g*r_a, r_g*d_a) > KFAC_NOALLOC_SCRATCH_FLOATS
+ * return KFAC_ERR_TOO_LARGE before any work is enqueued.
+ *
+ * The first call on a device resolves the array's device address for that
+ * device (cudaGetSymbolAddress with the device current); make that first call
+ * before any stream capture. All calls share the one array and it keeps the
+ * previous call's contents (every element read is written first in the same
+ * call, so nothing needs clearing); calls whose work overlaps on the GPU (two
+ * streams, or two host threads) race on it and must be serialised by the
+ * caller. Argument errors return KFAC_ERR_INVALID_ARG; launch errors
+ * KFAC_ERR_CUDA. There is no device status word: NaN/Inf propagate to S. */
+#define KFAC_NOALLOC_SCRATCH_FLOATS (2 * 1024 * 1024)
+KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, const float* J, int ldj,
+                                               const float* U_a, int ld_ua, const float* coef_a, int r_a,
+                                               const float* U_g, int ld_ug, const float* coef_g, int r_g,
+                                               float lambda, kfac_precision prec, float* S, int lds);
 
 /* Synchronise the context's stream, return KFAC_OK or the most severe device
  * condition recorded since the last call, store the raw KFAC_FLAG_* bits in

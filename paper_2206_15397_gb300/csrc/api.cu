@@ -254,6 +254,7 @@ KFAC_API const char* kfac_status_string(kfac_status st) {
     case KFAC_ERR_NONFINITE: return "KFAC_ERR_NONFINITE";
     case KFAC_ERR_TIMEOUT: return "KFAC_ERR_TIMEOUT";
     case KFAC_ERR_UNSUPPORTED: return "KFAC_ERR_UNSUPPORTED";
+    case KFAC_ERR_TOO_LARGE: return "KFAC_ERR_TOO_LARGE";
   }
   return "KFAC_ERR_UNKNOWN";
 }

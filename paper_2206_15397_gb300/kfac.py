@@ -53,6 +53,8 @@ def lib():
         L.kfac_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d), ctypes.POINTER(i), i,
                                         ctypes.POINTER(i)]
         L.kfac_kernel_launch_count.restype = ctypes.c_uint64
+        L.kfac_precondition_noalloc.argtypes = [vp, i, i, vp, i, vp, i, vp, i, vp, i, vp, i, f, i, vp, i]
+        L.kfac_precondition_noalloc.restype = i
         L.kfac_stats_read.argtypes = [vp, ctypes.POINTER(i64), i]
         for name in ("kfac_create", "kfac_destroy", "kfac_set_stream", "kfac_reserve", "kfac_set_option",
                      "kfac_get_status", "kfac_ea_update", "kfac_rsvd_invert", "kfac_precondition",
@@ -208,3 +210,29 @@ def kfac_stats_read(ctx: Context) -> dict:
     out = (ctypes.c_int64 * 4)()
     _check(lib().kfac_stats_read(ctx.handle, out, 4), "kfac_stats_read")
     return {"jacobi_sweeps": out[0], "jacobi_solves": out[1], "cholesky": out[2], "cholesky_retries": out[3]}
+
+
+NOALLOC_SCRATCH_FLOATS = 2 * 1024 * 1024
+
+
+def kfac_precondition_noalloc(J: torch.Tensor, U_a: torch.Tensor, coef_a: torch.Tensor, U_g: torch.Tensor,
+                              coef_g: torch.Tensor, lam: float, prec: str = "fp32", out: torch.Tensor | None = None,
+                              stream: torch.cuda.Stream | None = None):
+    """kfac_precondition without any device allocation inside the library: for
+    callers that cannot allocate at call time (graph capture, pre-reserved memory
+    pools). Runs on `stream` (default: the current stream) of J's device; the
+    output tensor must be supplied by the caller or is allocated here by torch."""
+    dg, da = J.shape
+    ra, rg = U_a.shape[1], U_g.shape[1]
+    pj, ldj = _mat(J, "J", dg, da)
+    pua, ldua = _mat(U_a, "U_a", da, ra)
+    pug, ldug = _mat(U_g, "U_g", dg, rg)
+    S = torch.empty_like(J) if out is None else out
+    ps, lds = _mat(S, "S", dg, da)
+    st = stream if stream is not None else torch.cuda.current_stream(J.device)
+    with torch.cuda.device(J.device):
+        _check(lib().kfac_precondition_noalloc(ctypes.c_void_p(st.cuda_stream), dg, da, pj, ldj, pua, ldua,
+                                               _vec(coef_a, "coef_a", ra), ra, pug, ldug,
+                                               _vec(coef_g, "coef_g", rg), rg, float(lam), PRECISION[prec], ps, lds),
+               "kfac_precondition_noalloc")
+    return S
