@@ -5,11 +5,11 @@
  * (C. O. Puiu, "Randomized K-FACs: Speeding up K-FAC with Randomized Numerical
  * Linear Algebra", arXiv 2206.15397):
  *   - the exponentially averaged (EA) Kronecker-factor update (Alg. 1, the
- *     forward- and backward-factor EA lines; closed form Eq. (6));
+ *     forward- and backward-factor EA updates; closed form Eq. (6));
  *   - the randomized low-rank eigendecomposition of a factor (Alg. 3, SREVD,
  *     with the power iterations of Sec. 2.2): Gaussian sketch, power
  *     iterations, orthonormalisation, projected eigenproblem C = Q^T F Q, lift;
- *   - the damped low-rank preconditioner apply (Alg. 4, the M and S lines,
+ *   - the damped low-rank preconditioner apply (Alg. 4, the M and S updates,
  *     with the low-rank inverse of Eq. (13); Alg. 5 feeds it U~).
  *
  * Conventions shared by every entry point
@@ -101,7 +101,7 @@ KFAC_API kfac_status kfac_set_stream(kfac_ctx* ctx, void* stream);
  * mn_max elements (0 = none). Needed before graph capture; optional otherwise. */
 KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t mn_max);
 
-/* EA K-factor update, Alg. 1 (forward / backward factor EA lines):
+/* EA K-factor update, Alg. 1 (forward / backward factor EA updates):
  *     F <- rho * F + (1 - rho) / n * X X^T
  * X: d x n batch matrix (one column per sample, row stride ldx >= n).
  * F: d x d symmetric factor, in/out (row stride ldf >= d); both triangles are
@@ -128,7 +128,7 @@ KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int 
                                       int power_iters, float lambda, const float* omega, int ldo,
                                       kfac_precision prec, float* U, int ldu, float* D, float* coef);
 
-/* Damped Kronecker preconditioner apply, Alg. 4 (M and S lines) with Eq. (13):
+/* Damped Kronecker preconditioner apply, Alg. 4 (M and S updates) with Eq. (13):
  *     M = J U_a diag(coef_a) U_a^T + J / lambda
  *     S = U_g diag(coef_g) U_g^T M + M / lambda
  * i.e. S = (U_g D_g U_g^T + lambda I)^-1 J (U_a D_a U_a^T + lambda I)^-1.

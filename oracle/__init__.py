@@ -11,13 +11,13 @@ compiles it with gcc on first use and wraps it with ctypes. Every wrapper takes
 and returns float64 numpy arrays, row-major.
 
 Functions and the passages they follow:
-  ea_update        Alg. 1, EA lines for the forward/backward K-factors; Eq. (6)
+  ea_update        Alg. 1, EA update of the forward/backward K-factors; Eq. (6)
   jacobi_eigh      "eig" of Alg. 1 / "Eigen_decomp" of Alg. 3 (cyclic Jacobi)
   qr               "QR_decomp" of Alg. 2 / Alg. 3 (Householder)
   srevd            Alg. 3 with the power iteration of Sec. 2.2
   damped_coef      Eq. (13), the diagonal (D + lam I)^-1 - I/lam
-  precondition     Alg. 4, the M and S lines (Alg. 5 supplies U~ for V~)
-  exact_apply      Alg. 1, eig + M/S lines: (G + lam I)^-1 J (A + lam I)^-1
+  precondition     Alg. 4, the M and S updates (Alg. 5 supplies U~ for V~)
+  exact_apply      Alg. 1, eig + M/S updates: (G + lam I)^-1 J (A + lam I)^-1
   rank_bound       Proposition 3.1, Eq. (7)
 """
 from __future__ import annotations

@@ -57,7 +57,8 @@ void orc_matmul(int m, int n, int kk, const double* A, int ta, const double* B, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* EA K-factor update: Alg. 1, forward-factor and backward-factor EA lines   */
+/* EA K-factor update: Alg. 1, the EA updates of the forward and backward    */
+/* factors.                                                                  */
 /* (Sec. 2.1), closed form Eq. (6).                                          */
 /* ------------------------------------------------------------------------ */
 
@@ -277,7 +278,7 @@ void orc_damped_coef(int r, const double* D, double lam, double* coef) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Preconditioner apply, Alg. 4 (the M and S lines; Alg. 5 feeds it U~ in    */
+/* Preconditioner apply, Alg. 4 (the M and S updates; Alg. 5 feeds it U~ in  */
 /* place of V~): M = J U_a diag(c_a) U_a^T + J/lam,                          */
 /*               S = U_g diag(c_g) U_g^T M + M/lam.                          */
 /* J = Mat(g) is d_g x d_a; U_a is d_a x r_a; U_g is d_g x r_g.              */
@@ -303,7 +304,8 @@ void orc_precondition(int dg, int da, const double* J, const double* Ua, const d
 
 /* ------------------------------------------------------------------------ */
 /* Exact damped Kronecker inverse apply through full eigendecompositions:    */
-/* Alg. 1 (the eig line and the M / S lines) with the identity of Sec. 2.1,   */
+/* Alg. 1 (eigendecomposition, then the M and S updates) with the identity   */
+/* of Sec. 2.1,                                                               */
 /* S = (G + lam I)^-1 J (A + lam I)^-1.                                      */
 /* ------------------------------------------------------------------------ */
 

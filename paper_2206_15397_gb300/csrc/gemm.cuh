@@ -9,7 +9,7 @@ namespace kfac {
 // shape and layout qualify, else to the SIMT kernel.
 cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t s);
 
-// F <- rho F + (1 - rho)/n X X^T (Alg. 1 EA lines), exactly symmetric result.
+// F <- rho F + (1 - rho)/n X X^T (Alg. 1 EA updates), exactly symmetric result.
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,
                     int ldf);
 

@@ -265,7 +265,7 @@ def _inv(a):
 
 
 def test_precondition_full_rank_equals_exact_inverse():
-    """With r = d, Alg. 4's M/S lines equal (G + lam I)^-1 J (A + lam I)^-1 (Sec. 2.1)."""
+    """With r = d, Alg. 4's M/S updates equal (G + lam I)^-1 J (A + lam I)^-1 (Sec. 2.1)."""
     da, dg, lam = 9, 6, 0.05
     fa, fg = rand_psd(da, 1), rand_psd(dg, 2)
     j = rng(3).standard_normal((dg, da))
