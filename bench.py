@@ -413,10 +413,11 @@ def main(argv=None):
     def step(i, xa=None, xg=None, j=None, oa=None, og=None):
         kfac.kfac_ea_update(ctx, XA[i % nb] if xa is None else xa, Fa, w["rho"], args.prec)
         kfac.kfac_ea_update(ctx, XG[i % nb] if xg is None else xg, Fg, w["rho"], args.prec)
-        kfac.kfac_rsvd_invert(ctx, Fa, r, w["p"], q, lam, OA[i % 2] if oa is None else oa, args.prec,
-                              out=(Ua, Da, Ca))
-        kfac.kfac_rsvd_invert(ctx, Fg, r, w["p"], q, lam, OG[i % 2] if og is None else og, args.prec,
-                              out=(Ug, Dg, Cg))
+        kfac.kfac_rsvd_invert_grouped(ctx, [
+            dict(F=Fa, rank=r, oversample=w["p"], power_iters=q, lam=lam, omega=OA[i % 2] if oa is None else oa,
+                 prec=args.prec, out=(Ua, Da, Ca)),
+            dict(F=Fg, rank=r, oversample=w["p"], power_iters=q, lam=lam, omega=OG[i % 2] if og is None else og,
+                 prec=args.prec, out=(Ug, Dg, Cg))])
         kfac.kfac_precondition(ctx, J[i % 2] if j is None else j, Ua, Ca, Ug, Cg, lam, args.prec, out=S)
 
     # ---- device-timed region -------------------------------------------------

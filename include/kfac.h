@@ -117,7 +117,9 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
  *     C = Q^T F Q; C = P diag(L) P^T (descending); U = Q P[:, :r]; D = L[:r];
  *     coef_i = 1/(max(D_i, 0) + lambda) - 1/lambda            (Eq. (13))
  * k = rank + oversample columns are sketched; r = min(rank, d) are returned.
- * When k >= d the factor is diagonalised directly (Q = I).
+ * When k >= d the factor is diagonalised directly (Q = I). The sketch width
+ * (or d on that direct path) is limited to 576: larger requests return
+ * KFAC_ERR_UNSUPPORTED.
  * omega: d x k Gaussian test matrix (row stride ldo >= k), caller-drawn (the
  *        library draws no random numbers). Ignored when k >= d (may be NULL).
  * U: d x r output (row stride ldu >= r); D, coef: r outputs.
@@ -127,6 +129,30 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
 KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
                                       int power_iters, float lambda, const float* omega, int ldo,
                                       kfac_precision prec, float* U, int ldu, float* D, float* coef);
+
+/* One factor of a grouped inversion: the arguments of kfac_rsvd_invert. */
+typedef struct {
+  int d;
+  const float* F;
+  int ldf;
+  int rank, oversample, power_iters;
+  float lambda;
+  const float* omega;
+  int ldo;
+  kfac_precision prec;
+  float* U;
+  int ldu;
+  float* D;
+  float* coef;
+} kfac_invert_desc;
+
+/* kfac_rsvd_invert for `count` independent factors (the per-layer loop of
+ * Alg. 4/5). The factors' pipelines are enqueued on up to 8 streams forked
+ * from the context stream (event fork/join, graph-capturable), each with its
+ * own workspace slice, so the latency-bound small-matrix steps of different
+ * factors overlap on the GPU. Arguments of every descriptor are checked before
+ * anything is enqueued; the host array may be reused once the call returns. */
+KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kfac_invert_desc* descs);
 
 /* Damped Kronecker preconditioner apply, Alg. 4 (M and S updates) with Eq. (13):
  *     M = J U_a diag(coef_a) U_a^T + J / lambda
@@ -181,11 +207,14 @@ KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags);
 /* Tunables (defaults in brackets). Returns KFAC_ERR_INVALID_ARG for an unknown
  * option or an out-of-range value. */
 typedef enum {
-  KFAC_OPT_CHOLQR_PASSES = 0,   /* CholeskyQR passes per orthonormalisation [3], 1..6     */
-  KFAC_OPT_CHOLQR_SHIFT = 1,    /* first-pass diagonal shift, relative to trace(G) [1e-6] */
+  KFAC_OPT_CHOLQR_PASSES = 0,   /* CholeskyQR passes for the final basis Q [3], 1..6      */
+  KFAC_OPT_CHOLQR_SHIFT = 1,    /* first-pass diagonal shift, relative to trace(G) [1e-5] */
   KFAC_OPT_EIG_REFINE = 2,      /* FP64 eigen-refinement steps after FP32 Jacobi [1], 0..3 */
   KFAC_OPT_EIG_MAX_SWEEPS = 3,  /* Jacobi sweep cap [40]                                  */
-  KFAC_OPT_EIG_TOL = 4          /* Jacobi pair-orthogonality threshold [4e-7]            */
+  KFAC_OPT_EIG_TOL = 4,         /* Jacobi pair-orthogonality threshold [2e-6]            */
+  KFAC_OPT_CHOLQR_INNER_PASSES = 5 /* passes for a basis that only feeds the next power
+                                      iteration [3], 1..6; fewer passes save time but      
+                                      lose accuracy on ill-conditioned sketches */
 } kfac_option;
 
 KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double value);

@@ -33,8 +33,13 @@ struct Profiler {
 };
 }  // namespace
 
+constexpr int kMaxSideStreams = 8;
+
 struct kfac_ctx {
   Profiler prof;
+  cudaStream_t side[kMaxSideStreams] = {};  // forked streams for grouped calls
+  cudaEvent_t join_ev[kMaxSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr;
   int device = 0;
   cudaStream_t stream = nullptr;
   void* ws = nullptr;
@@ -43,7 +48,8 @@ struct kfac_ctx {
   unsigned long long* dstats = nullptr;  // STAT_COUNT device counters
   // options
   int cholqr_passes = 3;
-  double cholqr_shift = 1e-6;
+  int cholqr_inner_passes = 3;
+  double cholqr_shift = 1e-5;
   int eig_refine = 1;
   int eig_max_sweeps = 40;
   double eig_tol = 2e-6;
@@ -207,14 +213,20 @@ kfac_status sketch_product(kfac_ctx* ctx, const float* Xt, long long ldx, const 
   return KFAC_OK;
 }
 
-kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, float*& other, int k, int d) {
-  for (int pass = 0; pass < ctx->cholqr_passes; ++pass) {
+kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, float*& other, int k, int d,
+                           int passes) {
+  for (int pass = 0; pass < passes; ++pass) {
     kfac_status st = gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM);
     if (st != KFAC_OK) return st;
     {
       STAGE(ctx, ST_CHOL);
-      CK(chol_f64_cluster(at<double>(ctx, L.g), k, pass == 0 ? ctx->cholqr_shift : 0.0, at<float>(ctx, L.l32),
-                          ctx->dflags, ctx->dstats, ctx->stream));
+      // First pass: shift relative to trace(G) (the sketch may be ill-conditioned
+      // beyond the FP32 Gram's accuracy). Middle passes: a tiny shift on the mean
+      // diagonal keeps the noise-level directions from breaking the factorization;
+      // the last pass (a near-orthonormal basis) is unshifted.
+      const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-6 : 0.0);
+      CK(chol_f64_cluster(at<double>(ctx, L.g), k, shift, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
+                          ctx->stream));
     }
     {
       STAGE(ctx, ST_TRSM);
@@ -228,11 +240,105 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
 kfac_status eigensolve(kfac_ctx* ctx, const double* C, int n, double* X, double* lam, double* work, float* jac) {
   {
     STAGE(ctx, ST_EIG);
-    CK(eig_onesided_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, X, lam, jac, ctx->dflags,
+    CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, X, lam, jac, ctx->dflags,
                         ctx->dstats, ctx->stream));
   }
   STAGE(ctx, ST_REFINE);
   for (int it = 0; it < ctx->eig_refine; ++it) CK(eig_refine_f64(C, n, X, lam, work, ctx->dflags, ctx->stream));
+  return KFAC_OK;
+}
+
+
+kfac_status check_invert(const kfac_invert_desc& a, int* r_out, int* k_out) {
+  if (a.d <= 0 || !a.F || a.ldf < a.d || a.rank <= 0 || a.oversample < 0 || a.power_iters < 0 || a.power_iters > 64)
+    return KFAC_ERR_INVALID_ARG;
+  if (!(a.lambda > 0.0f) || a.prec < KFAC_PREC_FP32 || a.prec > KFAC_PREC_BF16) return KFAC_ERR_INVALID_ARG;
+  const int r = std::min(a.rank, a.d);
+  const long long kl = (long long)a.rank + a.oversample;
+  if (!a.U || a.ldu < r || !a.D || !a.coef) return KFAC_ERR_INVALID_ARG;
+  const bool exact = kl >= a.d;
+  if (!exact && (!a.omega || a.ldo < kl)) return KFAC_ERR_INVALID_ARG;
+  if ((exact ? (long long)a.d : kl) > kMaxSketch) return KFAC_ERR_UNSUPPORTED;
+  const int k = (int)kl;
+  *r_out = r;
+  *k_out = k;
+  return KFAC_OK;
+}
+
+// The randomized inversion of one factor, enqueued on ctx->stream, with its
+// workspace slices offset by `base` bytes.
+kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L, size_t base) {
+  const int d = a.d, r = std::min(a.rank, a.d), k = a.rank + a.oversample;
+  const float* F = a.F;
+  const int ldf = a.ldf;
+  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.l32, &L.c, &L.x, &L.lam, &L.work, &L.jac, &L.p32}) *o += base;
+  cudaStream_t s = ctx->stream;
+  kfac_status st;
+  if (k >= d) {  // nothing to sketch: diagonalise F itself (Q = I)
+    double* C = at<double>(ctx, L.c);
+    CK(convert_f32_to_f64(F, ldf, d, d, C, d, ctx->dflags, s));
+    st = eigensolve(ctx, C, d, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
+                    at<float>(ctx, L.jac));
+    if (st != KFAC_OK) return st;
+    STAGE(ctx, ST_SELECT);
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), d, r, a.lambda, nullptr, a.D, a.coef, a.U, a.ldu,
+                  s));
+    return KFAC_OK;
+  }
+  // Omega^T (k x d) so that every sketch product reads K-contiguous rows.
+  float* Om = at<float>(ctx, L.om);
+  float* cur = at<float>(ctx, L.y);
+  float* other = at<float>(ctx, L.q);
+  {
+    STAGE(ctx, ST_TRANSPOSE);
+    CK(transpose_f32(a.omega, a.ldo, d, k, Om, L.dp, s));
+  }
+  st = sketch_product(ctx, Om, L.dp, F, ldf, k, d, a.prec, cur, L.dp);  // Y^T = Omega^T F
+  if (st != KFAC_OK) return st;
+  for (int it = 0;; ++it) {
+    st = orthonormalise(ctx, L, cur, other, k, d,
+                        it == a.power_iters ? ctx->cholqr_passes : ctx->cholqr_inner_passes);  // Q^T in cur
+    if (st != KFAC_OK) return st;
+    if (it == a.power_iters) break;
+    st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);  // Y^T = Q^T F
+    if (st != KFAC_OK) return st;
+    std::swap(cur, other);
+  }
+  // Projection C = Q^T F Q = Q^T (F Q): Z^T = Q^T F into `other`, then C = Q^T Z.
+  st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);
+  if (st != KFAC_OK) return st;
+  double* C = at<double>(ctx, L.c);
+  st = gram_f64(ctx, L, cur, other, L.dp, k, d, KFAC_PREC_FP32, C, ST_PROJ);
+  if (st != KFAC_OK) return st;
+  st = eigensolve(ctx, C, k, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
+                  at<float>(ctx, L.jac));
+  if (st != KFAC_OK) return st;
+  float* P32 = at<float>(ctx, L.p32);
+  {
+    STAGE(ctx, ST_SELECT);
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, a.lambda, P32, a.D, a.coef, nullptr, 0, s));
+  }
+  // Lift: U (d x r) = Q P[:, :r] = (Q^T)^T P32.
+  GemmDesc<float> g = {};
+  g.M = d; g.N = r; g.K = k;
+  g.A = cur; g.sam = 1; g.sak = L.dp;
+  g.B = P32; g.sbn = 1; g.sbk = r;
+  g.D = a.U; g.ldd = a.ldu;
+  g.alpha = 1.0f; g.zsplit = 1;
+  STAGE(ctx, ST_LIFT);
+  CK(gemm_f32(g, KFAC_PREC_FP32, s));
+  return KFAC_OK;
+}
+
+kfac_status ensure_side_streams(kfac_ctx* ctx, int n) {
+  if (!ctx->fork_ev && cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+    return KFAC_ERR_CUDA;
+  for (int q = 0; q < n; ++q) {
+    if (!ctx->side[q] && cudaStreamCreateWithFlags(&ctx->side[q], cudaStreamNonBlocking) != cudaSuccess)
+      return KFAC_ERR_CUDA;
+    if (!ctx->join_ev[q] && cudaEventCreateWithFlags(&ctx->join_ev[q], cudaEventDisableTiming) != cudaSuccess)
+      return KFAC_ERR_CUDA;
+  }
   return KFAC_OK;
 }
 
@@ -289,6 +395,11 @@ KFAC_API kfac_status kfac_destroy(kfac_ctx* ctx) {
   if (!ctx) return KFAC_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (int q = 0; q < kMaxSideStreams; ++q) {
+    if (ctx->side[q]) { cudaStreamSynchronize(ctx->side[q]); cudaStreamDestroy(ctx->side[q]); }
+    if (ctx->join_ev[q]) cudaEventDestroy(ctx->join_ev[q]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->dflags) cudaFree(ctx->dflags);
   delete ctx;
@@ -323,6 +434,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
     case KFAC_OPT_EIG_TOL:
       if (!(v > 0 && v < 1)) return KFAC_ERR_INVALID_ARG;
       ctx->eig_tol = v;
+      return KFAC_OK;
+    case KFAC_OPT_CHOLQR_INNER_PASSES:
+      if (v < 1 || v > 6) return KFAC_ERR_INVALID_ARG;
+      ctx->cholqr_inner_passes = (int)v;
       return KFAC_OK;
   }
   return KFAC_ERR_INVALID_ARG;
@@ -374,77 +489,55 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
 KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
                                       int power_iters, float lambda, const float* omega, int ldo,
                                       kfac_precision prec, float* U, int ldu, float* D, float* coef) {
-  if (!ctx || d <= 0 || !F || ldf < d || rank <= 0 || oversample < 0 || power_iters < 0 || power_iters > 64)
-    return KFAC_ERR_INVALID_ARG;
-  if (!(lambda > 0.0f) || prec < KFAC_PREC_FP32 || prec > KFAC_PREC_BF16) return KFAC_ERR_INVALID_ARG;
-  const int r = std::min(rank, d);
-  const long long kl = (long long)rank + oversample;
-  if (kl > 4096) return KFAC_ERR_UNSUPPORTED;
-  const int k = (int)kl;
-  if (!U || ldu < r || !D || !coef) return KFAC_ERR_INVALID_ARG;
-  const bool exact = k >= d;
-  if (!exact && (!omega || ldo < k)) return KFAC_ERR_INVALID_ARG;
-  if (exact && d > 4096) return KFAC_ERR_UNSUPPORTED;
+  if (!ctx) return KFAC_ERR_INVALID_ARG;
+  kfac_invert_desc a = {d, F, ldf, rank, oversample, power_iters, lambda, omega, ldo, prec, U, ldu, D, coef};
+  int r = 0, k = 0;
+  kfac_status st = check_invert(a, &r, &k);
+  if (st != KFAC_OK) return st;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   InvertLayout L = invert_layout(d, k, r);
-  kfac_status st = ensure_ws(ctx, L.total);
-  if (st != KFAC_OK) return st;
-  cudaStream_t s = ctx->stream;
+  if ((st = ensure_ws(ctx, L.total)) != KFAC_OK) return st;
+  return invert_run(ctx, a, L, 0);
+}
 
-  if (exact) {  // nothing to sketch: diagonalise F itself (Q = I)
-    double* C = at<double>(ctx, L.c);
-    CK(convert_f32_to_f64(F, ldf, d, d, C, d, ctx->dflags, s));
-    st = eigensolve(ctx, C, d, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
-                    at<float>(ctx, L.jac));
+KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kfac_invert_desc* descs) {
+  if (!ctx || count < 0 || (count > 0 && !descs)) return KFAC_ERR_INVALID_ARG;
+  if (count == 0) return KFAC_OK;
+  std::vector<InvertLayout> lay(count);
+  for (int f = 0; f < count; ++f) {
+    int r = 0, k = 0;
+    kfac_status st = check_invert(descs[f], &r, &k);
     if (st != KFAC_OK) return st;
-    STAGE(ctx, ST_SELECT);
-    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), d, r, lambda, nullptr, D, coef, U, ldu, s));
-    return KFAC_OK;
+    lay[f] = invert_layout(descs[f].d, k, r);
   }
-
-  // Omega^T (k x d) so that every sketch product reads K-contiguous rows.
-  float* Om = at<float>(ctx, L.om);
-  float* cur = at<float>(ctx, L.y);
-  float* other = at<float>(ctx, L.q);
-  {
-    STAGE(ctx, ST_TRANSPOSE);
-    CK(transpose_f32(omega, ldo, d, k, Om, L.dp, s));
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  const int ns = std::min(count, kMaxSideStreams);
+  std::vector<size_t> base(ns + 1, 0);
+  for (int q = 0; q < ns; ++q) {
+    size_t m = 0;
+    for (int f = q; f < count; f += ns) m = std::max(m, lay[f].total);
+    base[q + 1] = base[q] + ((m + 255) & ~size_t(255));
   }
-  st = sketch_product(ctx, Om, L.dp, F, ldf, k, d, prec, cur, L.dp);  // Y^T = Omega^T F
+  kfac_status st = ensure_ws(ctx, base[ns]);
   if (st != KFAC_OK) return st;
-  for (int it = 0;; ++it) {
-    st = orthonormalise(ctx, L, cur, other, k, d);  // Q^T in cur
-    if (st != KFAC_OK) return st;
-    if (it == power_iters) break;
-    st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, prec, other, L.dp);  // Y^T = Q^T F
-    if (st != KFAC_OK) return st;
-    std::swap(cur, other);
+  if (count == 1) return invert_run(ctx, descs[0], lay[0], 0);
+  if ((st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
+  cudaStream_t main_s = ctx->stream;
+  CK(cudaEventRecord(ctx->fork_ev, main_s));
+  for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(ctx->side[q], ctx->fork_ev, 0));
+  kfac_status first_err = KFAC_OK;
+  for (int f = 0; f < count && first_err == KFAC_OK; ++f) {
+    ctx->stream = ctx->side[f % ns];
+    first_err = invert_run(ctx, descs[f], lay[f], base[f % ns]);
   }
-  // Projection C = Q^T F Q = Q^T (F Q): Z^T = Q^T F into `other`, then C = Q^T Z.
-  st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, prec, other, L.dp);
-  if (st != KFAC_OK) return st;
-  double* C = at<double>(ctx, L.c);
-  st = gram_f64(ctx, L, cur, other, L.dp, k, d, KFAC_PREC_FP32, C, ST_PROJ);
-  if (st != KFAC_OK) return st;
-  st = eigensolve(ctx, C, k, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
-                  at<float>(ctx, L.jac));
-  if (st != KFAC_OK) return st;
-  float* P32 = at<float>(ctx, L.p32);
-  {
-    STAGE(ctx, ST_SELECT);
-    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, lambda, P32, D, coef, nullptr, 0, s));
+  ctx->stream = main_s;
+  for (int q = 0; q < ns; ++q) {
+    CK(cudaEventRecord(ctx->join_ev[q], ctx->side[q]));
+    CK(cudaStreamWaitEvent(main_s, ctx->join_ev[q], 0));
   }
-  // Lift: U (d x r) = Q P[:, :r] = (Q^T)^T P32.
-  GemmDesc<float> g = {};
-  g.M = d; g.N = r; g.K = k;
-  g.A = cur; g.sam = 1; g.sak = L.dp;
-  g.B = P32; g.sbn = 1; g.sbk = r;
-  g.D = U; g.ldd = ldu;
-  g.alpha = 1.0f; g.zsplit = 1;
-  STAGE(ctx, ST_LIFT);
-  CK(gemm_f32(g, KFAC_PREC_FP32, s));
-  return KFAC_OK;
+  return first_err;
 }
 
 KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const float* J, int ldj,

@@ -25,17 +25,28 @@ namespace {
 constexpr int CHOL_THREADS = 256;
 constexpr int CHOL_ATTEMPTS = 4;
 
+// 1/sqrt(x) for x > 0 in FP64: an FP32 estimate refined by two Newton steps
+// y <- y (3 - x y^2) / 2 (each roughly doubles the number of correct bits:
+// ~2^-23 -> 2^-46 -> rounding). Far cheaper here than FP64 sqrt + divide.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  return y;
+}
+
 struct CholSmem {
-  double* W;      // nloc x k, own rows
-  double* D;      // B x B diagonal block (replicated)
-  double* Li;     // B x B inverse of L11 (local)
-  double* P[2];   // k x B panel rows (replicated, double-buffered)
+  double* W;      // nloc x k, own rows (row-major, lower part used)
+  double* D;      // B x B diagonal block (replicated in every CTA)
+  double* dinv;   // B reciprocals of diag(L11)
+  double* P[2];   // panel L21, column-major B x k: P[t * k + i] (replicated, double-buffered)
   int* flag;      // breakdown flag
 };
 
-__global__ void __launch_bounds__(CHOL_THREADS) k_chol_cluster(const double* __restrict__ G, int k, int B, int nloc,
-                                                                double shift_rel, float* __restrict__ L32,
-                                                                int* flags, unsigned long long* stats) {
+__global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* __restrict__ G, int k, int B,
+                                                                   int nloc, double shift_rel,
+                                                                   float* __restrict__ L32, int* flags,
+                                                                   unsigned long long* stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int NC = (int)cluster.num_blocks();
@@ -46,8 +57,8 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_cluster(const double* __r
   double* base = reinterpret_cast<double*>(smem_raw);
   sm.W = base;
   sm.D = sm.W + (size_t)nloc * k;
-  sm.Li = sm.D + B * B;
-  sm.P[0] = sm.Li + B * B;
+  sm.dinv = sm.D + B * B;
+  sm.P[0] = sm.dinv + B;
   sm.P[1] = sm.P[0] + (size_t)k * B;
   sm.flag = reinterpret_cast<int*>(sm.P[1] + (size_t)k * B);
 
@@ -62,8 +73,11 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_cluster(const double* __r
   __syncthreads();
   const double trace = s_trace;
   const bool finite_in = isfinite(trace) && trace > 0.0;
+  const double piv_min = 1e-13 * trace;
 
-  double shift = shift_rel > 0.0 ? shift_rel * trace : 0.0;
+  // shift_rel > 0: relative to trace(G); shift_rel < 0: |shift_rel| times the
+  // mean diagonal trace(G) / k.
+  double shift = shift_rel > 0.0 ? shift_rel * trace : (shift_rel < 0.0 ? -shift_rel * trace / k : 0.0);
   int ok = 0;
   for (int attempt = 0; attempt < CHOL_ATTEMPTS && finite_in; ++attempt) {
     if (attempt > 0) {
@@ -84,102 +98,89 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_cluster(const double* __r
     }
     if (tid == 0) *sm.flag = 0;
     __syncthreads();
-    cluster.sync();
+    cluster.sync();  // also: every CTA has started before the first remote store
 
     int buf = 0;
     int bad = 0;
     for (int j0 = 0; j0 < k; j0 += B) {
       const int jb = min(B, k - j0);
-      // (a) broadcast diagonal-block rows owned here.
-      for (int e = tid; e < jb * jb * NC; e += CHOL_THREADS) {
-        int q = e / (jb * jb), rem = e % (jb * jb), u = rem / jb, t = rem % jb;
-        int i = j0 + u;
+      // (a) owners broadcast the rows of the diagonal block (lower part).
+      for (int e = tid; e < jb * jb; e += CHOL_THREADS) {
+        const int u = e / jb, t = e % jb, i = j0 + u;
         if (i % NC != rank) continue;
-        double v = (t <= u) ? sm.W[(size_t)(i / NC) * k + j0 + t] : 0.0;
-        double* dst = cluster.map_shared_rank(sm.D, q);
-        dst[u * B + t] = v;
+        const double v = (t <= u) ? sm.W[(size_t)(i / NC) * k + j0 + t] : 0.0;
+        for (int q = 0; q < NC; ++q) cluster.map_shared_rank(sm.D, q)[u * B + t] = v;
       }
       cluster.sync();
-      // (b) factor the diagonal block (warp 0) and invert L11.
-      if (tid < 32) {
-        const int lane = tid;
-        for (int t = 0; t < jb; ++t) {
-          double piv = sm.D[t * B + t];
-          bool good = isfinite(piv) && piv > 1e-13 * trace;
-          if (!good) { if (lane == 0) *sm.flag = 1; break; }
-          double l = sqrt(piv);
-          __syncwarp();
-          if (lane == t) sm.D[t * B + t] = l;
-          if (lane > t && lane < jb) sm.D[lane * B + t] /= l;
-          __syncwarp();
-          if (lane > t && lane < jb) {
-            double lu = sm.D[lane * B + t];
-            for (int v = t + 1; v <= lane; ++v) sm.D[lane * B + v] -= lu * sm.D[v * B + t];
-          }
-          __syncwarp();
+      // (b) factor the diagonal block in place, all threads (same data and code
+      //     in every CTA -> identical pivots and breakdown decisions).
+      for (int t = 0; t < jb; ++t) {
+        const double piv = sm.D[t * B + t];
+        if (!(isfinite(piv) && piv > piv_min)) { bad = 1; break; }
+        // FP64 issues per warp instruction whatever the active lanes, so the
+        // reciprocal square root is evaluated by one thread only.
+        __syncthreads();  // everyone has read D[t][t]
+        if (tid == 0) {
+          const double y = rsqrt_newton(piv);
+          sm.D[t * B + t] = piv * y;
+          sm.dinv[t] = y;
         }
-        __syncwarp();
-        if (*sm.flag == 0 && lane < jb) {  // column `lane` of L11^-1 by forward substitution
-          const int c = lane;
-          for (int t = 0; t < jb; ++t) {
-            double x = (t == c) ? 1.0 : 0.0;
-            if (t >= c) {
-              for (int u = c; u < t; ++u) x -= sm.D[t * B + u] * sm.Li[u * B + c];
-              x /= sm.D[t * B + t];
-            } else {
-              x = 0.0;
-            }
-            sm.Li[t * B + c] = x;
-          }
+        __syncthreads();
+        const double y = sm.dinv[t];
+        for (int u = t + 1 + tid; u < jb; u += CHOL_THREADS) sm.D[u * B + t] *= y;
+        __syncthreads();
+        const int n = jb - t - 1;  // trailing (u, v), t < v <= u < jb
+        for (int e = tid; e < n * n; e += CHOL_THREADS) {
+          const int u = t + 1 + e / n, v = t + 1 + e % n;
+          if (v <= u) sm.D[u * B + v] = fma(-sm.D[u * B + t], sm.D[v * B + t], sm.D[u * B + v]);
         }
+        __syncthreads();
       }
-      __syncthreads();
-      bad = *sm.flag;
-      if (bad) break;  // identical decision in every CTA; no remote writes pending
-      // (b') own diagonal rows take L11; own rows below solve L21 = A21 L11^-T and broadcast.
+      if (bad) break;  // identical decision in every CTA; no remote stores pending
+      // (b') own diagonal rows take L11; own rows below solve L21 = A21 L11^-T
+      //      by forward substitution (thread per row) and broadcast the panel.
       for (int e = tid; e < jb * jb; e += CHOL_THREADS) {
-        int u = e / jb, t = e % jb, i = j0 + u;
+        const int u = e / jb, t = e % jb, i = j0 + u;
         if (i % NC == rank && t <= u) sm.W[(size_t)(i / NC) * k + j0 + t] = sm.D[u * B + t];
       }
       const int first = j0 + jb;
-      // own rows i >= first: li from li0
       int li0 = (first - rank + NC - 1) / NC;
       if (li0 < 0) li0 = 0;
       const int nrows = nloc - li0;
-      if (nrows > 0) {
-        // compute into registers first (reads of W row segment happen before writes)
-        for (int e = tid; e < nrows * jb; e += CHOL_THREADS) {
-          int lr = li0 + e / jb, t = e % jb, i = lr * NC + rank;
-          if (i >= k) continue;
-          double s = 0.0;
-          for (int u = 0; u <= t; ++u) s += sm.W[(size_t)lr * k + j0 + u] * sm.Li[t * B + u];
-          sm.P[buf][(size_t)i * B + t] = s;  // local staging; broadcast below
+      double* P = sm.P[buf];
+      for (int lr = li0 + tid; lr < nloc; lr += CHOL_THREADS) {
+        const int i = lr * NC + rank;
+        if (i >= k) continue;
+        double* wrow = sm.W + (size_t)lr * k + j0;
+        for (int t = 0; t < jb; ++t) {
+          double x = wrow[t];
+          for (int u = 0; u < t; ++u) x = fma(-wrow[u], sm.D[t * B + u], x);
+          x *= sm.dinv[t];
+          wrow[t] = x;
+          P[(size_t)t * k + i] = x;
         }
-        __syncthreads();
+      }
+      __syncthreads();
+      if (NC > 1 && nrows > 0) {
         for (int e = tid; e < nrows * jb; e += CHOL_THREADS) {
-          int lr = li0 + e / jb, t = e % jb, i = lr * NC + rank;
+          const int lr = li0 + e / jb, t = e % jb, i = lr * NC + rank;
           if (i >= k) continue;
-          double s = sm.P[buf][(size_t)i * B + t];
-          sm.W[(size_t)lr * k + j0 + t] = s;
-          for (int q = 0; q < NC; ++q) {
-            if (q == rank) continue;
-            double* dst = cluster.map_shared_rank(sm.P[buf], q);
-            dst[(size_t)i * B + t] = s;
-          }
+          const double x = P[(size_t)t * k + i];
+          for (int q = 0; q < NC; ++q)
+            if (q != rank) cluster.map_shared_rank(P, q)[(size_t)t * k + i] = x;
         }
       }
       cluster.sync();
-      // (c) trailing update of own rows: W[i][j] -= sum_t L21[i][t] L21[j][t], first <= j <= i.
-      if (nrows > 0) {
-        const int ncols = k - first;
-        for (long long e = tid; e < (long long)nrows * ncols; e += CHOL_THREADS) {
-          int lr = li0 + (int)(e / ncols), j = first + (int)(e % ncols), i = lr * NC + rank;
-          if (i >= k || j > i) continue;
-          const double* pi = sm.P[buf] + (size_t)i * B;
-          const double* pj = sm.P[buf] + (size_t)j * B;
-          double s = 0.0;
-          for (int t = 0; t < jb; ++t) s += pi[t] * pj[t];
-          sm.W[(size_t)lr * k + j] -= s;
+      // (c) trailing update of own rows: W[i][j] -= sum_t L21[i][t] L21[j][t],
+      //     first <= j <= i; warp per row, lanes over j (P reads conflict-free).
+      for (int lr = li0 + (tid >> 5); lr < nloc; lr += CHOL_THREADS / 32) {
+        const int i = lr * NC + rank;
+        if (i >= k) continue;
+        double* wrow = sm.W + (size_t)lr * k;
+        for (int j = first + (tid & 31); j <= i; j += 32) {
+          double acc = 0.0;
+          for (int t = 0; t < jb; ++t) acc = fma(P[(size_t)t * k + i], P[(size_t)t * k + j], acc);
+          wrow[j] -= acc;
         }
       }
       __syncthreads();
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_cluster(const double* __r
 }
 
 size_t chol_smem_bytes(int k, int nloc, int B) {
-  return sizeof(double) * ((size_t)nloc * k + 2 * (size_t)B * B + 2 * (size_t)k * B) + 16;
+  return sizeof(double) * ((size_t)nloc * k + (size_t)B * B + B + 2 * (size_t)k * B) + 16;
 }
 
 }  // namespace

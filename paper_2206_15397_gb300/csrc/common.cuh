@@ -13,6 +13,11 @@ namespace kfac {
 // minus 1 KB kept for static shared variables.
 constexpr int kSmemOptin = 227 * 1024 - 1024;
 
+// Largest sketch width k = rank + oversample (and largest factor diagonalised
+// directly when k >= d): the FP64 Cholesky keeps the k x k Gram and the
+// Jacobi keeps its column blocks in the shared memory of a 16-CTA cluster.
+constexpr int kMaxSketch = 576;
+
 // Process-wide count of kernel launches issued by this library.
 void note_launch(unsigned n = 1);
 unsigned long long launch_count();
@@ -41,11 +46,15 @@ __device__ __forceinline__ float round_operand(float x, Round r) {
   return x;
 }
 
-// Generic strided GEMM description: D[m, n] = alpha * rowscale[m] * colscale[n] *
-// sum_k A(m, k) B(n, k) + beta * C0[m, n], with A(m, k) = A[m*sam + k*sak] and
-// B(n, k) = B[n*sbn + k*sbk]. When zsplit > 1 the K range is cut into zsplit
-// chunks and chunk z writes its raw partial sums to D + z*zstride (alpha, scales,
-// beta ignored); a reduction kernel combines them.
+// Generic strided GEMM description: D(m, n) = alpha * rowscale[m] * colscale[n] *
+// sum_k A(m, k) B(n, k) + beta * C0(m, n), with A(m, k) = A[m*sam + k*sak] and
+// B(n, k) = B[n*sbn + k*sbk]. D(m, n) is D[m*ldd + n], or D[n*ldd + m] with
+// d_trans; C0 likewise with c0_trans. sym (M == N, A B^T symmetric): only
+// elements with m <= n are computed and each is also written at (n, m), so the
+// result is exactly symmetric. When zsplit > 1 the K range is cut into zsplit
+// chunks (kchunk a multiple of 32) and chunk z writes its raw partial sums to
+// D + z*zstride in D's layout (alpha, scales, beta ignored); the caller reduces
+// them. ws (ws_floats floats, optional) lets the dispatcher split K by itself.
 template <typename T>
 struct GemmDesc {
   int M, N, K;
@@ -63,6 +72,11 @@ struct GemmDesc {
   int zsplit;
   int kchunk;
   long long zstride;
+  int d_trans;
+  int c0_trans;
+  int sym;
+  T* ws;
+  long long ws_floats;
 };
 
 // ---- launchers (host) --------------------------------------------------------
@@ -79,7 +93,8 @@ cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int col
 
 // FP64 Cholesky of (G + shift I) on a thread-block cluster; writes the lower
 // factor L as FP32 (k x k row-major, upper part zero). shift = shift_rel *
-// trace(G); on breakdown the shift grows (bounded retries) and flags record it.
+// trace(G) for shift_rel > 0, |shift_rel| * trace(G) / k for shift_rel < 0; on
+// breakdown the shift grows (bounded retries) and flags record it.
 cudaError_t chol_f64_cluster(const double* G, int k, double shift_rel, float* L32, int* flags,
                              unsigned long long* stats, cudaStream_t s);
 
@@ -87,11 +102,11 @@ cudaError_t chol_f64_cluster(const double* G, int k, double shift_rel, float* L3
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
                            cudaStream_t s);
 
-// One-CTA FP32 one-sided Jacobi on chol(C + s I): writes X (k x k FP64, column j
-// = unit eigenvector) and lam (k, unsorted). gscratch: k*k floats used when the
-// working matrix does not fit in shared memory.
-cudaError_t eig_onesided_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
-                             double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s);
+// FP32 one-sided Jacobi on chol(C + s I) over a thread-block cluster: writes X
+// (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:
+// k*k floats (the column store shared by the cluster's CTAs).
+cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
+                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s);
 
 // One FP64 refinement step (Ogita-Aishima) of eigenpairs (X, lam) of C.
 // Workspace: 5 k*k doubles. X and lam are updated in place.

@@ -1,13 +1,14 @@
 // Eigensolver for the small projected matrix C = Q^T F Q ("Eigen_decomp" of
 // Alg. 3), and for whole factors with d <= k.
 //
-//  1. eig_onesided_f32: one CTA per matrix. C + s I (s a small PD shift) is
-//     Cholesky-factored in FP32 in shared memory, C + s I = L L^T, and the
-//     columns of W = L are made mutually orthogonal by one-sided (Hestenes)
-//     Jacobi rotations W <- W J in a round-robin parallel ordering (one warp per
-//     column pair). Since W W^T = C + s I is invariant, at convergence the unit
-//     columns of W are eigenvectors of C and |w_j|^2 - s its eigenvalues. Only
-//     one k x k FP32 matrix is stored (k <= 238 fits in shared memory).
+//  1. eig_jacobi_f32: C + s I (s a small PD shift) is Cholesky-factored in FP32
+//     (C + s I = L L^T) and the columns of W = L are made mutually orthogonal by
+//     one-sided (Hestenes) Jacobi rotations W <- W J. Since W W^T = C + s I is
+//     invariant, at convergence the unit columns of W are eigenvectors of C and
+//     |w_j|^2 - s its eigenvalues; only one k x k FP32 matrix is stored. The
+//     sweeps run on a thread-block cluster (up to 8 CTAs) as a block
+//     round-robin: one warp per column pair, one cluster barrier per
+//     block-round.
 //  2. eig_refine_f64: one FP64 refinement step of all eigenpairs (Ogita and
 //     Aishima, "Iterative refinement for symmetric eigenvalue decomposition",
 //     2018): from R = I - X^T X and S = X^T C X, lam_i = S_ii / (1 - R_ii) and
@@ -15,147 +16,282 @@
 //     separated pairs, R_ij / 2 otherwise. The products are FP64 GEMMs spread
 //     over many CTAs; it lifts FP32-accurate pairs to near FP64 accuracy.
 //  3. eig_select: descending stable sort, leading r pairs, damping coefficients.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace kfac {
 namespace {
 
 constexpr int EIG_THREADS = 512;
 constexpr int EIG_WARPS = EIG_THREADS / 32;
-constexpr int EIG_SMEM_MAX = kSmemOptin;
+constexpr int EIG_MAX_NC = 16;  // non-portable cluster size, enabled at launch
 
 __device__ __forceinline__ float warp_sum_bcast(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return __shfl_sync(0xffffffffu, v, 0);  // one value for every lane
 }
 
-__global__ void __launch_bounds__(EIG_THREADS) k_eig_onesided(const double* __restrict__ C, int k, double shift_rel,
-                                                               int max_sweeps, float tol, double* __restrict__ X,
-                                                               double* __restrict__ lam, float* gscratch, int use_smem,
-                                                               int* flags, unsigned long long* stats) {
-  extern __shared__ __align__(16) float esm[];
-  float* W = use_smem ? esm : gscratch;  // column-major: W[j * k + i]
-  __shared__ double s_trace, s_shift;
-  __shared__ int s_bad, s_count;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Rotate columns wa, wb (length k) to make them orthogonal (one warp). Returns 1
+// if a rotation was applied. `sm` is the kernel's dynamic shared array and the
+// columns are given as offsets into it, so every access stays a shared-memory
+// access (a generic pointer would turn them into generic loads).
+__device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, int kp, float tol, int lane) {
+  // Columns are zero-padded to kp (a multiple of 128): each lane moves float4s,
+  // and the padding stays zero under rotations.
+  float4* a4 = reinterpret_cast<float4*>(sm + oa);
+  float4* b4 = reinterpret_cast<float4*>(sm + ob);
+  const int n4 = kp >> 2;
+  float al = 0.f, be = 0.f, ga = 0.f;
+  for (int i = lane; i < n4; i += 32) {
+    const float4 x = a4[i], y = b4[i];
+    al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+    be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+    ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
+  }
+  al = warp_sum_bcast(al);
+  be = warp_sum_bcast(be);
+  ga = warp_sum_bcast(ga);
+  if (!(ga != 0.0f && fabsf(ga) > tol * sqrtf(al * be))) return 0;
+  // 2x2 symmetric Schur step on the Gram [[al, ga], [ga, be]]: J = [[c, s], [-s, c]].
+  float zeta = (be - al) / (2.0f * ga);
+  float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+  float cs = rsqrtf(1.0f + t * t), sn = cs * t;
+  for (int i = lane; i < n4; i += 32) {
+    const float4 x = a4[i], y = b4[i];
+    a4[i] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z, cs * x.w - sn * y.w);
+    b4[i] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z, sn * x.w + cs * y.w);
+  }
+  return 1;
+}
 
-  if (tid < 32) {
-    double t = 0.0;
-    for (int i = tid; i < k; i += 32) t += C[(size_t)i * k + i];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (tid == 0) {
-      s_trace = t;
-      s_shift = fmax(shift_rel * fabs(t), 1e-30);
+// Position p (0 <= p < m) of a round-robin tournament of m players at round r:
+// player 0 never moves, the others rotate. Pairing position p with m-1-p over
+// rounds r = 0..m-2 meets every pair of players exactly once.
+__device__ __forceinline__ int rr_player(int p, int r, int m) {
+  return p == 0 ? 0 : 1 + (p - 1 + r) % (m - 1);
+}
+
+struct EigArgs {
+  const double* C;
+  int k;
+  double shift_rel;
+  int max_sweeps;
+  float tol;
+  double* X;
+  double* lam;
+  float* Wg;      // k x k FP32 scratch, column-major (Cholesky factor when it does not fit in shared memory)
+  int* flags;
+  unsigned long long* stats;
+  int b;          // columns per block (the cluster holds 2 * NC blocks)
+  int kp;         // padded column length in shared memory (multiple of 128)
+  int chol_smem;  // CTA 0 factors in shared memory (else in Wg)
+};
+
+// One-sided Jacobi on the columns of L = chol(C + sI), spread over a cluster.
+// The k columns form 2*NC blocks of b columns ("players" of a round-robin
+// tournament); CTA c plays the blocks at positions c (top slot) and 2NC-1-c
+// (bottom slot), so every pair of blocks meets once per sweep of 2NC-1
+// block-rounds. Block-round 0 of a sweep treats all pairs among the CTA's 2b
+// columns (covering the pairs inside every block); later rounds only the b x b
+// cross pairs, b disjoint pairs per inner round, one warp per pair. Between
+// block-rounds the blocks move one position along the tournament circle: each
+// CTA pushes its top block into the top slot of CTA c-1 and its bottom block
+// into the bottom slot of CTA c+1 (distributed shared memory stores into the
+// next of two slot buffers), then the cluster meets at one barrier. CTAs only
+// synchronise through cluster barriers, taken the same number of times by all
+// of them (no spin waits).
+__global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
+  extern __shared__ __align__(16) float esm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int NC = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = a.k, b = a.b, kp = a.kp, nb = 2 * NC;
+  const int slot = b * kp;  // floats per slot; buffer x starts at offset 2 * slot * x (top slot, then bottom)
+  __shared__ double s_shift, s_trace;
+  __shared__ int s_bad, s_count, s_total;
+  if (tid == 0) s_total = 0;
+
+  // ---- CTA 0: FP32 Cholesky of C + s I (column-major, stride k) -------------
+  if (rank == 0) {
+    float* W = a.chol_smem ? esm : a.Wg;
+    if (tid < 32) {
+      double t = 0.0;
+      for (int i = tid; i < k; i += 32) t += a.C[(size_t)i * k + i];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (tid == 0) {
+        s_trace = t;
+        s_shift = fmax(a.shift_rel * fabs(t), 1e-30);
+      }
+    }
+    __syncthreads();
+    for (int attempt = 0;; ++attempt) {
+      const double sh = s_shift;
+      for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) {
+        int j = (int)(e / k), i = (int)(e % k);
+        W[e] = (i >= j) ? (float)(a.C[(size_t)i * k + j] + (i == j ? sh : 0.0)) : 0.0f;
+      }
+      if (tid == 0) s_bad = isfinite(s_trace) ? 0 : 2;
+      __syncthreads();
+      for (int j = 0; j < k && !s_bad; ++j) {
+        if (tid == 0) {
+          float p = W[(size_t)j * k + j];
+          if (!(p > 0.0f) || !isfinite(p)) s_bad = 1;
+          else W[(size_t)j * k + j] = sqrtf(p);
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const float ljj = W[(size_t)j * k + j];
+        for (int i = j + 1 + tid; i < k; i += EIG_THREADS) W[(size_t)j * k + i] /= ljj;
+        __syncthreads();
+        for (int l = j + 1 + warp; l < k; l += EIG_WARPS) {  // trailing update, warp per column
+          const float wl = W[(size_t)j * k + l];
+          float* col = W + (size_t)l * k;
+          const float* cj = W + (size_t)j * k;
+          for (int i = l + lane; i < k; i += 32) col[i] = fmaf(-cj[i], wl, col[i]);
+        }
+        __syncthreads();
+      }
+      if (!s_bad) break;
+      if (s_bad == 2 || attempt >= 4) {
+        if (tid == 0) raise_flag(a.flags, s_bad == 2 ? KFAC_FLAG_NONFINITE : KFAC_FLAG_CHOL_FAILED);
+        break;
+      }
+      if (tid == 0) {
+        s_shift = fmax(s_shift * 100.0, 1e-6 * fabs(s_trace));
+        raise_flag(a.flags, KFAC_FLAG_EIG_SHIFTED);
+      }
+      __syncthreads();
+    }
+    if (s_bad) {  // keep downstream finite: W = identity
+      for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) W[e] = ((e / k) == (e % k)) ? 1.0f : 0.0f;
+      if (tid == 0) s_shift = 0.0;
+    }
+    __syncthreads();
+    if (a.chol_smem)
+      for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) __stcg(a.Wg + e, esm[e]);
+    __threadfence();
+  }
+  // Every CTA has started (distributed shared memory is usable only after this
+  // barrier) and CTA 0's factor and shift are published.
+  cluster.sync();
+  if (rank != 0 && tid == 0) s_shift = *cluster.map_shared_rank(&s_shift, 0);
+
+  // ---- initial blocks (round 0 positions) from the factor ------------------
+  {
+    const int blk[2] = {rr_player(rank, 0, nb), rr_player(nb - 1 - rank, 0, nb)};
+    for (int sl = 0; sl < 2; ++sl) {
+      const int c0 = min(k, blk[sl] * b), nc = min(k, c0 + b) - c0;
+      const int dst = sl * slot;
+      for (int e = tid; e < b * kp; e += EIG_THREADS) {
+        int c = e / kp, i = e % kp;
+        esm[dst + e] = (c < nc && i < k) ? __ldcg(a.Wg + (size_t)(c0 + c) * k + i) : 0.0f;
+      }
     }
   }
   __syncthreads();
-  if (!isfinite(s_trace)) {
-    if (tid == 0) raise_flag(flags, KFAC_FLAG_NONFINITE);
-    for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) X[e] = ((e / k) == (e % k)) ? 1.0 : 0.0;
-    for (int i = tid; i < k; i += EIG_THREADS) lam[i] = 0.0;
-    return;
-  }
 
-  // ---- FP32 Cholesky of C + s I, growing s on breakdown --------------------
-  for (int attempt = 0;; ++attempt) {
-    const double sh = s_shift;
-    for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) {
-      int j = (int)(e / k), i = (int)(e % k);
-      W[e] = (i >= j) ? (float)(C[(size_t)i * k + j] + (i == j ? sh : 0.0)) : 0.0f;
-    }
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-      if (tid == 0) {
-        float p = W[(size_t)j * k + j];
-        if (!(p > 0.0f) || !isfinite(p)) s_bad = 1;
-        else W[(size_t)j * k + j] = sqrtf(p);
-      }
-      __syncthreads();
-      if (s_bad) break;
-      const float ljj = W[(size_t)j * k + j];
-      for (int i = j + 1 + tid; i < k; i += EIG_THREADS) W[(size_t)j * k + i] /= ljj;
-      __syncthreads();
-      const int n = k - j - 1;  // trailing (i, l) with j < l <= i < k
-      for (long long e = tid; e < (long long)n * n; e += EIG_THREADS) {
-        int l = j + 1 + (int)(e / n), i = j + 1 + (int)(e % n);
-        if (i >= l) W[(size_t)l * k + i] -= W[(size_t)j * k + i] * W[(size_t)j * k + l];
-      }
-      __syncthreads();
-    }
-    if (!s_bad) break;
-    if (attempt >= 4) {
-      if (tid == 0) raise_flag(flags, KFAC_FLAG_CHOL_FAILED);
-      break;
-    }
-    if (tid == 0) {
-      s_shift = fmax(s_shift * 100.0, 1e-6 * fabs(s_trace));
-      raise_flag(flags, KFAC_FLAG_EIG_SHIFTED);
-    }
-    __syncthreads();
-  }
-
-  // ---- one-sided Jacobi, round-robin ordering -------------------------------
-  // Players 0..m-1 (m even, a phantom column when k is odd). Round r pairs
-  // (r, m-1) and ((r+p) mod (m-1), (r-p) mod (m-1)) for p = 1..m/2-1; m-1
-  // rounds visit every pair once.
-  const int m = k + (k & 1);
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
+  // ---- sweeps ---------------------------------------------------------------
+  int sweep = 0, cur = 0;
+  for (; sweep < a.max_sweeps; ++sweep) {
     if (tid == 0) s_count = 0;
     __syncthreads();
-    for (int r = 0; r < m - 1; ++r) {
-      for (int p = warp; p < m / 2; p += EIG_WARPS) {
-        int a, b;
-        if (p == 0) { a = r; b = m - 1; }
-        else { a = (r + p) % (m - 1); b = (r - p + (m - 1)) % (m - 1); }
-        if (a >= k || b >= k) continue;
-        float* wa = W + (size_t)a * k;
-        float* wb = W + (size_t)b * k;
-        float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < k; i += 32) {
-          float x = wa[i], y = wb[i];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
-        }
-        al = warp_sum_bcast(al);
-        be = warp_sum_bcast(be);
-        ga = warp_sum_bcast(ga);
-        if (ga != 0.0f && fabsf(ga) > tol * sqrtf(al * be)) {
-          float zeta = (be - al) / (2.0f * ga);
-          float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-          float cs = rsqrtf(1.0f + t * t), sn = cs * t;
-          for (int i = lane; i < k; i += 32) {
-            float x = wa[i], y = wb[i];
-            wa[i] = cs * x - sn * y;
-            wb[i] = sn * x + cs * y;
+    for (int t = 0; t < nb - 1; ++t) {
+      const int blkA = rr_player(rank, t, nb), blkB = rr_player(nb - 1 - rank, t, nb);
+      const int ba = max(0, min(k, blkA * b + b) - blkA * b);
+      const int bb = max(0, min(k, blkB * b + b) - blkB * b);
+      const int top = 2 * slot * cur;
+      const int bot = top + slot;
+      int cnt = 0;
+      if (t == 0) {  // every pair among the ba + bb local columns
+        const int n2 = ba + bb, m2 = n2 + (n2 & 1);
+        for (int r = 0; r < m2 - 1; ++r) {
+          for (int p = warp; p < m2 / 2; p += EIG_WARPS) {
+            int u = rr_player(p, r, m2), v = rr_player(m2 - 1 - p, r, m2);
+            if (u < n2 && v < n2) {
+              const int cu = u < ba ? top + u * kp : bot + (u - ba) * kp;
+              const int cv = v < ba ? top + v * kp : bot + (v - ba) * kp;
+              cnt += jacobi_pair(esm, cu, cv, kp, a.tol, lane);
+            }
           }
-          if (lane == 0) atomicAdd(&s_count, 1);
+          __syncthreads();
+        }
+      } else {  // the ba x bb cross pairs, max(ba, bb) disjoint pairs per inner round
+        const int bmax = max(ba, bb);
+        for (int r = 0; r < bmax; ++r) {
+          for (int i = warp; i < bmax; i += EIG_WARPS) {
+            int j = (i + r) % bmax;
+            if (i < ba && j < bb) cnt += jacobi_pair(esm, top + i * kp, bot + j * kp, kp, a.tol, lane);
+          }
+          __syncthreads();
         }
       }
-      __syncthreads();
+      if (lane == 0 && cnt) atomicAdd(&s_count, cnt);
+      // Move the blocks one position along the circle (position 0 stays):
+      // top of CTA c -> top of c-1 (CTA 1's top -> bottom of CTA 0), bottom of
+      // CTA c -> bottom of c+1 (the last CTA's bottom -> its own top).
+      if (NC > 1) {
+        const int nxt = cur ^ 1;
+        int dq_top, ds_top, dq_bot, ds_bot;  // destination CTA and slot
+        if (rank == 0) { dq_top = 0; ds_top = 0; }
+        else if (rank == 1) { dq_top = 0; ds_top = 1; }
+        else { dq_top = rank - 1; ds_top = 0; }
+        if (rank == NC - 1) { dq_bot = rank; ds_bot = 0; }
+        else { dq_bot = rank + 1; ds_bot = 1; }
+        float4* d1 = reinterpret_cast<float4*>(cluster.map_shared_rank(esm + 2 * slot * nxt + ds_top * slot, dq_top));
+        float4* d2 = reinterpret_cast<float4*>(cluster.map_shared_rank(esm + 2 * slot * nxt + ds_bot * slot, dq_bot));
+        const float4* s1 = reinterpret_cast<const float4*>(esm + top);
+        const float4* s2 = reinterpret_cast<const float4*>(esm + bot);
+        const int n4 = slot / 4;
+        for (int e = tid; e < n4; e += EIG_THREADS) {
+          d1[e] = s1[e];
+          d2[e] = s2[e];
+        }
+        cluster.sync();
+        cur = nxt;
+      }
     }
-    if (s_count == 0) break;
+    __syncthreads();  // every warp's count is in s_count (a 1-CTA cluster has no barrier above)
+    // convergence: total rotations of the sweep over the cluster
+    if (tid == 0 && s_count) atomicAdd(cluster.map_shared_rank(&s_total, 0), s_count);
+    cluster.sync();
+    const int total = *cluster.map_shared_rank(&s_total, 0);
+    cluster.sync();
+    if (rank == 0 && tid == 0) s_total = 0;
+    if (total == 0) break;
   }
-  if (sweep >= max_sweeps && tid == 0) raise_flag(flags, KFAC_FLAG_EIG_NOCONV);
-  if (stats && tid == 0) {
-    atomicAdd(stats + STAT_SWEEPS, (unsigned long long)(sweep < max_sweeps ? sweep + 1 : sweep));
-    atomicAdd(stats + STAT_EIG_SOLVES, 1ull);
+  if (rank == 0 && tid == 0) {
+    if (sweep >= a.max_sweeps) raise_flag(a.flags, KFAC_FLAG_EIG_NOCONV);
+    if (a.stats) {
+      atomicAdd(a.stats + STAT_SWEEPS, (unsigned long long)(sweep < a.max_sweeps ? sweep + 1 : sweep));
+      atomicAdd(a.stats + STAT_EIG_SOLVES, 1ull);
+    }
   }
 
-  // ---- eigenpairs: lam_j = |w_j|^2 - s, x_j = w_j / |w_j| -------------------
+  // ---- eigenpairs of the blocks held here: lam_j = |w_j|^2 - s, x_j = w_j / |w_j|
+  // After a whole number of sweeps the blocks are back at their round-0 positions.
   const double sh = s_shift;
-  for (int j = warp; j < k; j += EIG_WARPS) {
-    const float* wj = W + (size_t)j * k;
-    double n2 = 0.0;
-    for (int i = lane; i < k; i += 32) n2 += (double)wj[i] * (double)wj[i];
-    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-    n2 = __shfl_sync(0xffffffffu, n2, 0);
-    double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-    for (int i = lane; i < k; i += 32) X[(size_t)i * k + j] = (double)wj[i] * inv;
-    if (lane == 0) lam[j] = n2 - sh;
+  const int blk[2] = {rr_player(rank, 0, nb), rr_player(nb - 1 - rank, 0, nb)};
+  for (int sl = 0; sl < 2; ++sl) {
+    const int c0 = blk[sl] * b;
+    const float* base = esm + 2 * slot * cur + sl * slot;
+    for (int c = warp; c < b; c += EIG_WARPS) {
+      const int j = c0 + c;
+      if (j >= k) continue;
+      const float* wj = base + (size_t)c * kp;
+      double n2 = 0.0;
+      for (int i = lane; i < k; i += 32) n2 += (double)wj[i] * (double)wj[i];
+      for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      n2 = __shfl_sync(0xffffffffu, n2, 0);
+      double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+      for (int i = lane; i < k; i += 32) a.X[(size_t)i * k + j] = (double)wj[i] * inv;
+      if (lane == 0) a.lam[j] = n2 - sh;
+    }
   }
+  cluster.sync();  // no CTA leaves while others may still address its shared memory
 }
 
 // Refinement combine (one CTA): E from R = I - X^T X (given as XtX) and S.
@@ -242,21 +378,44 @@ __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ 
 
 }  // namespace
 
-cudaError_t eig_onesided_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
-                             double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s) {
+cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
+                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_eig_onesided, cudaFuncAttributeMaxDynamicSharedMemorySize, EIG_SMEM_MAX);
+    cudaError_t e = cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  size_t need = sizeof(float) * (size_t)k * k;
-  int use_smem = need <= (size_t)EIG_SMEM_MAX - 1024;
-  k_eig_onesided<<<1, EIG_THREADS, use_smem ? need : 0, s>>>(C, k, shift_rel, max_sweeps, tol, X, lam, gscratch,
-                                                             use_smem, flags, stats);
+  int nc = (k + 31) / 32;  // b = ceil(k / 2nc) <= 16: one warp per pair of a cross round
+  nc = nc < 1 ? 1 : (nc > EIG_MAX_NC ? EIG_MAX_NC : nc);
+  const int b = (k + 2 * nc - 1) / (2 * nc);
+  const int kp = (k + 127) / 128 * 128;  // float4 per lane, 32 lanes
+  const size_t blocks_bytes = sizeof(float) * 4 * (size_t)b * kp;  // 2 buffers x 2 slots
+  const size_t chol_bytes = sizeof(float) * (size_t)k * k;
+  EigArgs a = {C, k, shift_rel, max_sweeps, tol, X, lam, gscratch, flags, stats, b, kp, 0};
+  size_t smem = blocks_bytes;
+  if (chol_bytes <= (size_t)kSmemOptin) {
+    a.chol_smem = 1;
+    smem = chol_bytes > smem ? chol_bytes : smem;
+  }
+  if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc, 1, 1);
+  cfg.blockDim = dim3(EIG_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   note_launch();
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, k_eig_cluster, a);
 }
 
 cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, double* work, int* flags, cudaStream_t s) {

@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(NT) k_gemm_simt(GemmDesc<T> g) {
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
+  if (g.sym && bm > bn + BN - 1) return;  // tile strictly below the diagonal
   const int kbeg = blockIdx.z * g.kchunk;
   const int kend = min(g.K, kbeg + g.kchunk);
   T acc[4][4];
@@ -68,15 +69,18 @@ __global__ void __launch_bounds__(NT) k_gemm_simt(GemmDesc<T> g) {
     for (int j = 0; j < 4; ++j) {
       int n = bn + tx + 16 * j;
       if (n >= g.N) continue;
-      if (g.zsplit > 1) {
-        g.D[blockIdx.z * g.zstride + (long long)m * g.ldd + n] = acc[i][j];
-      } else {
-        T v = acc[i][j] * g.alpha;
+      if (g.sym && m > n) continue;
+      T v = acc[i][j];
+      if (g.zsplit <= 1) {
+        v *= g.alpha;
         if (g.rowscale) v *= g.rowscale[m];
         if (g.colscale) v *= g.colscale[n];
-        if (g.beta != T(0)) v = fma(g.beta, g.C0[(long long)m * g.ldc + n], v);
-        g.D[(long long)m * g.ldd + n] = v;
+        if (g.beta != T(0))
+          v = fma(g.beta, g.C0[g.c0_trans ? (long long)n * g.ldc + m : (long long)m * g.ldc + n], v);
       }
+      T* D = g.D + (g.zsplit > 1 ? blockIdx.z * g.zstride : 0);
+      D[g.d_trans ? (long long)n * g.ldd + m : (long long)m * g.ldd + n] = v;
+      if (g.sym && m != n) D[g.d_trans ? (long long)m * g.ldd + n : (long long)n * g.ldd + m] = v;
     }
   }
 }
@@ -91,6 +95,40 @@ cudaError_t launch_gemm(const GemmDesc<T>& g, cudaStream_t s) {
   k_gemm_simt<T, R><<<grid, NT, 0, s>>>(d);
   note_launch();
   return cudaGetLastError();
+}
+
+// FP64 GEMM with 16 x 16 output tiles, one output per thread: FP64 issues at
+// ~2 FMA/clock/SM on this part, so small tiles spread a k x k product over as
+// many SMs as possible (k = 230 gives 225 CTAs).
+__global__ void __launch_bounds__(256) k_gemm_f64_t16(GemmDesc<double> g) {
+  __shared__ double As[16][17];
+  __shared__ double Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m = blockIdx.y * 16 + ty, n = blockIdx.x * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < g.K; k0 += 16) {
+    {  // A tile: element (row ty, k tx) or transposed pattern for coalescing
+      int mm = ty, kk = tx;
+      if (g.sak != 1) { mm = tx; kk = ty; }
+      int am = blockIdx.y * 16 + mm, ak = k0 + kk;
+      As[mm][kk] = (am < g.M && ak < g.K) ? g.A[(long long)am * g.sam + (long long)ak * g.sak] : 0.0;
+      int nn = ty, kb = tx;
+      if (g.sbk != 1) { nn = tx; kb = ty; }
+      int bn = blockIdx.x * 16 + nn, bk = k0 + kb;
+      Bs[nn][kb] = (bn < g.N && bk < g.K) ? g.B[(long long)bn * g.sbn + (long long)bk * g.sbk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fma(As[ty][kk], Bs[tx][kk], acc);
+    __syncthreads();
+  }
+  if (m < g.M && n < g.N) {
+    double v = acc * g.alpha;
+    if (g.rowscale) v *= g.rowscale[m];
+    if (g.colscale) v *= g.colscale[n];
+    if (g.beta != 0.0) v = fma(g.beta, g.C0[g.c0_trans ? (long long)n * g.ldc + m : (long long)m * g.ldc + n], v);
+    g.D[g.d_trans ? (long long)n * g.ldd + m : (long long)m * g.ldd + n] = v;
+  }
 }
 
 __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
@@ -148,7 +186,14 @@ cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s) {
   }
 }
 
-cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s) { return launch_gemm<double, Round::None>(g, s); }
+cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.zsplit > 1) return launch_gemm<double, Round::None>(g, s);
+  dim3 grid((g.N + 15) / 16, (g.M + 15) / 16);
+  k_gemm_f64_t16<<<grid, 256, 0, s>>>(g);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out, int ldo,
                               int symmetrize, int* flags, cudaStream_t s) {

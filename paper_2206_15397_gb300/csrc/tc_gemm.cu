@@ -1,0 +1,392 @@
+// Tensor-core GEMM for sm_100-family (tcgen05 + TMA + TMEM), FP32 storage.
+//
+//   D[m, n] = alpha * rowscale[m] * colscale[n] * sum_k A[m, k] B[n, k] + beta * C0(m, n)
+//
+// A (M x K) and B (N x K) are row-major with K contiguous ("K-major"). One CTA
+// computes a 128 x BN tile:
+//   * warp 0 / lane 0 streams A and B tiles of 32 FP32 columns (128 bytes = one
+//     128B-swizzle row) with cp.async.bulk.tensor into a ring of shared-memory
+//     stages, each guarded by a "full" mbarrier (transaction bytes);
+//   * in the 3xTF32 mode warps 4-7 split every staged value in place into its
+//     TF32 head and a TF32 tail (x = hi + lo, both exactly TF32), fence the
+//     generic-proxy writes for the async proxy and arrive on a "split" barrier;
+//   * warp 1 / lane 0 issues tcgen05.mma.kind::tf32 (M = 128, N = BN, K = 8 per
+//     instruction) into a TMEM accumulator: hi*hi, plus hi*lo and lo*hi in the
+//     3xTF32 mode (FP32-accurate products, the lo*lo term is below FP32
+//     rounding), and hands each stage back with tcgen05.commit -> "empty";
+//   * all 8 warps then read TMEM with tcgen05.ld (warp w reads lanes
+//     32*(w%4)..+31, warps 0-3 the first half of the columns, 4-7 the second),
+//     apply the epilogue and store. Row-major D / C0 go through a per-warp
+//     shared-memory tile so global accesses are coalesced; transposed D / C0
+//     (D[n][m]) are coalesced directly since TMEM lanes are consecutive rows.
+// Every mbarrier wait is bounded by a clock deadline; on expiry the kernel
+// raises KFAC_FLAG_TIMEOUT, drains what it issued and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+namespace kfac {
+namespace tc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;  // FP32 columns per stage (128 bytes)
+constexpr int THREADS = 256;
+constexpr long long kDeadlineCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of `bar` with the given parity to complete, or give up
+// after the deadline (raising the timeout flag). Returns true on completion.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* flags) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kDeadlineCycles) {
+      raise_flag(flags, KFAC_FLAG_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading-dimension offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride-dimension offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;            // descriptor format constant
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int BN, int MODE>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 4;
+  static constexpr int B_BYTES = BN * BK * 4;
+  static constexpr int RAW = A_BYTES + B_BYTES;
+  static constexpr int STAGE = MODE == 1 ? 2 * RAW : RAW;
+  static constexpr int STAGES = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
+  static constexpr int BAR_BYTES = 8 * (3 * STAGES + 1) + 16;
+  static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES;
+};
+
+template <int BN, int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
+  using C = Cfg<BN, MODE>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * C::STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), split0 = full0 + 8 * C::STAGES, empty0 = split0 + 8 * C::STAGES;
+  const uint32_t accb = empty0 + 8 * C::STAGES;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (p.sym && m0 > n0 + BN - 1) return;  // whole tile below the diagonal (uniform exit, nothing started)
+  const int kb0 = blockIdx.z * p.kchunk;
+  const int ke = min(p.K, kb0 + p.kchunk);
+  const int nk = ke > kb0 ? (ke - kb0 + BK - 1) / BK : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(split0 + 8 * s, 128);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer --------------------------------------------------------
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags)) break;
+      const uint32_t st = smem_u32(smem + s * C::STAGE);
+      mbar_expect_tx(full0 + 8 * s, C::RAW);
+      tma_load_2d(st, &tmA, kb0 + kb * BK, m0, full0 + 8 * s);
+      tma_load_2d(st + C::A_BYTES, &tmB, kb0 + kb * BK, n0, full0 + 8 * s);
+      ++issued;
+    }
+    // Drain: every issued copy has landed before this CTA may exit (the MMA
+    // issuer consumes them in the normal path; this matters after a timeout).
+    for (int kb = (issued > C::STAGES ? issued - C::STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----------------------------------------------------------
+    constexpr uint32_t idesc = idesc_tf32(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      if (!mbar_wait((MODE == 1 ? split0 : full0) + 8 * s, ph, p.flags)) break;
+      tc_fence_after();
+      const uint32_t st = smem_u32(smem + s * C::STAGE);
+      const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per instruction
+        const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4
+        mma_tf32(taddr, ad + off, bd + off, idesc, (kb | kk) ? 1u : 0u);
+        if (MODE == 1) {
+          const uint64_t adl = sdesc_k128(st + C::RAW), bdl = sdesc_k128(st + C::RAW + C::A_BYTES);
+          mma_tf32(taddr, ad + off, bdl + off, idesc, 1u);
+          mma_tf32(taddr, adl + off, bd + off, idesc, 1u);
+        }
+      }
+      mma_commit(empty0 + 8 * s);  // stage reusable once these MMAs completed
+    }
+    mma_commit(accb);  // accumulator ready (also completes when nothing was issued)
+  } else if (MODE == 1 && warp >= 4) {
+    // ---- 3xTF32 splitter: x -> hi (in place) + lo (tail buffer) -------------
+    const int t = tid - 128;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      if (!mbar_wait(full0 + 8 * s, ph, p.flags)) break;
+      float4* raw = reinterpret_cast<float4*>(smem + s * C::STAGE);
+      float4* lo = reinterpret_cast<float4*>(smem + s * C::STAGE + C::RAW);
+      for (int e = t; e < C::RAW / 16; e += 128) {
+        float4 x = raw[e], h, l;
+        h.x = tf32_round(x.x); l.x = tf32_round(x.x - h.x);
+        h.y = tf32_round(x.y); l.y = tf32_round(x.y - h.y);
+        h.z = tf32_round(x.z); l.z = tf32_round(x.z - h.z);
+        h.w = tf32_round(x.w); l.w = tf32_round(x.w - h.w);
+        raw[e] = h;
+        lo[e] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(split0 + 8 * s);
+    }
+  }
+  __syncwarp();
+
+  // ---- epilogue ----------------------------------------------------------------
+  const bool acc_ok = mbar_wait(accb, 0, p.flags);
+  tc_fence_after();
+  float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // per-warp 32 x 33 staging
+  const int q = warp & 3;
+  const int m = m0 + 32 * q + lane;
+  const int cbeg = (warp < 4) ? 0 : BN / 2;
+  const float rs = (p.rowscale && m < p.M) ? p.rowscale[m] : 1.0f;
+  for (int c0 = cbeg; c0 < cbeg + BN / 2; c0 += 32) {
+    const int nb = n0 + c0;
+    if (nb >= p.N) break;  // uniform across the warp
+    float v[32];
+    if (nk > 0 && acc_ok) {
+      tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+    }
+    if (!p.partial) {
+      float cin[32];
+      if (p.beta != 0.0f && p.C0) {
+        if (p.c0_trans) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = nb + j;
+            cin[j] = (m < p.M && n < p.N) ? p.C0[(long long)n * p.ldc + m] : 0.0f;
+          }
+        } else {  // rows of C0 through the staging tile
+          __syncwarp();
+          for (int r = 0; r < 32; ++r) {
+            const int mr = m0 + 32 * q + r, n = nb + lane;
+            stage_tile[r * 33 + lane] = (mr < p.M && n < p.N) ? p.C0[(long long)mr * p.ldc + n] : 0.0f;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) cin[j] = stage_tile[lane * 33 + j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = nb + j;
+        float x = v[j] * p.alpha * rs;
+        if (p.colscale && n < p.N) x *= p.colscale[n];
+        if (p.beta != 0.0f && p.C0) x = fmaf(p.beta, cin[j], x);
+        v[j] = x;
+      }
+    }
+    if (p.d_trans) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = nb + j;
+        if (m < p.M && n < p.N) p.D[(long long)n * p.ldd + m] = v[j];
+      }
+    } else {
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) stage_tile[lane * 33 + j] = v[j];
+      __syncwarp();
+      for (int r = 0; r < 32; ++r) {
+        const int mr = m0 + 32 * q + r, n = nb + lane;
+        if (mr < p.M && n < p.N && (!p.sym || mr <= n)) p.D[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
+      }
+      if (p.sym) {  // mirror: D[n][m] for m < n, consecutive lanes -> consecutive m
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = nb + j;
+          if (m < p.M && n < p.N && m < n) p.D[(long long)n * p.ldd + m] = v[j];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(BN) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D map of a row-major FP32 matrix (rows x cols, row stride ld) read in
+// boxes of 32 columns x box_rows rows with the 128-byte swizzle.
+bool make_map(CUtensorMap* map, const float* ptr, int rows, int cols, long long ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int MODE>
+cudaError_t launch(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
+                   cudaStream_t s) {
+  using C = Cfg<BN, MODE>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, BN)) return cudaErrorInvalidValue;
+  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zsplit);
+  k_tc_gemm<BN, MODE><<<grid, THREADS, C::SMEM, s>>>(ma, mb, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool eligible(const float* A, long long lda, const float* B, long long ldb, int M, int N, int K) {
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  return M > 0 && N > 0 && K > 0 && al16(A) && al16(B) && (lda % 4) == 0 && (ldb % 4) == 0 && lda >= K && ldb >= K &&
+         encode_fn() != nullptr;
+}
+
+cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
+                 bool split3, cudaStream_t s) {
+  if (a.N > 128) {
+    return split3 ? launch<256, 1>(a, A, lda, B, ldb, zsplit, s) : launch<256, 0>(a, A, lda, B, ldb, zsplit, s);
+  }
+  return split3 ? launch<128, 1>(a, A, lda, B, ldb, zsplit, s) : launch<128, 0>(a, A, lda, B, ldb, zsplit, s);
+}
+
+}  // namespace tc
+}  // namespace kfac

@@ -17,12 +17,21 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 _lib = None
 
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
-OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_sweeps": 3, "eig_tol": 4}
+OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_sweeps": 3, "eig_tol": 4,
+           "cholqr_inner_passes": 5}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
 class KfacError(RuntimeError):
     pass
+
+
+class InvertDesc(ctypes.Structure):
+    """Mirror of kfac_invert_desc."""
+    _fields_ = [("d", ctypes.c_int), ("F", ctypes.c_void_p), ("ldf", ctypes.c_int), ("rank", ctypes.c_int),
+                ("oversample", ctypes.c_int), ("power_iters", ctypes.c_int), ("lam", ctypes.c_float),
+                ("omega", ctypes.c_void_p), ("ldo", ctypes.c_int), ("prec", ctypes.c_int), ("U", ctypes.c_void_p),
+                ("ldu", ctypes.c_int), ("D", ctypes.c_void_p), ("coef", ctypes.c_void_p)]
 
 
 def library_path() -> str:
@@ -53,6 +62,8 @@ def lib():
         L.kfac_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d), ctypes.POINTER(i), i,
                                         ctypes.POINTER(i)]
         L.kfac_kernel_launch_count.restype = ctypes.c_uint64
+        L.kfac_rsvd_invert_grouped.argtypes = [vp, i, ctypes.POINTER(InvertDesc)]
+        L.kfac_rsvd_invert_grouped.restype = i
         L.kfac_precondition_noalloc.argtypes = [vp, i, i, vp, i, vp, i, vp, i, vp, i, vp, i, f, i, vp, i]
         L.kfac_precondition_noalloc.restype = i
         L.kfac_stats_read.argtypes = [vp, ctypes.POINTER(i64), i]
@@ -236,3 +247,35 @@ def kfac_precondition_noalloc(J: torch.Tensor, U_a: torch.Tensor, coef_a: torch.
                                                _vec(coef_g, "coef_g", rg), rg, float(lam), PRECISION[prec], ps, lds),
                "kfac_precondition_noalloc")
     return S
+
+
+def kfac_rsvd_invert_grouped(ctx: Context, items):
+    """Grouped kfac_rsvd_invert. items: sequence of dicts with keys F, rank,
+    oversample, power_iters, lam, omega, prec (optional) and out (optional
+    (U, D, coef)). Returns the list of (U, D, coef)."""
+    descs = (InvertDesc * len(items))()
+    outs = []
+    for it, dsc in zip(items, descs):
+        F = it["F"]
+        d = F.shape[0]
+        r = min(it["rank"], d)
+        k = it["rank"] + it["oversample"]
+        pf, ldf = _mat(F, "F", d, d)
+        om = it.get("omega")
+        po, ldo = _mat(om, "omega", d, k) if om is not None else (ctypes.c_void_p(0), max(k, 1))
+        if it.get("out") is None:
+            U = torch.empty((d, r), device=F.device, dtype=torch.float32)
+            D = torch.empty((r,), device=F.device, dtype=torch.float32)
+            coef = torch.empty((r,), device=F.device, dtype=torch.float32)
+        else:
+            U, D, coef = it["out"]
+        pu, ldu = _mat(U, "U", d, r)
+        dsc.d, dsc.F, dsc.ldf = d, pf.value, ldf
+        dsc.rank, dsc.oversample, dsc.power_iters = int(it["rank"]), int(it["oversample"]), int(it["power_iters"])
+        dsc.lam, dsc.omega, dsc.ldo = float(it["lam"]), po.value, ldo
+        dsc.prec = PRECISION[it.get("prec", "fp32")]
+        dsc.U, dsc.ldu = pu.value, ldu
+        dsc.D, dsc.coef = _vec(D, "D", r).value, _vec(coef, "coef", r).value
+        outs.append((U, D, coef))
+    _check(lib().kfac_rsvd_invert_grouped(ctx.handle, len(items), descs), "kfac_rsvd_invert_grouped")
+    return outs

@@ -181,3 +181,19 @@ def test_c1_end_to_end(kf, ctx, prec, lam_rule):
     assert np.abs(host(Da) - da_).max() / da_[0] <= tol_e
     assert np.abs(host(Dg) - dg_).max() / dg_[0] <= tol_e
     assert rel_fro(host(S), s_or) <= S_TOL[prec], rel_fro(host(S), s_or)
+
+
+# ----------------------------------------------------------------------------- grouped calls
+
+def test_invert_grouped_matches_single_calls(kf, ctx):
+    """The grouped entry point runs the same kernels per factor on forked
+    streams: results are bitwise those of the single-factor calls."""
+    cases = [workloads.spectral(31, 300, 40, alpha=1.0, n=64, steps=4),
+             workloads.spectral(32, 257, 40, alpha=1.5, n=64, steps=4, bias=True),
+             workloads.spectral(33, 20, 40, alpha=1.0, n=16, steps=3)]   # d <= k: exact path
+    items = [dict(F=cuda(f), rank=30, oversample=10, power_iters=1, lam=0.1, omega=cuda(om)) for f, om in cases]
+    grouped = kf.kfac_rsvd_invert_grouped(ctx, items)
+    assert_status_ok(kf, ctx)
+    for it, (U, D, c) in zip(items, grouped):
+        U1, D1, c1 = kf.kfac_rsvd_invert(ctx, it["F"], 30, 10, 1, 0.1, it["omega"])
+        assert torch.equal(U, U1) and torch.equal(D, D1) and torch.equal(c, c1)
