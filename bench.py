@@ -392,22 +392,28 @@ def main(argv=None):
     stream = torch.cuda.Stream(dev)
     ctx = kfac.Context(local, stream)
     kfac.kfac_reserve(ctx, max(da, dg), k, da * dg)
+    def padded(rows, cols):
+        """rows x cols view with a row stride rounded up to 4 floats (16 bytes): the
+        tensor-core kernels read operands through TMA, which needs 16-byte strides."""
+        return torch.zeros((rows, (cols + 3) // 4 * 4), device=dev)[:, :cols]
+
     with torch.cuda.stream(stream):
         T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, non_blocking=False)
+        TP = lambda a: padded(*a.shape).copy_(T(a))
         XA = [T(x) for x in host["xa"]]
         XG = [T(x) for x in host["xg"]]
-        J = [T(x) for x in host["j"]]
+        J = [TP(x) for x in host["j"]]
         OA = [T(x) for x in host["om_a"]]
         OG = [T(x) for x in host["om_g"]]
-        Fa = torch.zeros((da, da), device=dev)
-        Fg = torch.zeros((dg, dg), device=dev)
+        Fa = padded(da, da)
+        Fg = padded(dg, dg)
         for x in host["xa_init"]:
             kfac.kfac_ea_update(ctx, T(x), Fa, w["rho"])
         for x in host["xg_init"]:
             kfac.kfac_ea_update(ctx, T(x), Fg, w["rho"])
         Ua = torch.empty((da, r), device=dev); Da = torch.empty(r, device=dev); Ca = torch.empty(r, device=dev)
         Ug = torch.empty((dg, r), device=dev); Dg = torch.empty(r, device=dev); Cg = torch.empty(r, device=dev)
-        S = torch.empty((dg, da), device=dev)
+        S = padded(dg, da)
     stream.synchronize()
 
     def step(i, xa=None, xg=None, j=None, oa=None, og=None):
@@ -457,7 +463,7 @@ def main(argv=None):
     hoa = [pin(x) for x in host["om_a"]]
     hog = [pin(x) for x in host["om_g"]]
     hs = torch.empty((dg, da), dtype=torch.float32).pin_memory()
-    dxa = torch.empty_like(XA[0]); dxg = torch.empty_like(XG[0]); dj = torch.empty_like(J[0])
+    dxa = torch.empty_like(XA[0]); dxg = torch.empty_like(XG[0]); dj = padded(dg, da)
     doa = torch.empty_like(OA[0]); dog = torch.empty_like(OG[0])
     h2d = sum(t.numel() * 4 for t in (hxa[0], hxg[0], hj[0], hoa[0], hog[0]))
     d2h = hs.numel() * 4
@@ -536,7 +542,7 @@ def evd_comparison(kfac, ctx, stream, Fa, Fg, J, OA, OG, w, q, prec, ms_rand):
     r, lam = w["r"], w["lam"]
     dev = Fa.device
     with torch.cuda.stream(stream):
-        fa, fg = Fa.clone(), Fg.clone()
+        fa, fg = Fa, Fg  # read-only here: eigh and the inversion do not modify their input
 
         def evd_path():
             wa, va = torch.linalg.eigh(fa)

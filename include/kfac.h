@@ -219,6 +219,16 @@ typedef enum {
 
 KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double value);
 
+/* Utility exposing the GEMM engine the entry points above are built on (used
+ * to test it directly): D = alpha * A B^T + beta * D for row-major A (M x K,
+ * lda), B (N x K, ldb) and D (M x N, ldd), device pointers. prec: FP32 (3xTF32
+ * tensor-core products), TF32 or BF16 (operands rounded, FP32 accumulation).
+ * The tcgen05 tensor-core kernel runs when A, B are 16-byte aligned with row
+ * strides that are multiples of 4 floats (TMA); otherwise a SIMT kernel with
+ * the same arithmetic. D must not overlap A or B. */
+KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const float* A, int lda, const float* B,
+                                  int ldb, float alpha, float beta, float* D, int ldd, kfac_precision prec);
+
 /* Per-stage device timing (CUDA events recorded on the context stream around
  * every kernel group; off by default). kfac_profile_enable(ctx, 1) starts
  * recording and clears the totals. kfac_profile_read() synchronises the stream,

@@ -143,10 +143,12 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, l32, c, x, lam, work, jac, p32, total;
-  long long dp;
+  size_t om, y, q, part, g, l32, c, x, lam, work, jac, p32, skws, total;
+  long long dp, skws_floats;
   int nsplit, kchunk;
 };
+
+constexpr int kSketchMaxSplit = 6;  // split-K partials of the sketch products
 
 InvertLayout invert_layout(int d, int k, int r) {
   InvertLayout L = {};
@@ -163,7 +165,7 @@ InvertLayout invert_layout(int d, int k, int r) {
   }
   L.dp = round_up(d, 4);
   L.nsplit = (int)std::min<long long>(16, std::max<long long>(1, d / 512));
-  L.kchunk = (int)round_up((d + L.nsplit - 1) / L.nsplit, 16);
+  L.kchunk = (int)round_up((d + L.nsplit - 1) / L.nsplit, 32);
   L.nsplit = (d + L.kchunk - 1) / L.kchunk;
   L.om = b.take<float>((size_t)k * L.dp);
   L.y = b.take<float>((size_t)k * L.dp);
@@ -177,6 +179,8 @@ InvertLayout invert_layout(int d, int k, int r) {
   L.work = b.take<double>(5 * (size_t)k * k);
   L.jac = b.take<float>((size_t)k * k);
   L.p32 = b.take<float>((size_t)k * r);
+  L.skws_floats = (long long)kSketchMaxSplit * k * d;
+  L.skws = b.take<float>((size_t)L.skws_floats);
   L.total = b.off;
   return L;
 }
@@ -192,22 +196,27 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.D = at<float>(ctx, L.part); g.ldd = k;
   g.alpha = 1.0f;
   g.zsplit = L.nsplit; g.kchunk = L.kchunk; g.zstride = (long long)k * k;
+  g.flags = ctx->dflags;
   StageScope sc(ctx, stage);
   CK(gemm_f32(g, prec, ctx->stream));
   CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, 1, ctx->dflags, ctx->stream));
   return KFAC_OK;
 }
 
-// Yt_out (k x d) = Xt (k x d) F: the sketch / power / projection product. F is
-// symmetric, so B(n, kk) = F[n][kk] reads F row-major.
-kfac_status sketch_product(kfac_ctx* ctx, const float* Xt, long long ldx, const float* F, int ldf, int k, int d,
-                           kfac_precision prec, float* out, long long ldo) {
+// Yt_out (k x d) = Xt (k x d) F: the sketch / power / projection product,
+// computed as (F Xt^T)^T. F is the large operand (A, M = d rows streamed once),
+// Xt the small one (B, N = k); the transposed store of the d x k product lands
+// row-major in Yt. F is symmetric, so A(m, kk) = F[m][kk] reads F row-major.
+kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt, long long ldx, const float* F,
+                           int ldf, int k, int d, kfac_precision prec, float* out, long long ldo) {
   GemmDesc<float> g = {};
-  g.M = k; g.N = d; g.K = d;
-  g.A = Xt; g.sam = ldx; g.sak = 1;
-  g.B = F; g.sbn = ldf; g.sbk = 1;
-  g.D = out; g.ldd = ldo;
+  g.M = d; g.N = k; g.K = d;
+  g.A = F; g.sam = ldf; g.sak = 1;
+  g.B = Xt; g.sbn = ldx; g.sbk = 1;
+  g.D = out; g.ldd = ldo; g.d_trans = 1;
   g.alpha = 1.0f; g.zsplit = 1;
+  g.ws = at<float>(ctx, L.skws); g.ws_floats = L.skws_floats;
+  g.flags = ctx->dflags;
   STAGE(ctx, ST_SKETCH);
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
@@ -293,19 +302,19 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     STAGE(ctx, ST_TRANSPOSE);
     CK(transpose_f32(a.omega, a.ldo, d, k, Om, L.dp, s));
   }
-  st = sketch_product(ctx, Om, L.dp, F, ldf, k, d, a.prec, cur, L.dp);  // Y^T = Omega^T F
+  st = sketch_product(ctx, L, Om, L.dp, F, ldf, k, d, a.prec, cur, L.dp);  // Y^T = Omega^T F
   if (st != KFAC_OK) return st;
   for (int it = 0;; ++it) {
     st = orthonormalise(ctx, L, cur, other, k, d,
                         it == a.power_iters ? ctx->cholqr_passes : ctx->cholqr_inner_passes);  // Q^T in cur
     if (st != KFAC_OK) return st;
     if (it == a.power_iters) break;
-    st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);  // Y^T = Q^T F
+    st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);  // Y^T = Q^T F
     if (st != KFAC_OK) return st;
     std::swap(cur, other);
   }
   // Projection C = Q^T F Q = Q^T (F Q): Z^T = Q^T F into `other`, then C = Q^T Z.
-  st = sketch_product(ctx, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);
+  st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);
   if (st != KFAC_OK) return st;
   double* C = at<double>(ctx, L.c);
   st = gram_f64(ctx, L, cur, other, L.dp, k, d, KFAC_PREC_FP32, C, ST_PROJ);
@@ -327,6 +336,97 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   g.alpha = 1.0f; g.zsplit = 1;
   STAGE(ctx, ST_LIFT);
   CK(gemm_f32(g, KFAC_PREC_FP32, s));
+  return KFAC_OK;
+}
+
+
+// Workspace of one preconditioner apply. All products read K-contiguous
+// operands: T = J U_a diag(c_a) (d_g x r_a), M^T = U_a T^T + J^T/lam (d_a x d_g),
+// T2^T = M^T U_g diag(c_g) (d_a x r_g), S = U_g (T2^T)^T + M/lam, with the small
+// transposes U_a^T, U_g^T; split-K partials for the two long-K products.
+struct PrecLayout {
+  size_t uat, ugt, t, mt, t2, ws, total;
+  long long ld_uat, ld_ugt, ld_t, ld_mt, ld_t2, ws_floats;
+};
+
+constexpr int kApplyMaxSplit = 6;
+
+PrecLayout prec_layout(int dg, int da, int ra, int rg) {
+  PrecLayout P = {};
+  Bump b;
+  P.ld_uat = round_up(da, 4);
+  P.ld_ugt = round_up(dg, 4);
+  P.ld_t = round_up(std::max(ra, 1), 4);
+  P.ld_mt = round_up(dg, 4);
+  P.ld_t2 = round_up(std::max(rg, 1), 4);
+  P.uat = b.take<float>((size_t)std::max(ra, 1) * P.ld_uat);
+  P.ugt = b.take<float>((size_t)std::max(rg, 1) * P.ld_ugt);
+  P.t = b.take<float>((size_t)dg * P.ld_t);
+  P.mt = b.take<float>((size_t)da * P.ld_mt);
+  P.t2 = b.take<float>((size_t)da * P.ld_t2);
+  P.ws_floats = (long long)kApplyMaxSplit * std::max((long long)dg * std::max(ra, 1), (long long)da * std::max(rg, 1));
+  P.ws = b.take<float>((size_t)P.ws_floats);
+  P.total = b.off;
+  return P;
+}
+
+kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, int ldj, const float* U_a, int ld_ua,
+                             const float* coef_a, int r_a, const float* U_g, int ld_ug, const float* coef_g, int r_g,
+                             float lambda, kfac_precision prec, float* S, int lds, PrecLayout P, size_t base) {
+  for (size_t* o : {&P.uat, &P.ugt, &P.t, &P.mt, &P.t2, &P.ws}) *o += base;
+  cudaStream_t s = ctx->stream;
+  const float inv_lam = 1.0f / lambda;
+  float* Uat = at<float>(ctx, P.uat);
+  float* Ugt = at<float>(ctx, P.ugt);
+  float* T = at<float>(ctx, P.t);
+  float* Mt = at<float>(ctx, P.mt);
+  float* T2t = at<float>(ctx, P.t2);
+  if (r_a > 0) {  // T = J U_a diag(c_a), through U_a^T
+    STAGE(ctx, ST_APPLY_T);
+    CK(transpose_f32(U_a, ld_ua, d_a, r_a, Uat, P.ld_uat, s));
+    GemmDesc<float> g = {};
+    g.M = d_g; g.N = r_a; g.K = d_a;
+    g.A = J; g.sam = ldj; g.sak = 1;
+    g.B = Uat; g.sbn = P.ld_uat; g.sbk = 1;
+    g.D = T; g.ldd = P.ld_t;
+    g.alpha = 1.0f; g.colscale = coef_a; g.zsplit = 1;
+    g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats; g.flags = ctx->dflags;
+    CK(gemm_f32(g, prec, s));
+  }
+  {  // M^T = U_a T^T + J^T / lambda
+    STAGE(ctx, ST_APPLY_M);
+    GemmDesc<float> g = {};
+    g.M = d_a; g.N = d_g; g.K = r_a;
+    g.A = U_a; g.sam = r_a > 0 ? ld_ua : 1; g.sak = 1;
+    g.B = T; g.sbn = P.ld_t; g.sbk = 1;
+    g.D = Mt; g.ldd = P.ld_mt;
+    g.alpha = 1.0f; g.beta = inv_lam; g.C0 = J; g.ldc = ldj; g.c0_trans = 1; g.zsplit = 1;
+    g.flags = ctx->dflags;
+    CK(gemm_f32(g, prec, s));
+  }
+  if (r_g > 0) {  // T2^T = M^T U_g diag(c_g), through U_g^T
+    STAGE(ctx, ST_APPLY_T2);
+    CK(transpose_f32(U_g, ld_ug, d_g, r_g, Ugt, P.ld_ugt, s));
+    GemmDesc<float> g = {};
+    g.M = d_a; g.N = r_g; g.K = d_g;
+    g.A = Mt; g.sam = P.ld_mt; g.sak = 1;
+    g.B = Ugt; g.sbn = P.ld_ugt; g.sbk = 1;
+    g.D = T2t; g.ldd = P.ld_t2;
+    g.alpha = 1.0f; g.colscale = coef_g; g.zsplit = 1;
+    g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats; g.flags = ctx->dflags;
+    CK(gemm_f32(g, prec, s));
+  }
+  {  // S = U_g T2 + M / lambda  (M read through M^T)
+    STAGE(ctx, ST_APPLY_S);
+    GemmDesc<float> g = {};
+    g.M = d_g; g.N = d_a; g.K = r_g;
+    g.A = U_g; g.sam = r_g > 0 ? ld_ug : 1; g.sak = 1;
+    g.B = T2t; g.sbn = P.ld_t2; g.sbk = 1;
+    g.D = S; g.ldd = lds;
+    g.alpha = 1.0f; g.beta = inv_lam; g.C0 = Mt; g.ldc = P.ld_mt; g.c0_trans = 1; g.zsplit = 1;
+    g.flags = ctx->dflags;
+    CK(gemm_f32(g, prec, s));
+  }
   return KFAC_OK;
 }
 
@@ -452,11 +552,34 @@ KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t m
     InvertLayout b = invert_layout(std::min(d_max, k_max), k_max, k_max);
     need = std::max(a.total, b.total);
   }
-  if (mn_max > 0) {
-    size_t p = (size_t)mn_max * sizeof(float) + 2 * (size_t)d_max * std::max(k_max, 1) * sizeof(float) + 4096;
+  if (mn_max > 0) {  // preconditioner apply: M^T plus thin intermediates and split-K partials
+    const size_t dk = (size_t)std::max(d_max, 1) * (std::max(k_max, 1) + 4);
+    size_t p = sizeof(float) * ((size_t)mn_max + 4 * (size_t)std::max(d_max, 1) + (4 + kApplyMaxSplit) * dk) +
+               8 * 256;
     need = std::max(need, p);
   }
   return ensure_ws(ctx, need);
+}
+
+KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const float* A, int lda, const float* B,
+                                  int ldb, float alpha, float beta, float* D, int ldd, kfac_precision prec) {
+  if (!ctx || M < 0 || N < 0 || K < 0 || prec < KFAC_PREC_FP32 || prec > KFAC_PREC_BF16) return KFAC_ERR_INVALID_ARG;
+  if ((long long)M * N == 0) return KFAC_OK;
+  if (!D || ldd < N || (K > 0 && (!A || !B || lda < K || ldb < K))) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  const long long ws_floats = std::min<long long>(6LL * M * N, 1LL << 24);
+  kfac_status st = ensure_ws(ctx, (size_t)ws_floats * sizeof(float));
+  if (st != KFAC_OK) return st;
+  GemmDesc<float> g = {};
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.sam = lda; g.sak = 1;
+  g.B = B; g.sbn = ldb; g.sbk = 1;
+  g.D = D; g.ldd = ldd;
+  g.alpha = alpha; g.beta = beta; g.C0 = D; g.ldc = ldd;
+  g.zsplit = 1; g.ws = at<float>(ctx, 0); g.ws_floats = ws_floats; g.flags = ctx->dflags;
+  CK(gemm_f32(g, prec, ctx->stream));
+  return KFAC_OK;
 }
 
 KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags) {
@@ -483,7 +606,7 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   STAGE(ctx, ST_EA);
-  return ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf) == cudaSuccess ? KFAC_OK : KFAC_ERR_CUDA;
+  return ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags) == cudaSuccess ? KFAC_OK : KFAC_ERR_CUDA;
 }
 
 KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
@@ -552,58 +675,11 @@ KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const fl
   if (r_g > 0 && (!U_g || ld_ug < r_g || !coef_g)) return KFAC_ERR_INVALID_ARG;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  Bump b;
-  size_t oT = b.take<float>((size_t)d_g * std::max(r_a, 1));
-  size_t oM = b.take<float>((size_t)d_g * d_a);
-  size_t oT2 = b.take<float>((size_t)std::max(r_g, 1) * d_a);
-  kfac_status st = ensure_ws(ctx, b.off);
+  PrecLayout P = prec_layout(d_g, d_a, r_a, r_g);
+  kfac_status st = ensure_ws(ctx, P.total);
   if (st != KFAC_OK) return st;
-  float* T = at<float>(ctx, oT);
-  float* M = at<float>(ctx, oM);
-  float* T2 = at<float>(ctx, oT2);
-  cudaStream_t s = ctx->stream;
-  const float inv_lam = 1.0f / lambda;
-  if (r_a > 0) {  // T = J U_a diag(c_a)
-    STAGE(ctx, ST_APPLY_T);
-    GemmDesc<float> g = {};
-    g.M = d_g; g.N = r_a; g.K = d_a;
-    g.A = J; g.sam = ldj; g.sak = 1;
-    g.B = U_a; g.sbn = 1; g.sbk = ld_ua;
-    g.D = T; g.ldd = r_a;
-    g.alpha = 1.0f; g.colscale = coef_a; g.zsplit = 1;
-    CK(gemm_f32(g, prec, s));
-  }
-  {  // M = T U_a^T + J / lambda
-    STAGE(ctx, ST_APPLY_M);
-    GemmDesc<float> g = {};
-    g.M = d_g; g.N = d_a; g.K = r_a;
-    g.A = T; g.sam = r_a > 0 ? r_a : 1; g.sak = 1;
-    g.B = U_a; g.sbn = ld_ua; g.sbk = 1;
-    g.D = M; g.ldd = d_a;
-    g.alpha = 1.0f; g.beta = inv_lam; g.C0 = J; g.ldc = ldj; g.zsplit = 1;
-    CK(gemm_f32(g, prec, s));
-  }
-  if (r_g > 0) {  // T2 = diag(c_g) U_g^T M
-    STAGE(ctx, ST_APPLY_T2);
-    GemmDesc<float> g = {};
-    g.M = r_g; g.N = d_a; g.K = d_g;
-    g.A = U_g; g.sam = 1; g.sak = ld_ug;
-    g.B = M; g.sbn = 1; g.sbk = d_a;
-    g.D = T2; g.ldd = d_a;
-    g.alpha = 1.0f; g.rowscale = coef_g; g.zsplit = 1;
-    CK(gemm_f32(g, prec, s));
-  }
-  {  // S = U_g T2 + M / lambda
-    STAGE(ctx, ST_APPLY_S);
-    GemmDesc<float> g = {};
-    g.M = d_g; g.N = d_a; g.K = r_g;
-    g.A = U_g; g.sam = ld_ug > 0 ? ld_ug : 1; g.sak = 1;
-    g.B = T2; g.sbn = 1; g.sbk = d_a;
-    g.D = S; g.ldd = lds;
-    g.alpha = 1.0f; g.beta = inv_lam; g.C0 = M; g.ldc = d_a; g.zsplit = 1;
-    CK(gemm_f32(g, prec, s));
-  }
-  return KFAC_OK;
+  return precondition_run(ctx, d_g, d_a, J, ldj, U_a, ld_ua, coef_a, r_a, U_g, ld_ug, coef_g, r_g, lambda, prec, S,
+                          lds, P, 0);
 }
 
 KFAC_API uint64_t kfac_kernel_launch_count(void) { return (uint64_t)launch_count(); }

@@ -77,6 +77,7 @@ struct GemmDesc {
   int sym;
   T* ws;
   long long ws_floats;
+  int* flags;  // device status word for bounded-wait timeouts (may be null)
 };
 
 // ---- launchers (host) --------------------------------------------------------

@@ -1,18 +1,84 @@
-// GEMM-shaped steps: dispatch and the EA SYRK.
+// GEMM-shaped steps: dispatch between the tcgen05 tensor-core kernel and the
+// SIMT kernel, split-K with a reducing epilogue, and the EA SYRK.
 #include "gemm.cuh"
+#include "tc_gemm.cuh"
 
 namespace kfac {
+namespace {
 
-static Round round_of(kfac_precision p) {
+Round round_of(kfac_precision p) {
   return p == KFAC_PREC_BF16 ? Round::BF16 : (p == KFAC_PREC_TF32 ? Round::TF32 : Round::None);
 }
 
+long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+// Sum z split-K partials (dense, in D's layout: rows x cols) and apply the
+// epilogue of g, writing D.
+__global__ void k_reduce_epilogue(const float* __restrict__ part, int z, long long zstride, int rows, int cols,
+                                  GemmDesc<float> g) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)rows * cols) return;
+  const int r = (int)(idx / cols), c = (int)(idx % cols);
+  const int m = g.d_trans ? c : r, n = g.d_trans ? r : c;
+  float v = 0.0f;
+  for (int q = 0; q < z; ++q) v += part[q * zstride + idx];
+  v *= g.alpha;
+  if (g.rowscale) v *= g.rowscale[m];
+  if (g.colscale) v *= g.colscale[n];
+  if (g.beta != 0.0f && g.C0)
+    v = fmaf(g.beta, g.C0[g.c0_trans ? (long long)n * g.ldc + m : (long long)m * g.ldc + n], v);
+  g.D[(long long)r * g.ldd + c] = v;
+}
+
+}  // namespace
+
 cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t s) {
-  return gemm_simt_f32(g, round_of(prec), s);
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  const bool kmajor = g.sak == 1 && g.sbk == 1;
+  const bool tc_ok = prec != KFAC_PREC_BF16 && kmajor && g.K > 0 &&
+                     tc::eligible(g.A, g.sam, g.B, g.sbn, g.M, g.N, g.K) &&
+                     (g.zsplit <= 1 || g.kchunk % 32 == 0) && !(g.sym && g.zsplit > 1);
+  if (!tc_ok) return gemm_simt_f32(g, round_of(prec), s);
+
+  tc::TcArgs a = {};
+  a.M = g.M; a.N = g.N; a.K = g.K;
+  a.alpha = g.alpha; a.beta = g.beta;
+  a.rowscale = g.rowscale; a.colscale = g.colscale;
+  a.C0 = g.C0; a.ldc = g.ldc; a.c0_trans = g.c0_trans;
+  a.D = g.D; a.ldd = g.ldd; a.d_trans = g.d_trans;
+  a.sym = g.sym; a.flags = g.flags;
+  const bool split3 = prec == KFAC_PREC_FP32;
+  if (g.zsplit > 1) {  // caller-managed raw partials
+    a.partial = 1; a.kchunk = g.kchunk; a.zstride = g.zstride;
+    return tc::gemm(a, g.A, g.sam, g.B, g.sbn, g.zsplit, split3, s);
+  }
+  const int bn = g.N > 128 ? 256 : 128;
+  long long tiles = cdiv(g.M, 128) * cdiv(g.N, bn);
+  if (g.sym) tiles = (tiles + 1) / 2;
+  const long long rows = g.d_trans ? g.N : g.M, cols = g.d_trans ? g.M : g.N;
+  int z = 1;
+  if (g.ws && !g.sym && tiles < 120 && g.K >= 1024) {
+    z = (int)std::min<long long>(cdiv(148, tiles), g.K / 512);
+    while (z > 1 && (long long)z * rows * cols > g.ws_floats) --z;
+  }
+  if (z > 1) {
+    const int kchunk = (int)(cdiv(cdiv(g.K, z), 32) * 32);
+    z = (int)cdiv(g.K, kchunk);
+    a.partial = 1; a.kchunk = kchunk; a.D = g.ws; a.ldd = cols; a.zstride = rows * cols;
+    cudaError_t e = tc::gemm(a, g.A, g.sam, g.B, g.sbn, z, split3, s);
+    if (e != cudaSuccess) return e;
+    const long long tot = rows * cols;
+    k_reduce_epilogue<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(g.ws, z, rows * cols, (int)rows, (int)cols, g);
+    note_launch();
+    return cudaGetLastError();
+  }
+  a.partial = 0;
+  a.kchunk = (int)(cdiv(g.K, 32) * 32);
+  return tc::gemm(a, g.A, g.sam, g.B, g.sbn, 1, split3, s);
 }
 
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,
-                    int ldf) {
+                    int ldf, int* flags) {
   GemmDesc<float> g = {};
   g.M = d; g.N = d; g.K = n;
   g.A = X; g.sam = ldx; g.sak = 1;
@@ -22,6 +88,8 @@ cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float
   g.alpha = n > 0 ? (1.0f - rho) / (float)n : 0.0f;
   g.beta = rho;
   g.zsplit = 1;
+  g.sym = 1;  // upper tiles computed once, mirrored: the factor stays exactly symmetric
+  g.flags = flags;
   if (rho == 0.0f) g.beta = 0.0f;
   return gemm_f32(g, prec, s);
 }

@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const bool acc_ok = mbar_wait(accb, 0, p.flags);
   tc_fence_after();
   float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // per-warp 32 x 33 staging
+  float* const Dz = p.D + (p.partial ? (long long)blockIdx.z * p.zstride : 0LL);  // split-K slice
   const int q = warp & 3;
   const int m = m0 + 32 * q + lane;
   const int cbeg = (warp < 4) ? 0 : BN / 2;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int n = nb + j;
-        if (m < p.M && n < p.N) p.D[(long long)n * p.ldd + m] = v[j];
+        if (m < p.M && n < p.N) Dz[(long long)n * p.ldd + m] = v[j];
       }
     } else {
       __syncwarp();
@@ -304,13 +305,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncwarp();
       for (int r = 0; r < 32; ++r) {
         const int mr = m0 + 32 * q + r, n = nb + lane;
-        if (mr < p.M && n < p.N && (!p.sym || mr <= n)) p.D[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
+        if (mr < p.M && n < p.N && (!p.sym || mr <= n)) Dz[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
       }
       if (p.sym) {  // mirror: D[n][m] for m < n, consecutive lanes -> consecutive m
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = nb + j;
-          if (m < p.M && n < p.N && m < n) p.D[(long long)n * p.ldd + m] = v[j];
+          if (m < p.M && n < p.N && m < n) Dz[(long long)n * p.ldd + m] = v[j];
         }
       }
     }

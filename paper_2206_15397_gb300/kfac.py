@@ -63,6 +63,8 @@ def lib():
                                         ctypes.POINTER(i)]
         L.kfac_kernel_launch_count.restype = ctypes.c_uint64
         L.kfac_rsvd_invert_grouped.argtypes = [vp, i, ctypes.POINTER(InvertDesc)]
+        L.kfac_gemm_nt.argtypes = [vp, i, i, i, vp, i, vp, i, f, f, vp, i, i]
+        L.kfac_gemm_nt.restype = i
         L.kfac_rsvd_invert_grouped.restype = i
         L.kfac_precondition_noalloc.argtypes = [vp, i, i, vp, i, vp, i, vp, i, vp, i, vp, i, f, i, vp, i]
         L.kfac_precondition_noalloc.restype = i
@@ -279,3 +281,16 @@ def kfac_rsvd_invert_grouped(ctx: Context, items):
         outs.append((U, D, coef))
     _check(lib().kfac_rsvd_invert_grouped(ctx.handle, len(items), descs), "kfac_rsvd_invert_grouped")
     return outs
+
+
+def kfac_gemm_nt(ctx: Context, A: torch.Tensor, B: torch.Tensor, D: torch.Tensor, alpha: float = 1.0,
+                 beta: float = 0.0, prec: str = "fp32"):
+    """D = alpha A B^T + beta D (GEMM engine utility)."""
+    M, K = A.shape
+    N = B.shape[0]
+    pa, lda = _mat(A, "A", M, K)
+    pb, ldb = _mat(B, "B", N, K)
+    pd, ldd = _mat(D, "D", M, N)
+    _check(lib().kfac_gemm_nt(ctx.handle, M, N, K, pa, lda, pb, ldb, float(alpha), float(beta), pd, ldd,
+                              PRECISION[prec]), "kfac_gemm_nt")
+    return D

@@ -50,7 +50,7 @@ def assert_status_ok(kf, ctx, allowed=("CHOL_SHIFTED", "EIG_SHIFTED")):
 
 # ----------------------------------------------------------------------------- EA update
 
-@pytest.mark.parametrize("d,n", [(1, 1), (7, 3), (65, 17), (130, 64), (257, 128), (300, 1)])
+@pytest.mark.parametrize("d,n", [(1, 1), (7, 3), (65, 17), (130, 64), (257, 128), (300, 1), (512, 256), (384, 32)])
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 def test_ea_update(kf, ctx, d, n, prec):
     rng = np.random.default_rng(d * 1000 + n)
