@@ -212,9 +212,15 @@ typedef enum {
   KFAC_OPT_EIG_REFINE = 2,      /* FP64 eigen-refinement steps after FP32 Jacobi [1], 0..3 */
   KFAC_OPT_EIG_MAX_SWEEPS = 3,  /* Jacobi sweep cap [40]                                  */
   KFAC_OPT_EIG_TOL = 4,         /* Jacobi pair-orthogonality threshold [2e-6]            */
-  KFAC_OPT_CHOLQR_INNER_PASSES = 5 /* passes for a basis that only feeds the next power
-                                      iteration [3], 1..6; fewer passes save time but      
-                                      lose accuracy on ill-conditioned sketches */
+  KFAC_OPT_CHOLQR_INNER_PASSES = 5, /* passes for a basis that only feeds the next power
+                                       iteration [3], 1..6; fewer passes save time but
+                                       lose accuracy on ill-conditioned sketches */
+  KFAC_OPT_CHOLQR_FP32_PASSES = 6   /* leading passes of every orthonormalisation whose
+                                       Cholesky runs in FP32 instead of FP64 [1], 0..5; the
+                                       last pass of a basis always runs in FP64. The first,
+                                       shifted pass only preconditions Y (any invertible R
+                                       leaves span(Y R^-1) = span(Y)), so its rounding is
+                                       corrected by the passes after it */
 } kfac_option;
 
 KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double value);

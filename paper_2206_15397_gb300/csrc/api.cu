@@ -49,6 +49,7 @@ struct kfac_ctx {
   // options
   int cholqr_passes = 3;
   int cholqr_inner_passes = 3;
+  int cholqr_fp32_passes = 1;
   double cholqr_shift = 1e-5;
   int eig_refine = 1;
   int eig_max_sweeps = 40;
@@ -143,7 +144,7 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, l32, c, x, lam, work, jac, p32, skws, total;
+  size_t om, y, q, part, g, l32, dinv, c, x, lam, work, jac, p32, skws, total;
   long long dp, skws_floats;
   int nsplit, kchunk;
 };
@@ -173,6 +174,7 @@ InvertLayout invert_layout(int d, int k, int r) {
   L.part = b.take<float>((size_t)L.nsplit * k * k);
   L.g = b.take<double>((size_t)k * k);
   L.l32 = b.take<float>((size_t)k * k);
+  L.dinv = b.take<float>((size_t)((k + 31) / 32) * 1024);
   L.c = b.take<double>((size_t)k * k);
   L.x = b.take<double>((size_t)k * k);
   L.lam = b.take<double>(k);
@@ -234,12 +236,13 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       // diagonal keeps the noise-level directions from breaking the factorization;
       // the last pass (a near-orthonormal basis) is unshifted.
       const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-6 : 0.0);
-      CK(chol_f64_cluster(at<double>(ctx, L.g), k, shift, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
-                          ctx->stream));
+      const bool fp64 = pass >= ctx->cholqr_fp32_passes || pass + 1 == passes;
+      CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
+                      ctx->stream));
     }
     {
       STAGE(ctx, ST_TRSM);
-      CK(trsm_lower_f32(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, ctx->stream));
+      CK(trsm_lower_f32(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<float>(ctx, L.dinv), ctx->stream));
     }
     std::swap(cur, other);
   }
@@ -280,7 +283,9 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const int d = a.d, r = std::min(a.rank, a.d), k = a.rank + a.oversample;
   const float* F = a.F;
   const int ldf = a.ldf;
-  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.l32, &L.c, &L.x, &L.lam, &L.work, &L.jac, &L.p32}) *o += base;
+  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.l32, &L.dinv, &L.c, &L.x, &L.lam, &L.work, &L.jac, &L.p32,
+                    &L.skws})
+    *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;
   if (k >= d) {  // nothing to sketch: diagonalise F itself (Q = I)
@@ -538,6 +543,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
     case KFAC_OPT_CHOLQR_INNER_PASSES:
       if (v < 1 || v > 6) return KFAC_ERR_INVALID_ARG;
       ctx->cholqr_inner_passes = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_CHOLQR_FP32_PASSES:
+      if (v < 0 || v > 5) return KFAC_ERR_INVALID_ARG;
+      ctx->cholqr_fp32_passes = (int)v;
       return KFAC_OK;
   }
   return KFAC_ERR_INVALID_ARG;

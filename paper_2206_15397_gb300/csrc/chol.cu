@@ -25,24 +25,32 @@ namespace {
 constexpr int CHOL_THREADS = 256;
 constexpr int CHOL_ATTEMPTS = 4;
 
-// 1/sqrt(x) for x > 0 in FP64: an FP32 estimate refined by two Newton steps
-// y <- y (3 - x y^2) / 2 (each roughly doubles the number of correct bits:
-// ~2^-23 -> 2^-46 -> rounding). Far cheaper here than FP64 sqrt + divide.
+// 1/sqrt(x) for x > 0 in FP64: an FP32 estimate refined by one Newton step
+// y <- y (3 - x y^2) / 2, which squares the relative error (~2^-23 -> ~2^-46):
+// far below the accuracy of the FP32-accumulated Gram it factors, and three
+// FP64 instructions instead of an FP64 sqrt and divide (an FP64 warp
+// instruction costs ~68 cycles on this part whatever its active lanes).
 __device__ __forceinline__ double rsqrt_newton(double x) {
   double y = (double)rsqrtf((float)x);
-  y = y * fma(-0.5 * x * y, y, 1.5);
-  y = y * fma(-0.5 * x * y, y, 1.5);
-  return y;
+  return y * fma(-0.5 * x * y, y, 1.5);
+}
+__device__ __forceinline__ float rsqrt_newton(float x) {
+  const float y = rsqrtf(x);
+  return y * fmaf(-0.5f * x * y, y, 1.5f);
 }
 
+template <typename T>
 struct CholSmem {
-  double* W;      // nloc x k, own rows (row-major, lower part used)
-  double* D;      // B x B diagonal block (replicated in every CTA)
-  double* dinv;   // B reciprocals of diag(L11)
-  double* P[2];   // panel L21, column-major B x k: P[t * k + i] (replicated, double-buffered)
-  int* flag;      // breakdown flag
+  T* W;      // nloc x k, own rows (row-major, lower part used)
+  T* D;      // B x B diagonal block (replicated in every CTA)
+  T* dinv;   // B reciprocals of diag(L11)
+  T* Xi;     // B x B inverse of L11 (replicated)
+  T* P[2];   // panel L21, column-major B x k: P[t * k + i] (replicated, double-buffered)
+  int* flag;     // breakdown flag (non-finite pivot)
+  int* clamped;  // a pivot was raised to the floor
 };
 
+template <typename T>
 __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* __restrict__ G, int k, int B,
                                                                    int nloc, double shift_rel,
                                                                    float* __restrict__ L32, int* flags,
@@ -53,14 +61,16 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
 
-  CholSmem sm;
-  double* base = reinterpret_cast<double*>(smem_raw);
+  CholSmem<T> sm;
+  T* base = reinterpret_cast<T*>(smem_raw);
   sm.W = base;
   sm.D = sm.W + (size_t)nloc * k;
   sm.dinv = sm.D + B * B;
-  sm.P[0] = sm.dinv + B;
+  sm.Xi = sm.dinv + B;
+  sm.P[0] = sm.Xi + B * B;
   sm.P[1] = sm.P[0] + (size_t)k * B;
   sm.flag = reinterpret_cast<int*>(sm.P[1] + (size_t)k * B);
+  sm.clamped = sm.flag + 1;
 
   // Trace (identical in every CTA: same reads, same order).
   __shared__ double s_trace;
@@ -73,7 +83,13 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
   __syncthreads();
   const double trace = s_trace;
   const bool finite_in = isfinite(trace) && trace > 0.0;
-  const double piv_min = 1e-13 * trace;
+  // Pivot floor. A pivot below it (the column is, to the Gram's FP32
+  // accuracy, in the span of the previous ones) is raised to it: the factor is
+  // then the exact Cholesky factor of G + shift I + diag(delta), delta >= 0,
+  // which keeps R invertible and span(Y R^-1) = span(Y). Relative to the mean
+  // diagonal, above the rounding noise of the FP32-accurate Gram (and of an
+  // FP32 factorisation).
+  const T pfloor = (T)(sizeof(T) == 4 ? fmax(1e-9 * trace, 1e-6 * trace / k) : fmax(1e-13 * trace, 1e-7 * trace / k));
 
   // shift_rel > 0: relative to trace(G); shift_rel < 0: |shift_rel| times the
   // mean diagonal trace(G) / k.
@@ -93,10 +109,10 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
       for (int j = tid; j < k; j += CHOL_THREADS) {
         double v = 0.0;
         if (i < k && j <= i) v = G[(size_t)i * k + j] + (i == j ? shift : 0.0);
-        sm.W[(size_t)li * k + j] = v;
+        sm.W[(size_t)li * k + j] = (T)v;
       }
     }
-    if (tid == 0) *sm.flag = 0;
+    if (tid == 0) { *sm.flag = 0; *sm.clamped = 0; }
     __syncthreads();
     cluster.sync();  // also: every CTA has started before the first remote store
 
@@ -108,37 +124,85 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
       for (int e = tid; e < jb * jb; e += CHOL_THREADS) {
         const int u = e / jb, t = e % jb, i = j0 + u;
         if (i % NC != rank) continue;
-        const double v = (t <= u) ? sm.W[(size_t)(i / NC) * k + j0 + t] : 0.0;
+        const T v = (t <= u) ? sm.W[(size_t)(i / NC) * k + j0 + t] : T(0);
         for (int q = 0; q < NC; ++q) cluster.map_shared_rank(sm.D, q)[u * B + t] = v;
       }
       cluster.sync();
-      // (b) factor the diagonal block in place, all threads (same data and code
-      //     in every CTA -> identical pivots and breakdown decisions).
-      for (int t = 0; t < jb; ++t) {
-        const double piv = sm.D[t * B + t];
-        if (!(isfinite(piv) && piv > piv_min)) { bad = 1; break; }
-        // FP64 issues per warp instruction whatever the active lanes, so the
-        // reciprocal square root is evaluated by one thread only.
-        __syncthreads();  // everyone has read D[t][t]
-        if (tid == 0) {
-          const double y = rsqrt_newton(piv);
-          sm.D[t * B + t] = piv * y;
-          sm.dinv[t] = y;
+      // (b) factor the diagonal block in place and form Xi = L11^-1 beside it
+      //     (same data and code in every CTA -> identical pivots and breakdown
+      //     decisions). An FP64 warp instruction costs ~68 cycles on its
+      //     sub-partition whatever its active lanes, so the element work runs
+      //     on warps 0-3 (one per sub-partition) and the chain through the
+      //     pivots on one thread of warp 4, one step ahead: while warps 0-3
+      //     apply step t's rank-1 update, that thread already holds the next
+      //     pivot (updated first) and computes its reciprocal root. Per step t:
+      //       A: column t of L and row t of Xi are scaled by y_t = L_tt^-1;
+      //          the pivot thread scales L_{t+1,t} and updates A_{t+1,t+1};
+      //       B: the trailing triangle {t < v <= u < jb} except (t+1, t+1) and
+      //          the Xi rows u > t take the update; the pivot thread checks
+      //          A_{t+1,t+1} and writes y_{t+1}.
+      //     Triangle entries are enumerated as (u', v') = (jb-1-u, jb-1-v),
+      //     u' <= v', ordered by v', so the active set is a prefix on full lanes.
+      if (tid < 160) {
+        if (tid < 128) {
+          for (int e = tid; e < jb * B; e += 128) sm.Xi[e] = T(0);
+        } else if (tid == 128) {
+          T piv = sm.D[0];
+          if (!isfinite(piv)) {
+            *sm.flag = 1;
+          } else {
+            if (!(piv > pfloor)) { piv = pfloor; sm.D[0] = piv; *sm.clamped = 1; }
+            sm.dinv[0] = rsqrt_newton(piv);
+          }
         }
-        __syncthreads();
-        const double y = sm.dinv[t];
-        for (int u = t + 1 + tid; u < jb; u += CHOL_THREADS) sm.D[u * B + t] *= y;
-        __syncthreads();
-        const int n = jb - t - 1;  // trailing (u, v), t < v <= u < jb
-        for (int e = tid; e < n * n; e += CHOL_THREADS) {
-          const int u = t + 1 + e / n, v = t + 1 + e % n;
-          if (v <= u) sm.D[u * B + v] = fma(-sm.D[u * B + t], sm.D[v * B + t], sm.D[u * B + v]);
+        asm volatile("bar.sync 1, 160;" ::: "memory");
+        for (int t = 0; t < jb; ++t) {
+          if (*sm.flag) break;  // written before the last barrier: uniform
+          const T y = sm.dinv[t];
+          if (tid < 128) {
+            if (tid == t) sm.D[t * B + t] *= y;  // L_tt = A_tt y_t = sqrt(A_tt)
+            else if (tid > t + 1 && tid < jb) sm.D[tid * B + t] *= y;
+            if (tid <= t) sm.Xi[t * B + tid] = (tid == t) ? y : sm.Xi[t * B + tid] * y;
+          } else if (tid == 128 && t + 1 < jb) {
+            const T l = sm.D[(t + 1) * B + t] * y;
+            sm.D[(t + 1) * B + t] = l;
+            sm.D[(t + 1) * B + t + 1] = fma(-l, l, sm.D[(t + 1) * B + t + 1]);
+          }
+          asm volatile("bar.sync 1, 160;" ::: "memory");
+          const int n = jb - t - 1;
+          if (tid < 128) {
+            const int ctri = n * (n + 1) / 2, total = ctri + n * (t + 1);
+            for (int e = tid; e < total; e += 128) {
+              if (e < ctri) {
+                const int vp = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f + 1e-4f);
+                const int up = e - vp * (vp + 1) / 2;
+                const int u = jb - 1 - up, v = jb - 1 - vp;
+                if (v == t + 1 && u == t + 1) continue;  // the next pivot: done in A
+                sm.D[u * B + v] = fma(-sm.D[u * B + t], sm.D[v * B + t], sm.D[u * B + v]);
+              } else {
+                const int e2 = e - ctri, u = t + 1 + e2 / (t + 1), c = e2 % (t + 1);
+                sm.Xi[u * B + c] = fma(-sm.D[u * B + t], sm.Xi[t * B + c], sm.Xi[u * B + c]);
+              }
+            }
+          } else if (tid == 128 && n > 0) {
+            T piv = sm.D[(t + 1) * B + t + 1];
+            if (!isfinite(piv)) {
+              *sm.flag = 1;
+            } else {
+              if (!(piv > pfloor)) { piv = pfloor; sm.D[(t + 1) * B + t + 1] = piv; *sm.clamped = 1; }
+              sm.dinv[t + 1] = rsqrt_newton(piv);
+            }
+          }
+          asm volatile("bar.sync 1, 160;" ::: "memory");
         }
-        __syncthreads();
       }
+      __syncthreads();
+      bad = *sm.flag;
       if (bad) break;  // identical decision in every CTA; no remote stores pending
-      // (b') own diagonal rows take L11; own rows below solve L21 = A21 L11^-T
-      //      by forward substitution (thread per row) and broadcast the panel.
+      // (b') own diagonal rows take L11; own rows below form L21 = A21 L11^-T
+      //      as one product, P[t][i] = sum_{s <= t} A21[i][s] Xi[t][s] (one
+      //      output per thread, a chain of t + 1 FMAs), into the panel buffer;
+      //      then the solved rows go back to W and to every other CTA.
       for (int e = tid; e < jb * jb; e += CHOL_THREADS) {
         const int u = e / jb, t = e % jb, i = j0 + u;
         if (i % NC == rank && t <= u) sm.W[(size_t)(i / NC) * k + j0 + t] = sm.D[u * B + t];
@@ -147,28 +211,24 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
       int li0 = (first - rank + NC - 1) / NC;
       if (li0 < 0) li0 = 0;
       const int nrows = nloc - li0;
-      double* P = sm.P[buf];
-      for (int lr = li0 + tid; lr < nloc; lr += CHOL_THREADS) {
-        const int i = lr * NC + rank;
+      T* P = sm.P[buf];
+      for (int e = tid; e < nrows * jb; e += CHOL_THREADS) {
+        const int lr = li0 + e / jb, t = e % jb, i = lr * NC + rank;
         if (i >= k) continue;
-        double* wrow = sm.W + (size_t)lr * k + j0;
-        for (int t = 0; t < jb; ++t) {
-          double x = wrow[t];
-          for (int u = 0; u < t; ++u) x = fma(-wrow[u], sm.D[t * B + u], x);
-          x *= sm.dinv[t];
-          wrow[t] = x;
-          P[(size_t)t * k + i] = x;
-        }
+        const T* a = sm.W + (size_t)lr * k + j0;
+        const T* xr = sm.Xi + t * B;
+        T acc = T(0);
+        for (int q = 0; q <= t; ++q) acc = fma(a[q], xr[q], acc);
+        P[(size_t)t * k + i] = acc;
       }
       __syncthreads();
-      if (NC > 1 && nrows > 0) {
-        for (int e = tid; e < nrows * jb; e += CHOL_THREADS) {
-          const int lr = li0 + e / jb, t = e % jb, i = lr * NC + rank;
-          if (i >= k) continue;
-          const double x = P[(size_t)t * k + i];
-          for (int q = 0; q < NC; ++q)
-            if (q != rank) cluster.map_shared_rank(P, q)[(size_t)t * k + i] = x;
-        }
+      for (int e = tid; e < nrows * jb; e += CHOL_THREADS) {
+        const int lr = li0 + e / jb, t = e % jb, i = lr * NC + rank;
+        if (i >= k) continue;
+        const T x = P[(size_t)t * k + i];
+        sm.W[(size_t)lr * k + j0 + t] = x;
+        for (int q = 0; q < NC; ++q)
+          if (q != rank) cluster.map_shared_rank(P, q)[(size_t)t * k + i] = x;
       }
       cluster.sync();
       // (c) trailing update of own rows: W[i][j] -= sum_t L21[i][t] L21[j][t],
@@ -176,9 +236,9 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
       for (int lr = li0 + (tid >> 5); lr < nloc; lr += CHOL_THREADS / 32) {
         const int i = lr * NC + rank;
         if (i >= k) continue;
-        double* wrow = sm.W + (size_t)lr * k;
+        T* wrow = sm.W + (size_t)lr * k;
         for (int j = first + (tid & 31); j <= i; j += 32) {
-          double acc = 0.0;
+          T acc = T(0);
           for (int t = 0; t < jb; ++t) acc = fma(P[(size_t)t * k + i], P[(size_t)t * k + j], acc);
           wrow[j] -= acc;
         }
@@ -187,7 +247,11 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
       buf ^= 1;
     }
     cluster.sync();
-    if (!bad) { ok = 1; break; }
+    if (!bad) {
+      if (*sm.clamped && rank == 0 && tid == 0) raise_flag(flags, KFAC_FLAG_CHOL_SHIFTED);
+      ok = 1;
+      break;
+    }
   }
 
   if (!ok) {
@@ -213,20 +277,18 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
   cluster.sync();  // no CTA leaves while others may still address its shared memory
 }
 
-size_t chol_smem_bytes(int k, int nloc, int B) {
-  return sizeof(double) * ((size_t)nloc * k + (size_t)B * B + B + 2 * (size_t)k * B) + 16;
+size_t chol_smem_bytes(int k, int nloc, int B, size_t elt) {
+  return elt * ((size_t)nloc * k + 2 * (size_t)B * B + B + 2 * (size_t)k * B) + 16;
 }
 
-}  // namespace
-
-cudaError_t chol_f64_cluster(const double* G, int k, double shift_rel, float* L32, int* flags,
-                             unsigned long long* stats, cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
+template <typename T>
+cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, int* flags,
+                        unsigned long long* stats, cudaStream_t s) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaFuncSetAttribute(k_chol_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
+    e = cudaFuncSetAttribute(k_chol_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -235,10 +297,10 @@ cudaError_t chol_f64_cluster(const double* G, int k, double shift_rel, float* L3
   if (nc < 1) nc = 1;
   int B = 16;
   int nloc = (k + nc - 1) / nc;
-  size_t smem = chol_smem_bytes(k, nloc, B);
+  size_t smem = chol_smem_bytes(k, nloc, B, sizeof(T));
   while (smem > (size_t)kSmemOptin && B > 4) {
     B /= 2;
-    smem = chol_smem_bytes(k, nloc, B);
+    smem = chol_smem_bytes(k, nloc, B, sizeof(T));
   }
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
@@ -254,26 +316,52 @@ cudaError_t chol_f64_cluster(const double* G, int k, double shift_rel, float* L3
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchKernelEx(&cfg, k_chol_cluster, G, k, B, nloc, shift_rel, L32, flags, stats);
+  return cudaLaunchKernelEx(&cfg, k_chol_cluster<T>, G, k, B, nloc, shift_rel, L32, flags, stats);
 }
 
+}  // namespace
+
+cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
+                         unsigned long long* stats, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s)
+              : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s);
+}
 
 // ---------------------------------------------------------------------------
-// Qt = L^-1 Yt: forward substitution with the FP32 lower factor, applied to all
-// d columns of Yt at once. Each CTA owns 32 columns and keeps its k x 32 slab of
-// the solution in shared memory; rows are processed in blocks of 32: the block
-// first receives the contributions of all solved rows (a small GEMM through
-// 32 x 32 tiles of L), then its 32 x 32 diagonal block is solved by one warp
-// (one lane per column).
+// Qt = L^-1 Yt with the FP32 lower factor, for all d columns of Yt at once.
+// The inverses of L's 32 x 32 diagonal blocks are formed first (one warp per
+// block, one lane per column); each CTA then owns 32 columns of Yt, keeps its
+// k x 32 slab of the solution in shared memory and, row block by row block,
+// subtracts the solved blocks (L_IJ X_J through 32 x 32 tiles of L) and applies
+// the block inverse: all multiply-adds, no sequential per-row solve.
 namespace {
 constexpr int TR_COLS = 32, TR_RB = 32, TR_THREADS = 256;
 
-__global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restrict__ L, int k,
-                                                            const float* __restrict__ Yt, long long ldy,
+__global__ void __launch_bounds__(32) k_diag_block_inv(const float* __restrict__ L, int k, float* __restrict__ Dinv) {
+  __shared__ float Lb[TR_RB][TR_RB + 1];
+  const int blk = blockIdx.x, i0 = blk * TR_RB, ib = min(TR_RB, k - i0), c = threadIdx.x;
+  for (int a = 0; a < TR_RB; ++a) Lb[a][c] = (a < ib && c < ib) ? L[(size_t)(i0 + a) * k + i0 + c] : (a == c ? 1.f : 0.f);
+  __syncwarp();
+  float x[TR_RB];  // column c of the block inverse
+#pragma unroll
+  for (int i = 0; i < TR_RB; ++i) {
+    float v = (i == c) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int u = 0; u < i; ++u) v = fmaf(-Lb[i][u], x[u], v);
+    x[i] = (i >= c) ? v / Lb[i][i] : 0.0f;
+  }
+  float* out = Dinv + (size_t)blk * TR_RB * TR_RB;
+#pragma unroll
+  for (int i = 0; i < TR_RB; ++i) out[i * TR_RB + c] = x[i];
+}
+
+__global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restrict__ L, const float* __restrict__ Dinv,
+                                                            int k, const float* __restrict__ Yt, long long ldy,
                                                             float* __restrict__ Qt, long long ldq, int d) {
   extern __shared__ __align__(16) float tsm[];
-  float* X = tsm;                                   // k x TR_COLS
-  float* Lt = X + (size_t)k * TR_COLS;              // TR_RB x (TR_RB + 1)
+  float* X = tsm;                          // k x TR_COLS
+  float* Lt = X + (size_t)k * TR_COLS;     // TR_RB x (TR_RB + 1)
   const int tid = threadIdx.x, c = tid & 31, r0 = tid >> 5;  // 8 row groups
   const int col0 = blockIdx.x * TR_COLS;
   const int col = col0 + c;
@@ -299,37 +387,38 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restri
       }
       __syncthreads();
     }
+    // X_I = Dinv_I * acc: stage acc, load the block inverse, multiply.
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int ri = r0 + 8 * u;
-      if (ri < ib) X[(size_t)(i0 + ri) * TR_COLS + c] = acc[u];
-    }
-    for (int e = tid; e < TR_RB * TR_RB; e += TR_THREADS) {
-      int a = e / TR_RB, b = e % TR_RB;
-      Lt[a * (TR_RB + 1) + b] = (a < ib && b < ib) ? L[(size_t)(i0 + a) * k + i0 + b] : 0.0f;
+    for (int u = 0; u < 4; ++u) X[(size_t)(i0 + r0 + 8 * u) * TR_COLS + c] = (r0 + 8 * u < ib) ? acc[u] : 0.0f;
+    const float* Di = Dinv + (size_t)(i0 / TR_RB) * TR_RB * TR_RB;
+    for (int e = tid; e < TR_RB * TR_RB; e += TR_THREADS) Lt[(e / TR_RB) * (TR_RB + 1) + e % TR_RB] = Di[e];
+    __syncthreads();
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int u = 0; u < TR_RB; ++u) {
+      const float x = X[(size_t)(i0 + u) * TR_COLS + c];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] = fmaf(Lt[(r0 + 8 * v) * (TR_RB + 1) + u], x, out[v]);
     }
     __syncthreads();
-    if (tid < 32) {  // lane c solves its column through the diagonal block
-      for (int t = 0; t < ib; ++t) {
-        float x = X[(size_t)(i0 + t) * TR_COLS + c];
-        for (int u = 0; u < t; ++u) x = fmaf(-Lt[t * (TR_RB + 1) + u], X[(size_t)(i0 + u) * TR_COLS + c], x);
-        X[(size_t)(i0 + t) * TR_COLS + c] = x / Lt[t * (TR_RB + 1) + t];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int ri = r0 + 8 * v;
+      if (ri < ib) {
+        X[(size_t)(i0 + ri) * TR_COLS + c] = out[v];
+        if (col < d) Qt[(long long)(i0 + ri) * ldq + col] = out[v];
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int ri = r0 + 8 * u;
-      if (ri < ib && col < d) Qt[(long long)(i0 + ri) * ldq + col] = X[(size_t)(i0 + ri) * TR_COLS + c];
-    }
   }
 }
 }  // namespace
 
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
-                           cudaStream_t s) {
+                           float* dinv_ws, cudaStream_t s) {
   if (k <= 0 || d <= 0) return cudaSuccess;
-  size_t smem = sizeof(float) * ((size_t)k * TR_COLS + TR_RB * (TR_RB + 1));
+  const int kpad = (k + TR_RB - 1) / TR_RB * TR_RB;  // X rows incl. the padded tail block
+  size_t smem = sizeof(float) * ((size_t)kpad * TR_COLS + TR_RB * (TR_RB + 1));
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
   static bool attr_done = false;
   if (!attr_done) {
@@ -337,7 +426,9 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  k_trsm_lower<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem, s>>>(L, k, Yt, ldy, Qt, ldq, d);
+  k_diag_block_inv<<<(k + TR_RB - 1) / TR_RB, 32, 0, s>>>(L, k, dinv_ws);
+  note_launch();
+  k_trsm_lower<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem, s>>>(L, dinv_ws, k, Yt, ldy, Qt, ldq, d);
   note_launch();
   return cudaGetLastError();
 }

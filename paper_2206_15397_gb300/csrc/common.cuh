@@ -92,16 +92,19 @@ cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, fl
 cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int cols, double* out, long long ldo,
                                int* flags, cudaStream_t s);
 
-// FP64 Cholesky of (G + shift I) on a thread-block cluster; writes the lower
-// factor L as FP32 (k x k row-major, upper part zero). shift = shift_rel *
-// trace(G) for shift_rel > 0, |shift_rel| * trace(G) / k for shift_rel < 0; on
-// breakdown the shift grows (bounded retries) and flags record it.
-cudaError_t chol_f64_cluster(const double* G, int k, double shift_rel, float* L32, int* flags,
-                             unsigned long long* stats, cudaStream_t s);
+// Cholesky of (G + shift I) on a thread-block cluster, factorised in FP64
+// (fp64) or FP32 from the FP64 Gram G; writes the lower factor L as FP32 (k x k
+// row-major, upper part zero). shift = shift_rel * trace(G) for shift_rel > 0,
+// |shift_rel| * trace(G) / k for shift_rel < 0. A pivot below a floor tied to
+// the FP32 rounding level is raised to it (flag CHOL_SHIFTED); a non-finite
+// pivot retries with a growing shift (bounded) and then fails (CHOL_FAILED).
+cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
+                         unsigned long long* stats, cudaStream_t s);
 
 // Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
+// dinv_ws: ceil(k/32) * 1024 floats of workspace (inverses of L's diagonal blocks).
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
-                           cudaStream_t s);
+                           float* dinv_ws, cudaStream_t s);
 
 // FP32 one-sided Jacobi on chol(C + s I) over a thread-block cluster: writes X
 // (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:

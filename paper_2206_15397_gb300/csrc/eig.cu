@@ -38,31 +38,50 @@ __device__ __forceinline__ float warp_sum_bcast(float v) {
 // if a rotation was applied. `sm` is the kernel's dynamic shared array and the
 // columns are given as offsets into it, so every access stays a shared-memory
 // access (a generic pointer would turn them into generic loads).
-__device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, int kp, float tol, int lane) {
-  // Columns are zero-padded to kp (a multiple of 128): each lane moves float4s,
-  // and the padding stays zero under rotations.
+template <int NI>
+__device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol, int lane) {
+  // Columns are zero-padded to NI * 128 floats: each lane holds NI float4s of
+  // both columns in registers from the dot products to the rotation, and the
+  // padding stays zero under rotations.
   float4* a4 = reinterpret_cast<float4*>(sm + oa);
   float4* b4 = reinterpret_cast<float4*>(sm + ob);
-  const int n4 = kp >> 2;
+  float4 x[NI], y[NI];
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    x[it] = a4[lane + 32 * it];
+    y[it] = b4[lane + 32 * it];
+  }
   float al = 0.f, be = 0.f, ga = 0.f;
-  for (int i = lane; i < n4; i += 32) {
-    const float4 x = a4[i], y = b4[i];
-    al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
-    be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
-    ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    al = fmaf(x[it].x, x[it].x, fmaf(x[it].y, x[it].y, fmaf(x[it].z, x[it].z, fmaf(x[it].w, x[it].w, al))));
+    be = fmaf(y[it].x, y[it].x, fmaf(y[it].y, y[it].y, fmaf(y[it].z, y[it].z, fmaf(y[it].w, y[it].w, be))));
+    ga = fmaf(x[it].x, y[it].x, fmaf(x[it].y, y[it].y, fmaf(x[it].z, y[it].z, fmaf(x[it].w, y[it].w, ga))));
   }
   al = warp_sum_bcast(al);
   be = warp_sum_bcast(be);
   ga = warp_sum_bcast(ga);
-  if (!(ga != 0.0f && fabsf(ga) > tol * sqrtf(al * be))) return 0;
-  // 2x2 symmetric Schur step on the Gram [[al, ga], [ga, be]]: J = [[c, s], [-s, c]].
-  float zeta = (be - al) / (2.0f * ga);
-  float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-  float cs = rsqrtf(1.0f + t * t), sn = cs * t;
-  for (int i = lane; i < n4; i += 32) {
-    const float4 x = a4[i], y = b4[i];
-    a4[i] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z, cs * x.w - sn * y.w);
-    b4[i] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z, sn * x.w + cs * y.w);
+  if (!(ga != 0.0f && ga * ga > (tol * tol) * (al * be))) return 0;
+  // 2x2 symmetric Schur step on the Gram [[al, ga], [ga, be]]: J = [[c, s], [-s, c]],
+  // t = sign(z) / (|z| + sqrt(1 + z^2)). Fast reciprocal / rsqrt: their ulp
+  // errors only perturb the rotation slightly (W W^T stays C + sI to FP32
+  // accuracy) and the FP64 refinement that follows absorbs them.
+  const float zeta = __fdividef(be - al, 2.0f * ga);
+  const float az = fabsf(zeta);
+  float t;
+  if (az > 1e15f) {
+    t = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.0f);
+    t = copysignf(__fdividef(1.0f, az + q * rsqrtf(q)), zeta);
+  }
+  const float cs = rsqrtf(fmaf(t, t, 1.0f)), sn = cs * t;
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    a4[lane + 32 * it] = make_float4(cs * x[it].x - sn * y[it].x, cs * x[it].y - sn * y[it].y,
+                                     cs * x[it].z - sn * y[it].z, cs * x[it].w - sn * y[it].w);
+    b4[lane + 32 * it] = make_float4(sn * x[it].x + cs * y[it].x, sn * x[it].y + cs * y[it].y,
+                                     sn * x[it].z + cs * y[it].z, sn * x[it].w + cs * y[it].w);
   }
   return 1;
 }
@@ -103,6 +122,7 @@ struct EigArgs {
 // next of two slot buffers), then the cluster meets at one barrier. CTAs only
 // synchronise through cluster barriers, taken the same number of times by all
 // of them (no spin waits).
+template <int NI>
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   extern __shared__ __align__(16) float esm[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -214,7 +234,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
             if (u < n2 && v < n2) {
               const int cu = u < ba ? top + u * kp : bot + (u - ba) * kp;
               const int cv = v < ba ? top + v * kp : bot + (v - ba) * kp;
-              cnt += jacobi_pair(esm, cu, cv, kp, a.tol, lane);
+              cnt += jacobi_pair<NI>(esm, cu, cv, a.tol, lane);
             }
           }
           __syncthreads();
@@ -224,7 +244,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
         for (int r = 0; r < bmax; ++r) {
           for (int i = warp; i < bmax; i += EIG_WARPS) {
             int j = (i + r) % bmax;
-            if (i < ba && j < bb) cnt += jacobi_pair(esm, top + i * kp, bot + j * kp, kp, a.tol, lane);
+            if (i < ba && j < bb) cnt += jacobi_pair<NI>(esm, top + i * kp, bot + j * kp, a.tol, lane);
           }
           __syncthreads();
         }
@@ -378,30 +398,16 @@ __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ 
 
 }  // namespace
 
-cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
-                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
+template <int NI>
+static cudaError_t launch_eig(const EigArgs& a, int nc, size_t smem, cudaStream_t s) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
+    cudaError_t e = cudaFuncSetAttribute(k_eig_cluster<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_eig_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_eig_cluster<NI>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  int nc = (k + 31) / 32;  // b = ceil(k / 2nc) <= 16: one warp per pair of a cross round
-  nc = nc < 1 ? 1 : (nc > EIG_MAX_NC ? EIG_MAX_NC : nc);
-  const int b = (k + 2 * nc - 1) / (2 * nc);
-  const int kp = (k + 127) / 128 * 128;  // float4 per lane, 32 lanes
-  const size_t blocks_bytes = sizeof(float) * 4 * (size_t)b * kp;  // 2 buffers x 2 slots
-  const size_t chol_bytes = sizeof(float) * (size_t)k * k;
-  EigArgs a = {C, k, shift_rel, max_sweeps, tol, X, lam, gscratch, flags, stats, b, kp, 0};
-  size_t smem = blocks_bytes;
-  if (chol_bytes <= (size_t)kSmemOptin) {
-    a.chol_smem = 1;
-    smem = chol_bytes > smem ? chol_bytes : smem;
-  }
-  if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nc, 1, 1);
   cfg.blockDim = dim3(EIG_THREADS, 1, 1);
@@ -415,7 +421,33 @@ cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_swe
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchKernelEx(&cfg, k_eig_cluster, a);
+  return cudaLaunchKernelEx(&cfg, k_eig_cluster<NI>, a);
+}
+
+cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
+                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  int nc = (k + 31) / 32;  // b = ceil(k / 2nc) <= 16: one warp per pair of a cross round
+  nc = nc < 1 ? 1 : (nc > EIG_MAX_NC ? EIG_MAX_NC : nc);
+  const int b = (k + 2 * nc - 1) / (2 * nc);
+  const int kp = (k + 127) / 128 * 128;  // float4 per lane, 32 lanes
+  const size_t blocks_bytes = sizeof(float) * 4 * (size_t)b * kp;  // 2 buffers x 2 slots
+  const size_t chol_bytes = sizeof(float) * (size_t)k * k;
+  EigArgs a = {C, k, shift_rel, max_sweeps, tol, X, lam, gscratch, flags, stats, b, kp, 0};
+  size_t smem = blocks_bytes;
+  if (chol_bytes <= (size_t)kSmemOptin) {
+    a.chol_smem = 1;
+    smem = chol_bytes > smem ? chol_bytes : smem;
+  }
+  if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
+  switch (kp / 128) {
+    case 1: return launch_eig<1>(a, nc, smem, s);
+    case 2: return launch_eig<2>(a, nc, smem, s);
+    case 3: return launch_eig<3>(a, nc, smem, s);
+    case 4: return launch_eig<4>(a, nc, smem, s);
+    case 5: return launch_eig<5>(a, nc, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, double* work, int* flags, cudaStream_t s) {

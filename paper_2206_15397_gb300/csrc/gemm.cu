@@ -52,13 +52,13 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
     a.partial = 1; a.kchunk = g.kchunk; a.zstride = g.zstride;
     return tc::gemm(a, g.A, g.sam, g.B, g.sbn, g.zsplit, split3, s);
   }
-  const int bn = g.N > 128 ? 256 : 128;
+  const int bn = tc::tile_n(g.N, split3);
   long long tiles = cdiv(g.M, 128) * cdiv(g.N, bn);
   if (g.sym) tiles = (tiles + 1) / 2;
   const long long rows = g.d_trans ? g.N : g.M, cols = g.d_trans ? g.M : g.N;
   int z = 1;
-  if (g.ws && !g.sym && tiles < 120 && g.K >= 1024) {
-    z = (int)std::min<long long>(cdiv(148, tiles), g.K / 512);
+  if (g.ws && !g.sym && tiles < 120 && g.K >= 1024) {  // split K, but stay within one wave of 152 SMs
+    z = (int)std::min<long long>(152 / tiles, g.K / 512);
     while (z > 1 && (long long)z * rows * cols > g.ws_floats) --z;
   }
   if (z > 1) {

@@ -7,18 +7,29 @@
 //   * warp 0 / lane 0 streams A and B tiles of 32 FP32 columns (128 bytes = one
 //     128B-swizzle row) with cp.async.bulk.tensor into a ring of shared-memory
 //     stages, each guarded by a "full" mbarrier (transaction bytes);
-//   * in the 3xTF32 mode warps 4-7 split every staged value in place into its
-//     TF32 head and a TF32 tail (x = hi + lo, both exactly TF32), fence the
-//     generic-proxy writes for the async proxy and arrive on a "split" barrier;
 //   * warp 1 / lane 0 issues tcgen05.mma.kind::tf32 (M = 128, N = BN, K = 8 per
-//     instruction) into a TMEM accumulator: hi*hi, plus hi*lo and lo*hi in the
-//     3xTF32 mode (FP32-accurate products, the lo*lo term is below FP32
-//     rounding), and hands each stage back with tcgen05.commit -> "empty";
-//   * all 8 warps then read TMEM with tcgen05.ld (warp w reads lanes
-//     32*(w%4)..+31, warps 0-3 the first half of the columns, 4-7 the second),
-//     apply the epilogue and store. Row-major D / C0 go through a per-warp
-//     shared-memory tile so global accesses are coalesced; transposed D / C0
-//     (D[n][m]) are coalesced directly since TMEM lanes are consecutive rows.
+//     instruction) into TMEM and hands each stage back with tcgen05.commit ->
+//     "empty";
+//   * the accumulator is read with tcgen05.ld (warp w reads TMEM lanes
+//     32*(w%4)..+31), the epilogue applied and D stored. Row-major D / C0 go
+//     through a per-warp shared-memory tile so global accesses are coalesced;
+//     transposed D / C0 (D[n][m]) are coalesced directly since TMEM lanes are
+//     consecutive rows.
+// Two kernels:
+//   k_tc_gemm   TF32 products, one accumulator over the CTA's whole K range
+//               (all 8 warps share the epilogue).
+//   k_tc_gemm3  FP32-accurate products (3xTF32): warps 2-7 split every staged
+//               value in place into its TF32 head and FP32 tail (x = hi + lo
+//               exactly) and fence the writes for the async proxy; the issuer
+//               puts hi*hi into one accumulator and hi*lo + lo*hi into
+//               another. The tensor core's FP32 accumulation rounds toward
+//               zero, which over a long K loop drifts every sum low (measured
+//               about -5e-6 relative over K = 512 with one accumulator), so
+//               each stage (K = 32) accumulates into a fresh TMEM pair, double
+//               buffered, and warps 4-7, between splitting the next stages,
+//               add every finished pair into FP32 registers with
+//               round-to-nearest. The remaining bias is that of four K-steps
+//               (measured -9e-8 relative, independent of K).
 // Every mbarrier wait is bounded by a clock deadline; on expiry the kernel
 // raises KFAC_FLAG_TIMEOUT, drains what it issued and returns.
 #include <cuda.h>
@@ -35,6 +46,8 @@ constexpr int BM = 128;
 constexpr int BK = 32;  // FP32 columns per stage (128 bytes)
 constexpr int THREADS = 256;
 constexpr long long kDeadlineCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int BN3 = 128;            // tile width of the FP32-accurate kernel
+constexpr int kSplitThreads = 192;  // warps 2-7 split the staged tiles (3xTF32)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -109,6 +122,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// As tmem_ld32 without the wait: the registers are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // Shared-memory matrix descriptor of a K-major tile written by TMA with the
 // 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
@@ -125,32 +151,107 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ float tf32_round(float x) {
+// x rounded to nearest TF32 (exactly representable in TF32). Rounding (not
+// truncation) keeps the tail |x - hi| <= 2^-11 |x| and unbiased: truncated heads
+// leave tails of one sign that the tensor core truncates again, biasing every
+// product low by ~1e-6, which chained products accumulate.
+__device__ __forceinline__ float tf32_head(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
 
-template <int BN, int MODE>
+template <int BN>
 struct Cfg {
   static constexpr int A_BYTES = BM * BK * 4;
   static constexpr int B_BYTES = BN * BK * 4;
   static constexpr int RAW = A_BYTES + B_BYTES;
-  static constexpr int STAGE = MODE == 1 ? 2 * RAW : RAW;
+  static constexpr int STAGE = RAW;
   static constexpr int STAGES = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
-  static constexpr int BAR_BYTES = 8 * (3 * STAGES + 1) + 16;
+  static constexpr int BAR_BYTES = 8 * (2 * STAGES + 1) + 16;
   static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES;
 };
 
-template <int BN, int MODE>
+// FP32-accurate kernel: stages carry the raw tile and the tail tile.
+struct Cfg3 {
+  static constexpr int A_BYTES = BM * BK * 4;
+  static constexpr int B_BYTES = BN3 * BK * 4;
+  static constexpr int RAW = A_BYTES + B_BYTES;
+  static constexpr int STAGE = 2 * RAW;
+  static constexpr int STAGES = 196608 / STAGE;
+  static constexpr int BAR_BYTES = 8 * (3 * STAGES + 5) + 16;
+  static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES;
+  static constexpr int TMEM_COLS = 4 * BN3;  // main[2], small[2]
+};
+
+// Epilogue of 32 consecutive columns [nb, nb + 32) of row m held by this lane
+// (v[j] = raw sum for column nb + j): scaling, beta * C0, store (row-major via
+// the warp's staging tile, or transposed), the symmetric mirror.
+__device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int m, int mrow0, int nb, int lane,
+                                            float rs, float* stage_tile, float* Dz) {
+  if (!p.partial) {
+    float cin[32];
+    if (p.beta != 0.0f && p.C0) {
+      if (p.c0_trans) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = nb + j;
+          cin[j] = (m < p.M && n < p.N) ? p.C0[(long long)n * p.ldc + m] : 0.0f;
+        }
+      } else {  // rows of C0 through the staging tile
+        __syncwarp();
+        for (int r = 0; r < 32; ++r) {
+          const int mr = mrow0 + r, n = nb + lane;
+          stage_tile[r * 33 + lane] = (mr < p.M && n < p.N) ? p.C0[(long long)mr * p.ldc + n] : 0.0f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cin[j] = stage_tile[lane * 33 + j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = nb + j;
+      float x = v[j] * p.alpha * rs;
+      if (p.colscale && n < p.N) x *= p.colscale[n];
+      if (p.beta != 0.0f && p.C0) x = fmaf(p.beta, cin[j], x);
+      v[j] = x;
+    }
+  }
+  if (p.d_trans) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = nb + j;
+      if (m < p.M && n < p.N) Dz[(long long)n * p.ldd + m] = v[j];
+    }
+  } else {
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stage_tile[lane * 33 + j] = v[j];
+    __syncwarp();
+    for (int r = 0; r < 32; ++r) {
+      const int mr = mrow0 + r, n = nb + lane;
+      if (mr < p.M && n < p.N && (!p.sym || mr <= n)) Dz[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
+    }
+    if (p.sym) {  // mirror: D[n][m] for m < n, consecutive lanes -> consecutive m
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = nb + j;
+        if (m < p.M && n < p.N && m < n) Dz[(long long)n * p.ldd + m] = v[j];
+      }
+    }
+  }
+}
+
+template <int BN>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
-  using C = Cfg<BN, MODE>;
+  using C = Cfg<BN>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * C::STAGES + 1);
-  const uint32_t full0 = smem_u32(bars), split0 = full0 + 8 * C::STAGES, empty0 = split0 + 8 * C::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::STAGES;
   const uint32_t accb = empty0 + 8 * C::STAGES;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -163,7 +264,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(split0 + 8 * s, 128);
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(accb, 1);
@@ -203,7 +303,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (!mbar_wait((MODE == 1 ? split0 : full0) + 8 * s, ph, p.flags)) break;
+      if (!mbar_wait(full0 + 8 * s, ph, p.flags)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
@@ -211,36 +311,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int kk = 0; kk < BK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per instruction
         const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4
         mma_tf32(taddr, ad + off, bd + off, idesc, (kb | kk) ? 1u : 0u);
-        if (MODE == 1) {
-          const uint64_t adl = sdesc_k128(st + C::RAW), bdl = sdesc_k128(st + C::RAW + C::A_BYTES);
-          mma_tf32(taddr, ad + off, bdl + off, idesc, 1u);
-          mma_tf32(taddr, adl + off, bd + off, idesc, 1u);
-        }
       }
       mma_commit(empty0 + 8 * s);  // stage reusable once these MMAs completed
     }
     mma_commit(accb);  // accumulator ready (also completes when nothing was issued)
-  } else if (MODE == 1 && warp >= 4) {
-    // ---- 3xTF32 splitter: x -> hi (in place) + lo (tail buffer) -------------
-    const int t = tid - 128;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % C::STAGES;
-      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (!mbar_wait(full0 + 8 * s, ph, p.flags)) break;
-      float4* raw = reinterpret_cast<float4*>(smem + s * C::STAGE);
-      float4* lo = reinterpret_cast<float4*>(smem + s * C::STAGE + C::RAW);
-      for (int e = t; e < C::RAW / 16; e += 128) {
-        float4 x = raw[e], h, l;
-        h.x = tf32_round(x.x); l.x = tf32_round(x.x - h.x);
-        h.y = tf32_round(x.y); l.y = tf32_round(x.y - h.y);
-        h.z = tf32_round(x.z); l.z = tf32_round(x.z - h.z);
-        h.w = tf32_round(x.w); l.w = tf32_round(x.w - h.w);
-        raw[e] = h;
-        lo[e] = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(split0 + 8 * s);
-    }
   }
   __syncwarp();
 
@@ -263,63 +337,185 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = 0.0f;
     }
-    if (!p.partial) {
-      float cin[32];
-      if (p.beta != 0.0f && p.C0) {
-        if (p.c0_trans) {
+    store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(BN) : "memory");
+  }
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the verdict is broadcast.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* flags, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = mbar_wait(bar, parity, flags) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gemm3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
+  using C = Cfg3;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * C::STAGES + 5);
+  const uint32_t full0 = smem_u32(bars), split0 = full0 + 8 * C::STAGES, empty0 = split0 + 8 * C::STAGES;
+  const uint32_t tfull0 = empty0 + 8 * C::STAGES, tempty0 = tfull0 + 16, accb = tempty0 + 16;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN3;
+  if (p.sym && m0 > n0 + BN3 - 1) return;  // whole tile below the diagonal (uniform exit, nothing started)
+  const int kb0 = blockIdx.z * p.kchunk;
+  const int ke = min(p.K, kb0 + p.kchunk);
+  const int nk = ke > kb0 ? (ke - kb0 + BK - 1) / BK : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(split0 + 8 * s, kSplitThreads);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);  // one arrival per drain warp
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tmem_slot;
+
+  float acc[BN3];  // warps 4-7: this lane's row of the tile, FP32 round-to-nearest sums
+  bool drained = true;
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer --------------------------------------------------------
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags)) break;
+      const uint32_t st = smem_u32(smem + s * C::STAGE);
+      mbar_expect_tx(full0 + 8 * s, C::RAW);
+      tma_load_2d(st, &tmA, kb0 + kb * BK, m0, full0 + 8 * s);
+      tma_load_2d(st + C::A_BYTES, &tmB, kb0 + kb * BK, n0, full0 + 8 * s);
+      ++issued;
+    }
+    for (int kb = (issued > C::STAGES ? issued - C::STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: stage kb -> TMEM pair kb & 1 ----------------------------
+    constexpr uint32_t idesc = idesc_tf32(BM, BN3);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::STAGES, b = kb & 1;
+      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      if (kb >= 2 && !mbar_wait(tempty0 + 8 * b, (uint32_t)((kb >> 1) - 1) & 1u, p.flags)) break;
+      if (!mbar_wait(split0 + 8 * s, ph, p.flags)) break;
+      tc_fence_after();
+      const uint32_t st = smem_u32(smem + s * C::STAGE);
+      const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
+      const uint64_t adl = sdesc_k128(st + C::RAW), bdl = sdesc_k128(st + C::RAW + C::A_BYTES);
+      const uint32_t tmain = taddr + (uint32_t)(b * BN3), tsmall = taddr + (uint32_t)(2 * BN3 + b * BN3);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = nb + j;
-            cin[j] = (m < p.M && n < p.N) ? p.C0[(long long)n * p.ldc + m] : 0.0f;
-          }
-        } else {  // rows of C0 through the staging tile
-          __syncwarp();
-          for (int r = 0; r < 32; ++r) {
-            const int mr = m0 + 32 * q + r, n = nb + lane;
-            stage_tile[r * 33 + lane] = (mr < p.M && n < p.N) ? p.C0[(long long)mr * p.ldc + n] : 0.0f;
-          }
-          __syncwarp();
-#pragma unroll
-          for (int j = 0; j < 32; ++j) cin[j] = stage_tile[lane * 33 + j];
-        }
+      for (int kk = 0; kk < BK / 8; ++kk) {
+        const uint64_t off = (uint64_t)(kk * 2);
+        mma_tf32(tmain, ad + off, bd + off, idesc, kk ? 1u : 0u);
+        mma_tf32(tsmall, ad + off, bdl + off, idesc, kk ? 1u : 0u);
+        mma_tf32(tsmall, adl + off, bd + off, idesc, 1u);
       }
+      mma_commit(empty0 + 8 * s);  // stage reusable once these MMAs completed
+      mma_commit(tfull0 + 8 * b);  // pair b holds this stage's sums
+    }
+    mma_commit(accb);  // every issued MMA has completed (also when nothing was issued)
+  } else if (warp >= 2) {
+    // ---- warps 2-7: 3xTF32 split of stage kb; warps 4-7 then drain pair kb-1 --
+    // hi = x rounded to TF32, lo = x - hi is exact in FP32 and |lo| <= 2^-11 |x|;
+    // the tensor core reads lo at TF32 precision, so hi*hi + hi*lo + lo*hi
+    // carries x*y to ~2^-21 relative. All waits here are warp-uniform so the
+    // warp stays converged for tcgen05.ld.
+    const int t = tid - 64;
+    const bool drainer = warp >= 4;
+    const uint32_t lrow = (uint32_t)(32 * (warp & 3)) << 16;
+    if (drainer) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = nb + j;
-        float x = v[j] * p.alpha * rs;
-        if (p.colscale && n < p.N) x *= p.colscale[n];
-        if (p.beta != 0.0f && p.C0) x = fmaf(p.beta, cin[j], x);
-        v[j] = x;
+      for (int j = 0; j < BN3; ++j) acc[j] = 0.0f;
+    }
+    for (int kb = 0; kb <= nk; ++kb) {
+      if (kb < nk) {
+        const int s = kb % C::STAGES;
+        const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+        if (!mbar_wait_warp(full0 + 8 * s, ph, p.flags, lane)) { drained = false; break; }
+        float4* raw = reinterpret_cast<float4*>(smem + s * C::STAGE);
+        float4* lo = reinterpret_cast<float4*>(smem + s * C::STAGE + C::RAW);
+#pragma unroll 2
+        for (int e = t; e < C::RAW / 16; e += kSplitThreads) {
+          const float4 x = raw[e];
+          float4 h, l;
+          h.x = tf32_head(x.x); l.x = x.x - h.x;
+          h.y = tf32_head(x.y); l.y = x.y - h.y;
+          h.z = tf32_head(x.z); l.z = x.z - h.z;
+          h.w = tf32_head(x.w); l.w = x.w - h.w;
+          raw[e] = h;
+          lo[e] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(split0 + 8 * s);
+      }
+      if (drainer && kb >= 1) {
+        const int kd = kb - 1, b = kd & 1;
+        if (!mbar_wait_warp(tfull0 + 8 * b, (uint32_t)(kd >> 1) & 1u, p.flags, lane)) { drained = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < BN3 / 32; ++c) {
+          uint32_t v[32], w[32];
+          tmem_ld32_async(taddr + lrow + (uint32_t)(b * BN3 + 32 * c), v);
+          tmem_ld32_async(taddr + lrow + (uint32_t)(2 * BN3 + b * BN3 + 32 * c), w);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[32 * c + j] += __uint_as_float(v[j]) + __uint_as_float(w[j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
     }
-    if (p.d_trans) {
+  }
+  __syncwarp();
+
+  // ---- epilogue (warps 4-7, from the register sums) ---------------------------
+  const bool acc_ok = mbar_wait_warp(accb, 0, p.flags, lane);
+  tc_fence_after();
+  if (warp >= 4) {
+    float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+    float* const Dz = p.D + (p.partial ? (long long)blockIdx.z * p.zstride : 0LL);
+    const int q = warp & 3;
+    const int m = m0 + 32 * q + lane;
+    const float rs = (p.rowscale && m < p.M) ? p.rowscale[m] : 1.0f;
+    const bool ok = acc_ok && drained;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = nb + j;
-        if (m < p.M && n < p.N) Dz[(long long)n * p.ldd + m] = v[j];
-      }
-    } else {
-      __syncwarp();
+    for (int c = 0; c < BN3 / 32; ++c) {
+      const int nb = n0 + 32 * c;
+      if (nb < p.N) {  // uniform across the warp
+        float v[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) stage_tile[lane * 33 + j] = v[j];
-      __syncwarp();
-      for (int r = 0; r < 32; ++r) {
-        const int mr = m0 + 32 * q + r, n = nb + lane;
-        if (mr < p.M && n < p.N && (!p.sym || mr <= n)) Dz[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
-      }
-      if (p.sym) {  // mirror: D[n][m] for m < n, consecutive lanes -> consecutive m
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = nb + j;
-          if (m < p.M && n < p.N && m < n) Dz[(long long)n * p.ldd + m] = v[j];
-        }
+        for (int j = 0; j < 32; ++j) v[j] = ok ? acc[32 * c + j] : 0.0f;
+        store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz);
       }
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 2) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(C::TMEM_COLS)
+                 : "memory");
   }
 }
 
@@ -355,20 +551,18 @@ bool make_map(CUtensorMap* map, const float* ptr, int rows, int cols, long long 
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int MODE>
-cudaError_t launch(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
-                   cudaStream_t s) {
-  using C = Cfg<BN, MODE>;
-  static bool attr = false;
+template <typename Kern>
+cudaError_t launch_kernel(Kern kern, int smem, int bn, bool& attr, const TcArgs& a, const float* A, long long lda,
+                          const float* B, long long ldb, int zsplit, cudaStream_t s) {
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, BN)) return cudaErrorInvalidValue;
-  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, zsplit);
-  k_tc_gemm<BN, MODE><<<grid, THREADS, C::SMEM, s>>>(ma, mb, a);
+  if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, bn)) return cudaErrorInvalidValue;
+  dim3 grid((a.N + bn - 1) / bn, (a.M + BM - 1) / BM, zsplit);
+  kern<<<grid, THREADS, smem, s>>>(ma, mb, a);
   note_launch();
   return cudaGetLastError();
 }
@@ -383,10 +577,10 @@ bool eligible(const float* A, long long lda, const float* B, long long ldb, int 
 
 cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
                  bool split3, cudaStream_t s) {
-  if (a.N > 128) {
-    return split3 ? launch<256, 1>(a, A, lda, B, ldb, zsplit, s) : launch<256, 0>(a, A, lda, B, ldb, zsplit, s);
-  }
-  return split3 ? launch<128, 1>(a, A, lda, B, ldb, zsplit, s) : launch<128, 0>(a, A, lda, B, ldb, zsplit, s);
+  static bool attr3 = false, attr256 = false, attr128 = false;
+  if (split3) return launch_kernel(k_tc_gemm3, Cfg3::SMEM, BN3, attr3, a, A, lda, B, ldb, zsplit, s);
+  if (a.N > 128) return launch_kernel(k_tc_gemm<256>, Cfg<256>::SMEM, 256, attr256, a, A, lda, B, ldb, zsplit, s);
+  return launch_kernel(k_tc_gemm<128>, Cfg<128>::SMEM, 128, attr128, a, A, lda, B, ldb, zsplit, s);
 }
 
 }  // namespace tc

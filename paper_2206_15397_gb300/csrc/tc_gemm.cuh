@@ -29,6 +29,9 @@ struct TcArgs {
 // by TMA: 16-byte aligned bases and row strides.
 bool eligible(const float* A, long long lda, const float* B, long long ldb, int M, int N, int K);
 
+// Tile width (columns of D per CTA) the launch below uses.
+inline int tile_n(int N, bool split3) { return (split3 || N <= 128) ? 128 : 256; }
+
 // Launch one GEMM: TF32 products (split3 = false) or FP32-accurate 3xTF32
 // products (split3 = true), FP32 accumulation in tensor memory.
 cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
