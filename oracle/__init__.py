@@ -17,6 +17,7 @@ Functions and the passages they follow:
   srevd            Alg. 3 with the power iteration of Sec. 2.2
   damped_coef      Eq. (13), the diagonal (D + lam I)^-1 - I/lam
   precondition     Alg. 4, the M and S updates (Alg. 5 supplies U~ for V~)
+  precondition_cols  the same S, selected columns only (full-size sampled checks)
   exact_apply      Alg. 1, eig + M/S updates: (G + lam I)^-1 J (A + lam I)^-1
   rank_bound       Proposition 3.1, Eq. (7)
 """
@@ -64,6 +65,8 @@ def _load():
             lib.orc_srevd.restype = i
             lib.orc_damped_coef.argtypes = [i, _dp, d, _dp]
             lib.orc_precondition.argtypes = [i, i, _dp, _dp, _dp, i, _dp, _dp, i, d, _dp]
+            ip = ctypes.POINTER(ctypes.c_int)
+            lib.orc_precondition_cols.argtypes = [i, i, _dp, _dp, _dp, i, _dp, _dp, i, d, i, ip, _dp]
             lib.orc_exact_apply.argtypes = [i, i, _dp, _dp, _dp, d, _dp]
             lib.orc_exact_apply.restype = i
             lib.orc_rank_bound.argtypes = [d, d, d, l, l]
@@ -155,6 +158,19 @@ def precondition(j, ua, ca, ug, cg, lam: float) -> np.ndarray:
     _load().orc_precondition(dg, da, _p(j), _p(ua), _p(ca), ua.shape[1], _p(ug), _p(cg), ug.shape[1],
                              float(lam), _p(s))
     return s
+
+
+def precondition_cols(j, ua, ca, ug, cg, lam: float, cols) -> np.ndarray:
+    """Columns `cols` of precondition(j, ua, ca, ug, cg, lam), shape (d_g, len(cols))."""
+    j, ua, ca, ug, cg = _c(j), _c(ua), _c(ca), _c(ug), _c(cg)
+    dg, da = j.shape
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    assert cols.ndim == 1 and np.all((cols >= 0) & (cols < da))
+    out = np.empty((dg, cols.shape[0]))
+    _load().orc_precondition_cols(dg, da, _p(j), _p(ua), _p(ca), ua.shape[1], _p(ug), _p(cg), ug.shape[1],
+                                  float(lam), int(cols.shape[0]), cols.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  _p(out))
+    return out
 
 
 def exact_apply(j, fa, fg, lam: float) -> np.ndarray:

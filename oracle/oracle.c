@@ -302,6 +302,43 @@ void orc_precondition(int dg, int da, const double* J, const double* Ua, const d
   free(T); free(M); free(T2);
 }
 
+/* Selected columns of the same S (for factor sizes where the full product  */
+/* is too slow for a test): column c of M = J (U_a diag(c_a) U_a^T + I/lam)  */
+/* is J v + J[:, c]/lam with v = U_a (c_a o U_a[c, :]); column c of S is     */
+/* U_g (c_g o U_g^T m) + m/lam. Output S_cols is d_g x ncols (column j of    */
+/* it = column cols[j] of S).                                                */
+void orc_precondition_cols(int dg, int da, const double* J, const double* Ua, const double* ca, int ra,
+                           const double* Ug, const double* cg, int rg, double lam, int ncols, const int* cols,
+                           double* S_cols) {
+  double* v = (double*)malloc(sizeof(double) * (size_t)da);
+  double* m = (double*)malloc(sizeof(double) * (size_t)dg);
+  double* t = (double*)malloc(sizeof(double) * (size_t)(rg > 0 ? rg : 1));
+  for (int jc = 0; jc < ncols; ++jc) {
+    const int c = cols[jc];
+    for (int i = 0; i < da; ++i) {                     /* v = U_a (c_a o U_a[c, :]) */
+      double s = 0.0;
+      for (int l = 0; l < ra; ++l) s += Ua[(size_t)i * ra + l] * ca[l] * Ua[(size_t)c * ra + l];
+      v[i] = s;
+    }
+    for (int i = 0; i < dg; ++i) {                     /* m = J v + J[:, c] / lam */
+      double s = 0.0;
+      for (int l = 0; l < da; ++l) s += J[(size_t)i * da + l] * v[l];
+      m[i] = s + J[(size_t)i * da + c] / lam;
+    }
+    for (int l = 0; l < rg; ++l) {                     /* t = c_g o (U_g^T m) */
+      double s = 0.0;
+      for (int i = 0; i < dg; ++i) s += Ug[(size_t)i * rg + l] * m[i];
+      t[l] = cg[l] * s;
+    }
+    for (int i = 0; i < dg; ++i) {                     /* S[:, c] = U_g t + m / lam */
+      double s = 0.0;
+      for (int l = 0; l < rg; ++l) s += Ug[(size_t)i * rg + l] * t[l];
+      S_cols[(size_t)i * ncols + jc] = s + m[i] / lam;
+    }
+  }
+  free(v); free(m); free(t);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Exact damped Kronecker inverse apply through full eigendecompositions:    */
 /* Alg. 1 (eigendecomposition, then the M and S updates) with the identity   */

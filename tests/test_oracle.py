@@ -297,6 +297,33 @@ def test_precondition_rank_one_closed_form():
     np.testing.assert_allclose(s2, j2 / lam ** 2, atol=1e-13)
 
 
+def test_precondition_cols_full_rank_equals_exact_inverse():
+    """Selected columns with r = d equal the columns of (G + lam I)^-1 J (A + lam I)^-1."""
+    da, dg, lam = 11, 7, 0.05
+    fa, fg = rand_psd(da, 4), rand_psd(dg, 5)
+    j = rng(6).standard_normal((dg, da))
+    wa, va, _ = oracle.jacobi_eigh(fa)
+    wg, vg, _ = oracle.jacobi_eigh(fg)
+    cols = np.array([0, 3, 10, 3])
+    got = oracle.precondition_cols(j, va, oracle.damped_coef(wa, lam), vg, oracle.damped_coef(wg, lam), lam, cols)
+    ref = np.linalg.solve(fg + lam * np.eye(dg), j) @ _inv(fa + lam * np.eye(da))
+    np.testing.assert_allclose(got, ref[:, cols], rtol=1e-10, atol=1e-10)
+
+
+def test_precondition_cols_rank_one_closed_form():
+    """J = u v^T with v a kept A mode: only column pattern v survives, scaled per Eq. (13)."""
+    da, dg, lam = 8, 5, 0.2
+    fa = inputs.spectrum_factor(1, da, np.linspace(2, 0.1, da))
+    fg = inputs.spectrum_factor(2, dg, np.linspace(3, 0.5, dg))
+    wa, va, _ = oracle.jacobi_eigh(fa)
+    wg, vg, _ = oracle.jacobi_eigh(fg)
+    j = np.outer(vg[:, 1], va[:, 2])
+    cols = np.arange(da)
+    got = oracle.precondition_cols(j, va[:, :3], oracle.damped_coef(wa[:3], lam), vg[:, :2],
+                                   oracle.damped_coef(wg[:2], lam), lam, cols)
+    np.testing.assert_allclose(got, j / ((wg[1] + lam) * (wa[2] + lam)), atol=1e-13)
+
+
 def test_precondition_empty_ranks():
     j = rng(5).standard_normal((4, 3))
     s = oracle.precondition(j, np.zeros((3, 0)), np.zeros(0), np.zeros((4, 0)), np.zeros(0), 0.5)
