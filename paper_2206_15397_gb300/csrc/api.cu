@@ -160,7 +160,7 @@ InvertLayout invert_layout(int d, int k, int r) {
     L.x = b.take<double>((size_t)n * n);
     L.lam = b.take<double>(n);
     L.work = b.take<double>(5 * (size_t)n * n);
-    L.jac = b.take<float>((size_t)n * n);
+    L.jac = b.take<float>(eig_scratch_floats(n));
     L.total = b.off;
     return L;
   }
@@ -179,7 +179,7 @@ InvertLayout invert_layout(int d, int k, int r) {
   L.x = b.take<double>((size_t)k * k);
   L.lam = b.take<double>(k);
   L.work = b.take<double>(5 * (size_t)k * k);
-  L.jac = b.take<float>((size_t)k * k);
+  L.jac = b.take<float>(eig_scratch_floats(k));
   L.p32 = b.take<float>((size_t)k * r);
   L.skws_floats = (long long)kSketchMaxSplit * k * d;
   L.skws = b.take<float>((size_t)L.skws_floats);
@@ -232,10 +232,12 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
     {
       STAGE(ctx, ST_CHOL);
       // First pass: shift relative to trace(G) (the sketch may be ill-conditioned
-      // beyond the FP32 Gram's accuracy). Middle passes: a tiny shift on the mean
-      // diagonal keeps the noise-level directions from breaking the factorization;
-      // the last pass (a near-orthonormal basis) is unshifted.
-      const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-6 : 0.0);
+      // beyond the FP32 Gram's accuracy). Middle passes: a shift of 1e-5 of the
+      // mean diagonal, above the FP32-accurate Gram's rounding noise (~1e-6 of
+      // it), so the directions the first pass left at noise level cannot make
+      // the factorisation indefinite; the last pass (a near-orthonormal basis)
+      // is unshifted.
+      const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-5 : 0.0);
       const bool fp64 = pass >= ctx->cholqr_fp32_passes || pass + 1 == passes;
       CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
                       ctx->stream));

@@ -39,6 +39,13 @@ __device__ __forceinline__ float rsqrt_newton(float x) {
   return y * fmaf(-0.5f * x * y, y, 1.5f);
 }
 
+// Replacement for a pivot below the floor: the column's original diagonal.
+template <typename T>
+__device__ __forceinline__ T raised_pivot(const double* G, int k, int j, double shift, T pfloor) {
+  const T g = (T)(G[(size_t)j * k + j] + shift);
+  return g > pfloor ? g : pfloor;
+}
+
 template <typename T>
 struct CholSmem {
   T* W;      // nloc x k, own rows (row-major, lower part used)
@@ -54,7 +61,7 @@ template <typename T>
 __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* __restrict__ G, int k, int B,
                                                                    int nloc, double shift_rel,
                                                                    float* __restrict__ L32, int* flags,
-                                                                   unsigned long long* stats) {
+                                                                   unsigned long long* stats, double* shift_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int NC = (int)cluster.num_blocks();
@@ -84,11 +91,15 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
   const double trace = s_trace;
   const bool finite_in = isfinite(trace) && trace > 0.0;
   // Pivot floor. A pivot below it (the column is, to the Gram's FP32
-  // accuracy, in the span of the previous ones) is raised to it: the factor is
-  // then the exact Cholesky factor of G + shift I + diag(delta), delta >= 0,
-  // which keeps R invertible and span(Y R^-1) = span(Y). Relative to the mean
-  // diagonal, above the rounding noise of the FP32-accurate Gram (and of an
-  // FP32 factorisation).
+  // accuracy, in the span of the previous ones) is replaced by the column's
+  // original diagonal G_jj + shift (at least the floor): the factor is then
+  // the exact Cholesky factor of G + shift I + diag(delta), delta >= 0, which
+  // keeps R invertible and span(Y R^-1) = span(Y), and the column's
+  // multipliers stay bounded by the rest of the matrix instead of growing by
+  // 1/sqrt(floor). The floor is relative to the mean diagonal, above the
+  // rounding noise of the FP32-accurate Gram (and of an FP32 factorisation).
+  // Should the raised pivots still let the factorisation overflow, the
+  // non-finite pivot restarts it with a larger shift.
   const T pfloor = (T)(sizeof(T) == 4 ? fmax(1e-9 * trace, 1e-6 * trace / k) : fmax(1e-13 * trace, 1e-7 * trace / k));
 
   // shift_rel > 0: relative to trace(G); shift_rel < 0: |shift_rel| times the
@@ -151,7 +162,7 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
           if (!isfinite(piv)) {
             *sm.flag = 1;
           } else {
-            if (!(piv > pfloor)) { piv = pfloor; sm.D[0] = piv; *sm.clamped = 1; }
+            if (!(piv > pfloor)) { piv = raised_pivot(G, k, j0, shift, pfloor); sm.D[0] = piv; *sm.clamped = 1; }
             sm.dinv[0] = rsqrt_newton(piv);
           }
         }
@@ -189,7 +200,11 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
             if (!isfinite(piv)) {
               *sm.flag = 1;
             } else {
-              if (!(piv > pfloor)) { piv = pfloor; sm.D[(t + 1) * B + t + 1] = piv; *sm.clamped = 1; }
+              if (!(piv > pfloor)) {
+                piv = raised_pivot(G, k, j0 + t + 1, shift, pfloor);
+                sm.D[(t + 1) * B + t + 1] = piv;
+                *sm.clamped = 1;
+              }
               sm.dinv[t + 1] = rsqrt_newton(piv);
             }
           }
@@ -249,13 +264,17 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
     cluster.sync();
     if (!bad) {
       if (*sm.clamped && rank == 0 && tid == 0) raise_flag(flags, KFAC_FLAG_CHOL_SHIFTED);
+      if (shift_out && rank == 0 && tid == 0) *shift_out = shift;
       ok = 1;
       break;
     }
   }
 
   if (!ok) {
-    if (rank == 0 && tid == 0) raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : KFAC_FLAG_NONFINITE);
+    if (rank == 0 && tid == 0) {
+      raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : KFAC_FLAG_NONFINITE);
+      if (shift_out) *shift_out = 0.0;
+    }
     // Keep downstream finite: L = diag(sqrt(max(G_ii, tiny))).
     for (int li = 0; li < nloc; ++li) {
       int i = li * NC + rank;
@@ -283,7 +302,7 @@ size_t chol_smem_bytes(int k, int nloc, int B, size_t elt) {
 
 template <typename T>
 cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, int* flags,
-                        unsigned long long* stats, cudaStream_t s) {
+                        unsigned long long* stats, cudaStream_t s, double* shift_out) {
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k_chol_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -316,16 +335,16 @@ cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, in
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchKernelEx(&cfg, k_chol_cluster<T>, G, k, B, nloc, shift_rel, L32, flags, stats);
+  return cudaLaunchKernelEx(&cfg, k_chol_cluster<T>, G, k, B, nloc, shift_rel, L32, flags, stats, shift_out);
 }
 
 }  // namespace
 
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
-                         unsigned long long* stats, cudaStream_t s) {
+                         unsigned long long* stats, cudaStream_t s, double* shift_out) {
   if (k <= 0) return cudaSuccess;
-  return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s)
-              : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s);
+  return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s, shift_out)
+              : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s, shift_out);
 }
 
 // ---------------------------------------------------------------------------

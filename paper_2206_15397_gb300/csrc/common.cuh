@@ -98,8 +98,9 @@ cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int col
 // |shift_rel| * trace(G) / k for shift_rel < 0. A pivot below a floor tied to
 // the FP32 rounding level is raised to it (flag CHOL_SHIFTED); a non-finite
 // pivot retries with a growing shift (bounded) and then fails (CHOL_FAILED).
+// shift_out (optional, device) receives the shift the successful attempt used.
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
-                         unsigned long long* stats, cudaStream_t s);
+                         unsigned long long* stats, cudaStream_t s, double* shift_out = nullptr);
 
 // Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
 // dinv_ws: ceil(k/32) * 1024 floats of workspace (inverses of L's diagonal blocks).
@@ -108,7 +109,8 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
 
 // FP32 one-sided Jacobi on chol(C + s I) over a thread-block cluster: writes X
 // (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:
-// k*k floats (the column store shared by the cluster's CTAs).
+// eig_scratch_floats(k) floats (the Cholesky factor and the shift it used).
+inline size_t eig_scratch_floats(int k) { return (((size_t)k * k + 1) & ~(size_t)1) + 4; }
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
                            double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s);
 

@@ -2,11 +2,11 @@
 // Alg. 3), and for whole factors with d <= k.
 //
 //  1. eig_jacobi_f32: C + s I (s a small PD shift) is Cholesky-factored in FP32
-//     (C + s I = L L^T) and the columns of W = L are made mutually orthogonal by
-//     one-sided (Hestenes) Jacobi rotations W <- W J. Since W W^T = C + s I is
-//     invariant, at convergence the unit columns of W are eigenvectors of C and
-//     |w_j|^2 - s its eigenvalues; only one k x k FP32 matrix is stored. The
-//     sweeps run on a thread-block cluster (up to 8 CTAs) as a block
+//     on a cluster (C + s I = L L^T) and the columns of W = L are made mutually
+//     orthogonal by one-sided (Hestenes) Jacobi rotations W <- W J. Since
+//     W W^T = C + s I is invariant, at convergence the unit columns of W are
+//     eigenvectors of C and |w_j|^2 - s its eigenvalues; only one k x k FP32
+//     matrix is stored. The sweeps run on a thread-block cluster as a block
 //     round-robin: one warp per column pair, one cluster barrier per
 //     block-round.
 //  2. eig_refine_f64: one FP64 refinement step of all eigenpairs (Ogita and
@@ -94,19 +94,17 @@ __device__ __forceinline__ int rr_player(int p, int r, int m) {
 }
 
 struct EigArgs {
-  const double* C;
+  const float* L;       // k x k lower factor of C + shift I, row-major FP32 (column j of W = column j of L)
+  const double* shift;  // device scalar: the shift that factorisation used
   int k;
-  double shift_rel;
   int max_sweeps;
   float tol;
   double* X;
   double* lam;
-  float* Wg;      // k x k FP32 scratch, column-major (Cholesky factor when it does not fit in shared memory)
   int* flags;
   unsigned long long* stats;
-  int b;          // columns per block (the cluster holds 2 * NC blocks)
-  int kp;         // padded column length in shared memory (multiple of 128)
-  int chol_smem;  // CTA 0 factors in shared memory (else in Wg)
+  int b;   // columns per block (the cluster holds 2 * NC blocks)
+  int kp;  // padded column length in shared memory (multiple of 128)
 };
 
 // One-sided Jacobi on the columns of L = chol(C + sI), spread over a cluster.
@@ -131,74 +129,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k, b = a.b, kp = a.kp, nb = 2 * NC;
   const int slot = b * kp;  // floats per slot; buffer x starts at offset 2 * slot * x (top slot, then bottom)
-  __shared__ double s_shift, s_trace;
-  __shared__ int s_bad, s_count, s_total;
+  __shared__ int s_count, s_total;
   if (tid == 0) s_total = 0;
-
-  // ---- CTA 0: FP32 Cholesky of C + s I (column-major, stride k) -------------
-  if (rank == 0) {
-    float* W = a.chol_smem ? esm : a.Wg;
-    if (tid < 32) {
-      double t = 0.0;
-      for (int i = tid; i < k; i += 32) t += a.C[(size_t)i * k + i];
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (tid == 0) {
-        s_trace = t;
-        s_shift = fmax(a.shift_rel * fabs(t), 1e-30);
-      }
-    }
-    __syncthreads();
-    for (int attempt = 0;; ++attempt) {
-      const double sh = s_shift;
-      for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) {
-        int j = (int)(e / k), i = (int)(e % k);
-        W[e] = (i >= j) ? (float)(a.C[(size_t)i * k + j] + (i == j ? sh : 0.0)) : 0.0f;
-      }
-      if (tid == 0) s_bad = isfinite(s_trace) ? 0 : 2;
-      __syncthreads();
-      for (int j = 0; j < k && !s_bad; ++j) {
-        if (tid == 0) {
-          float p = W[(size_t)j * k + j];
-          if (!(p > 0.0f) || !isfinite(p)) s_bad = 1;
-          else W[(size_t)j * k + j] = sqrtf(p);
-        }
-        __syncthreads();
-        if (s_bad) break;
-        const float ljj = W[(size_t)j * k + j];
-        for (int i = j + 1 + tid; i < k; i += EIG_THREADS) W[(size_t)j * k + i] /= ljj;
-        __syncthreads();
-        for (int l = j + 1 + warp; l < k; l += EIG_WARPS) {  // trailing update, warp per column
-          const float wl = W[(size_t)j * k + l];
-          float* col = W + (size_t)l * k;
-          const float* cj = W + (size_t)j * k;
-          for (int i = l + lane; i < k; i += 32) col[i] = fmaf(-cj[i], wl, col[i]);
-        }
-        __syncthreads();
-      }
-      if (!s_bad) break;
-      if (s_bad == 2 || attempt >= 4) {
-        if (tid == 0) raise_flag(a.flags, s_bad == 2 ? KFAC_FLAG_NONFINITE : KFAC_FLAG_CHOL_FAILED);
-        break;
-      }
-      if (tid == 0) {
-        s_shift = fmax(s_shift * 100.0, 1e-6 * fabs(s_trace));
-        raise_flag(a.flags, KFAC_FLAG_EIG_SHIFTED);
-      }
-      __syncthreads();
-    }
-    if (s_bad) {  // keep downstream finite: W = identity
-      for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) W[e] = ((e / k) == (e % k)) ? 1.0f : 0.0f;
-      if (tid == 0) s_shift = 0.0;
-    }
-    __syncthreads();
-    if (a.chol_smem)
-      for (long long e = tid; e < (long long)k * k; e += EIG_THREADS) __stcg(a.Wg + e, esm[e]);
-    __threadfence();
-  }
-  // Every CTA has started (distributed shared memory is usable only after this
-  // barrier) and CTA 0's factor and shift are published.
-  cluster.sync();
-  if (rank != 0 && tid == 0) s_shift = *cluster.map_shared_rank(&s_shift, 0);
 
   // ---- initial blocks (round 0 positions) from the factor ------------------
   {
@@ -208,11 +140,12 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
       const int dst = sl * slot;
       for (int e = tid; e < b * kp; e += EIG_THREADS) {
         int c = e / kp, i = e % kp;
-        esm[dst + e] = (c < nc && i < k) ? __ldcg(a.Wg + (size_t)(c0 + c) * k + i) : 0.0f;
+        esm[dst + e] = (c < nc && i < k && i >= c0 + c) ? __ldg(a.L + (size_t)i * k + c0 + c) : 0.0f;
       }
     }
   }
-  __syncthreads();
+  // Every CTA has its blocks before the first distributed shared memory store.
+  cluster.sync();
 
   // ---- sweeps ---------------------------------------------------------------
   int sweep = 0, cur = 0;
@@ -293,7 +226,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
 
   // ---- eigenpairs of the blocks held here: lam_j = |w_j|^2 - s, x_j = w_j / |w_j|
   // After a whole number of sweeps the blocks are back at their round-0 positions.
-  const double sh = s_shift;
+  const double sh = *a.shift;
   const int blk[2] = {rr_player(rank, 0, nb), rr_player(nb - 1 - rank, 0, nb)};
   for (int sl = 0; sl < 2; ++sl) {
     const int c0 = blk[sl] * b;
@@ -427,19 +360,20 @@ static cudaError_t launch_eig(const EigArgs& a, int nc, size_t smem, cudaStream_
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
                            double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  int nc = (k + 31) / 32;  // b = ceil(k / 2nc) <= 16: one warp per pair of a cross round
+  // W = L with L L^T = C + sI, factorised on a cluster in FP32; the shift it
+  // used (grown on breakdown) is stored after the factor.
+  double* shift = reinterpret_cast<double*>(gscratch + (((size_t)k * k + 1) & ~(size_t)1));
+  cudaError_t e = chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift);
+  if (e != cudaSuccess) return e;
+  // b = ceil(k / 2nc) <= 8 where the cluster allows it: a cross round's b pairs
+  // then leave each sub-partition at most two busy warps.
+  int nc = (k + 15) / 16;
   nc = nc < 1 ? 1 : (nc > EIG_MAX_NC ? EIG_MAX_NC : nc);
   const int b = (k + 2 * nc - 1) / (2 * nc);
   const int kp = (k + 127) / 128 * 128;  // float4 per lane, 32 lanes
-  const size_t blocks_bytes = sizeof(float) * 4 * (size_t)b * kp;  // 2 buffers x 2 slots
-  const size_t chol_bytes = sizeof(float) * (size_t)k * k;
-  EigArgs a = {C, k, shift_rel, max_sweeps, tol, X, lam, gscratch, flags, stats, b, kp, 0};
-  size_t smem = blocks_bytes;
-  if (chol_bytes <= (size_t)kSmemOptin) {
-    a.chol_smem = 1;
-    smem = chol_bytes > smem ? chol_bytes : smem;
-  }
+  const size_t smem = sizeof(float) * 4 * (size_t)b * kp;  // 2 buffers x 2 slots
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
+  EigArgs a = {gscratch, shift, k, max_sweeps, tol, X, lam, flags, stats, b, kp};
   switch (kp / 128) {
     case 1: return launch_eig<1>(a, nc, smem, s);
     case 2: return launch_eig<2>(a, nc, smem, s);
