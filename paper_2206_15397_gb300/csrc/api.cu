@@ -144,7 +144,7 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, l32, dinv, c, x, lam, work, jac, p32, skws, total;
+  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, p32, skws, total;
   long long dp, skws_floats;
   int nsplit, kchunk;
 };
@@ -159,7 +159,7 @@ InvertLayout invert_layout(int d, int k, int r) {
     L.c = b.take<double>((size_t)n * n);
     L.x = b.take<double>((size_t)n * n);
     L.lam = b.take<double>(n);
-    L.work = b.take<double>(5 * (size_t)n * n);
+    L.work = b.take<double>(eig_refine_doubles(n));
     L.jac = b.take<float>(eig_scratch_floats(n));
     L.total = b.off;
     return L;
@@ -173,12 +173,14 @@ InvertLayout invert_layout(int d, int k, int r) {
   L.q = b.take<float>((size_t)k * L.dp);
   L.part = b.take<float>((size_t)L.nsplit * k * k);
   L.g = b.take<double>((size_t)k * k);
+  L.g32 = b.take<float>((size_t)k * k);
   L.l32 = b.take<float>((size_t)k * k);
   L.dinv = b.take<float>((size_t)((k + 31) / 32) * 1024);
   L.c = b.take<double>((size_t)k * k);
+  L.c32 = b.take<float>((size_t)k * k);
   L.x = b.take<double>((size_t)k * k);
   L.lam = b.take<double>(k);
-  L.work = b.take<double>(5 * (size_t)k * k);
+  L.work = b.take<double>(eig_refine_doubles(k));
   L.jac = b.take<float>(eig_scratch_floats(k));
   L.p32 = b.take<float>((size_t)k * r);
   L.skws_floats = (long long)kSketchMaxSplit * k * d;
@@ -190,7 +192,7 @@ InvertLayout invert_layout(int d, int k, int r) {
 // Gram-type product out = A A'^T (k x k, K = d) for two k x d row-major
 // operands, split over K with FP32 partials reduced (and symmetrised) in FP64.
 kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const float* Bm, long long ld, int k,
-                     int d, kfac_precision prec, double* out, int stage) {
+                     int d, kfac_precision prec, double* out, int stage, float* out32) {
   GemmDesc<float> g = {};
   g.M = k; g.N = k; g.K = d;
   g.A = A; g.sam = ld; g.sak = 1;
@@ -201,7 +203,8 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.flags = ctx->dflags;
   StageScope sc(ctx, stage);
   CK(gemm_f32(g, prec, ctx->stream));
-  CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, 1, ctx->dflags, ctx->stream));
+  CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, 1, ctx->dflags, ctx->stream,
+                       out32));
   return KFAC_OK;
 }
 
@@ -227,7 +230,8 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
 kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, float*& other, int k, int d,
                            int passes) {
   for (int pass = 0; pass < passes; ++pass) {
-    kfac_status st = gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM);
+    kfac_status st =
+        gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM, at<float>(ctx, L.g32));
     if (st != KFAC_OK) return st;
     {
       STAGE(ctx, ST_CHOL);
@@ -240,7 +244,7 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-5 : 0.0);
       const bool fp64 = pass >= ctx->cholqr_fp32_passes || pass + 1 == passes;
       CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
-                      ctx->stream));
+                      ctx->stream, nullptr, at<float>(ctx, L.g32), k));
     }
     {
       STAGE(ctx, ST_TRSM);
@@ -251,11 +255,12 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
   return KFAC_OK;
 }
 
-kfac_status eigensolve(kfac_ctx* ctx, const double* C, int n, double* X, double* lam, double* work, float* jac) {
+kfac_status eigensolve(kfac_ctx* ctx, const double* C, const float* C32, long long ld32, int n, double* X,
+                       double* lam, double* work, float* jac) {
   {
     STAGE(ctx, ST_EIG);
     CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, X, lam, jac, ctx->dflags,
-                        ctx->dstats, ctx->stream));
+                        ctx->dstats, ctx->stream, C32, ld32));
   }
   STAGE(ctx, ST_REFINE);
   for (int it = 0; it < ctx->eig_refine; ++it) CK(eig_refine_f64(C, n, X, lam, work, ctx->dflags, ctx->stream));
@@ -285,7 +290,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const int d = a.d, r = std::min(a.rank, a.d), k = a.rank + a.oversample;
   const float* F = a.F;
   const int ldf = a.ldf;
-  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.l32, &L.dinv, &L.c, &L.x, &L.lam, &L.work, &L.jac, &L.p32,
+  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac, &L.p32,
                     &L.skws})
     *o += base;
   cudaStream_t s = ctx->stream;
@@ -293,7 +298,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   if (k >= d) {  // nothing to sketch: diagonalise F itself (Q = I)
     double* C = at<double>(ctx, L.c);
     CK(convert_f32_to_f64(F, ldf, d, d, C, d, ctx->dflags, s));
-    st = eigensolve(ctx, C, d, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
+    st = eigensolve(ctx, C, F, ldf, d, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
                     at<float>(ctx, L.jac));
     if (st != KFAC_OK) return st;
     STAGE(ctx, ST_SELECT);
@@ -324,10 +329,10 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);
   if (st != KFAC_OK) return st;
   double* C = at<double>(ctx, L.c);
-  st = gram_f64(ctx, L, cur, other, L.dp, k, d, KFAC_PREC_FP32, C, ST_PROJ);
+  st = gram_f64(ctx, L, cur, other, L.dp, k, d, KFAC_PREC_FP32, C, ST_PROJ, at<float>(ctx, L.c32));
   if (st != KFAC_OK) return st;
-  st = eigensolve(ctx, C, k, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
-                  at<float>(ctx, L.jac));
+  st = eigensolve(ctx, C, at<float>(ctx, L.c32), k, k, at<double>(ctx, L.x), at<double>(ctx, L.lam),
+                  at<double>(ctx, L.work), at<float>(ctx, L.jac));
   if (st != KFAC_OK) return st;
   float* P32 = at<float>(ctx, L.p32);
   {

@@ -70,24 +70,31 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
 
   CholSmem<T> sm;
   T* base = reinterpret_cast<T*>(smem_raw);
-  sm.W = base;
+  sm.P[0] = base;  // first: 16-byte aligned (it also stages the FP64 diagonal)
+  sm.P[1] = sm.P[0] + (size_t)k * B;
+  sm.W = sm.P[1] + (size_t)k * B;
   sm.D = sm.W + (size_t)nloc * k;
   sm.dinv = sm.D + B * B;
   sm.Xi = sm.dinv + B;
-  sm.P[0] = sm.Xi + B * B;
-  sm.P[1] = sm.P[0] + (size_t)k * B;
-  sm.flag = reinterpret_cast<int*>(sm.P[1] + (size_t)k * B);
+  sm.flag = reinterpret_cast<int*>(sm.Xi + B * B);
   sm.clamped = sm.flag + 1;
 
-  // Trace (identical in every CTA: same reads, same order).
+  // Trace (identical in every CTA: same reads, same order). The diagonal is
+  // staged in the (still unused) panel buffer with all loads in flight at once.
   __shared__ double s_trace;
-  if (tid < 32) {  // fixed summation order: lane-strided partial sums, then a fixed shuffle tree
-    double t = 0.0;
-    for (int i = tid; i < k; i += 32) t += G[(size_t)i * k + i];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (tid == 0) s_trace = t;
+  {
+    double* dg = reinterpret_cast<double*>(sm.P[0]);  // k doubles fit in k * B (B >= 4) elements of T
+    for (int i = tid; i < k; i += CHOL_THREADS) cp_async8(dg + i, G + (size_t)i * k + i);
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid < 32) {  // fixed summation order: lane-strided partial sums, then a fixed shuffle tree
+      double t = 0.0;
+      for (int i = tid; i < k; i += 32) t += dg[i];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (tid == 0) s_trace = t;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const double trace = s_trace;
   const bool finite_in = isfinite(trace) && trace > 0.0;
   // Pivot floor. A pivot below it (the column is, to the Gram's FP32
@@ -114,13 +121,26 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
         if (stats) atomicAdd(stats + STAT_CHOL_RETRY, 1ull);
       }
     }
-    // Load own rows (lower triangle, shifted diagonal).
-    for (int li = 0; li < nloc; ++li) {
-      int i = li * NC + rank;
-      for (int j = tid; j < k; j += CHOL_THREADS) {
-        double v = 0.0;
-        if (i < k && j <= i) v = G[(size_t)i * k + j] + (i == j ? shift : 0.0);
-        sm.W[(size_t)li * k + j] = (T)v;
+    // Load own rows (lower triangle, shifted diagonal), eight independent
+    // loads per thread in flight before their stores.
+    {
+      const int total = nloc * k;
+      for (int base = 0; base < total; base += 8 * CHOL_THREADS) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = base + q * CHOL_THREADS + tid;
+          const int li = e / k, j = e - li * k, i = li * NC + rank;
+          v[q] = (e < total && i < k && j <= i) ? G[(size_t)i * k + j] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = base + q * CHOL_THREADS + tid;
+          if (e < total) {
+            const int li = e / k, j = e - li * k, i = li * NC + rank;
+            sm.W[e] = (T)(v[q] + (i == j ? shift : 0.0));
+          }
+        }
       }
     }
     if (tid == 0) { *sm.flag = 0; *sm.clamped = 0; }
@@ -338,11 +358,237 @@ cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, in
   return cudaLaunchKernelEx(&cfg, k_chol_cluster<T>, G, k, B, nloc, shift_rel, L32, flags, stats, shift_out);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 Cholesky of (G + shift I) on one CTA with the whole matrix in shared
+// memory (k <= CTA_KMAX), for the shifted first CholeskyQR pass and the
+// eigensolver's factor: no cluster barriers or distributed-memory broadcasts,
+// which dominate the cluster kernel at these sizes. Right-looking, 32-column
+// panels:
+//   (1) warp 0 factors the 32 x 32 diagonal block in registers: lane r holds
+//       row r; per pivot t the pivot and column t travel by shuffles, and the
+//       lane's trailing row entries update in place (fully unrolled, static
+//       register indices). Reciprocal pivots go to shared memory;
+//   (2) one thread per row below solves its panel row against L11
+//       (right-looking substitution, L11 read as shared-memory broadcasts);
+//   (3) all threads apply the rank-32 update to the trailing lower triangle,
+//       4 x 4 output tiles per thread, 128-bit reads along the panel.
+// Pivot floor, raised pivots and restarts follow the cluster kernel.
+constexpr int CTA_THREADS = 512;
+constexpr int CTA_KMAX = 236;
+
+__host__ __device__ inline int cta_ks(int k) { return k | 1; }  // odd row stride: rows hit distinct banks
+__host__ __device__ inline size_t cta_smem_bytes(int k) { return sizeof(float) * ((size_t)k * cta_ks(k) + 64) + 16; }
+
+__global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* __restrict__ G,
+                                                                const float* __restrict__ G32, long long ld32,
+                                                                int k, double shift_rel, float* __restrict__ L32,
+                                                                int* flags, unsigned long long* stats,
+                                                                double* shift_out) {
+  extern __shared__ __align__(16) float csm[];
+  const int ks = cta_ks(k);
+  float* A = csm;                        // k x ks, row-major, lower part used
+  float* rinv = A + (size_t)k * ks;      // 32 reciprocal pivots of the current panel
+  int* sflag = reinterpret_cast<int*>(rinv + 32);  // [0] non-finite, [1] clamped
+  __shared__ double s_trace;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (warp == 0) {  // fixed-order trace
+    double t = 0.0;
+    for (int i = lane; i < k; i += 32) t += G[(size_t)i * k + i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s_trace = t;
+  }
+  __syncthreads();
+  const double trace = s_trace;
+  const bool finite_in = isfinite(trace) && trace > 0.0;
+  const float pfloor = (float)fmax(1e-9 * trace, 1e-6 * trace / k);
+  double shift = shift_rel > 0.0 ? shift_rel * trace : (shift_rel < 0.0 ? -shift_rel * trace / k : 0.0);
+  int ok = 0;
+  for (int attempt = 0; attempt < CHOL_ATTEMPTS && finite_in; ++attempt) {
+    if (attempt > 0) {
+      shift = fmax(shift, 1e-7 * trace) * 100.0;
+      if (tid == 0) {
+        raise_flag(flags, KFAC_FLAG_CHOL_SHIFTED);
+        if (stats) atomicAdd(stats + STAT_CHOL_RETRY, 1ull);
+      }
+    }
+    {  // load the lower triangle (+ shift), eight loads in flight per thread
+      const int total = k * k;
+      const float shf = (float)shift;
+      for (int base = 0; base < total; base += 8 * CTA_THREADS) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = base + q * CTA_THREADS + tid;
+          const int i = e / k, j = e - i * k;
+          // G32 avoids a per-element FP64 -> FP32 conversion on the FP64 pipe
+          v[q] = (e < total && j <= i) ? (G32 ? G32[(long long)i * ld32 + j] : (float)G[(size_t)i * k + j]) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = base + q * CTA_THREADS + tid;
+          if (e < total) {
+            const int i = e / k, j = e - i * k;
+            A[(size_t)i * ks + j] = v[q] + (i == j ? shf : 0.0f);
+          }
+        }
+      }
+    }
+    if (tid == 0) { sflag[0] = 0; sflag[1] = 0; }
+    __syncthreads();
+    for (int j0 = 0; j0 < k; j0 += 32) {
+      const int jb = min(32, k - j0);
+      // (1) diagonal block in registers of warp 0 (padded rows/columns: identity)
+      if (warp == 0) {
+        float x[32];
+        const int r = lane;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          x[c] = (r < jb && c < jb) ? (c <= r ? A[(size_t)(j0 + r) * ks + j0 + c] : 0.0f) : (r == c ? 1.0f : 0.0f);
+        int bad = 0, clamped = 0;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          float piv = __shfl_sync(0xffffffffu, x[t], t);
+          if (t < jb) {
+            if (!isfinite(piv)) bad = 1;
+            else if (!(piv > pfloor)) {
+              piv = raised_pivot(G, k, j0 + t, shift, pfloor);
+              clamped = 1;
+            }
+          }
+          const float y = rsqrt_newton(piv);
+          if (r == t) { x[t] = piv * y; rinv[t] = y; }
+          const float lt = (r > t) ? x[t] * y : 0.0f;  // L[r][t]
+          if (r > t) x[t] = lt;
+#pragma unroll
+          for (int c = t + 1; c < 32; ++c) {
+            const float lc = __shfl_sync(0xffffffffu, lt, c);  // L[c][t]
+            x[c] = fmaf(-lt, lc, x[c]);
+          }
+        }
+        if (r < jb) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (c <= r) A[(size_t)(j0 + r) * ks + j0 + c] = x[c];
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        clamped = __any_sync(0xffffffffu, clamped);
+        if (lane == 0) { if (bad) sflag[0] = 1; if (clamped) sflag[1] = 1; }
+      }
+      __syncthreads();
+      if (sflag[0]) break;
+      // (2) panel rows below: x_s = a_s / L_ss, a_t -= x_s L_ts (t > s)
+      const int first = j0 + jb;
+      for (int i = first + tid; i < k; i += CTA_THREADS) {
+        float a[32];
+        float* row = A + (size_t)i * ks + j0;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) a[q] = q < jb ? row[q] : 0.0f;
+#pragma unroll
+        for (int sidx = 0; sidx < 32; ++sidx) {
+          if (sidx < jb) {
+            a[sidx] *= rinv[sidx];
+            const float xs = a[sidx];
+            const float* lcol = A + (size_t)j0 * ks + j0 + sidx;  // L[t][s] = lcol[t * ks]
+#pragma unroll
+            for (int t = sidx + 1; t < 32; ++t)
+              if (t < jb) a[t] = fmaf(-xs, lcol[(size_t)t * ks], a[t]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (q < jb) row[q] = a[q];
+      }
+      __syncthreads();
+      // (3) trailing update of the lower triangle [first, k)^2, 4 x 4 tiles
+      const int n = k - first;
+      if (n > 0) {
+        const int T = (n + 3) / 4, ntiles = T * (T + 1) / 2;
+        for (int tile = tid; tile < ntiles; tile += CTA_THREADS) {
+          int bi = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+          while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+          while (bi * (bi + 1) / 2 > tile) --bi;
+          const int bj = tile - bi * (bi + 1) / 2;  // bj <= bi
+          const int i0 = first + 4 * bi, c0 = first + 4 * bj;
+          float acc[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+          const float* pi[4];
+          const float* pc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            pi[u] = A + (size_t)min(i0 + u, k - 1) * ks + j0;
+            pc[u] = A + (size_t)min(c0 + u, k - 1) * ks + j0;
+          }
+          for (int t = 0; t < jb; ++t) {  // rows an odd stride apart: conflict-free scalar reads
+            float ri[4], rc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { ri[u] = pi[u][t]; rc[u] = pc[u][t]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ri[u], rc[v], acc[u][v]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int i = i0 + u, c = c0 + v;
+              if (i < k && c <= i) A[(size_t)i * ks + c] -= acc[u][v];
+            }
+        }
+      }
+      __syncthreads();
+    }
+    if (!sflag[0]) {
+      if (tid == 0) {
+        if (sflag[1]) raise_flag(flags, KFAC_FLAG_CHOL_SHIFTED);
+        if (shift_out) *shift_out = shift;
+      }
+      ok = 1;
+      break;
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) {
+      raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : KFAC_FLAG_NONFINITE);
+      if (shift_out) *shift_out = 0.0;
+    }
+    for (int e = tid; e < k * k; e += CTA_THREADS) {
+      const int i = e / k, j = e - i * k;
+      const double g = G[(size_t)i * k + i];
+      L32[e] = (i == j) ? (float)sqrt(isfinite(g) && g > 1e-30 ? g : 1.0) : 0.0f;
+    }
+  } else {
+    for (int e = tid; e < k * k; e += CTA_THREADS) {
+      const int i = e / k, j = e - i * k;
+      L32[e] = (j <= i) ? A[(size_t)i * ks + j] : 0.0f;
+    }
+  }
+  if (stats && tid == 0) atomicAdd(stats + STAT_CHOL, 1ull);
+}
+
 }  // namespace
 
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
-                         unsigned long long* stats, cudaStream_t s, double* shift_out) {
+                         unsigned long long* stats, cudaStream_t s, double* shift_out, const float* G32,
+                         long long ld32) {
   if (k <= 0) return cudaSuccess;
+  if (!fp64 && k <= CTA_KMAX && cta_smem_bytes(k) <= (size_t)kSmemOptin) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_chol_cta_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_chol_cta_f32<<<1, CTA_THREADS, cta_smem_bytes(k), s>>>(G, G32, ld32, k, shift_rel, L32, flags, stats,
+                                                               shift_out);
+    note_launch();
+    return cudaGetLastError();
+  }
   return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s, shift_out)
               : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s, shift_out);
 }
@@ -368,7 +614,7 @@ __global__ void __launch_bounds__(32) k_diag_block_inv(const float* __restrict__
     float v = (i == c) ? 1.0f : 0.0f;
 #pragma unroll
     for (int u = 0; u < i; ++u) v = fmaf(-Lb[i][u], x[u], v);
-    x[i] = (i >= c) ? v / Lb[i][i] : 0.0f;
+    x[i] = (i >= c) ? v * __frcp_rn(Lb[i][i]) : 0.0f;  // correctly rounded reciprocal, no divide slow path
   }
   float* out = Dinv + (size_t)blk * TR_RB * TR_RB;
 #pragma unroll
@@ -431,6 +677,83 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restri
     __syncthreads();
   }
 }
+// The same solve with the whole lower factor resident in shared memory (for
+// k <= 32 * TS_MAXT): the 32-row block rows of L are packed once (their
+// diagonal blocks replaced by the block inverses) and the CTA's 32 columns of
+// Yt are kept column-major, so the block substitution runs from shared memory
+// with 128-bit reads: per 4 steps of the inner product, one float4 of the
+// column and one broadcast float4 of each of the thread's 4 rows of L.
+constexpr int TS_MAXT = 9;
+
+__host__ __device__ inline size_t trsm_smem_floats(int T) {
+  return (size_t)1024 * T * (T + 1) / 2 + (size_t)32 * (32 * T + 4) + 32 * 33;
+}
+
+__global__ void __launch_bounds__(TR_THREADS) k_trsm_lower_smem(const float* __restrict__ L,
+                                                                 const float* __restrict__ Dinv, int k, int T,
+                                                                 const float* __restrict__ Yt, long long ldy,
+                                                                 float* __restrict__ Qt, long long ldq, int d) {
+  extern __shared__ __align__(16) float tsm[];
+  const int kpad = 32 * T, xs = kpad + 4;
+  float* Lp = tsm;                                     // block row I at 1024 I (I+1) / 2: [32][32 (I+1)]
+  float* Xc = Lp + (size_t)1024 * T * (T + 1) / 2;     // [32 columns][xs]: the solution, column-major
+  float* Ts = Xc + (size_t)32 * xs;                    // [32][33]: one block of partial sums
+  const int tid = threadIdx.x, c = tid & 31, w = tid >> 5;  // w: rows 4w..4w+3 of a block
+  const int col0 = blockIdx.x * TR_COLS, col = col0 + c;
+  for (int I = 0; I < T; ++I) {
+    const int width = 32 * (I + 1);
+    float* Lb = Lp + (size_t)512 * I * (I + 1);
+    for (int a = w; a < 32; a += TR_THREADS / 32) {  // warp per row, lanes along the row
+      const int row = 32 * I + a;
+      for (int cc = c; cc < width; cc += 32) {
+        if (cc >= 32 * I) cp_async4(Lb + (size_t)a * width + cc, Dinv + (size_t)I * 1024 + a * 32 + (cc - 32 * I), true);
+        else cp_async4(Lb + (size_t)a * width + cc, L + (size_t)(row < k ? row : 0) * k + cc, row < k);
+      }
+    }
+  }
+  for (int i = w; i < kpad; i += TR_THREADS / 32) {  // warp per row of Yt, lanes over the 32 columns
+    const bool ok = i < k && col < d;
+    cp_async4(Xc + (size_t)c * xs + i, Yt + (ok ? (long long)i * ldy + col : 0), ok);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const float* xcol = Xc + (size_t)c * xs;
+  for (int I = 0; I < T; ++I) {
+    const int width = 32 * (I + 1);
+    const float* Lb = Lp + (size_t)512 * I * (I + 1);
+    float acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = xcol[32 * I + 4 * w + u];
+    for (int mm = 0; mm < 32 * I; mm += 4) {
+      const float4 x = *reinterpret_cast<const float4*>(xcol + mm);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 l = *reinterpret_cast<const float4*>(Lb + (size_t)(4 * w + u) * width + mm);
+        acc[u] = fmaf(-l.x, x.x, acc[u]);
+        acc[u] = fmaf(-l.y, x.y, acc[u]);
+        acc[u] = fmaf(-l.z, x.z, acc[u]);
+        acc[u] = fmaf(-l.w, x.w, acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Ts[c * 33 + 4 * w + u] = acc[u];
+    __syncthreads();
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int v = 0; v < 32; ++v) {
+      const float tv = Ts[c * 33 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) out[u] = fmaf(Lb[(size_t)(4 * w + u) * width + 32 * I + v], tv, out[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = 32 * I + 4 * w + u;
+      Xc[(size_t)c * xs + row] = out[u];
+      if (row < k && col < d) Qt[(long long)row * ldq + col] = out[u];
+    }
+    __syncthreads();
+  }
+}
 }  // namespace
 
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
@@ -447,6 +770,22 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
   }
   k_diag_block_inv<<<(k + TR_RB - 1) / TR_RB, 32, 0, s>>>(L, k, dinv_ws);
   note_launch();
+  const int T = kpad / TR_RB;
+  if (T <= TS_MAXT) {
+    static bool attr_smem = false;
+    if (!attr_smem) {
+      cudaError_t e = cudaFuncSetAttribute(k_trsm_lower_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
+      if (e != cudaSuccess) return e;
+      attr_smem = true;
+    }
+    const size_t smem_all = sizeof(float) * trsm_smem_floats(T);
+    if (smem_all <= (size_t)kSmemOptin) {
+      k_trsm_lower_smem<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem_all, s>>>(L, dinv_ws, k, T, Yt, ldy, Qt,
+                                                                                  ldq, d);
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
   k_trsm_lower<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem, s>>>(L, dinv_ws, k, Yt, ldy, Qt, ldq, d);
   note_launch();
   return cudaGetLastError();

@@ -26,6 +26,21 @@ unsigned long long launch_count();
 enum { STAT_SWEEPS = 0, STAT_EIG_SOLVES = 1, STAT_CHOL = 2, STAT_CHOL_RETRY = 3, STAT_COUNT = 4 };
 
 // Device-side status word: kernels OR KFAC_FLAG_* bits into it.
+// Asynchronous 4-byte global -> shared copy (zero-filled when !valid). A loop
+// of plain loads feeding shared memory waits out the L2 latency (~1000 cycles
+// for a far-die hit) once per iteration; these copies are all in flight at
+// once and cp_async_wait_all() waits for them together.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src, bool valid) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(gmem_src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void raise_flag(int* flags, int bit) {
   if (flags) atomicOr(flags, bit);
 }
@@ -85,8 +100,9 @@ cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s);
 cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s);
 // out[i, j] = sum_z part[z][i, j] in FP64 (n x n), optionally symmetrised as
 // (S + S^T) / 2. part has row stride ldp and z stride zstride.
+// out32 (optional): an FP32 copy of the result, n x n dense.
 cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out,
-                              int ldo, int symmetrize, int* flags, cudaStream_t s);
+                              int ldo, int symmetrize, int* flags, cudaStream_t s, float* out32 = nullptr);
 cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, float* out, long long ldo,
                           cudaStream_t s);
 cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int cols, double* out, long long ldo,
@@ -99,8 +115,11 @@ cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int col
 // the FP32 rounding level is raised to it (flag CHOL_SHIFTED); a non-finite
 // pivot retries with a growing shift (bounded) and then fails (CHOL_FAILED).
 // shift_out (optional, device) receives the shift the successful attempt used.
+// G32 (optional, row stride ld32): an FP32 copy of G that the FP32 path reads
+// instead of converting G (a conversion runs on the FP64 pipe).
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
-                         unsigned long long* stats, cudaStream_t s, double* shift_out = nullptr);
+                         unsigned long long* stats, cudaStream_t s, double* shift_out = nullptr,
+                         const float* G32 = nullptr, long long ld32 = 0);
 
 // Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
 // dinv_ws: ceil(k/32) * 1024 floats of workspace (inverses of L's diagonal blocks).
@@ -112,10 +131,12 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
 // eig_scratch_floats(k) floats (the Cholesky factor and the shift it used).
 inline size_t eig_scratch_floats(int k) { return (((size_t)k * k + 1) & ~(size_t)1) + 4; }
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
-                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s);
+                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s,
+                           const float* C32 = nullptr, long long ld32 = 0);
 
 // One FP64 refinement step (Ogita-Aishima) of eigenpairs (X, lam) of C.
-// Workspace: 5 k*k doubles. X and lam are updated in place.
+// Workspace: eig_refine_doubles(k) doubles. X and lam are updated in place.
+inline size_t eig_refine_doubles(int k) { return 5 * (size_t)k * k + 3 * 128; }
 cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, double* work, int* flags,
                            cudaStream_t s);
 

@@ -133,16 +133,19 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   if (tid == 0) s_total = 0;
 
   // ---- initial blocks (round 0 positions) from the factor ------------------
+  // (asynchronous copies, all in flight at once; zero outside the factor)
   {
     const int blk[2] = {rr_player(rank, 0, nb), rr_player(nb - 1 - rank, 0, nb)};
     for (int sl = 0; sl < 2; ++sl) {
       const int c0 = min(k, blk[sl] * b), nc = min(k, c0 + b) - c0;
       const int dst = sl * slot;
       for (int e = tid; e < b * kp; e += EIG_THREADS) {
-        int c = e / kp, i = e % kp;
-        esm[dst + e] = (c < nc && i < k && i >= c0 + c) ? __ldg(a.L + (size_t)i * k + c0 + c) : 0.0f;
+        const int c = e / kp, i = e % kp;
+        const bool ok = c < nc && i < k && i >= c0 + c;
+        cp_async4(esm + dst + e, a.L + (ok ? (size_t)i * k + c0 + c : 0), ok);
       }
     }
+    cp_async_wait_all();
   }
   // Every CTA has its blocks before the first distributed shared memory store.
   cluster.sync();
@@ -247,50 +250,90 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   cluster.sync();  // no CTA leaves while others may still address its shared memory
 }
 
-// Refinement combine (one CTA): E from R = I - X^T X (given as XtX) and S.
-__global__ void __launch_bounds__(1024) k_refine_combine(const double* __restrict__ C, const double* __restrict__ XtX,
-                                                          const double* __restrict__ S, int k, double* __restrict__ E,
-                                                          double* __restrict__ lam, int* flags) {
-  __shared__ double red[3][32];
+// Refinement combine, spread over many CTAs (FP64 runs at ~2 operations per
+// clock per SM, so one CTA would spend ~0.2 ms on the k^2 divisions):
+//  k_refine_norms: lam_i = S_ii / (X^T X)_ii and per-CTA partial sums of
+//    ||S - diag(lam)||_F^2, ||C||_F^2, ||R||_F^2 (R = I - X^T X);
+//  k_refine_E: the separation threshold delta = 2 (||S - diag(lam)|| +
+//    ||C|| ||R||) from the partials (same fixed order in every CTA), then
+//    E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) where |lam_j - lam_i| > delta,
+//    R_ij / 2 otherwise.
+constexpr int REF_THREADS = 256;
+constexpr int REF_MAX_BLOCKS = 128;
+
+__device__ __forceinline__ double block_sum_ref(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < REF_THREADS / 32; ++w) t += red[w];
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(REF_THREADS) k_refine_norms(const double* __restrict__ C,
+                                                               const double* __restrict__ XtX,
+                                                               const double* __restrict__ S, int k,
+                                                               double* __restrict__ lam, double* __restrict__ part) {
+  __shared__ double red[REF_THREADS / 32];
+  const long long kk = (long long)k * k, step = (long long)gridDim.x * REF_THREADS;
+  const long long g0 = (long long)blockIdx.x * REF_THREADS + threadIdx.x;
+  if (g0 < k) lam[g0] = S[(size_t)g0 * k + g0] / XtX[(size_t)g0 * k + g0];  // S_ii / (1 - R_ii)
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (long long e = g0; e < kk; e += step) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    const double sv = S[e] - (i == j ? S[e] / XtX[e] : 0.0);
+    const double rv = (i == j ? 1.0 : 0.0) - XtX[e];
+    a = fma(sv, sv, a);
+    b = fma(C[e], C[e], b);
+    c = fma(rv, rv, c);
+  }
+  const double A = block_sum_ref(a, red);
+  const double Bn = block_sum_ref(b, red);
+  const double Cn = block_sum_ref(c, red);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x + 0] = A;
+    part[3 * blockIdx.x + 1] = Bn;
+    part[3 * blockIdx.x + 2] = Cn;
+  }
+}
+
+__global__ void __launch_bounds__(REF_THREADS) k_refine_E(const double* __restrict__ XtX,
+                                                           const double* __restrict__ S, int k,
+                                                           const double* __restrict__ lam,
+                                                           const double* __restrict__ part, int nparts,
+                                                           double* __restrict__ E, int* flags) {
   __shared__ double s_delta;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < k; i += blockDim.x) {
-    double xx = XtX[(size_t)i * k + i];
-    lam[i] = S[(size_t)i * k + i] / xx;  // S_ii / (1 - R_ii)
-  }
-  __syncthreads();
-  double a = 0.0, b = 0.0, c = 0.0;  // ||S - diag(lam)||_F^2, ||C||_F^2, ||R||_F^2
-  for (long long e = tid; e < (long long)k * k; e += blockDim.x) {
-    int i = (int)(e / k), j = (int)(e % k);
-    double sv = S[e] - (i == j ? lam[i] : 0.0);
-    double rv = (i == j ? 1.0 : 0.0) - XtX[e];
-    a += sv * sv;
-    b += C[e] * C[e];
-    c += rv * rv;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-  }
-  if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
-  __syncthreads();
-  if (tid == 0) {
-    double A = 0, Bn = 0, Cn = 0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) { A += red[0][w]; Bn += red[1][w]; Cn += red[2][w]; }
-    s_delta = 2.0 * (sqrt(A) + sqrt(Bn) * sqrt(Cn));
-    if (!isfinite(s_delta)) raise_flag(flags, KFAC_FLAG_NONFINITE);
+  if (threadIdx.x < 32) {  // fixed order: lane-strided partials, then a fixed shuffle tree
+    double A = 0.0, Bn = 0.0, Cn = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += 32) {
+      A += part[3 * p];
+      Bn += part[3 * p + 1];
+      Cn += part[3 * p + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      A += __shfl_xor_sync(0xffffffffu, A, o);
+      Bn += __shfl_xor_sync(0xffffffffu, Bn, o);
+      Cn += __shfl_xor_sync(0xffffffffu, Cn, o);
+    }
+    if (threadIdx.x == 0) {
+      s_delta = 2.0 * (sqrt(A) + sqrt(Bn) * sqrt(Cn));
+      if (blockIdx.x == 0 && !isfinite(s_delta)) raise_flag(flags, KFAC_FLAG_NONFINITE);
+    }
   }
   __syncthreads();
   const double delta = s_delta;
-  for (long long e = tid; e < (long long)k * k; e += blockDim.x) {
-    int i = (int)(e / k), j = (int)(e % k);
-    double rij = (i == j ? 1.0 : 0.0) - XtX[e];
+  const long long kk = (long long)k * k, step = (long long)gridDim.x * REF_THREADS;
+  for (long long e = (long long)blockIdx.x * REF_THREADS + threadIdx.x; e < kk; e += step) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    const double rij = (i == j ? 1.0 : 0.0) - XtX[e];
     double v;
     if (i == j) {
       v = 0.5 * rij;
     } else {
-      double gap = lam[j] - lam[i];
+      const double gap = lam[j] - lam[i];
       v = (fabs(gap) > delta) ? (S[e] + lam[j] * rij) / gap : 0.5 * rij;
     }
     E[e] = v;
@@ -301,27 +344,40 @@ __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ 
                                                       int k, int r, float lambda, float* __restrict__ P32,
                                                       float* __restrict__ D, float* __restrict__ coef,
                                                       float* __restrict__ Uout, long long ldu) {
-  extern __shared__ int order[];  // order[rank] = index
+  // Every CTA ranks the k eigenvalues (from shared memory) and copies its
+  // slice of the selected columns; CTA 0 also writes D and the coefficients.
+  // Ranking compares order-preserving integer keys of the FP64 values (an
+  // FP64 compare would run on the FP64 pipe at ~1/64 rate).
+  extern __shared__ unsigned long long sel_sm[];
+  unsigned long long* key = sel_sm;                 // k keys, NaN ranked last
+  int* order = reinterpret_cast<int*>(sel_sm + k);  // order[rank] = index
   const int tid = threadIdx.x;
   for (int i = tid; i < k; i += blockDim.x) {
-    double li = lam[i];
-    if (li != li) li = -INFINITY;
+    const long long bits = __double_as_longlong(lam[i]);
+    const bool nan = (bits & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+    key[i] = nan ? 0ull : (bits < 0 ? ~(unsigned long long)bits : (unsigned long long)bits | (1ull << 63));
+  }
+  __syncthreads();
+  for (int i = tid; i < k; i += blockDim.x) {
+    const unsigned long long ki = key[i];
     int rk = 0;
     for (int j = 0; j < k; ++j) {
-      double lj = lam[j];
-      if (lj != lj) lj = -INFINITY;
-      rk += (lj > li) || (lj == li && j < i);
+      const unsigned long long kj = key[j];
+      rk += (kj > ki) || (kj == ki && j < i);
     }
     order[rk] = i;
   }
   __syncthreads();
-  for (int t = tid; t < r; t += blockDim.x) {
-    double v = lam[order[t]];
-    double dv = v > 0.0 ? v : 0.0;
-    if (D) D[t] = (float)v;
-    if (coef) coef[t] = (float)(1.0 / (dv + (double)lambda) - 1.0 / (double)lambda);
+  if (blockIdx.x == 0) {
+    for (int t = tid; t < r; t += blockDim.x) {
+      double v = lam[order[t]];
+      double dv = v > 0.0 ? v : 0.0;
+      if (D) D[t] = (float)v;
+      if (coef) coef[t] = (float)(1.0 / (dv + (double)lambda) - 1.0 / (double)lambda);
+    }
   }
-  for (long long e = tid; e < (long long)k * r; e += blockDim.x) {
+  const long long total = (long long)k * r, step = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < total; e += step) {
     int row = (int)(e / r), t = (int)(e % r);
     float v = (float)X[(size_t)row * k + order[t]];
     if (P32) P32[e] = v;
@@ -358,12 +414,13 @@ static cudaError_t launch_eig(const EigArgs& a, int nc, size_t smem, cudaStream_
 }
 
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
-                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s) {
+                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s,
+                           const float* C32, long long ld32) {
   if (k <= 0) return cudaSuccess;
   // W = L with L L^T = C + sI, factorised on a cluster in FP32; the shift it
   // used (grown on breakdown) is stored after the factor.
   double* shift = reinterpret_cast<double*>(gscratch + (((size_t)k * k + 1) & ~(size_t)1));
-  cudaError_t e = chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift);
+  cudaError_t e = chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift, C32, ld32);
   if (e != cudaSuccess) return e;
   // b = ceil(k / 2nc) <= 8 where the cluster allows it: a cross round's b pairs
   // then leave each sub-partition at most two busy warps.
@@ -404,7 +461,15 @@ cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, doubl
   // S = X^T (C X)
   g.A = X; g.sam = 1; g.sak = k; g.B = CX; g.sbn = 1; g.sbk = k; g.D = S; g.ldd = k;
   if ((e = gemm_simt_f64(g, s)) != cudaSuccess) return e;
-  k_refine_combine<<<1, 1024, 0, s>>>(C, XtX, S, k, E, lam, flags);
+  {
+    const long long kk2 = (long long)k * k;
+    int nb = (int)((kk2 + 4 * REF_THREADS - 1) / (4 * REF_THREADS));
+    nb = nb < 1 ? 1 : (nb > REF_MAX_BLOCKS ? REF_MAX_BLOCKS : nb);
+    double* part = work + 5 * kk;  // 3 * REF_MAX_BLOCKS doubles after the five k x k blocks
+    k_refine_norms<<<nb, REF_THREADS, 0, s>>>(C, XtX, S, k, lam, part);
+    note_launch();
+    k_refine_E<<<nb, REF_THREADS, 0, s>>>(XtX, S, k, lam, part, nb, E, flags);
+  }
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // Xn = X + X E
@@ -417,7 +482,11 @@ cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, doubl
 cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* P32, float* D,
                        float* coef, float* Uout, long long ldu, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  k_eig_select<<<1, 1024, sizeof(int) * k, s>>>(X, lam, k, r, lambda, P32, D, coef, Uout, ldu);
+  const long long total = (long long)k * r;
+  int grid = (int)((total + 4095) / 4096);
+  grid = grid < 1 ? 1 : (grid > 152 ? 152 : grid);
+  k_eig_select<<<grid, 1024, (sizeof(double) + sizeof(int)) * k + 8, s>>>(X, lam, k, r, lambda, P32, D, coef, Uout,
+                                                                           ldu);
   note_launch();
   return cudaGetLastError();
 }

@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(256) k_gemm_f64_t16(GemmDesc<double> g) {
 }
 
 __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
-                                double* __restrict__ out, int ldo, int symmetrize, int* flags) {
+                                double* __restrict__ out, int ldo, int symmetrize, float* __restrict__ out32,
+                                int* flags) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)n * n) return;
   int i = (int)(idx / n), j = (int)(idx % n);
@@ -145,6 +146,7 @@ __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long
   }
   if (!isfinite(s)) raise_flag(flags, KFAC_FLAG_NONFINITE);
   out[(long long)i * ldo + j] = s;
+  if (out32) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
 }
 
 __global__ void k_transpose(const float* __restrict__ in, long long ldi, int rows, int cols, float* __restrict__ out,
@@ -196,11 +198,11 @@ cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s) {
 }
 
 cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out, int ldo,
-                              int symmetrize, int* flags, cudaStream_t s) {
+                              int symmetrize, int* flags, cudaStream_t s, float* out32) {
   long long tot = (long long)n * n;
   if (tot == 0) return cudaSuccess;
   k_reduce_splitk<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, zstride, n, ldp, out, ldo, symmetrize,
-                                                                  flags);
+                                                                  out32, flags);
   note_launch();
   return cudaGetLastError();
 }
