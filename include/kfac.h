@@ -111,6 +111,23 @@ KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t m
 KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X, int ldx, float rho,
                                     kfac_precision prec, float* F, int ldf);
 
+/* One factor of a grouped EA update (arguments as kfac_ea_update). */
+typedef struct {
+  int d, n;
+  const float* X;
+  int ldx;
+  float rho;
+  kfac_precision prec;
+  float* F;
+  int ldf;
+} kfac_ea_desc;
+
+/* kfac_ea_update for `count` factors (every layer's forward and backward
+ * factor, Alg. 1), enqueued on up to 8 streams forked from the context stream
+ * (event fork/join, graph-capturable; no workspace). All descriptors are
+ * checked before anything is enqueued; factors must not alias each other. */
+KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac_ea_desc* descs);
+
 /* Randomized low-rank eigendecomposition + damping coefficients of one
  * symmetric PSD factor F (d x d), Alg. 3 with power iterations (Sec. 2.2):
  *     Y = F Omega; Q = orth(Y); repeat power_iters times: Q = orth(F Q);
@@ -168,6 +185,31 @@ KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const fl
                                        const float* U_g, int ld_ug, const float* coef_g, int r_g,
                                        float lambda, kfac_precision prec, float* S, int lds);
 
+/* One layer of a grouped preconditioner apply (arguments as kfac_precondition). */
+typedef struct {
+  int d_g, d_a;
+  const float* J;
+  int ldj;
+  const float* U_a;
+  int ld_ua;
+  const float* coef_a;
+  int r_a;
+  const float* U_g;
+  int ld_ug;
+  const float* coef_g;
+  int r_g;
+  float lambda;
+  kfac_precision prec;
+  float* S;
+  int lds;
+} kfac_precond_desc;
+
+/* kfac_precondition for `count` layers (the per-layer loop of Alg. 4),
+ * enqueued on up to 8 streams forked from the context stream, each stream with
+ * its own workspace slice (graph-capturable once kfac_reserve or an earlier
+ * call has sized the workspace). All descriptors are checked first. */
+KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const kfac_precond_desc* descs);
+
 /* Allocation-free variant of kfac_precondition (the paper has no counterpart:
  * this is a deployment interface). It is for callers that cannot allocate GPU
  * memory at call time: code that runs while a CUDA graph is being captured,
@@ -215,6 +257,13 @@ typedef enum {
   KFAC_OPT_CHOLQR_INNER_PASSES = 5, /* passes for a basis that only feeds the next power
                                        iteration [3], 1..6; fewer passes save time but
                                        lose accuracy on ill-conditioned sketches */
+  KFAC_OPT_BASIS_POLISH = 7,        /* 1 [default]: after the final orthonormalisation the
+                                       Rayleigh-Ritz step uses Q M, M = (3I - Q^T Q)/2 (one
+                                       Newton-Schulz step, applied to the k x k projected
+                                       matrix and to the eigenvectors), which restores
+                                       orthonormality to second order when the sketch is so
+                                       ill-conditioned that FP32-stored CholeskyQR3 leaves
+                                       ~1e-4; 0: off */
   KFAC_OPT_CHOLQR_FP32_PASSES = 6   /* leading passes of every orthonormalisation whose
                                        Cholesky runs in FP32 instead of FP64 [1], 0..5; the
                                        last pass of a basis always runs in FP64. The first,
@@ -241,7 +290,7 @@ KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const floa
  * and for i < min(max_stages, KFAC_NUM_STAGES) stores the stage name (static
  * string), the summed device milliseconds and the number of timed launches,
  * sets *n_stages to the number of stages written, and clears the totals. */
-#define KFAC_NUM_STAGES 15
+#define KFAC_NUM_STAGES 16
 KFAC_API kfac_status kfac_profile_enable(kfac_ctx* ctx, int on);
 KFAC_API kfac_status kfac_profile_read(kfac_ctx* ctx, const char** names, double* total_ms, int* launches,
                                        int max_stages, int* n_stages);

@@ -14,11 +14,12 @@
 namespace {
 enum Stage {
   ST_EA, ST_TRANSPOSE, ST_SKETCH, ST_GRAM, ST_CHOL, ST_TRSM, ST_PROJ, ST_EIG, ST_REFINE, ST_SELECT, ST_LIFT,
-  ST_APPLY_T, ST_APPLY_M, ST_APPLY_T2, ST_APPLY_S, ST_COUNT
+  ST_APPLY_T, ST_APPLY_M, ST_APPLY_T2, ST_APPLY_S, ST_POLISH, ST_COUNT
 };
 const char* const kStageNames[ST_COUNT] = {
     "ea_syrk", "omega_transpose", "sketch_gemm", "cholqr_gram", "cholqr_chol", "cholqr_trsm", "projection_gram",
-    "eig_jacobi", "eig_refine", "eig_select", "lift_gemm", "apply_T", "apply_M", "apply_T2", "apply_S"};
+    "eig_jacobi", "eig_refine", "eig_select", "lift_gemm", "apply_T", "apply_M", "apply_T2", "apply_S",
+    "basis_polish"};
 static_assert(ST_COUNT == KFAC_NUM_STAGES, "stage table");
 
 // CUDA-event pairs recorded around each kernel group when profiling is on.
@@ -50,6 +51,7 @@ struct kfac_ctx {
   int cholqr_passes = 3;
   int cholqr_inner_passes = 3;
   int cholqr_fp32_passes = 1;
+  int basis_polish = 1;
   double cholqr_shift = 1e-5;
   int eig_refine = 1;
   int eig_max_sweeps = 40;
@@ -268,6 +270,16 @@ kfac_status eigensolve(kfac_ctx* ctx, const double* C, const float* C32, long lo
 }
 
 
+// D = A B for k x k row-major FP64 matrices.
+cudaError_t small_product_f64(const double* A, const double* B, double* D, int k, cudaStream_t s) {
+  GemmDesc<double> g = {};
+  g.M = k; g.N = k; g.K = k; g.alpha = 1.0; g.beta = 0.0; g.zsplit = 1;
+  g.A = A; g.sam = k; g.sak = 1;
+  g.B = B; g.sbn = 1; g.sbk = k;  // B(n, kk) = B[kk][n]
+  g.D = D; g.ldd = k;
+  return gemm_simt_f64(g, s);
+}
+
 kfac_status check_invert(const kfac_invert_desc& a, int* r_out, int* k_out) {
   if (a.d <= 0 || !a.F || a.ldf < a.d || a.rank <= 0 || a.oversample < 0 || a.power_iters < 0 || a.power_iters > 64)
     return KFAC_ERR_INVALID_ARG;
@@ -325,15 +337,39 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     if (st != KFAC_OK) return st;
     std::swap(cur, other);
   }
+  // Newton-Schulz polish of the final basis, in the k x k space: M = (3I - Q^T Q)/2
+  // makes Q M orthonormal to second order; the Rayleigh-Ritz step below uses
+  // Q M (C <- M C M, X <- M X) without touching the d x k basis.
+  double* Mpol = nullptr;
+  if (ctx->basis_polish) {
+    st = gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_POLISH, nullptr);
+    if (st != KFAC_OK) return st;
+    STAGE(ctx, ST_POLISH);
+    CK(polish_factor(at<double>(ctx, L.g), k, s));
+    Mpol = at<double>(ctx, L.g);
+  }
   // Projection C = Q^T F Q = Q^T (F Q): Z^T = Q^T F into `other`, then C = Q^T Z.
   st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);
   if (st != KFAC_OK) return st;
   double* C = at<double>(ctx, L.c);
   st = gram_f64(ctx, L, cur, other, L.dp, k, d, KFAC_PREC_FP32, C, ST_PROJ, at<float>(ctx, L.c32));
   if (st != KFAC_OK) return st;
+  if (Mpol) {  // C <- M (C M), with its FP32 copy for the eigensolver's factorisation
+    STAGE(ctx, ST_POLISH);
+    double* T = at<double>(ctx, L.work);
+    CK(small_product_f64(C, Mpol, T, k, s));
+    CK(small_product_f64(Mpol, T, C, k, s));
+    CK(convert_f64_to_f32(C, (long long)k * k, at<float>(ctx, L.c32), s));
+  }
   st = eigensolve(ctx, C, at<float>(ctx, L.c32), k, k, at<double>(ctx, L.x), at<double>(ctx, L.lam),
                   at<double>(ctx, L.work), at<float>(ctx, L.jac));
   if (st != KFAC_OK) return st;
+  if (Mpol) {  // eigenvectors in the polished basis: X <- M X
+    STAGE(ctx, ST_POLISH);
+    double* T = at<double>(ctx, L.work);
+    CK(small_product_f64(Mpol, at<double>(ctx, L.x), T, k, s));
+    CK(cudaMemcpyAsync(at<double>(ctx, L.x), T, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, s));
+  }
   float* P32 = at<float>(ctx, L.p32);
   {
     STAGE(ctx, ST_SELECT);
@@ -551,6 +587,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       if (v < 1 || v > 6) return KFAC_ERR_INVALID_ARG;
       ctx->cholqr_inner_passes = (int)v;
       return KFAC_OK;
+    case KFAC_OPT_BASIS_POLISH:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->basis_polish = (int)v;
+      return KFAC_OK;
     case KFAC_OPT_CHOLQR_FP32_PASSES:
       if (v < 0 || v > 5) return KFAC_ERR_INVALID_ARG;
       ctx->cholqr_fp32_passes = (int)v;
@@ -625,6 +665,50 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
   return ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags) == cudaSuccess ? KFAC_OK : KFAC_ERR_CUDA;
 }
 
+static kfac_status check_ea(const kfac_ea_desc& a) {
+  if (a.d < 0 || a.n < 0 || a.ldf < a.d || (a.d > 0 && !a.F) || (a.n > 0 && (!a.X || a.ldx < a.n)))
+    return KFAC_ERR_INVALID_ARG;
+  if (!(a.rho >= 0.0f && a.rho <= 1.0f) || a.prec < KFAC_PREC_FP32 || a.prec > KFAC_PREC_BF16)
+    return KFAC_ERR_INVALID_ARG;
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac_ea_desc* descs) {
+  if (!ctx || count < 0 || (count > 0 && !descs)) return KFAC_ERR_INVALID_ARG;
+  for (int f = 0; f < count; ++f) {
+    kfac_status st = check_ea(descs[f]);
+    if (st != KFAC_OK) return st;
+  }
+  if (count == 0) return KFAC_OK;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  const int ns = std::min(count, kMaxSideStreams);
+  kfac_status st;
+  if (ns > 1 && (st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
+  cudaStream_t main_s = ctx->stream;
+  if (ns > 1) {
+    CK(cudaEventRecord(ctx->fork_ev, main_s));
+    for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(ctx->side[q], ctx->fork_ev, 0));
+  }
+  kfac_status first_err = KFAC_OK;
+  for (int f = 0; f < count && first_err == KFAC_OK; ++f) {
+    const kfac_ea_desc& a = descs[f];
+    if (a.d == 0) continue;
+    ctx->stream = ns > 1 ? ctx->side[f % ns] : main_s;
+    STAGE(ctx, ST_EA);
+    if (ea_syrk(ctx->stream, a.d, a.n, a.X, a.ldx, a.rho, a.prec, a.F, a.ldf, ctx->dflags) != cudaSuccess)
+      first_err = KFAC_ERR_CUDA;
+  }
+  ctx->stream = main_s;
+  if (ns > 1) {
+    for (int q = 0; q < ns; ++q) {
+      CK(cudaEventRecord(ctx->join_ev[q], ctx->side[q]));
+      CK(cudaStreamWaitEvent(main_s, ctx->join_ev[q], 0));
+    }
+  }
+  return first_err;
+}
+
 KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
                                       int power_iters, float lambda, const float* omega, int ldo,
                                       kfac_precision prec, float* U, int ldu, float* D, float* coef) {
@@ -696,6 +780,60 @@ KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const fl
   if (st != KFAC_OK) return st;
   return precondition_run(ctx, d_g, d_a, J, ldj, U_a, ld_ua, coef_a, r_a, U_g, ld_ug, coef_g, r_g, lambda, prec, S,
                           lds, P, 0);
+}
+
+static kfac_status check_precond(const kfac_precond_desc& a) {
+  if (a.d_g < 0 || a.d_a < 0 || a.r_a < 0 || a.r_g < 0 || a.r_a > a.d_a || a.r_g > a.d_g) return KFAC_ERR_INVALID_ARG;
+  if (!(a.lambda > 0.0f) || a.prec < KFAC_PREC_FP32 || a.prec > KFAC_PREC_BF16) return KFAC_ERR_INVALID_ARG;
+  if ((long long)a.d_g * a.d_a == 0) return KFAC_OK;
+  if (!a.J || a.ldj < a.d_a || !a.S || a.lds < a.d_a || a.S == a.J) return KFAC_ERR_INVALID_ARG;
+  if (a.r_a > 0 && (!a.U_a || a.ld_ua < a.r_a || !a.coef_a)) return KFAC_ERR_INVALID_ARG;
+  if (a.r_g > 0 && (!a.U_g || a.ld_ug < a.r_g || !a.coef_g)) return KFAC_ERR_INVALID_ARG;
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const kfac_precond_desc* descs) {
+  if (!ctx || count < 0 || (count > 0 && !descs)) return KFAC_ERR_INVALID_ARG;
+  for (int f = 0; f < count; ++f) {
+    kfac_status st = check_precond(descs[f]);
+    if (st != KFAC_OK) return st;
+  }
+  if (count == 0) return KFAC_OK;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  std::vector<PrecLayout> lay(count);
+  for (int f = 0; f < count; ++f) lay[f] = prec_layout(descs[f].d_g, descs[f].d_a, descs[f].r_a, descs[f].r_g);
+  const int ns = std::min(count, kMaxSideStreams);
+  std::vector<size_t> base(ns + 1, 0);
+  for (int q = 0; q < ns; ++q) {
+    size_t m = 0;
+    for (int f = q; f < count; f += ns) m = std::max(m, lay[f].total);
+    base[q + 1] = base[q] + ((m + 255) & ~size_t(255));
+  }
+  kfac_status st = ensure_ws(ctx, base[ns]);
+  if (st != KFAC_OK) return st;
+  auto run = [&](int f, size_t off) -> kfac_status {
+    const kfac_precond_desc& a = descs[f];
+    if ((long long)a.d_g * a.d_a == 0) return KFAC_OK;
+    return precondition_run(ctx, a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.coef_a, a.r_a, a.U_g, a.ld_ug,
+                            a.coef_g, a.r_g, a.lambda, a.prec, a.S, a.lds, lay[f], off);
+  };
+  if (count == 1) return run(0, 0);
+  if ((st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
+  cudaStream_t main_s = ctx->stream;
+  CK(cudaEventRecord(ctx->fork_ev, main_s));
+  for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(ctx->side[q], ctx->fork_ev, 0));
+  kfac_status first_err = KFAC_OK;
+  for (int f = 0; f < count && first_err == KFAC_OK; ++f) {
+    ctx->stream = ctx->side[f % ns];
+    first_err = run(f, base[f % ns]);
+  }
+  ctx->stream = main_s;
+  for (int q = 0; q < ns; ++q) {
+    CK(cudaEventRecord(ctx->join_ev[q], ctx->side[q]));
+    CK(cudaStreamWaitEvent(main_s, ctx->join_ev[q], 0));
+  }
+  return first_err;
 }
 
 KFAC_API uint64_t kfac_kernel_launch_count(void) { return (uint64_t)launch_count(); }

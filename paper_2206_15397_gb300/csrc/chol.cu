@@ -625,8 +625,9 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restri
                                                             int k, const float* __restrict__ Yt, long long ldy,
                                                             float* __restrict__ Qt, long long ldq, int d) {
   extern __shared__ __align__(16) float tsm[];
-  float* X = tsm;                          // k x TR_COLS
-  float* Lt = X + (size_t)k * TR_COLS;     // TR_RB x (TR_RB + 1)
+  float* X = tsm;                          // kpad x TR_COLS
+  const int kpad = (k + TR_RB - 1) / TR_RB * TR_RB;
+  float* Lt = X + (size_t)kpad * TR_COLS;  // TR_RB x (TR_RB + 1), after the padded tail rows of X
   const int tid = threadIdx.x, c = tid & 31, r0 = tid >> 5;  // 8 row groups
   const int col0 = blockIdx.x * TR_COLS;
   const int col = col0 + c;

@@ -134,6 +134,12 @@ cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_swe
                            double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s,
                            const float* C32 = nullptr, long long ld32 = 0);
 
+// G <- (3 I - G) / 2 in place (k x k FP64): one Newton-Schulz step towards
+// G^-1/2 for a Gram G = Q^T Q near I, so Q (3I - G)/2 is orthonormal to
+// second order in ||G - I||.
+cudaError_t polish_factor(double* G, int k, cudaStream_t s);
+cudaError_t convert_f64_to_f32(const double* in, long long n, float* out, cudaStream_t s);
+
 // One FP64 refinement step (Ogita-Aishima) of eigenpairs (X, lam) of C.
 // Workspace: eig_refine_doubles(k) doubles. X and lam are updated in place.
 inline size_t eig_refine_doubles(int k) { return 5 * (size_t)k * k + 3 * 128; }

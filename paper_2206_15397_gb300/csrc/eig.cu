@@ -16,6 +16,7 @@
 //     separated pairs, R_ij / 2 otherwise. The products are FP64 GEMMs spread
 //     over many CTAs; it lifts FP32-accurate pairs to near FP64 accuracy.
 //  3. eig_select: descending stable sort, leading r pairs, damping coefficients.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -477,6 +478,37 @@ cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, doubl
   g.ldc = k;
   if ((e = gemm_simt_f64(g, s)) != cudaSuccess) return e;
   return cudaMemcpyAsync(X, Xn, kk * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+namespace {
+__global__ void k_polish_factor(double* __restrict__ G, int k) {
+  const long long kk = (long long)k * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < kk; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    G[e] = (i == j ? 1.5 : 0.0) - 0.5 * G[e];
+  }
+}
+__global__ void k_f64_to_f32(const double* __restrict__ in, long long n, float* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+}  // namespace
+
+cudaError_t polish_factor(double* G, int k, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  const long long kk = (long long)k * k;
+  const int grid = (int)std::min<long long>(304, (kk + 255) / 256);
+  k_polish_factor<<<grid, 256, 0, s>>>(G, k);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t convert_f64_to_f32(const double* in, long long n, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>(304, (n + 255) / 256);
+  k_f64_to_f32<<<grid, 256, 0, s>>>(in, n, out);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* P32, float* D,

@@ -85,12 +85,28 @@ def standard_normal(seed: int, count: int, stream: int = 0) -> np.ndarray:
     return z[:count]
 
 
+def uniform(seed: int, count: int, stream: int = 0) -> np.ndarray:
+    """`count` i.i.d. U(0, 1) FP64 values for (seed, stream) (one Philox block each)."""
+    idx = np.arange(count, dtype=np.uint64)
+    ctr = np.zeros((count, 4), dtype=np.uint32)
+    ctr[:, 0] = (idx & _MASK32).astype(np.uint32)
+    ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
+    ctr[:, 2] = np.uint32(stream & 0xFFFFFFFF)
+    ctr[:, 3] = np.uint32((stream >> 32) & 0xFFFFFFFF)
+    key = np.empty((count, 2), dtype=np.uint32)
+    key[:, 0] = np.uint32(seed & 0xFFFFFFFF)
+    key[:, 1] = np.uint32((seed >> 32) & 0xFFFFFFFF)
+    w = philox4x32_10(ctr, key)
+    return _uniform53(w[:, 0], w[:, 1])
+
+
 # Streams keep the draws of different objects of one workload independent.
 STREAM_OMEGA = 1
 STREAM_HAAR = 2
 STREAM_BATCH = 3
 STREAM_GRAD = 4
 STREAM_MISC = 5
+STREAM_SHAPES = 6
 
 
 def gaussian(seed: int, shape, stream: int = STREAM_MISC, std: float = 1.0) -> np.ndarray:
@@ -114,22 +130,36 @@ def haar(seed: int, d: int, salt: int = 0) -> np.ndarray:
     return q * np.sign(np.diag(r))[None, :]
 
 
+def stiefel(seed: int, d: int, m: int, salt: int = 0) -> np.ndarray:
+    """d x m matrix with orthonormal columns, uniformly distributed (the first m
+    columns of a Haar matrix): QR of a d x m Gaussian with the signs of diag(R)
+    moved into Q."""
+    g = gaussian(seed, (d, m), stream=(STREAM_HAAR << 32) + (1 << 24) + salt)
+    q, r = np.linalg.qr(g)
+    return q * np.sign(np.diag(r))[None, :]
+
+
 def power_spectrum(d: int, alpha: float, scale: float = 1.0) -> np.ndarray:
     i = np.arange(1, d + 1, dtype=np.float64)
     return scale * i ** (-alpha)
 
 
 def activation_batches(seed: int, d: int, n: int, steps: int, alpha: float, scale: float = 1.0,
-                       bias: bool = False, salt: int = 0, v: np.ndarray | None = None):
+                       bias: bool = False, salt: int = 0, v: np.ndarray | None = None,
+                       rank_cap: int | None = None):
     """`steps` batch matrices of shape (d_out, n), d_out = d + bias, drawn as
-    a = z diag(s) V^T (one row of a per sample) and transposed. Returns FP32."""
+    a = z diag(s) V^T (one row of a per sample) and transposed. Returns FP32.
+    With rank_cap = m < d only the m leading directions are drawn (V is d x m,
+    uniform on the Stiefel manifold, s = s_1..s_m): the same recipe with the
+    spectrum cut off at m, which keeps generation O(d m^2) for wide layers."""
+    m = d if rank_cap is None else min(d, int(rank_cap))
     if v is None:
-        v = haar(seed, d, salt)
-    s = power_spectrum(d, alpha, scale)
-    vs = v * s[None, :]                     # V diag(s)
+        v = haar(seed, d, salt) if m == d else stiefel(seed, d, m, salt)
+    s = power_spectrum(m, alpha, scale)
+    vs = v[:, :m] * s[None, :]              # V diag(s)
     out = []
     for t in range(steps):
-        z = gaussian(seed, (n, d), stream=(STREAM_BATCH << 32) + (salt << 16) + t)
+        z = gaussian(seed, (n, m), stream=(STREAM_BATCH << 32) + (salt << 16) + t)
         x = vs @ z.T                        # (d, n) = V diag(s) z^T
         if bias:
             x = np.vstack([x, np.ones((1, n))])
@@ -154,3 +184,13 @@ def low_rank_factor(seed: int, d: int, spectrum, salt: int = 0):
     sp = np.asarray(spectrum, dtype=np.float64)
     v = haar(seed, d, salt)[:, : sp.shape[0]]
     return (v * sp[None, :]) @ v.T, v, sp
+
+
+def batching_stress_shapes(seed: int = 0, count: int = 64):
+    """The batching-stress factor set: per factor d ~ U{256..8192}, decay
+    alpha ~ U[0.8, 2], rank r from {64, 128, 256, 512} capped at d (seeded)."""
+    u = uniform(seed, 3 * count, stream=STREAM_SHAPES << 32)
+    d = 256 + np.minimum((u[0::3] * (8192 - 256 + 1)).astype(np.int64), 8192 - 256)
+    alpha = 0.8 + 1.2 * u[1::3]
+    r = np.array([64, 128, 256, 512])[np.minimum((u[2::3] * 4).astype(np.int64), 3)]
+    return [dict(d=int(di), alpha=float(ai), r=int(min(ri, di))) for di, ai, ri in zip(d, alpha, r)]

@@ -18,7 +18,8 @@ _lib = None
 
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
 OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_sweeps": 3, "eig_tol": 4,
-           "cholqr_inner_passes": 5, "cholqr_fp32_passes": 6}
+           "cholqr_inner_passes": 5, "cholqr_fp32_passes": 6,
+           "basis_polish": 7}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
@@ -32,6 +33,20 @@ class InvertDesc(ctypes.Structure):
                 ("oversample", ctypes.c_int), ("power_iters", ctypes.c_int), ("lam", ctypes.c_float),
                 ("omega", ctypes.c_void_p), ("ldo", ctypes.c_int), ("prec", ctypes.c_int), ("U", ctypes.c_void_p),
                 ("ldu", ctypes.c_int), ("D", ctypes.c_void_p), ("coef", ctypes.c_void_p)]
+
+
+class EaDesc(ctypes.Structure):
+    """Mirror of kfac_ea_desc."""
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int),
+                ("rho", ctypes.c_float), ("prec", ctypes.c_int), ("F", ctypes.c_void_p), ("ldf", ctypes.c_int)]
+
+
+class PrecondDesc(ctypes.Structure):
+    """Mirror of kfac_precond_desc."""
+    _fields_ = [("d_g", ctypes.c_int), ("d_a", ctypes.c_int), ("J", ctypes.c_void_p), ("ldj", ctypes.c_int),
+                ("U_a", ctypes.c_void_p), ("ld_ua", ctypes.c_int), ("coef_a", ctypes.c_void_p), ("r_a", ctypes.c_int),
+                ("U_g", ctypes.c_void_p), ("ld_ug", ctypes.c_int), ("coef_g", ctypes.c_void_p), ("r_g", ctypes.c_int),
+                ("lam", ctypes.c_float), ("prec", ctypes.c_int), ("S", ctypes.c_void_p), ("lds", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -63,6 +78,10 @@ def lib():
                                         ctypes.POINTER(i)]
         L.kfac_kernel_launch_count.restype = ctypes.c_uint64
         L.kfac_rsvd_invert_grouped.argtypes = [vp, i, ctypes.POINTER(InvertDesc)]
+        L.kfac_ea_update_grouped.argtypes = [vp, i, ctypes.POINTER(EaDesc)]
+        L.kfac_ea_update_grouped.restype = i
+        L.kfac_precondition_grouped.argtypes = [vp, i, ctypes.POINTER(PrecondDesc)]
+        L.kfac_precondition_grouped.restype = i
         L.kfac_gemm_nt.argtypes = [vp, i, i, i, vp, i, vp, i, f, f, vp, i, i]
         L.kfac_gemm_nt.restype = i
         L.kfac_rsvd_invert_grouped.restype = i
@@ -280,6 +299,45 @@ def kfac_rsvd_invert_grouped(ctx: Context, items):
         dsc.D, dsc.coef = _vec(D, "D", r).value, _vec(coef, "coef", r).value
         outs.append((U, D, coef))
     _check(lib().kfac_rsvd_invert_grouped(ctx.handle, len(items), descs), "kfac_rsvd_invert_grouped")
+    return outs
+
+
+def kfac_ea_update_grouped(ctx: Context, items):
+    """Grouped kfac_ea_update. items: sequence of dicts with keys X (d x n),
+    F (d x d, updated in place), rho and prec (optional)."""
+    descs = (EaDesc * len(items))()
+    for it, dsc in zip(items, descs):
+        F, X = it["F"], it["X"]
+        d, n = X.shape
+        px, ldx = _mat(X, "X", d, n)
+        pf, ldf = _mat(F, "F", d, d)
+        dsc.d, dsc.n, dsc.X, dsc.ldx = d, n, px.value, ldx
+        dsc.rho, dsc.prec, dsc.F, dsc.ldf = float(it["rho"]), PRECISION[it.get("prec", "fp32")], pf.value, ldf
+    _check(lib().kfac_ea_update_grouped(ctx.handle, len(items), descs), "kfac_ea_update_grouped")
+    return [it["F"] for it in items]
+
+
+def kfac_precondition_grouped(ctx: Context, items):
+    """Grouped kfac_precondition. items: sequence of dicts with keys J, U_a,
+    coef_a, U_g, coef_g, lam, prec (optional) and out (optional S). Returns the
+    list of S."""
+    descs = (PrecondDesc * len(items))()
+    outs = []
+    for it, dsc in zip(items, descs):
+        J, Ua, Ug = it["J"], it["U_a"], it["U_g"]
+        dg, da = J.shape
+        ra, rg = Ua.shape[1], Ug.shape[1]
+        pj, ldj = _mat(J, "J", dg, da)
+        pua, ldua = _mat(Ua, "U_a", da, ra)
+        pug, ldug = _mat(Ug, "U_g", dg, rg)
+        S = torch.empty_like(J) if it.get("out") is None else it["out"]
+        ps, lds = _mat(S, "S", dg, da)
+        dsc.d_g, dsc.d_a, dsc.J, dsc.ldj = dg, da, pj.value, ldj
+        dsc.U_a, dsc.ld_ua, dsc.coef_a, dsc.r_a = pua.value, ldua, _vec(it["coef_a"], "coef_a", ra).value, ra
+        dsc.U_g, dsc.ld_ug, dsc.coef_g, dsc.r_g = pug.value, ldug, _vec(it["coef_g"], "coef_g", rg).value, rg
+        dsc.lam, dsc.prec, dsc.S, dsc.lds = float(it["lam"]), PRECISION[it.get("prec", "fp32")], ps.value, lds
+        outs.append(S)
+    _check(lib().kfac_precondition_grouped(ctx.handle, len(items), descs), "kfac_precondition_grouped")
     return outs
 
 

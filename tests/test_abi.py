@@ -50,6 +50,9 @@ def test_null_arguments_rejected_without_device(libkfac):
     assert libkfac.kfac_destroy(None) == 1
     assert libkfac.kfac_get_status(None, None) == 1
     assert libkfac.kfac_ea_update(None, 4, 4, None, 4, ctypes.c_float(0.9), 0, None, 4) == 1
+    assert libkfac.kfac_ea_update_grouped(None, 1, None) == 1
+    assert libkfac.kfac_precondition_grouped(None, 1, None) == 1
+    assert libkfac.kfac_rsvd_invert_grouped(None, 1, None) == 1
 
 
 def test_create_without_gpu_fails_loudly(libkfac):

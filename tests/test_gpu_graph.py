@@ -1,0 +1,74 @@
+"""CUDA-graph capture of a whole K-factor step (grouped EA update, grouped
+randomized inversion on forked streams, grouped preconditioner apply): once an
+eager call has sized the workspace and created the side streams, the same calls
+record into a graph without allocating, and replays reproduce the eager
+results bit for bit (also after the inputs change in place)."""
+import numpy as np
+import pytest
+
+from paper_2206_15397_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_2206_15397_gb300 import build, kfac
+    build.build()
+    return kfac
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def make_step(kf, ctx, bufs):
+    """One step: EA of both factors, grouped inversion, precondition; every
+    output goes to a preallocated buffer."""
+    kf.kfac_ea_update_grouped(ctx, [dict(X=bufs["xa"], F=bufs["fa"], rho=0.95),
+                                    dict(X=bufs["xg"], F=bufs["fg"], rho=0.95)])
+    kf.kfac_rsvd_invert_grouped(ctx, [
+        dict(F=bufs["fa"], rank=40, oversample=10, power_iters=1, lam=0.1, omega=bufs["oa"], out=bufs["inv_a"]),
+        dict(F=bufs["fg"], rank=30, oversample=10, power_iters=1, lam=0.1, omega=bufs["og"], out=bufs["inv_g"])])
+    (Ua, _, ca), (Ug, _, cg) = bufs["inv_a"], bufs["inv_g"]
+    kf.kfac_precondition_grouped(ctx, [dict(J=bufs["j"], U_a=Ua, coef_a=ca, U_g=Ug, coef_g=cg, lam=0.1,
+                                            out=bufs["s"])])
+
+
+def test_step_captures_and_replays_bitwise(kf):
+    da, dg, n = 513, 300, 64
+    xa = inputs.activation_batches(5, da - 1, n, 2, alpha=1.0, bias=True, salt=1)
+    xg = inputs.activation_batches(5, dg, n, 2, alpha=1.0, salt=2)
+    bufs = dict(xa=cuda(xa[0]), xg=cuda(xg[0]), fa=torch.zeros(da, da, device="cuda"),
+                fg=torch.zeros(dg, dg, device="cuda"), oa=cuda(inputs.omega(5, da, 50, salt=3)),
+                og=cuda(inputs.omega(5, dg, 40, salt=4)), j=cuda(inputs.gradient(5, dg, da, std=0.1)),
+                s=torch.empty(dg, da, device="cuda"))
+    bufs["inv_a"] = (torch.empty(da, 40, device="cuda"), torch.empty(40, device="cuda"), torch.empty(40, device="cuda"))
+    bufs["inv_g"] = (torch.empty(dg, 30, device="cuda"), torch.empty(30, device="cuda"), torch.empty(30, device="cuda"))
+    ctx = kf.Context(0)
+    # eager: two steps (the second sees a non-zero factor) -> reference results
+    fa0, fg0 = bufs["fa"].clone(), bufs["fg"].clone()
+    make_step(kf, ctx, bufs)
+    bufs["xa"].copy_(cuda(xa[1])); bufs["xg"].copy_(cuda(xg[1]))
+    make_step(kf, ctx, bufs)
+    torch.cuda.synchronize()
+    assert kf.kfac_get_status(ctx)[0] == 0
+    ref = [t.clone() for t in (bufs["fa"], bufs["fg"], bufs["s"], *bufs["inv_a"], *bufs["inv_g"])]
+    # capture one step, replay twice from the same starting state
+    bufs["fa"].copy_(fa0); bufs["fg"].copy_(fg0); bufs["xa"].copy_(cuda(xa[0])); bufs["xg"].copy_(cuda(xg[0]))
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ctx.set_stream(torch.cuda.current_stream())
+        make_step(kf, ctx, bufs)
+    ctx.set_stream(torch.cuda.current_stream())
+    graph.replay()
+    bufs["xa"].copy_(cuda(xa[1])); bufs["xg"].copy_(cuda(xg[1]))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert kf.kfac_get_status(ctx)[0] == 0
+    got = [bufs["fa"], bufs["fg"], bufs["s"], *bufs["inv_a"], *bufs["inv_g"]]
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+    ctx.close()

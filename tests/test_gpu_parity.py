@@ -111,6 +111,13 @@ def test_invert_ill_conditioned(kf, ctx):
     check_invert(kf, ctx, f, om, 120, 20, 1, 0.1)
 
 
+def test_invert_wide_sketch_ragged(kf, ctx):
+    """k = 322 (not a multiple of 32, above the shared-memory TRSM and
+    single-CTA Cholesky limits): the tiled TRSM and the cluster factorisations."""
+    f, om = workloads.spectral(13, 1200, 322, alpha=1.0, n=96, steps=6)
+    check_invert(kf, ctx, f, om, 300, 22, 1, 0.1)
+
+
 @pytest.mark.parametrize("d,r,p", [(1, 4, 2), (2, 1, 1), (5, 3, 2), (40, 30, 10), (64, 64, 10)])
 def test_invert_exact_path(kf, ctx, d, r, p):
     """k = r + p >= d: the factor is diagonalised directly (Q = I)."""
