@@ -243,6 +243,25 @@ def roofline(profile: dict, w, q: int, steps: int, stats: dict, traffic=None):
     return out
 
 
+def sketch_roofline(profile: dict, w, q: int, steps: int, prec: str):
+    """Tensor-core roofline of the sketch / power / projection products (d^2 k
+    per pass, (q + 2) passes per factor). FP32-accurate 3xTF32 issues three TF32
+    products per FP32 product, so its FP32-equivalent peak is the TF32 peak / 3;
+    the TF32 peak is the measured BF16 burst peak x 1/2 (nominal TF32:BF16 ratio)."""
+    pk, src = load_peaks()
+    ms, launches = profile.get("sketch_gemm", (0.0, 0))
+    if ms <= 0:
+        return None
+    flops, _ = stage_work("sketch_gemm", w, q, steps)
+    tf32 = pk["bf16_tflops"] / 2.0
+    peak = tf32 / 3.0 if prec == "fp32" else (tf32 if prec == "tf32" else pk["bf16_tflops"])
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "sketch_gemm", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": f"{src} bf16_tflops x "
+            + ("1/2 (TF32) x 1/3 (3xTF32 products)" if prec == "fp32" else ("1/2 (TF32)" if prec == "tf32" else "1")),
+            "avg_launch_ms": ms / max(launches, 1), "launches": launches}
+
+
 # ----------------------------------------------------------------------------- CPU oracle sample
 
 def oracle_step_sample(w, q: int, fa: np.ndarray, fg: np.ndarray, j: np.ndarray, om_g: np.ndarray,
@@ -417,8 +436,9 @@ def main(argv=None):
     stream.synchronize()
 
     def step(i, xa=None, xg=None, j=None, oa=None, og=None):
-        kfac.kfac_ea_update(ctx, XA[i % nb] if xa is None else xa, Fa, w["rho"], args.prec)
-        kfac.kfac_ea_update(ctx, XG[i % nb] if xg is None else xg, Fg, w["rho"], args.prec)
+        kfac.kfac_ea_update_grouped(ctx, [
+            dict(X=XA[i % nb] if xa is None else xa, F=Fa, rho=w["rho"], prec=args.prec),
+            dict(X=XG[i % nb] if xg is None else xg, F=Fg, rho=w["rho"], prec=args.prec)])
         kfac.kfac_rsvd_invert_grouped(ctx, [
             dict(F=Fa, rank=r, oversample=w["p"], power_iters=q, lam=lam, omega=OA[i % 2] if oa is None else oa,
                  prec=args.prec, out=(Ua, Da, Ca)),
@@ -504,6 +524,7 @@ def main(argv=None):
                   "stage_ms_per_step": {kname: round(v[0] / args.steps, 4) for kname, v in prof.items()},
                   "jacobi_sweeps_per_solve": stats["jacobi_sweeps"] / max(stats["jacobi_solves"], 1)}
         result["roofline"] = roofline(prof, w, q, args.steps, stats, args.traffic)
+        result["roofline_sketch_gemm"] = sketch_roofline(prof, w, q, args.steps, args.prec)
 
     # ---- full-EVD comparator on the same GPU and accuracy at equal rank -----------
     if rank == 0 and not args.no_evd:

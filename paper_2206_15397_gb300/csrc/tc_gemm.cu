@@ -198,12 +198,16 @@ __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int
           const int n = nb + j;
           cin[j] = (m < p.M && n < p.N) ? p.C0[(long long)n * p.ldc + m] : 0.0f;
         }
-      } else {  // rows of C0 through the staging tile
-        __syncwarp();
+      } else {  // rows of C0 through the staging tile: all 32 row loads in flight, then the stores
+        float rowv[32];
+#pragma unroll
         for (int r = 0; r < 32; ++r) {
           const int mr = mrow0 + r, n = nb + lane;
-          stage_tile[r * 33 + lane] = (mr < p.M && n < p.N) ? p.C0[(long long)mr * p.ldc + n] : 0.0f;
+          rowv[r] = (mr < p.M && n < p.N) ? __ldg(p.C0 + (long long)mr * p.ldc + n) : 0.0f;
         }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) stage_tile[r * 33 + lane] = rowv[r];
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < 32; ++j) cin[j] = stage_tile[lane * 33 + j];
