@@ -257,6 +257,12 @@ typedef enum {
   KFAC_OPT_CHOLQR_INNER_PASSES = 5, /* passes for a basis that only feeds the next power
                                        iteration [3], 1..6; fewer passes save time but
                                        lose accuracy on ill-conditioned sketches */
+  KFAC_OPT_CHOLQR_INNER_FP32 = 8,   /* 1 [default]: every CholeskyQR pass of a basis that
+                                       only feeds the next power iteration factors in FP32
+                                       (its span, not its orthonormality to FP64 accuracy,
+                                       is what the next product needs); the final basis
+                                       keeps FP64 after its shifted first pass. 0: inner
+                                       bases follow KFAC_OPT_CHOLQR_FP32_PASSES too */
   KFAC_OPT_BASIS_POLISH = 7,        /* 1 [default]: after the final orthonormalisation the
                                        Rayleigh-Ritz step uses Q M, M = (3I - Q^T Q)/2 (one
                                        Newton-Schulz step, applied to the k x k projected

@@ -52,6 +52,7 @@ struct kfac_ctx {
   int cholqr_inner_passes = 3;
   int cholqr_fp32_passes = 1;
   int basis_polish = 1;
+  int cholqr_inner_fp32 = 1;
   double cholqr_shift = 1e-5;
   int eig_refine = 1;
   int eig_max_sweeps = 40;
@@ -229,8 +230,11 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
   return KFAC_OK;
 }
 
+// `final_basis`: the basis the eigenpairs are taken in (the last one of Alg. 3);
+// a basis that only feeds the next power iteration may factor every pass in
+// FP32 (KFAC_OPT_CHOLQR_INNER_FP32).
 kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, float*& other, int k, int d,
-                           int passes) {
+                           int passes, bool final_basis) {
   for (int pass = 0; pass < passes; ++pass) {
     kfac_status st =
         gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM, at<float>(ctx, L.g32));
@@ -244,7 +248,7 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       // the factorisation indefinite; the last pass (a near-orthonormal basis)
       // is unshifted.
       const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-5 : 0.0);
-      const bool fp64 = pass >= ctx->cholqr_fp32_passes || pass + 1 == passes;
+      const bool fp64 = (final_basis || !ctx->cholqr_inner_fp32) && (pass >= ctx->cholqr_fp32_passes || pass + 1 == passes);
       CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
                       ctx->stream, nullptr, at<float>(ctx, L.g32), k));
     }
@@ -330,7 +334,8 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   if (st != KFAC_OK) return st;
   for (int it = 0;; ++it) {
     st = orthonormalise(ctx, L, cur, other, k, d,
-                        it == a.power_iters ? ctx->cholqr_passes : ctx->cholqr_inner_passes);  // Q^T in cur
+                        it == a.power_iters ? ctx->cholqr_passes : ctx->cholqr_inner_passes,
+                        it == a.power_iters);  // Q^T in cur
     if (st != KFAC_OK) return st;
     if (it == a.power_iters) break;
     st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);  // Y^T = Q^T F
@@ -586,6 +591,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
     case KFAC_OPT_CHOLQR_INNER_PASSES:
       if (v < 1 || v > 6) return KFAC_ERR_INVALID_ARG;
       ctx->cholqr_inner_passes = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_CHOLQR_INNER_FP32:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->cholqr_inner_fp32 = (int)v;
       return KFAC_OK;
     case KFAC_OPT_BASIS_POLISH:
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
