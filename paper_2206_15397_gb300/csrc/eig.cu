@@ -30,9 +30,11 @@ constexpr int EIG_THREADS = 512;
 constexpr int EIG_WARPS = EIG_THREADS / 32;
 constexpr int EIG_MAX_NC = 16;  // non-portable cluster size, enabled at launch
 
-__device__ __forceinline__ float warp_sum_bcast(float v) {
+// Butterfly sum: every lane ends with the same total (each level adds the same
+// two operands in every lane, and FP addition is commutative).
+__device__ __forceinline__ float warp_sum_all(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return __shfl_sync(0xffffffffu, v, 0);  // one value for every lane
+  return v;
 }
 
 // Rotate columns wa, wb (length k) to make them orthogonal (one warp). Returns 1
@@ -59,14 +61,15 @@ __device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol,
     be = fmaf(y[it].x, y[it].x, fmaf(y[it].y, y[it].y, fmaf(y[it].z, y[it].z, fmaf(y[it].w, y[it].w, be))));
     ga = fmaf(x[it].x, y[it].x, fmaf(x[it].y, y[it].y, fmaf(x[it].z, y[it].z, fmaf(x[it].w, y[it].w, ga))));
   }
-  al = warp_sum_bcast(al);
-  be = warp_sum_bcast(be);
-  ga = warp_sum_bcast(ga);
+  al = warp_sum_all(al);
+  be = warp_sum_all(be);
+  ga = warp_sum_all(ga);
   if (!(ga != 0.0f && ga * ga > (tol * tol) * (al * be))) return 0;
   // 2x2 symmetric Schur step on the Gram [[al, ga], [ga, be]]: J = [[c, s], [-s, c]],
-  // t = sign(z) / (|z| + sqrt(1 + z^2)). Fast reciprocal / rsqrt: their ulp
-  // errors only perturb the rotation slightly (W W^T stays C + sI to FP32
-  // accuracy) and the FP64 refinement that follows absorbs them.
+  // t = sign(z) / (|z| + sqrt(1 + z^2)), z = (be - al) / (2 ga): scale-invariant
+  // (a form that squares be - al and ga underflows on factors of scale ~1e-6).
+  // Fast reciprocal / rsqrt: their ulp errors only perturb the rotation slightly
+  // (W W^T stays C + sI to FP32 accuracy) and the FP64 refinement absorbs them.
   const float zeta = __fdividef(be - al, 2.0f * ga);
   const float az = fabsf(zeta);
   float t;
