@@ -35,9 +35,11 @@ __global__ void k_reduce_epilogue(const float* __restrict__ part, int z, long lo
 cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   const bool kmajor = g.sak == 1 && g.sbk == 1;
-  const bool tc_ok = prec != KFAC_PREC_BF16 && kmajor && g.K > 0 &&
+  const tc::Mode mode = prec == KFAC_PREC_FP32 ? tc::Mode::Fp32 : (prec == KFAC_PREC_TF32 ? tc::Mode::Tf32 : tc::Mode::Bf16);
+  const int kalign = tc::k_step(mode);  // a K-chunk must cover whole K-steps of the kernel
+  const bool tc_ok = kmajor && g.K > 0 &&
                      tc::eligible(g.A, g.sam, g.B, g.sbn, g.M, g.N, g.K) &&
-                     (g.zsplit <= 1 || g.kchunk % 32 == 0) && !(g.sym && g.zsplit > 1);
+                     (g.zsplit <= 1 || g.kchunk % kalign == 0) && !(g.sym && g.zsplit > 1);
   if (!tc_ok) return gemm_simt_f32(g, round_of(prec), s);
 
   tc::TcArgs a = {};
@@ -47,12 +49,11 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
   a.C0 = g.C0; a.ldc = g.ldc; a.c0_trans = g.c0_trans;
   a.D = g.D; a.ldd = g.ldd; a.d_trans = g.d_trans;
   a.sym = g.sym; a.flags = g.flags;
-  const bool split3 = prec == KFAC_PREC_FP32;
   if (g.zsplit > 1) {  // caller-managed raw partials
     a.partial = 1; a.kchunk = g.kchunk; a.zstride = g.zstride;
-    return tc::gemm(a, g.A, g.sam, g.B, g.sbn, g.zsplit, split3, s);
+    return tc::gemm(a, g.A, g.sam, g.B, g.sbn, g.zsplit, mode, s);
   }
-  const int bn = tc::tile_n(g.N, split3);
+  const int bn = tc::tile_n(g.N, mode);
   long long tiles = cdiv(g.M, 128) * cdiv(g.N, bn);
   if (g.sym) tiles = (tiles + 1) / 2;
   const long long rows = g.d_trans ? g.N : g.M, cols = g.d_trans ? g.M : g.N;
@@ -62,10 +63,10 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
     while (z > 1 && (long long)z * rows * cols > g.ws_floats) --z;
   }
   if (z > 1) {
-    const int kchunk = (int)(cdiv(cdiv(g.K, z), 32) * 32);
+    const int kchunk = (int)(cdiv(cdiv(g.K, z), kalign) * kalign);
     z = (int)cdiv(g.K, kchunk);
     a.partial = 1; a.kchunk = kchunk; a.D = g.ws; a.ldd = cols; a.zstride = rows * cols;
-    cudaError_t e = tc::gemm(a, g.A, g.sam, g.B, g.sbn, z, split3, s);
+    cudaError_t e = tc::gemm(a, g.A, g.sam, g.B, g.sbn, z, mode, s);
     if (e != cudaSuccess) return e;
     const long long tot = rows * cols;
     k_reduce_epilogue<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(g.ws, z, rows * cols, (int)rows, (int)cols, g);
@@ -73,8 +74,8 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
     return cudaGetLastError();
   }
   a.partial = 0;
-  a.kchunk = (int)(cdiv(g.K, 32) * 32);
-  return tc::gemm(a, g.A, g.sam, g.B, g.sbn, 1, split3, s);
+  a.kchunk = (int)(cdiv(g.K, kalign) * kalign);
+  return tc::gemm(a, g.A, g.sam, g.B, g.sbn, 1, mode, s);
 }
 
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,

@@ -30,6 +30,13 @@
 //               add every finished pair into FP32 registers with
 //               round-to-nearest. The remaining bias is that of four K-steps
 //               (measured -9e-8 relative, independent of K).
+//   k_tc_gemm16 BF16 operands (the reduced-precision path): TMA stages FP32
+//               tiles of 64 K-columns (two 32-column boxes per operand) in a
+//               ring of its own; warps 2-7 round them to BF16 (round to nearest)
+//               into a second ring of 128-byte-swizzled K-major tiles and hand
+//               the FP32 stage straight back to TMA; warp 1 issues
+//               tcgen05.mma.kind::f16 (BF16 x BF16, K = 16 per instruction,
+//               FP32 accumulator in TMEM).
 // Every mbarrier wait is bounded by a clock deadline; on expiry the kernel
 // raises KFAC_FLAG_TIMEOUT, drains what it issued and returns.
 #include <cuda.h>
@@ -151,6 +158,27 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with BF16 A and B, F32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Two FP32 values rounded to nearest BF16, packed low = a, high = b.
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+
 // x rounded to nearest TF32 (exactly representable in TF32). Rounding (not
 // truncation) keeps the tail |x - hi| <= 2^-11 |x| and unbiased: truncated heads
 // leave tails of one sign that the tensor core truncates again, biasing every
@@ -182,6 +210,23 @@ struct Cfg3 {
   static constexpr int BAR_BYTES = 8 * (3 * STAGES + 5) + 16;
   static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES;
   static constexpr int TMEM_COLS = 4 * BN3;  // main[2], small[2]
+};
+
+// BF16 kernel: FP32 stages of 64 K-columns (2 boxes per operand) and BF16
+// stages of the same K-range (one 128-byte row per matrix row).
+constexpr int BN16 = 128;
+constexpr int BK16 = 64;
+constexpr int kConvThreads = 192;  // warps 2-7
+struct Cfg16 {
+  static constexpr int A_RAW = BM * BK16 * 4;
+  static constexpr int B_RAW = BN16 * BK16 * 4;
+  static constexpr int RAW = A_RAW + B_RAW;
+  static constexpr int A_H = BM * BK16 * 2;
+  static constexpr int B_H = BN16 * BK16 * 2;
+  static constexpr int HALF = A_H + B_H;
+  static constexpr int RAW_STAGES = 2, H_STAGES = 2;
+  static constexpr int BAR_BYTES = 8 * (2 * RAW_STAGES + 2 * H_STAGES + 1) + 16;
+  static constexpr int SMEM = 1024 + RAW_STAGES * RAW + H_STAGES * HALF + BAR_BYTES;
 };
 
 // Epilogue of 32 consecutive columns [nb, nb + 32) of row m held by this lane
@@ -523,6 +568,149 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gemm16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
+  using C = Cfg16;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* raw0 = smem;                                 // FP32 stages
+  uint8_t* half0 = smem + C::RAW_STAGES * C::RAW;       // BF16 stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(half0 + C::H_STAGES * C::HALF);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::RAW_STAGES + 2 * C::H_STAGES + 1);
+  const uint32_t rfull0 = smem_u32(bars), rempty0 = rfull0 + 8 * C::RAW_STAGES;
+  const uint32_t hfull0 = rempty0 + 8 * C::RAW_STAGES, hempty0 = hfull0 + 8 * C::H_STAGES;
+  const uint32_t accb = hempty0 + 8 * C::H_STAGES;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN16;
+  if (p.sym && m0 > n0 + BN16 - 1) return;  // whole tile below the diagonal (uniform exit, nothing started)
+  const int kb0 = blockIdx.z * p.kchunk;
+  const int ke = min(p.K, kb0 + p.kchunk);
+  const int nk = ke > kb0 ? (ke - kb0 + BK16 - 1) / BK16 : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < C::RAW_STAGES; ++s) {
+      mbar_init(rfull0 + 8 * s, 1);
+      mbar_init(rempty0 + 8 * s, kConvThreads);
+    }
+    for (int h = 0; h < C::H_STAGES; ++h) {
+      mbar_init(hfull0 + 8 * h, kConvThreads);
+      mbar_init(hempty0 + 8 * h, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN16)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: 64 K-columns = two 32-column boxes per operand --------
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::RAW_STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::RAW_STAGES) & 1u;
+      if (kb >= C::RAW_STAGES && !mbar_wait(rempty0 + 8 * s, ph ^ 1u, p.flags)) break;
+      const uint32_t st = smem_u32(raw0 + s * C::RAW);
+      const int kx = kb0 + kb * BK16;
+      mbar_expect_tx(rfull0 + 8 * s, C::RAW);
+      tma_load_2d(st, &tmA, kx, m0, rfull0 + 8 * s);
+      tma_load_2d(st + C::A_RAW / 2, &tmA, kx + 32, m0, rfull0 + 8 * s);
+      tma_load_2d(st + C::A_RAW, &tmB, kx, n0, rfull0 + 8 * s);
+      tma_load_2d(st + C::A_RAW + C::B_RAW / 2, &tmB, kx + 32, n0, rfull0 + 8 * s);
+      ++issued;
+    }
+    for (int kb = (issued > C::RAW_STAGES ? issued - C::RAW_STAGES : 0); kb < issued; ++kb)
+      mbar_wait(rfull0 + 8 * (kb % C::RAW_STAGES), (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: 4 x (K = 16) per BF16 stage -----------------------------
+    constexpr uint32_t idesc = idesc_bf16(BM, BN16);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int h = kb % C::H_STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::H_STAGES) & 1u;
+      if (!mbar_wait(hfull0 + 8 * h, ph, p.flags)) break;
+      tc_fence_after();
+      const uint32_t hb = smem_u32(half0 + h * C::HALF);
+      const uint64_t ad = sdesc_k128(hb), bd = sdesc_k128(hb + C::A_H);
+#pragma unroll
+      for (int kk = 0; kk < BK16 / 16; ++kk) {  // K = 16 BF16 = 32 bytes per instruction
+        const uint64_t off = (uint64_t)(kk * 2);
+        mma_bf16(taddr, ad + off, bd + off, idesc, (kb | kk) ? 1u : 0u);
+      }
+      mma_commit(hempty0 + 8 * h);  // BF16 stage reusable once these MMAs completed
+    }
+    mma_commit(accb);
+  } else if (warp >= 2) {
+    // ---- converters: FP32 (TMA 128B swizzle) -> BF16 (128B swizzle) ----------
+    // An FP32 box row r holds 32 values in 8 chunks of 16 bytes, chunk c at
+    // physical chunk c ^ (r % 8); a BF16 row holds the 64 values of both boxes
+    // in 8 chunks of 8 values, chunk j at physical chunk j ^ (r % 8).
+    const int t = tid - 64;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::RAW_STAGES, h = kb % C::H_STAGES;
+      if (!mbar_wait_warp(rfull0 + 8 * s, (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags, lane)) break;
+      if (kb >= C::H_STAGES &&
+          !mbar_wait_warp(hempty0 + 8 * h, ((uint32_t)(kb / C::H_STAGES) & 1u) ^ 1u, p.flags, lane))
+        break;
+      const uint8_t* rs = raw0 + s * C::RAW;
+      uint8_t* hs = half0 + h * C::HALF;
+      for (int q = t; q < (BM + BN16) * 8; q += kConvThreads) {
+        const int row = q >> 3, j = q & 7;
+        const bool isB = row >= BM;
+        const int r = isB ? row - BM : row;
+        const uint8_t* box = rs + (isB ? C::A_RAW : 0) + (j >> 2) * (isB ? C::B_RAW / 2 : C::A_RAW / 2) + r * 128;
+        const int c0 = 2 * (j & 3), sw = r & 7;
+        const float4 x0 = *reinterpret_cast<const float4*>(box + ((c0 ^ sw) << 4));
+        const float4 x1 = *reinterpret_cast<const float4*>(box + (((c0 + 1) ^ sw) << 4));
+        uint4 o;
+        o.x = pack_bf16x2(x0.x, x0.y);
+        o.y = pack_bf16x2(x0.z, x0.w);
+        o.z = pack_bf16x2(x1.x, x1.y);
+        o.w = pack_bf16x2(x1.z, x1.w);
+        *reinterpret_cast<uint4*>(hs + (isB ? C::A_H : 0) + r * 128 + ((j ^ sw) << 4)) = o;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(hfull0 + 8 * h);
+      mbar_arrive(rempty0 + 8 * s);
+    }
+  }
+  __syncwarp();
+
+  // ---- epilogue (all 8 warps, as the TF32 kernel) --------------------------------
+  const bool acc_ok = mbar_wait(accb, 0, p.flags);
+  tc_fence_after();
+  float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+  float* const Dz = p.D + (p.partial ? (long long)blockIdx.z * p.zstride : 0LL);
+  const int q = warp & 3;
+  const int m = m0 + 32 * q + lane;
+  const int cbeg = (warp < 4) ? 0 : BN16 / 2;
+  const float rs = (p.rowscale && m < p.M) ? p.rowscale[m] : 1.0f;
+  for (int c0 = cbeg; c0 < cbeg + BN16 / 2; c0 += 32) {
+    const int nb = n0 + c0;
+    if (nb >= p.N) break;
+    float v[32];
+    if (nk > 0 && acc_ok) {
+      tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+    }
+    store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(BN16) : "memory");
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
@@ -580,9 +768,10 @@ bool eligible(const float* A, long long lda, const float* B, long long ldb, int 
 }
 
 cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
-                 bool split3, cudaStream_t s) {
-  static bool attr3 = false, attr256 = false, attr128 = false;
-  if (split3) return launch_kernel(k_tc_gemm3, Cfg3::SMEM, BN3, attr3, a, A, lda, B, ldb, zsplit, s);
+                 Mode mode, cudaStream_t s) {
+  static bool attr3 = false, attr256 = false, attr128 = false, attr16 = false;
+  if (mode == Mode::Fp32) return launch_kernel(k_tc_gemm3, Cfg3::SMEM, BN3, attr3, a, A, lda, B, ldb, zsplit, s);
+  if (mode == Mode::Bf16) return launch_kernel(k_tc_gemm16, Cfg16::SMEM, BN16, attr16, a, A, lda, B, ldb, zsplit, s);
   if (a.N > 128) return launch_kernel(k_tc_gemm<256>, Cfg<256>::SMEM, 256, attr256, a, A, lda, B, ldb, zsplit, s);
   return launch_kernel(k_tc_gemm<128>, Cfg<128>::SMEM, 128, attr128, a, A, lda, B, ldb, zsplit, s);
 }

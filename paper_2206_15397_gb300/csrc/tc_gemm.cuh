@@ -29,13 +29,19 @@ struct TcArgs {
 // by TMA: 16-byte aligned bases and row strides.
 bool eligible(const float* A, long long lda, const float* B, long long ldb, int M, int N, int K);
 
-// Tile width (columns of D per CTA) the launch below uses.
-inline int tile_n(int N, bool split3) { return (split3 || N <= 128) ? 128 : 256; }
+// Operand arithmetic of a launch: FP32-accurate 3xTF32 products, TF32 or
+// BF16 (round to nearest) operands; FP32 accumulation in tensor memory.
+enum class Mode { Fp32, Tf32, Bf16 };
 
-// Launch one GEMM: TF32 products (split3 = false) or FP32-accurate 3xTF32
-// products (split3 = true), FP32 accumulation in tensor memory.
+// Tile width (columns of D per CTA) the launch below uses.
+inline int tile_n(int N, Mode mode) { return (mode != Mode::Tf32 || N <= 128) ? 128 : 256; }
+
+// K-columns one pipeline stage of the launch consumes.
+inline int k_step(Mode mode) { return mode == Mode::Bf16 ? 64 : 32; }
+
+// Launch one GEMM.
 cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
-                 bool split3, cudaStream_t s);
+                 Mode mode, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace kfac

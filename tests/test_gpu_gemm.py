@@ -59,3 +59,25 @@ def test_gemm_nt_zero_k(kf, ctx):
     D = torch.ones(8, 8, device="cuda")
     kf.kfac_gemm_nt(ctx, A, torch.zeros(8, 0, device="cuda"), D, alpha=1.0, beta=2.0)
     assert torch.equal(D, torch.full_like(D, 2.0))
+
+
+@pytest.mark.parametrize("M,N,K,pad", [
+    (128, 128, 64, 0),       # one tile, one BF16 K-step
+    (130, 230, 97, 3),       # ragged M, N, K (K-step 64 with a zero-filled tail)
+    (1000, 230, 4097, 3),    # split-K into 64-aligned chunks
+    (256, 384, 1000, 0),
+])
+def test_gemm_nt_bf16_exact_operands(kf, ctx, M, N, K, pad):
+    """BF16 operand path: each operand is rounded to nearest BF16 and the
+    products are summed in FP32, so against the FP64 product of the rounded
+    operands only FP32 accumulation error remains (a wrong rounding mode, a
+    mis-swizzled K-chunk or a dropped K-step shows up far above 2e-5)."""
+    A = padded(M, K, pad, 11)
+    B = padded(N, K, pad, 12)
+    D = torch.zeros(M, N, device="cuda")
+    kf.kfac_gemm_nt(ctx, A, B, D, alpha=1.0, beta=0.0, prec="bf16")
+    st, flags = kf.kfac_get_status(ctx)
+    assert st == 0, flags
+    ref = A.bfloat16().double() @ B.bfloat16().double().T
+    err = (torch.linalg.norm(D.double() - ref) / torch.linalg.norm(ref)).item()
+    assert err <= 2e-5, err
