@@ -363,21 +363,139 @@ cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, in
 // memory (k <= CTA_KMAX), for the shifted first CholeskyQR pass and the
 // eigensolver's factor: no cluster barriers or distributed-memory broadcasts,
 // which dominate the cluster kernel at these sizes. Right-looking, 32-column
-// panels:
-//   (1) warp 0 factors the 32 x 32 diagonal block in registers: lane r holds
-//       row r; per pivot t the pivot and column t travel by shuffles, and the
-//       lane's trailing row entries update in place (fully unrolled, static
-//       register indices). Reciprocal pivots go to shared memory;
-//   (2) one thread per row below solves its panel row against L11
-//       (right-looking substitution, L11 read as shared-memory broadcasts);
-//   (3) all threads apply the rank-32 update to the trailing lower triangle,
-//       4 x 4 output tiles per thread, 128-bit reads along the panel.
+// panels with a look-ahead of one panel:
+//   (1) panel rows below the diagonal block: one warp per group of rows, lane
+//       c owning column c; the substitution x_s = a_s / L_ss, a_c -= L_cs x_s
+//       passes x_s by shuffle, L11's row c held in lane c's registers;
+//   (2) the rank-32 update of the next block column (rows below it included);
+//   (3) warp 0 factors the next 32 x 32 diagonal block in registers (lane r
+//       holds row r; per pivot t the pivot and column t travel by shuffles)
+//       while the other 15 warps apply the rank-32 update to the rest of the
+//       trailing lower triangle.
+// The updates use 4 x 4 output tiles per thread, a warp covering 8 x 4 tiles
+// so that its row reads fall in distinct banks (odd row stride).
 // Pivot floor, raised pivots and restarts follow the cluster kernel.
 constexpr int CTA_THREADS = 512;
+constexpr int CTA_WARPS = CTA_THREADS / 32;
 constexpr int CTA_KMAX = 236;
 
 __host__ __device__ inline int cta_ks(int k) { return k | 1; }  // odd row stride: rows hit distinct banks
 __host__ __device__ inline size_t cta_smem_bytes(int k) { return sizeof(float) * ((size_t)k * cta_ks(k) + 64) + 16; }
+
+// Warp 0: factor the diagonal block A[j0 .. j0+jb)^2 in place; reciprocal
+// pivots to rinv. Sets sflag[0] on a non-finite pivot, sflag[1] on a raised one.
+__device__ __forceinline__ void cta_factor_diag(float* A, int ks, int j0, int jb, float* rinv, const double* G, int k,
+                                                double shift, float pfloor, int* sflag, int lane) {
+  float x[32];
+  const int r = lane;
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    x[c] = (r < jb && c < jb) ? (c <= r ? A[(size_t)(j0 + r) * ks + j0 + c] : 0.0f) : (r == c ? 1.0f : 0.0f);
+  int bad = 0, clamped = 0;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    if (t >= jb) break;  // uniform: padded pivots are identity
+    float piv = __shfl_sync(0xffffffffu, x[t], t);
+    if (!isfinite(piv)) bad = 1;
+    else if (!(piv > pfloor)) {
+      piv = raised_pivot(G, k, j0 + t, shift, pfloor);
+      clamped = 1;
+    }
+    const float y = rsqrt_newton(piv);
+    if (r == t) { x[t] = piv * y; rinv[t] = y; }
+    const float lt = (r > t) ? x[t] * y : 0.0f;  // L[r][t]
+    if (r > t) x[t] = lt;
+#pragma unroll
+    for (int c = t + 1; c < 32; ++c) {
+      const float lc = __shfl_sync(0xffffffffu, lt, c);  // L[c][t]
+      x[c] = fmaf(-lt, lc, x[c]);
+    }
+  }
+  if (r < jb) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c <= r) A[(size_t)(j0 + r) * ks + j0 + c] = x[c];
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  clamped = __any_sync(0xffffffffu, clamped);
+  if (lane == 0) { if (bad) sflag[0] = 1; if (clamped) sflag[1] = 1; }
+}
+
+// Rows [first, k) of the panel columns [j0, j0 + jb): L21 = A21 L11^-T by
+// substitution, 4 rows per warp pass. Warps [w0, CTA_WARPS).
+__device__ __forceinline__ void cta_panel_solve(float* A, int ks, int k, int j0, int jb, const float* rinv, int warp,
+                                                int lane) {
+  const int first = j0 + jb;
+  float l[32];  // lane c: L11[c][s], s < c
+#pragma unroll
+  for (int s2 = 0; s2 < 32; ++s2) l[s2] = (s2 < lane && lane < jb) ? A[(size_t)(j0 + lane) * ks + j0 + s2] : 0.0f;
+  const float rc = lane < jb ? rinv[lane] : 0.0f;
+  constexpr int R = 4;
+  for (int i0 = first + R * warp; i0 < k; i0 += R * CTA_WARPS) {
+    float a[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      a[q] = (i0 + q < k && lane < jb) ? A[(size_t)(i0 + q) * ks + j0 + lane] : 0.0f;
+#pragma unroll
+    for (int s2 = 0; s2 < 32; ++s2) {
+      if (s2 >= jb) break;  // uniform
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const float xs = __shfl_sync(0xffffffffu, a[q] * rc, s2);
+        if (lane == s2) a[q] = xs;
+        else if (lane > s2) a[q] = fmaf(-l[s2], xs, a[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      if (i0 + q < k && lane < jb) A[(size_t)(i0 + q) * ks + j0 + lane] = a[q];
+  }
+}
+
+// A[i][c] -= sum_t A[i][j0+t] A[c][j0+t] for i in [r0, r1), c in [r0, c1),
+// c <= i, t < jb. Warps [w0, w0 + nw); each warp takes groups of 8 x 4 tiles
+// (32 rows x 16 columns), a lane one 4 x 4 tile.
+__device__ __forceinline__ void cta_rank_update(float* A, int ks, int k, int j0, int jb, int r0, int r1, int c1,
+                                                int w0, int nw, int warp, int lane) {
+  if (warp < w0 || r1 <= r0 || c1 <= r0) return;
+  const int GR = (r1 - r0 + 31) / 32, GC = (c1 - r0 + 15) / 16;
+  int ngroups = 0;
+  for (int gr = 0; gr < GR; ++gr) ngroups += min(GC, 2 * gr + 2);
+  for (int grp = warp - w0; grp < ngroups; grp += nw) {
+    int gr = 0, rem = grp;
+    while (rem >= min(GC, 2 * gr + 2)) { rem -= min(GC, 2 * gr + 2); ++gr; }
+    const int i0 = r0 + 32 * gr + 4 * (lane >> 2), c0 = r0 + 16 * rem + 4 * (lane & 3);
+    if (i0 >= r1 || c0 >= c1 || c0 > i0 + 3) continue;
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+    const float* pi[4];
+    const float* pc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pi[u] = A + (size_t)min(i0 + u, k - 1) * ks + j0;
+      pc[u] = A + (size_t)min(c0 + u, k - 1) * ks + j0;
+    }
+    for (int t = 0; t < jb; ++t) {
+      float ri[4], rcv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { ri[u] = pi[u][t]; rcv[u] = pc[u][t]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ri[u], rcv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = i0 + u, c = c0 + v;
+        if (i < r1 && c < c1 && c <= i) A[(size_t)i * ks + c] -= acc[u][v];
+      }
+  }
+}
 
 __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* __restrict__ G,
                                                                 const float* __restrict__ G32, long long ld32,
@@ -387,7 +505,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
   extern __shared__ __align__(16) float csm[];
   const int ks = cta_ks(k);
   float* A = csm;                        // k x ks, row-major, lower part used
-  float* rinv = A + (size_t)k * ks;      // 32 reciprocal pivots of the current panel
+  float* rinv = A + (size_t)k * ks;      // 32 reciprocal pivots of the current diagonal block
   int* sflag = reinterpret_cast<int*>(rinv + 32);  // [0] non-finite, [1] clamped
   __shared__ double s_trace;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -412,134 +530,43 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
         if (stats) atomicAdd(stats + STAT_CHOL_RETRY, 1ull);
       }
     }
-    {  // load the lower triangle (+ shift), eight loads in flight per thread
-      const int total = k * k;
+    {  // load the lower triangle (+ shift): a warp per row pair, 16 loads in flight per lane
       const float shf = (float)shift;
-      for (int base = 0; base < total; base += 8 * CTA_THREADS) {
-        float v[8];
+      for (int i = 2 * warp; i < k; i += 2 * CTA_WARPS) {
+        float v[2][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int e = base + q * CTA_THREADS + tid;
-          const int i = e / k, j = e - i * k;
-          // G32 avoids a per-element FP64 -> FP32 conversion on the FP64 pipe
-          v[q] = (e < total && j <= i) ? (G32 ? G32[(long long)i * ld32 + j] : (float)G[(size_t)i * k + j]) : 0.0f;
-        }
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int e = base + q * CTA_THREADS + tid;
-          if (e < total) {
-            const int i = e / k, j = e - i * k;
-            A[(size_t)i * ks + j] = v[q] + (i == j ? shf : 0.0f);
+          for (int q = 0; q < 8; ++q) {
+            const int ii = i + h, j = lane + 32 * q;
+            // G32 avoids a per-element FP64 -> FP32 conversion on the FP64 pipe
+            v[h][q] = (ii < k && j <= ii) ? (G32 ? G32[(long long)ii * ld32 + j] : (float)G[(size_t)ii * k + j]) : 0.0f;
           }
-        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int ii = i + h, j = lane + 32 * q;
+            if (ii < k && j <= ii) A[(size_t)ii * ks + j] = v[h][q] + (ii == j ? shf : 0.0f);
+          }
       }
     }
     if (tid == 0) { sflag[0] = 0; sflag[1] = 0; }
     __syncthreads();
-    for (int j0 = 0; j0 < k; j0 += 32) {
+    if (warp == 0) cta_factor_diag(A, ks, 0, min(32, k), rinv, G, k, shift, pfloor, sflag, lane);
+    __syncthreads();
+    for (int j0 = 0; j0 < k && !sflag[0]; j0 += 32) {
       const int jb = min(32, k - j0);
-      // (1) diagonal block in registers of warp 0 (padded rows/columns: identity)
-      if (warp == 0) {
-        float x[32];
-        const int r = lane;
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          x[c] = (r < jb && c < jb) ? (c <= r ? A[(size_t)(j0 + r) * ks + j0 + c] : 0.0f) : (r == c ? 1.0f : 0.0f);
-        int bad = 0, clamped = 0;
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          float piv = __shfl_sync(0xffffffffu, x[t], t);
-          if (t < jb) {
-            if (!isfinite(piv)) bad = 1;
-            else if (!(piv > pfloor)) {
-              piv = raised_pivot(G, k, j0 + t, shift, pfloor);
-              clamped = 1;
-            }
-          }
-          const float y = rsqrt_newton(piv);
-          if (r == t) { x[t] = piv * y; rinv[t] = y; }
-          const float lt = (r > t) ? x[t] * y : 0.0f;  // L[r][t]
-          if (r > t) x[t] = lt;
-#pragma unroll
-          for (int c = t + 1; c < 32; ++c) {
-            const float lc = __shfl_sync(0xffffffffu, lt, c);  // L[c][t]
-            x[c] = fmaf(-lt, lc, x[c]);
-          }
-        }
-        if (r < jb) {
-#pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (c <= r) A[(size_t)(j0 + r) * ks + j0 + c] = x[c];
-        }
-        bad = __any_sync(0xffffffffu, bad);
-        clamped = __any_sync(0xffffffffu, clamped);
-        if (lane == 0) { if (bad) sflag[0] = 1; if (clamped) sflag[1] = 1; }
-      }
-      __syncthreads();
-      if (sflag[0]) break;
-      // (2) panel rows below: x_s = a_s / L_ss, a_t -= x_s L_ts (t > s)
       const int first = j0 + jb;
-      for (int i = first + tid; i < k; i += CTA_THREADS) {
-        float a[32];
-        float* row = A + (size_t)i * ks + j0;
-#pragma unroll
-        for (int q = 0; q < 32; ++q) a[q] = q < jb ? row[q] : 0.0f;
-#pragma unroll
-        for (int sidx = 0; sidx < 32; ++sidx) {
-          if (sidx < jb) {
-            a[sidx] *= rinv[sidx];
-            const float xs = a[sidx];
-            const float* lcol = A + (size_t)j0 * ks + j0 + sidx;  // L[t][s] = lcol[t * ks]
-#pragma unroll
-            for (int t = sidx + 1; t < 32; ++t)
-              if (t < jb) a[t] = fmaf(-xs, lcol[(size_t)t * ks], a[t]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (q < jb) row[q] = a[q];
-      }
+      if (first >= k) break;
+      const int jb1 = min(32, k - first);
+      cta_panel_solve(A, ks, k, j0, jb, rinv, warp, lane);
       __syncthreads();
-      // (3) trailing update of the lower triangle [first, k)^2, 4 x 4 tiles
-      const int n = k - first;
-      if (n > 0) {
-        const int T = (n + 3) / 4, ntiles = T * (T + 1) / 2;
-        for (int tile = tid; tile < ntiles; tile += CTA_THREADS) {
-          int bi = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
-          while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
-          while (bi * (bi + 1) / 2 > tile) --bi;
-          const int bj = tile - bi * (bi + 1) / 2;  // bj <= bi
-          const int i0 = first + 4 * bi, c0 = first + 4 * bj;
-          float acc[4][4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-          const float* pi[4];
-          const float* pc[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            pi[u] = A + (size_t)min(i0 + u, k - 1) * ks + j0;
-            pc[u] = A + (size_t)min(c0 + u, k - 1) * ks + j0;
-          }
-          for (int t = 0; t < jb; ++t) {  // rows an odd stride apart: conflict-free scalar reads
-            float ri[4], rc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { ri[u] = pi[u][t]; rc[u] = pc[u][t]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ri[u], rc[v], acc[u][v]);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const int i = i0 + u, c = c0 + v;
-              if (i < k && c <= i) A[(size_t)i * ks + c] -= acc[u][v];
-            }
-        }
-      }
+      // next block column (its diagonal block and the rows below it)
+      cta_rank_update(A, ks, k, j0, jb, first, k, first + jb1, 0, CTA_WARPS, warp, lane);
+      __syncthreads();
+      if (warp == 0) cta_factor_diag(A, ks, first, jb1, rinv, G, k, shift, pfloor, sflag, lane);
+      else cta_rank_update(A, ks, k, j0, jb, first + jb1, k, k, 1, CTA_WARPS - 1, warp, lane);
       __syncthreads();
     }
     if (!sflag[0]) {
@@ -557,16 +584,14 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
       raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : KFAC_FLAG_NONFINITE);
       if (shift_out) *shift_out = 0.0;
     }
-    for (int e = tid; e < k * k; e += CTA_THREADS) {
-      const int i = e / k, j = e - i * k;
+    for (int i = warp; i < k; i += CTA_WARPS) {
       const double g = G[(size_t)i * k + i];
-      L32[e] = (i == j) ? (float)sqrt(isfinite(g) && g > 1e-30 ? g : 1.0) : 0.0f;
+      for (int j = lane; j < k; j += 32)
+        L32[(size_t)i * k + j] = (i == j) ? (float)sqrt(isfinite(g) && g > 1e-30 ? g : 1.0) : 0.0f;
     }
   } else {
-    for (int e = tid; e < k * k; e += CTA_THREADS) {
-      const int i = e / k, j = e - i * k;
-      L32[e] = (j <= i) ? A[(size_t)i * ks + j] : 0.0f;
-    }
+    for (int i = warp; i < k; i += CTA_WARPS)
+      for (int j = lane; j < k; j += 32) L32[(size_t)i * k + j] = (j <= i) ? A[(size_t)i * ks + j] : 0.0f;
   }
   if (stats && tid == 0) atomicAdd(stats + STAT_CHOL, 1ull);
 }
