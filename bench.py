@@ -201,9 +201,10 @@ def stage_work(stage: str, w, q: int, steps: int):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each
 # stage's kernels from one ncu capture of this bench on a GB300 (the captures
-# summarised under profiles/, same kernels as built here). The Cholesky stage's
-# FP64 cluster and FP32 single-CTA kernels both read the k x k FP64 Gram once.
-NCU_TRAFFIC_PER_LAUNCH = {"cholqr_chol": 298496.0, "eig_jacobi": 189696.0, "sketch_gemm": 72509184.0}
+# summarised under profiles/, same kernels as built here). The Cholesky stage
+# runs the FP32 single-CTA kernel, which reads the k x k Gram once; the Jacobi
+# kernel reads the k x k FP32 factor once.
+NCU_TRAFFIC_PER_LAUNCH = {"cholqr_chol": 307968.0, "eig_jacobi": 196352.0, "sketch_gemm": 72509184.0}
 
 
 def load_peaks():

@@ -260,9 +260,8 @@ typedef enum {
   KFAC_OPT_CHOLQR_INNER_FP32 = 8,   /* 1 [default]: every CholeskyQR pass of a basis that
                                        only feeds the next power iteration factors in FP32
                                        (its span, not its orthonormality to FP64 accuracy,
-                                       is what the next product needs); the final basis
-                                       keeps FP64 after its shifted first pass. 0: inner
-                                       bases follow KFAC_OPT_CHOLQR_FP32_PASSES too */
+                                       is what the next product needs). 0: inner bases
+                                       follow KFAC_OPT_CHOLQR_FP32_PASSES like the final one */
   KFAC_OPT_BASIS_POLISH = 7,        /* 1 [default]: after the final orthonormalisation the
                                        Rayleigh-Ritz step uses Q M, M = (3I - Q^T Q)/2 (one
                                        Newton-Schulz step, applied to the k x k projected
@@ -270,12 +269,22 @@ typedef enum {
                                        orthonormality to second order when the sketch is so
                                        ill-conditioned that FP32-stored CholeskyQR3 leaves
                                        ~1e-4; 0: off */
-  KFAC_OPT_CHOLQR_FP32_PASSES = 6   /* leading passes of every orthonormalisation whose
-                                       Cholesky runs in FP32 instead of FP64 [1], 0..5; the
-                                       last pass of a basis always runs in FP64. The first,
-                                       shifted pass only preconditions Y (any invertible R
-                                       leaves span(Y R^-1) = span(Y)), so its rounding is
-                                       corrected by the passes after it */
+  KFAC_OPT_CHOLQR_FP32_PASSES = 6,  /* leading passes of every orthonormalisation whose
+                                       Cholesky runs in FP32 instead of FP64 [6 = all],
+                                       0..6; the last pass of a basis runs in FP64 unless
+                                       the value covers every pass. FP32 suffices: the
+                                       first, shifted pass only preconditions Y (any
+                                       invertible R leaves span(Y R^-1) = span(Y)), each
+                                       later pass squares the orthogonality error, and the
+                                       basis polish (KFAC_OPT_BASIS_POLISH) squares what is
+                                       left */
+  KFAC_OPT_EIG_STOP_TOL = 9         /* [3e-3]: Jacobi also stops after a sweep in which
+                                       every pair cosine, taken before its rotation, was <= v;
+                                       cyclic Jacobi converges quadratically, so that sweep
+                                       leaves them near v^2, and the FP64 refinement that
+                                       follows squares the remaining error again. 0: sweep
+                                       until a sweep rotates no pair (every pair cosine <=
+                                       KFAC_OPT_EIG_TOL) */
 } kfac_option;
 
 KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double value);

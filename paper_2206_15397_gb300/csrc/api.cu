@@ -50,13 +50,14 @@ struct kfac_ctx {
   // options
   int cholqr_passes = 3;
   int cholqr_inner_passes = 3;
-  int cholqr_fp32_passes = 1;
+  int cholqr_fp32_passes = 6;
   int basis_polish = 1;
   int cholqr_inner_fp32 = 1;
   double cholqr_shift = 1e-5;
   int eig_refine = 1;
   int eig_max_sweeps = 40;
   double eig_tol = 2e-6;
+  double eig_stop_tol = 3e-3;
 };
 
 namespace {
@@ -248,7 +249,8 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       // the factorisation indefinite; the last pass (a near-orthonormal basis)
       // is unshifted.
       const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-5 : 0.0);
-      const bool fp64 = (final_basis || !ctx->cholqr_inner_fp32) && (pass >= ctx->cholqr_fp32_passes || pass + 1 == passes);
+      const bool fp64 = (final_basis || !ctx->cholqr_inner_fp32) &&
+                        (pass >= ctx->cholqr_fp32_passes || (pass + 1 == passes && ctx->cholqr_fp32_passes < passes));
       CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
                       ctx->stream, nullptr, at<float>(ctx, L.g32), k));
     }
@@ -265,7 +267,8 @@ kfac_status eigensolve(kfac_ctx* ctx, const double* C, const float* C32, long lo
                        double* lam, double* work, float* jac) {
   {
     STAGE(ctx, ST_EIG);
-    CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, X, lam, jac, ctx->dflags,
+    CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, (float)ctx->eig_stop_tol, X, lam, jac,
+                      ctx->dflags,
                         ctx->dstats, ctx->stream, C32, ld32));
   }
   STAGE(ctx, ST_REFINE);
@@ -601,8 +604,12 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       ctx->basis_polish = (int)v;
       return KFAC_OK;
     case KFAC_OPT_CHOLQR_FP32_PASSES:
-      if (v < 0 || v > 5) return KFAC_ERR_INVALID_ARG;
+      if (v < 0 || v > 6) return KFAC_ERR_INVALID_ARG;
       ctx->cholqr_fp32_passes = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_EIG_STOP_TOL:
+      if (!(v >= 0 && v < 1)) return KFAC_ERR_INVALID_ARG;
+      ctx->eig_stop_tol = v;
       return KFAC_OK;
   }
   return KFAC_ERR_INVALID_ARG;

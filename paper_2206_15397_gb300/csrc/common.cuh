@@ -130,9 +130,10 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
 // (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:
 // eig_scratch_floats(k) floats (the Cholesky factor and the shift it used).
 inline size_t eig_scratch_floats(int k) { return (((size_t)k * k + 1) & ~(size_t)1) + 4; }
-cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
-                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s,
-                           const float* C32 = nullptr, long long ld32 = 0);
+// stop_tol > 0 ends the sweeps after one whose largest pair cosine was below it.
+cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, float stop_tol,
+                           double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
+                           cudaStream_t s, const float* C32 = nullptr, long long ld32 = 0);
 
 // G <- (3 I - G) / 2 in place (k x k FP64): one Newton-Schulz step towards
 // G^-1/2 for a Gram G = Q^T Q near I, so Q (3I - G)/2 is orthonormal to

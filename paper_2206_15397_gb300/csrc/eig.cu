@@ -42,7 +42,7 @@ __device__ __forceinline__ float warp_sum_all(float v) {
 // columns are given as offsets into it, so every access stays a shared-memory
 // access (a generic pointer would turn them into generic loads).
 template <int NI>
-__device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol, int lane) {
+__device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol, float& off2, int lane) {
   // Columns are zero-padded to NI * 128 floats: each lane holds NI float4s of
   // both columns in registers from the dot products to the rotation, and the
   // padding stays zero under rotations.
@@ -64,7 +64,9 @@ __device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol,
   al = warp_sum_all(al);
   be = warp_sum_all(be);
   ga = warp_sum_all(ga);
-  if (!(ga != 0.0f && ga * ga > (tol * tol) * (al * be))) return 0;
+  const float g2 = ga * ga, ab = al * be;
+  if (ab > 0.0f) off2 = fmaxf(off2, __fdividef(g2, ab));  // squared cosine of the pair's angle
+  if (!(ga != 0.0f && g2 > (tol * tol) * ab)) return 0;
   // 2x2 symmetric Schur step on the Gram [[al, ga], [ga, be]]: J = [[c, s], [-s, c]],
   // t = sign(z) / (|z| + sqrt(1 + z^2)), z = (be - al) / (2 ga): scale-invariant
   // (a form that squares be - al and ga underflows on factors of scale ~1e-6).
@@ -109,6 +111,7 @@ struct EigArgs {
   unsigned long long* stats;
   int b;   // columns per block (the cluster holds 2 * NC blocks)
   int kp;  // padded column length in shared memory (multiple of 128)
+  float stop_tol;  // > 0: stop after a sweep whose largest pair cosine was below it
 };
 
 // One-sided Jacobi on the columns of L = chol(C + sI), spread over a cluster.
@@ -134,7 +137,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   const int k = a.k, b = a.b, kp = a.kp, nb = 2 * NC;
   const int slot = b * kp;  // floats per slot; buffer x starts at offset 2 * slot * x (top slot, then bottom)
   __shared__ int s_count, s_total;
-  if (tid == 0) s_total = 0;
+  __shared__ unsigned s_off, s_offmax;  // largest squared pair cosine of a sweep (FP32 bits, >= 0)
+  if (tid == 0) { s_total = 0; s_offmax = 0u; }
 
   // ---- initial blocks (round 0 positions) from the factor ------------------
   // (asynchronous copies, all in flight at once; zero outside the factor)
@@ -155,10 +159,11 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   cluster.sync();
 
   // ---- sweeps ---------------------------------------------------------------
-  int sweep = 0, cur = 0;
-  for (; sweep < a.max_sweeps; ++sweep) {
-    if (tid == 0) s_count = 0;
+  int sweep = 0, cur = 0, done = 0;
+  for (; sweep < a.max_sweeps && !done; ++sweep) {
+    if (tid == 0) { s_count = 0; s_off = 0u; }
     __syncthreads();
+    float off2 = 0.0f;
     for (int t = 0; t < nb - 1; ++t) {
       const int blkA = rr_player(rank, t, nb), blkB = rr_player(nb - 1 - rank, t, nb);
       const int ba = max(0, min(k, blkA * b + b) - blkA * b);
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
             if (u < n2 && v < n2) {
               const int cu = u < ba ? top + u * kp : bot + (u - ba) * kp;
               const int cv = v < ba ? top + v * kp : bot + (v - ba) * kp;
-              cnt += jacobi_pair<NI>(esm, cu, cv, a.tol, lane);
+              cnt += jacobi_pair<NI>(esm, cu, cv, a.tol, off2, lane);
             }
           }
           __syncthreads();
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
         for (int r = 0; r < bmax; ++r) {
           for (int i = warp; i < bmax; i += EIG_WARPS) {
             int j = (i + r) % bmax;
-            if (i < ba && j < bb) cnt += jacobi_pair<NI>(esm, top + i * kp, bot + j * kp, a.tol, lane);
+            if (i < ba && j < bb) cnt += jacobi_pair<NI>(esm, top + i * kp, bot + j * kp, a.tol, off2, lane);
           }
           __syncthreads();
         }
@@ -214,19 +219,26 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
         cur = nxt;
       }
     }
+    if (lane == 0 && off2 > 0.0f) atomicMax(&s_off, __float_as_uint(off2));
     __syncthreads();  // every warp's count is in s_count (a 1-CTA cluster has no barrier above)
-    // convergence: total rotations of the sweep over the cluster
+    // convergence: total rotations of the sweep over the cluster, and its
+    // largest pair cosine (non-negative floats order as their bit patterns)
     if (tid == 0 && s_count) atomicAdd(cluster.map_shared_rank(&s_total, 0), s_count);
+    if (tid == 0 && s_off) atomicMax(cluster.map_shared_rank(&s_offmax, 0), s_off);
     cluster.sync();
     const int total = *cluster.map_shared_rank(&s_total, 0);
+    const float offmax = __uint_as_float(*cluster.map_shared_rank(&s_offmax, 0));
     cluster.sync();
-    if (rank == 0 && tid == 0) s_total = 0;
-    if (total == 0) break;
+    if (rank == 0 && tid == 0) { s_total = 0; s_offmax = 0u; }
+    // Done when a sweep rotated nothing. Cyclic Jacobi converges quadratically:
+    // a sweep that started with every pair cosine below stop_tol leaves them
+    // near stop_tol^2, so the sweep that would only confirm it is skipped.
+    done = total == 0 || (a.stop_tol > 0.0f && offmax <= a.stop_tol * a.stop_tol);
   }
   if (rank == 0 && tid == 0) {
-    if (sweep >= a.max_sweeps) raise_flag(a.flags, KFAC_FLAG_EIG_NOCONV);
+    if (!done) raise_flag(a.flags, KFAC_FLAG_EIG_NOCONV);
     if (a.stats) {
-      atomicAdd(a.stats + STAT_SWEEPS, (unsigned long long)(sweep < a.max_sweeps ? sweep + 1 : sweep));
+      atomicAdd(a.stats + STAT_SWEEPS, (unsigned long long)sweep);
       atomicAdd(a.stats + STAT_EIG_SOLVES, 1ull);
     }
   }
@@ -417,9 +429,9 @@ static cudaError_t launch_eig(const EigArgs& a, int nc, size_t smem, cudaStream_
   return cudaLaunchKernelEx(&cfg, k_eig_cluster<NI>, a);
 }
 
-cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, double* X,
-                           double* lam, float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s,
-                           const float* C32, long long ld32) {
+cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, float stop_tol,
+                           double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
+                           cudaStream_t s, const float* C32, long long ld32) {
   if (k <= 0) return cudaSuccess;
   // W = L with L L^T = C + sI, factorised on a cluster in FP32; the shift it
   // used (grown on breakdown) is stored after the factor.
@@ -434,7 +446,7 @@ cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_swe
   const int kp = (k + 127) / 128 * 128;  // float4 per lane, 32 lanes
   const size_t smem = sizeof(float) * 4 * (size_t)b * kp;  // 2 buffers x 2 slots
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
-  EigArgs a = {gscratch, shift, k, max_sweeps, tol, X, lam, flags, stats, b, kp};
+  EigArgs a = {gscratch, shift, k, max_sweeps, tol, X, lam, flags, stats, b, kp, stop_tol};
   switch (kp / 128) {
     case 1: return launch_eig<1>(a, nc, smem, s);
     case 2: return launch_eig<2>(a, nc, smem, s);
