@@ -251,7 +251,7 @@ KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags);
 typedef enum {
   KFAC_OPT_CHOLQR_PASSES = 0,   /* CholeskyQR passes for the final basis Q [3], 1..6      */
   KFAC_OPT_CHOLQR_SHIFT = 1,    /* first-pass diagonal shift, relative to trace(G) [1e-5] */
-  KFAC_OPT_EIG_REFINE = 2,      /* FP64 eigen-refinement steps after FP32 Jacobi [1], 0..3 */
+  KFAC_OPT_EIG_REFINE = 2,      /* eigen-refinement steps after FP32 Jacobi [1], 0..3    */
   KFAC_OPT_EIG_MAX_SWEEPS = 3,  /* Jacobi sweep cap [40]                                  */
   KFAC_OPT_EIG_TOL = 4,         /* Jacobi pair-orthogonality threshold [2e-6]            */
   KFAC_OPT_CHOLQR_INNER_PASSES = 5, /* passes for a basis that only feeds the next power
@@ -284,7 +284,13 @@ typedef enum {
                                        leaves them near v^2, and the FP64 refinement that
                                        follows squares the remaining error again. 0: sweep
                                        until a sweep rotates no pair (every pair cosine <=
-                                       KFAC_OPT_EIG_TOL) */
+                                       KFAC_OPT_EIG_TOL) */,
+  KFAC_OPT_EIG_REFINE_FP64 = 10     /* 0 [default]: the eigen-refinement and basis-polish
+                                       k x k products run in FP32 (FP64 carries the matrices
+                                       between steps); their rounding, ~6e-8 of ||C||, is at
+                                       the accuracy the FP32-accurate projection C carries.
+                                       1: FP64 products (FP64 issues at ~1/64 of the FP32
+                                       rate on this part) */
 } kfac_option;
 
 KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double value);

@@ -58,6 +58,7 @@ struct kfac_ctx {
   int eig_max_sweeps = 40;
   double eig_tol = 2e-6;
   double eig_stop_tol = 3e-3;
+  int eig_refine_fp64 = 0;
 };
 
 namespace {
@@ -148,7 +149,7 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, p32, skws, total;
+  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, p32, skws, total;
   long long dp, skws_floats;
   int nsplit, kchunk;
 };
@@ -165,6 +166,7 @@ InvertLayout invert_layout(int d, int k, int r) {
     L.lam = b.take<double>(n);
     L.work = b.take<double>(eig_refine_doubles(n));
     L.jac = b.take<float>(eig_scratch_floats(n));
+    L.r32 = b.take<float>(eig_refine_floats(n));
     L.total = b.off;
     return L;
   }
@@ -186,6 +188,7 @@ InvertLayout invert_layout(int d, int k, int r) {
   L.lam = b.take<double>(k);
   L.work = b.take<double>(eig_refine_doubles(k));
   L.jac = b.take<float>(eig_scratch_floats(k));
+  L.r32 = b.take<float>(eig_refine_floats(k) + 3 * (size_t)k * k);  // refinement, then the polish's E, P, Q
   L.p32 = b.take<float>((size_t)k * r);
   L.skws_floats = (long long)kSketchMaxSplit * k * d;
   L.skws = b.take<float>((size_t)L.skws_floats);
@@ -264,15 +267,17 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
 }
 
 kfac_status eigensolve(kfac_ctx* ctx, const double* C, const float* C32, long long ld32, int n, double* X,
-                       double* lam, double* work, float* jac) {
+                       double* lam, double* work, float* jac, float* r32) {
   {
     STAGE(ctx, ST_EIG);
     CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, (float)ctx->eig_stop_tol, X, lam, jac,
-                      ctx->dflags,
-                        ctx->dstats, ctx->stream, C32, ld32));
+                      ctx->dflags, ctx->dstats, ctx->stream, C32, ld32));
   }
   STAGE(ctx, ST_REFINE);
-  for (int it = 0; it < ctx->eig_refine; ++it) CK(eig_refine_f64(C, n, X, lam, work, ctx->dflags, ctx->stream));
+  for (int it = 0; it < ctx->eig_refine; ++it) {
+    if (ctx->eig_refine_fp64) CK(eig_refine_f64(C, n, X, lam, work, ctx->dflags, ctx->stream));
+    else CK(eig_refine_f32(C32, ld32, n, X, lam, r32, work, ctx->dflags, ctx->stream));
+  }
   return KFAC_OK;
 }
 
@@ -309,8 +314,8 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const int d = a.d, r = std::min(a.rank, a.d), k = a.rank + a.oversample;
   const float* F = a.F;
   const int ldf = a.ldf;
-  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac, &L.p32,
-                    &L.skws})
+  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
+                    &L.r32, &L.p32, &L.skws})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;
@@ -318,7 +323,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     double* C = at<double>(ctx, L.c);
     CK(convert_f32_to_f64(F, ldf, d, d, C, d, ctx->dflags, s));
     st = eigensolve(ctx, C, F, ldf, d, at<double>(ctx, L.x), at<double>(ctx, L.lam), at<double>(ctx, L.work),
-                    at<float>(ctx, L.jac));
+                    at<float>(ctx, L.jac), at<float>(ctx, L.r32));
     if (st != KFAC_OK) return st;
     STAGE(ctx, ST_SELECT);
     CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), d, r, a.lambda, nullptr, a.D, a.coef, a.U, a.ldu,
@@ -348,13 +353,19 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   // Newton-Schulz polish of the final basis, in the k x k space: M = (3I - Q^T Q)/2
   // makes Q M orthonormal to second order; the Rayleigh-Ritz step below uses
   // Q M (C <- M C M, X <- M X) without touching the d x k basis.
+  // With FP32 products (default) the polish works on E = Q^T Q - I (M = I - E/2);
+  // the FP64 form builds M and multiplies by it.
+  const bool polish = ctx->basis_polish != 0, polish64 = polish && ctx->eig_refine_fp64;
+  float* pw32 = at<float>(ctx, L.r32) + eig_refine_floats(k);  // E, P, Q of the FP32 polish
   double* Mpol = nullptr;
-  if (ctx->basis_polish) {
+  if (polish) {
     st = gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_POLISH, nullptr);
     if (st != KFAC_OK) return st;
-    STAGE(ctx, ST_POLISH);
-    CK(polish_factor(at<double>(ctx, L.g), k, s));
-    Mpol = at<double>(ctx, L.g);
+    if (polish64) {
+      STAGE(ctx, ST_POLISH);
+      CK(polish_factor(at<double>(ctx, L.g), k, s));
+      Mpol = at<double>(ctx, L.g);
+    }
   }
   // Projection C = Q^T F Q = Q^T (F Q): Z^T = Q^T F into `other`, then C = Q^T Z.
   st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);
@@ -368,15 +379,21 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     CK(small_product_f64(C, Mpol, T, k, s));
     CK(small_product_f64(Mpol, T, C, k, s));
     CK(convert_f64_to_f32(C, (long long)k * k, at<float>(ctx, L.c32), s));
+  } else if (polish) {
+    STAGE(ctx, ST_POLISH);
+    CK(polish_projected_f32(at<double>(ctx, L.g), C, at<float>(ctx, L.c32), k, pw32, s));
   }
   st = eigensolve(ctx, C, at<float>(ctx, L.c32), k, k, at<double>(ctx, L.x), at<double>(ctx, L.lam),
-                  at<double>(ctx, L.work), at<float>(ctx, L.jac));
+                  at<double>(ctx, L.work), at<float>(ctx, L.jac), at<float>(ctx, L.r32));
   if (st != KFAC_OK) return st;
   if (Mpol) {  // eigenvectors in the polished basis: X <- M X
     STAGE(ctx, ST_POLISH);
     double* T = at<double>(ctx, L.work);
     CK(small_product_f64(Mpol, at<double>(ctx, L.x), T, k, s));
     CK(cudaMemcpyAsync(at<double>(ctx, L.x), T, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, s));
+  } else if (polish) {
+    STAGE(ctx, ST_POLISH);
+    CK(polish_vectors_f32(at<double>(ctx, L.x), k, pw32, s));
   }
   float* P32 = at<float>(ctx, L.p32);
   {
@@ -610,6 +627,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
     case KFAC_OPT_EIG_STOP_TOL:
       if (!(v >= 0 && v < 1)) return KFAC_ERR_INVALID_ARG;
       ctx->eig_stop_tol = v;
+      return KFAC_OK;
+    case KFAC_OPT_EIG_REFINE_FP64:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->eig_refine_fp64 = (int)v;
       return KFAC_OK;
   }
   return KFAC_ERR_INVALID_ARG;

@@ -98,6 +98,8 @@ struct GemmDesc {
 // ---- launchers (host) --------------------------------------------------------
 cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s);
 cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s);
+// FP32 product with 16 x 16 output tiles (plain FP32 FMA), for k x k matrices.
+cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s);
 // out[i, j] = sum_z part[z][i, j] in FP64 (n x n), optionally symmetrised as
 // (S + S^T) / 2. part has row stride ldp and z stride zstride.
 // out32 (optional): an FP32 copy of the result, n x n dense.
@@ -146,6 +148,17 @@ cudaError_t convert_f64_to_f32(const double* in, long long n, float* out, cudaSt
 inline size_t eig_refine_doubles(int k) { return 5 * (size_t)k * k + 3 * 128; }
 cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, double* work, int* flags,
                            cudaStream_t s);
+// The same step with FP32 k x k products (C32 = FP32 copy of C, row stride
+// ldc32): their rounding (~6e-8 of ||C||) is at the accuracy C itself carries.
+// w32: eig_refine_floats(k) floats; part: 3 * 128 doubles.
+inline size_t eig_refine_floats(int k) { return 7 * (size_t)k * k; }
+cudaError_t eig_refine_f32(const float* C32, long long ldc32, int k, double* X, double* lam, float* w32, double* part,
+                           int* flags, cudaStream_t s);
+// Basis polish in FP32 products: with E = G - I (G = Q^T Q, FP64) and
+// M = I - E/2 = (3I - G)/2, C <- M C M (C32 updated too) keeps E in the first
+// 3 k^2 floats of w32 for polish_vectors_f32, which applies X <- M X.
+cudaError_t polish_projected_f32(const double* G, double* C, float* C32, int k, float* w32, cudaStream_t s);
+cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s);
 
 // Sort eigenpairs descending (stable by index), emit the r leading ones:
 // P32 (k x r FP32, columns = eigenvectors), D and coef (FP32, Eq. (13)), and

@@ -507,6 +507,127 @@ __global__ void k_f64_to_f32(const double* __restrict__ in, long long n, float* 
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
 }
+
+// ---- FP32 refinement and polish (k x k) ------------------------------------
+// X (FP64) -> X32 = X and Xt32 = X^T in FP32, 32 x 32 tiles through shared
+// memory (both stores coalesced).
+__global__ void k_split_f32_t(const double* __restrict__ X, int k, float* __restrict__ X32, float* __restrict__ Xt32) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int r = r0 + y, c = c0 + tx;
+    float v = 0.0f;
+    if (r < k && c < k) {
+      v = (float)X[(size_t)r * k + c];
+      if (X32) X32[(size_t)r * k + c] = v;
+    }
+    tile[y][tx] = v;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int c = c0 + y, r = r0 + tx;  // Xt32[c][r] = X[r][c]
+    if (r < k && c < k) Xt32[(size_t)c * k + r] = tile[tx][y];
+  }
+}
+
+// lam_i = S_ii / G_ii (G = X^T X) and per-CTA partial sums of ||S - diag(lam)||^2,
+// ||C||^2, ||I - G||^2; a CTA takes whole rows.
+__global__ void __launch_bounds__(REF_THREADS) k_refine_norms32(const float* __restrict__ C32, long long ldc32,
+                                                                 const float* __restrict__ G,
+                                                                 const float* __restrict__ S, int k,
+                                                                 double* __restrict__ lam, double* __restrict__ part) {
+  __shared__ double red[REF_THREADS / 32];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = blockIdx.x; i < k; i += gridDim.x) {
+    const float* Si = S + (size_t)i * k;
+    const float* Gi = G + (size_t)i * k;
+    const float* Ci = C32 + (size_t)i * ldc32;
+    if (threadIdx.x == 0) lam[i] = (double)Si[i] / (double)Gi[i];
+    for (int j = threadIdx.x; j < k; j += REF_THREADS) {
+      const double sv = i == j ? (double)Si[i] - (double)Si[i] / (double)Gi[i] : (double)Si[j];  // S - diag(lam)
+      const float rv = (i == j ? 1.0f : 0.0f) - Gi[j];
+      a = fma(sv, sv, a);
+      b = fma((double)Ci[j], (double)Ci[j], b);
+      c = fma((double)rv, (double)rv, c);
+    }
+  }
+  const double A = block_sum_ref(a, red);
+  const double Bn = block_sum_ref(b, red);
+  const double Cn = block_sum_ref(c, red);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x + 0] = A;
+    part[3 * blockIdx.x + 1] = Bn;
+    part[3 * blockIdx.x + 2] = Cn;
+  }
+}
+
+// E^T (FP32): E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) for separated
+// pairs, R_ij / 2 otherwise (R = I - G); the threshold as k_refine_E.
+__global__ void __launch_bounds__(REF_THREADS) k_refine_Et32(const float* __restrict__ G, const float* __restrict__ S,
+                                                              int k, const double* __restrict__ lam,
+                                                              const double* __restrict__ part, int nparts,
+                                                              float* __restrict__ Et, int* flags) {
+  __shared__ double s_delta;
+  if (threadIdx.x < 32) {
+    double A = 0.0, Bn = 0.0, Cn = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += 32) {
+      A += part[3 * p];
+      Bn += part[3 * p + 1];
+      Cn += part[3 * p + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      A += __shfl_xor_sync(0xffffffffu, A, o);
+      Bn += __shfl_xor_sync(0xffffffffu, Bn, o);
+      Cn += __shfl_xor_sync(0xffffffffu, Cn, o);
+    }
+    if (threadIdx.x == 0) {
+      s_delta = 2.0 * (sqrt(A) + sqrt(Bn) * sqrt(Cn));
+      if (blockIdx.x == 0 && !isfinite(s_delta)) raise_flag(flags, KFAC_FLAG_NONFINITE);
+    }
+  }
+  __syncthreads();
+  const float delta = (float)s_delta;
+  for (int j = blockIdx.x; j < k; j += gridDim.x) {  // row j of E^T = column j of E
+    const float lj = (float)lam[j];
+    for (int i = threadIdx.x; i < k; i += REF_THREADS) {
+      const float rij = (i == j ? 1.0f : 0.0f) - G[(size_t)i * k + j];
+      float v;
+      if (i == j) {
+        v = 0.5f * rij;
+      } else {
+        const float gap = (float)(lam[j] - lam[i]);
+        v = (fabsf(gap) > delta) ? __fdiv_rn(fmaf(lj, rij, S[(size_t)i * k + j]), gap) : 0.5f * rij;
+      }
+      Et[(size_t)j * k + i] = v;
+    }
+  }
+}
+
+// X += alpha * D (FP64 += FP32), k x k.
+__global__ void k_axpy_f64_f32(double* __restrict__ X, const float* __restrict__ D, long long n, double alpha) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    X[e] = fma(alpha, (double)D[e], X[e]);
+}
+
+// E32 = G - I in FP32 (from the FP64 Gram, so the diagonal keeps its small part).
+__global__ void k_polish_E32(const double* __restrict__ G, int k, float* __restrict__ E32) {
+  for (int i = blockIdx.x; i < k; i += gridDim.x)
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+      E32[(size_t)i * k + j] = (float)(G[(size_t)i * k + j] - (i == j ? 1.0 : 0.0));
+}
+
+// C <- C - (P + P^T)/2 + (Q + Q^T)/8 with P = E C and Q = E C E: the same
+// symmetric result as M C M for M = I - E/2, and C32 = C.
+__global__ void k_polish_apply(double* __restrict__ C, const float* __restrict__ P, const float* __restrict__ Q,
+                               int k, float* __restrict__ C32) {
+  for (int i = blockIdx.x; i < k; i += gridDim.x)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      const size_t ij = (size_t)i * k + j, ji = (size_t)j * k + i;
+      const double v = C[ij] - 0.5 * ((double)P[ij] + (double)P[ji]) + 0.125 * ((double)Q[ij] + (double)Q[ji]);
+      C[ij] = v;
+      C32[ij] = (float)v;
+    }
+}
 }  // namespace
 
 cudaError_t polish_factor(double* G, int k, cudaStream_t s) {
@@ -534,6 +655,85 @@ cudaError_t eig_select(const double* X, const double* lam, int k, int r, float l
   grid = grid < 1 ? 1 : (grid > 152 ? 152 : grid);
   k_eig_select<<<grid, 1024, (sizeof(double) + sizeof(int)) * k + 8, s>>>(X, lam, k, r, lambda, P32, D, coef, Uout,
                                                                            ldu);
+  note_launch();
+  return cudaGetLastError();
+}
+
+
+namespace {
+// D (k x k, row stride k) = A B^T for row-major A (row stride lda) and B in FP32.
+cudaError_t small_nt(const float* A, const float* B, float* D, int k, bool d_trans, cudaStream_t s,
+                     long long lda = 0) {
+  GemmDesc<float> g = {};
+  g.M = k; g.N = k; g.K = k; g.alpha = 1.0f; g.beta = 0.0f; g.zsplit = 1;
+  g.A = A; g.sam = lda > 0 ? lda : k; g.sak = 1;
+  g.B = B; g.sbn = k; g.sbk = 1;
+  g.D = D; g.ldd = k; g.d_trans = d_trans ? 1 : 0;
+  return gemm_small_f32(g, s);
+}
+int row_grid(int k) { return k < 1 ? 1 : (k > REF_MAX_BLOCKS ? REF_MAX_BLOCKS : k); }
+}  // namespace
+
+cudaError_t eig_refine_f32(const float* C32, long long ldc32, int k, double* X, double* lam, float* w32, double* part,
+                           int* flags, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  const size_t kk = (size_t)k * k;
+  float* X32 = w32;
+  float* Xt = w32 + kk;
+  float* G = w32 + 2 * kk;
+  float* CXt = w32 + 3 * kk;
+  float* S = w32 + 4 * kk;
+  float* Et = w32 + 5 * kk;
+  float* XE = w32 + 6 * kk;
+  const dim3 tg((k + 31) / 32, (k + 31) / 32);
+  k_split_f32_t<<<tg, dim3(32, 8), 0, s>>>(X, k, X32, Xt);
+  note_launch();
+  cudaError_t e;
+  if ((e = small_nt(Xt, Xt, G, k, false, s)) != cudaSuccess) return e;   // G = X^T X
+  if ((e = small_nt(C32, Xt, CXt, k, true, s, ldc32)) != cudaSuccess) return e; // (C X)^T
+  if ((e = small_nt(Xt, CXt, S, k, false, s)) != cudaSuccess) return e;  // S = X^T C X
+  const int nb = row_grid(k);
+  k_refine_norms32<<<nb, REF_THREADS, 0, s>>>(C32, ldc32, G, S, k, lam, part);
+  note_launch();
+  k_refine_Et32<<<nb, REF_THREADS, 0, s>>>(G, S, k, lam, part, nb, Et, flags);
+  note_launch();
+  if ((e = small_nt(X32, Et, XE, k, false, s)) != cudaSuccess) return e;  // X E
+  const int ag = (int)std::min<long long>(304, ((long long)kk + 255) / 256);
+  k_axpy_f64_f32<<<ag, 256, 0, s>>>(X, XE, (long long)kk, 1.0);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t polish_projected_f32(const double* G, double* C, float* C32, int k, float* w32, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  const size_t kk = (size_t)k * k;
+  float* E = w32;  // kept for polish_vectors_f32
+  float* P = w32 + kk;
+  float* Q = w32 + 2 * kk;
+  const int nb = row_grid(k);
+  k_polish_E32<<<nb, 256, 0, s>>>(G, k, E);
+  note_launch();
+  cudaError_t e;
+  if ((e = small_nt(E, C32, P, k, false, s)) != cudaSuccess) return e;  // P = E C (C symmetric)
+  if ((e = small_nt(P, E, Q, k, false, s)) != cudaSuccess) return e;    // Q = P E (E symmetric)
+  k_polish_apply<<<nb, 256, 0, s>>>(C, P, Q, k, C32);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  const size_t kk = (size_t)k * k;
+  const float* E = w32;
+  float* Xt = w32 + kk;
+  float* EX = w32 + 2 * kk;
+  const dim3 tg((k + 31) / 32, (k + 31) / 32);
+  k_split_f32_t<<<tg, dim3(32, 8), 0, s>>>(X, k, nullptr, Xt);
+  note_launch();
+  cudaError_t e;
+  if ((e = small_nt(E, Xt, EX, k, false, s)) != cudaSuccess) return e;  // E X
+  const int ag = (int)std::min<long long>(304, ((long long)kk + 255) / 256);
+  k_axpy_f64_f32<<<ag, 256, 0, s>>>(X, EX, (long long)kk, -0.5);
   note_launch();
   return cudaGetLastError();
 }

@@ -97,25 +97,27 @@ cudaError_t launch_gemm(const GemmDesc<T>& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// FP64 GEMM with 16 x 16 output tiles, one output per thread: FP64 issues at
-// ~2 FMA/clock/SM on this part, so small tiles spread a k x k product over as
-// many SMs as possible (k = 230 gives 225 CTAs).
-__global__ void __launch_bounds__(256) k_gemm_f64_t16(GemmDesc<double> g) {
-  __shared__ double As[16][17];
-  __shared__ double Bs[16][17];
+// Small GEMM with 16 x 16 output tiles, one output per thread, for k x k
+// products (k = 230 gives 225 CTAs): FP64 issues at ~2 FMA/clock/SM on this
+// part, and a k x k FP32 product is latency-bound, so small tiles spread it
+// over as many SMs as possible.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_t16(GemmDesc<T> g) {
+  __shared__ T As[16][17];
+  __shared__ T Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m = blockIdx.y * 16 + ty, n = blockIdx.x * 16 + tx;
-  double acc = 0.0;
+  T acc = T(0);
   for (int k0 = 0; k0 < g.K; k0 += 16) {
     {  // A tile: element (row ty, k tx) or transposed pattern for coalescing
       int mm = ty, kk = tx;
       if (g.sak != 1) { mm = tx; kk = ty; }
       int am = blockIdx.y * 16 + mm, ak = k0 + kk;
-      As[mm][kk] = (am < g.M && ak < g.K) ? g.A[(long long)am * g.sam + (long long)ak * g.sak] : 0.0;
+      As[mm][kk] = (am < g.M && ak < g.K) ? g.A[(long long)am * g.sam + (long long)ak * g.sak] : T(0);
       int nn = ty, kb = tx;
       if (g.sbk != 1) { nn = tx; kb = ty; }
       int bn = blockIdx.x * 16 + nn, bk = k0 + kb;
-      Bs[nn][kb] = (bn < g.N && bk < g.K) ? g.B[(long long)bn * g.sbn + (long long)bk * g.sbk] : 0.0;
+      Bs[nn][kb] = (bn < g.N && bk < g.K) ? g.B[(long long)bn * g.sbn + (long long)bk * g.sbk] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -123,10 +125,10 @@ __global__ void __launch_bounds__(256) k_gemm_f64_t16(GemmDesc<double> g) {
     __syncthreads();
   }
   if (m < g.M && n < g.N) {
-    double v = acc * g.alpha;
+    T v = acc * g.alpha;
     if (g.rowscale) v *= g.rowscale[m];
     if (g.colscale) v *= g.colscale[n];
-    if (g.beta != 0.0) v = fma(g.beta, g.C0[g.c0_trans ? (long long)n * g.ldc + m : (long long)m * g.ldc + n], v);
+    if (g.beta != T(0)) v = fma(g.beta, g.C0[g.c0_trans ? (long long)n * g.ldc + m : (long long)m * g.ldc + n], v);
     g.D[g.d_trans ? (long long)n * g.ldd + m : (long long)m * g.ldd + n] = v;
   }
 }
@@ -192,7 +194,16 @@ cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (g.zsplit > 1) return launch_gemm<double, Round::None>(g, s);
   dim3 grid((g.N + 15) / 16, (g.M + 15) / 16);
-  k_gemm_f64_t16<<<grid, 256, 0, s>>>(g);
+  k_gemm_t16<double><<<grid, 256, 0, s>>>(g);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.zsplit > 1) return launch_gemm<float, Round::None>(g, s);
+  dim3 grid((g.N + 15) / 16, (g.M + 15) / 16);
+  k_gemm_t16<float><<<grid, 256, 0, s>>>(g);
   note_launch();
   return cudaGetLastError();
 }
