@@ -360,95 +360,139 @@ cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, in
 
 // ---------------------------------------------------------------------------
 // FP32 Cholesky of (G + shift I) on one CTA with the whole matrix in shared
-// memory (k <= CTA_KMAX), for the shifted first CholeskyQR pass and the
-// eigensolver's factor: no cluster barriers or distributed-memory broadcasts,
-// which dominate the cluster kernel at these sizes. Right-looking, 32-column
-// panels with a look-ahead of one panel:
-//   (1) panel rows below the diagonal block: one warp per group of rows, lane
-//       c owning column c; the substitution x_s = a_s / L_ss, a_c -= L_cs x_s
-//       passes x_s by shuffle, L11's row c held in lane c's registers;
-//   (2) the rank-32 update of the next block column (rows below it included);
-//   (3) warp 0 factors the next 32 x 32 diagonal block in registers (lane r
-//       holds row r; per pivot t the pivot and column t travel by shuffles)
-//       while the other 15 warps apply the rank-32 update to the rest of the
-//       trailing lower triangle.
-// The updates use 4 x 4 output tiles per thread, a warp covering 8 x 4 tiles
-// so that its row reads fall in distinct banks (odd row stride).
-// Pivot floor, raised pivots and restarts follow the cluster kernel.
+// memory (k <= CTA_KMAX), for the CholeskyQR passes and the eigensolver's
+// factor: no cluster barriers or distributed-memory broadcasts, which dominate
+// the cluster kernel at these sizes. Right-looking, PW-column panels with a
+// look-ahead of one panel:
+//   (1) panel rows below the diagonal block: L21 = A21 L11^-T as a product
+//       with the explicit inverse of L11 (formed with the factor), 4 x 4
+//       output tiles per thread;
+//   (2) the rank-PW update of the next block column (rows below it included);
+//   (3) warp 0 factors and inverts the next PW x PW diagonal block in
+//       registers (pivot and columns by shuffles) while the other 15 warps
+//       apply the rank-PW update to the rest of the trailing lower triangle.
+// The diagonal block's pivot chain is the critical path of (3) and its cost
+// grows with PW^2, while the number of phases grows as k / PW: 16-column
+// panels balance the two at k ~ 230. The updates use 4 x 4 output tiles per
+// thread, a warp covering 8 x 4 tiles so that its row reads fall in distinct
+// banks (odd row stride). Pivot floor, raised pivots and restarts follow the
+// cluster kernel.
 constexpr int CTA_THREADS = 512;
 constexpr int CTA_WARPS = CTA_THREADS / 32;
 constexpr int CTA_KMAX = 236;
+constexpr int PW = 16;          // panel width
+constexpr int XI_LD = PW + 1;   // row stride of the diagonal-block inverse
 
 __host__ __device__ inline int cta_ks(int k) { return k | 1; }  // odd row stride: rows hit distinct banks
-__host__ __device__ inline size_t cta_smem_bytes(int k) { return sizeof(float) * ((size_t)k * cta_ks(k) + 64) + 16; }
+// A (k x ks), rinv (PW), Xi (PW x XI_LD), flags.
+__host__ __device__ inline size_t cta_smem_bytes(int k) {
+  return sizeof(float) * ((size_t)k * cta_ks(k) + PW + PW * XI_LD) + 16;
+}
 
-// Warp 0: factor the diagonal block A[j0 .. j0+jb)^2 in place; reciprocal
-// pivots to rinv. Sets sflag[0] on a non-finite pivot, sflag[1] on a raised one.
-__device__ __forceinline__ void cta_factor_diag(float* A, int ks, int j0, int jb, float* rinv, const double* G, int k,
-                                                double shift, float pfloor, int* sflag, int lane) {
-  float x[32];
+// Warp 0: factor the diagonal block A[j0 .. j0+jb)^2 (jb <= PW) in place,
+// reciprocal pivots to rinv, the inverse of the factor to Xi (Xi[j][c] =
+// (L11^-1)_jc, lower). Lane r < PW holds row r of the block and row r of W,
+// which starts as I and takes the same row operations as the factorisation
+// (scale row t by 1/L_tt, subtract L_rt times row t from the rows below), so
+// that it ends as L11^-1. Sets sflag[0] on a non-finite pivot, sflag[1] on a
+// raised one.
+__device__ __forceinline__ void cta_factor_diag(float* A, int ks, int j0, int jb, float* rinv, float* Xi,
+                                                const double* G, int k, double shift, float pfloor, int* sflag,
+                                                int lane) {
+  float x[PW], w[PW];
   const int r = lane;
 #pragma unroll
-  for (int c = 0; c < 32; ++c)
+  for (int c = 0; c < PW; ++c) {
     x[c] = (r < jb && c < jb) ? (c <= r ? A[(size_t)(j0 + r) * ks + j0 + c] : 0.0f) : (r == c ? 1.0f : 0.0f);
+    w[c] = (r == c) ? 1.0f : 0.0f;
+  }
+  // The replacement for a pivot below the floor, one FP64 operation per lane
+  // up front (the FP64 pipe is slow, and the compiler may hoist the rare path).
+  const float rp = r < jb ? raised_pivot(G, k, j0 + r, shift, pfloor) : 1.0f;
   int bad = 0, clamped = 0;
 #pragma unroll
-  for (int t = 0; t < 32; ++t) {
+  for (int t = 0; t < PW; ++t) {
     if (t >= jb) break;  // uniform: padded pivots are identity
     float piv = __shfl_sync(0xffffffffu, x[t], t);
+    const float rpt = __shfl_sync(0xffffffffu, rp, t);
     if (!isfinite(piv)) bad = 1;
     else if (!(piv > pfloor)) {
-      piv = raised_pivot(G, k, j0 + t, shift, pfloor);
+      piv = rpt;
       clamped = 1;
     }
     const float y = rsqrt_newton(piv);
-    if (r == t) { x[t] = piv * y; rinv[t] = y; }
+    if (r == t) {
+      x[t] = piv * y;
+      rinv[t] = y;
+#pragma unroll
+      for (int c = 0; c <= t; ++c) w[c] *= y;
+    }
     const float lt = (r > t) ? x[t] * y : 0.0f;  // L[r][t]
     if (r > t) x[t] = lt;
 #pragma unroll
-    for (int c = t + 1; c < 32; ++c) {
+    for (int c = t + 1; c < PW; ++c) {
       const float lc = __shfl_sync(0xffffffffu, lt, c);  // L[c][t]
       x[c] = fmaf(-lt, lc, x[c]);
+    }
+#pragma unroll
+    for (int c = 0; c <= t; ++c) {
+      const float wt = __shfl_sync(0xffffffffu, w[c], t);  // row t of L11^-1, final
+      if (r > t) w[c] = fmaf(-lt, wt, w[c]);
     }
   }
   if (r < jb) {
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
+    for (int c = 0; c < PW; ++c)
       if (c <= r) A[(size_t)(j0 + r) * ks + j0 + c] = x[c];
+  }
+  if (r < PW) {
+#pragma unroll
+    for (int c = 0; c < PW; ++c) Xi[r * XI_LD + c] = (r < jb && c <= r) ? w[c] : 0.0f;
   }
   bad = __any_sync(0xffffffffu, bad);
   clamped = __any_sync(0xffffffffu, clamped);
   if (lane == 0) { if (bad) sflag[0] = 1; if (clamped) sflag[1] = 1; }
 }
 
-// Rows [first, k) of the panel columns [j0, j0 + jb): L21 = A21 L11^-T by
-// substitution, 4 rows per warp pass. Warps [w0, CTA_WARPS).
-__device__ __forceinline__ void cta_panel_solve(float* A, int ks, int k, int j0, int jb, const float* rinv, int warp,
+// Rows [first, k) of the panel columns [j0, j0 + jb): L21 = A21 L11^-T, i.e.
+// L21[i][c] = sum_s A21[i][s] Xi[c][s]. A warp owns (32 / CG) row groups x CG
+// column groups of 4 x 4 outputs, CG = PW / 4 (at most one such task per
+// warp for k <= CTA_KMAX); results are held in registers over a CTA barrier,
+// then stored in place.
+__device__ __forceinline__ void cta_panel_solve(float* A, int ks, int k, int j0, int jb, const float* Xi, int warp,
                                                 int lane) {
+  constexpr int CG = PW / 4, RG = 32 / CG;
   const int first = j0 + jb;
-  float l[32];  // lane c: L11[c][s], s < c
+  const int i0 = first + 4 * RG * warp + 4 * (lane / CG), c0 = 4 * (lane % CG);
+  const bool active = i0 < k && c0 < jb;
+  float acc[4][4];
 #pragma unroll
-  for (int s2 = 0; s2 < 32; ++s2) l[s2] = (s2 < lane && lane < jb) ? A[(size_t)(j0 + lane) * ks + j0 + s2] : 0.0f;
-  const float rc = lane < jb ? rinv[lane] : 0.0f;
-  constexpr int R = 4;
-  for (int i0 = first + R * warp; i0 < k; i0 += R * CTA_WARPS) {
-    float a[R];
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int q = 0; q < R; ++q)
-      a[q] = (i0 + q < k && lane < jb) ? A[(size_t)(i0 + q) * ks + j0 + lane] : 0.0f;
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+  if (active) {
+    const float* pa[4];
 #pragma unroll
-    for (int s2 = 0; s2 < 32; ++s2) {
-      if (s2 >= jb) break;  // uniform
+    for (int u = 0; u < 4; ++u) pa[u] = A + (size_t)min(i0 + u, k - 1) * ks + j0;
+    for (int s2 = 0; s2 < jb; ++s2) {
+      float av[4], xv[4];
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        const float xs = __shfl_sync(0xffffffffu, a[q] * rc, s2);
-        if (lane == s2) a[q] = xs;
-        else if (lane > s2) a[q] = fmaf(-l[s2], xs, a[q]);
-      }
+      for (int u = 0; u < 4; ++u) av[u] = pa[u][s2];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) xv[v] = Xi[(c0 + v) * XI_LD + s2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], xv[v], acc[u][v]);
     }
+  }
+  __syncthreads();  // every read of A21 done before any store
+  if (active) {
 #pragma unroll
-    for (int q = 0; q < R; ++q)
-      if (i0 + q < k && lane < jb) A[(size_t)(i0 + q) * ks + j0 + lane] = a[q];
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (i0 + u < k && c0 + v < jb) A[(size_t)(i0 + u) * ks + j0 + c0 + v] = acc[u][v];
   }
 }
 
@@ -505,8 +549,9 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
   extern __shared__ __align__(16) float csm[];
   const int ks = cta_ks(k);
   float* A = csm;                        // k x ks, row-major, lower part used
-  float* rinv = A + (size_t)k * ks;      // 32 reciprocal pivots of the current diagonal block
-  int* sflag = reinterpret_cast<int*>(rinv + 32);  // [0] non-finite, [1] clamped
+  float* rinv = A + (size_t)k * ks;      // PW reciprocal pivots of the current diagonal block
+  float* Xi = rinv + PW;                 // PW x XI_LD: inverse of the current diagonal block
+  int* sflag = reinterpret_cast<int*>(Xi + PW * XI_LD);  // [0] non-finite, [1] clamped
   __shared__ double s_trace;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -530,42 +575,34 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
         if (stats) atomicAdd(stats + STAT_CHOL_RETRY, 1ull);
       }
     }
-    {  // load the lower triangle (+ shift): a warp per row pair, 16 loads in flight per lane
-      const float shf = (float)shift;
-      for (int i = 2 * warp; i < k; i += 2 * CTA_WARPS) {
-        float v[2][8];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int ii = i + h, j = lane + 32 * q;
-            // G32 avoids a per-element FP64 -> FP32 conversion on the FP64 pipe
-            v[h][q] = (ii < k && j <= ii) ? (G32 ? G32[(long long)ii * ld32 + j] : (float)G[(size_t)ii * k + j]) : 0.0f;
-          }
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int ii = i + h, j = lane + 32 * q;
-            if (ii < k && j <= ii) A[(size_t)ii * ks + j] = v[h][q] + (ii == j ? shf : 0.0f);
-          }
+    const float shf = (float)shift;
+    if (G32) {  // lower triangle by asynchronous copies (no registers, all in flight), then the shift
+      for (int i = warp; i < k; i += CTA_WARPS) {
+#pragma unroll 1
+        for (int j = lane; j <= i; j += 32) cp_async4(A + (size_t)i * ks + j, G32 + (long long)i * ld32 + j, true);
       }
+      cp_async_wait_all();
+      __syncthreads();
+      if (tid < k) A[(size_t)tid * ks + tid] += shf;
+    } else {  // FP64 input (no FP32 copy given): converted element by element
+      for (int i = warp; i < k; i += CTA_WARPS)
+        for (int j = lane; j <= i; j += 32) A[(size_t)i * ks + j] = (float)G[(size_t)i * k + j] + (i == j ? shf : 0.0f);
     }
     if (tid == 0) { sflag[0] = 0; sflag[1] = 0; }
     __syncthreads();
-    if (warp == 0) cta_factor_diag(A, ks, 0, min(32, k), rinv, G, k, shift, pfloor, sflag, lane);
+    if (warp == 0) cta_factor_diag(A, ks, 0, min(PW, k), rinv, Xi, G, k, shift, pfloor, sflag, lane);
     __syncthreads();
-    for (int j0 = 0; j0 < k && !sflag[0]; j0 += 32) {
-      const int jb = min(32, k - j0);
+    for (int j0 = 0; j0 < k && !sflag[0]; j0 += PW) {
+      const int jb = min(PW, k - j0);
       const int first = j0 + jb;
       if (first >= k) break;
-      const int jb1 = min(32, k - first);
-      cta_panel_solve(A, ks, k, j0, jb, rinv, warp, lane);
+      const int jb1 = min(PW, k - first);
+      cta_panel_solve(A, ks, k, j0, jb, Xi, warp, lane);
       __syncthreads();
       // next block column (its diagonal block and the rows below it)
       cta_rank_update(A, ks, k, j0, jb, first, k, first + jb1, 0, CTA_WARPS, warp, lane);
       __syncthreads();
-      if (warp == 0) cta_factor_diag(A, ks, first, jb1, rinv, G, k, shift, pfloor, sflag, lane);
+      if (warp == 0) cta_factor_diag(A, ks, first, jb1, rinv, Xi, G, k, shift, pfloor, sflag, lane);
       else cta_rank_update(A, ks, k, j0, jb, first + jb1, k, k, 1, CTA_WARPS - 1, warp, lane);
       __syncthreads();
     }
@@ -590,8 +627,10 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
         L32[(size_t)i * k + j] = (i == j) ? (float)sqrt(isfinite(g) && g > 1e-30 ? g : 1.0) : 0.0f;
     }
   } else {
-    for (int i = warp; i < k; i += CTA_WARPS)
+    for (int i = warp; i < k; i += CTA_WARPS) {
+#pragma unroll 4
       for (int j = lane; j < k; j += 32) L32[(size_t)i * k + j] = (j <= i) ? A[(size_t)i * ks + j] : 0.0f;
+    }
   }
   if (stats && tid == 0) atomicAdd(stats + STAT_CHOL, 1ull);
 }
