@@ -171,8 +171,10 @@ InvertLayout invert_layout(int d, int k, int r) {
     return L;
   }
   L.dp = round_up(d, 4);
-  L.nsplit = (int)std::min<long long>(16, std::max<long long>(1, d / 512));
-  L.kchunk = (int)round_up((d + L.nsplit - 1) / L.nsplit, 32);
+  // Grams (k x k, K = d): ~128-deep K-chunks so that the few output tiles
+  // still spread over most SMs (the pipeline of one CTA is then short).
+  L.nsplit = (int)std::min<long long>(32, std::max<long long>(1, d / 128));
+  L.kchunk = (int)round_up((d + L.nsplit - 1) / L.nsplit, 64);
   L.nsplit = (d + L.kchunk - 1) / L.kchunk;
   L.om = b.take<float>((size_t)k * L.dp);
   L.y = b.take<float>((size_t)k * L.dp);

@@ -37,32 +37,41 @@ __device__ __forceinline__ float warp_sum_all(float v) {
   return v;
 }
 
-// Rotate columns wa, wb (length k) to make them orthogonal (one warp). Returns 1
-// if a rotation was applied. `sm` is the kernel's dynamic shared array and the
-// columns are given as offsets into it, so every access stays a shared-memory
-// access (a generic pointer would turn them into generic loads).
+// Sum of squares of a register column, the same total in every lane.
 template <int NI>
-__device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol, float& off2, int lane) {
-  // Columns are zero-padded to NI * 128 floats: each lane holds NI float4s of
-  // both columns in registers from the dot products to the rotation, and the
-  // padding stays zero under rotations.
-  float4* a4 = reinterpret_cast<float4*>(sm + oa);
-  float4* b4 = reinterpret_cast<float4*>(sm + ob);
-  float4 x[NI], y[NI];
+__device__ __forceinline__ float col_sumsq(const float4 (&x)[NI]) {
+  float s = 0.f;
 #pragma unroll
-  for (int it = 0; it < NI; ++it) {
-    x[it] = a4[lane + 32 * it];
-    y[it] = b4[lane + 32 * it];
-  }
-  float al = 0.f, be = 0.f, ga = 0.f;
+  for (int it = 0; it < NI; ++it)
+    s = fmaf(x[it].x, x[it].x, fmaf(x[it].y, x[it].y, fmaf(x[it].z, x[it].z, fmaf(x[it].w, x[it].w, s))));
+  return warp_sum_all(s);
+}
+
+// Columns are zero-padded to NI * 128 floats: each lane holds NI float4s of a
+// column (lane + 32 * it), and the padding stays zero under rotations.
+template <int NI>
+__device__ __forceinline__ void col_load(const float* sm, int off, float4 (&x)[NI], int lane) {
+  const float4* p = reinterpret_cast<const float4*>(sm + off);
 #pragma unroll
-  for (int it = 0; it < NI; ++it) {
-    al = fmaf(x[it].x, x[it].x, fmaf(x[it].y, x[it].y, fmaf(x[it].z, x[it].z, fmaf(x[it].w, x[it].w, al))));
-    be = fmaf(y[it].x, y[it].x, fmaf(y[it].y, y[it].y, fmaf(y[it].z, y[it].z, fmaf(y[it].w, y[it].w, be))));
+  for (int it = 0; it < NI; ++it) x[it] = p[lane + 32 * it];
+}
+template <int NI>
+__device__ __forceinline__ void col_store(float* sm, int off, const float4 (&x)[NI], int lane) {
+  float4* p = reinterpret_cast<float4*>(sm + off);
+#pragma unroll
+  for (int it = 0; it < NI; ++it) p[lane + 32 * it] = x[it];
+}
+
+// Rotate register columns x, y (squared norms al, be, warp-uniform) to make
+// them orthogonal (one warp). Returns 1 if a rotation was applied; al and be
+// then hold the new squared norms.
+template <int NI>
+__device__ __forceinline__ int jacobi_rot(float4 (&x)[NI], float4 (&y)[NI], float& al, float& be, float tol,
+                                          float& off2) {
+  float ga = 0.f;
+#pragma unroll
+  for (int it = 0; it < NI; ++it)
     ga = fmaf(x[it].x, y[it].x, fmaf(x[it].y, y[it].y, fmaf(x[it].z, y[it].z, fmaf(x[it].w, y[it].w, ga))));
-  }
-  al = warp_sum_all(al);
-  be = warp_sum_all(be);
   ga = warp_sum_all(ga);
   const float g2 = ga * ga, ab = al * be;
   if (ab > 0.0f) off2 = fmaxf(off2, __fdividef(g2, ab));  // squared cosine of the pair's angle
@@ -71,7 +80,7 @@ __device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol,
   // t = sign(z) / (|z| + sqrt(1 + z^2)), z = (be - al) / (2 ga): scale-invariant
   // (a form that squares be - al and ga underflows on factors of scale ~1e-6).
   // Fast reciprocal / rsqrt: their ulp errors only perturb the rotation slightly
-  // (W W^T stays C + sI to FP32 accuracy) and the FP64 refinement absorbs them.
+  // (W W^T stays C + sI to FP32 accuracy) and the refinement absorbs them.
   const float zeta = __fdividef(be - al, 2.0f * ga);
   const float az = fabsf(zeta);
   float t;
@@ -84,11 +93,20 @@ __device__ __forceinline__ int jacobi_pair(float* sm, int oa, int ob, float tol,
   const float cs = rsqrtf(fmaf(t, t, 1.0f)), sn = cs * t;
 #pragma unroll
   for (int it = 0; it < NI; ++it) {
-    a4[lane + 32 * it] = make_float4(cs * x[it].x - sn * y[it].x, cs * x[it].y - sn * y[it].y,
-                                     cs * x[it].z - sn * y[it].z, cs * x[it].w - sn * y[it].w);
-    b4[lane + 32 * it] = make_float4(sn * x[it].x + cs * y[it].x, sn * x[it].y + cs * y[it].y,
-                                     sn * x[it].z + cs * y[it].z, sn * x[it].w + cs * y[it].w);
+    const float4 a4 = x[it], b4 = y[it];
+    x[it] = make_float4(cs * a4.x - sn * b4.x, cs * a4.y - sn * b4.y, cs * a4.z - sn * b4.z, cs * a4.w - sn * b4.w);
+    y[it] = make_float4(sn * a4.x + cs * b4.x, sn * a4.y + cs * b4.y, sn * a4.z + cs * b4.z, sn * a4.w + cs * b4.w);
   }
+  // t solves t^2 + 2 z t - 1 = 0, so the squared norms become al - t ga and
+  // be + t ga (their sum is invariant). One of them shrinks; where it loses
+  // more than half, the update would cancel and both are recomputed.
+  float al2 = fmaf(-t, ga, al), be2 = fmaf(t, ga, be);
+  if (!(al2 > 0.5f * al) || !(be2 > 0.5f * be)) {
+    al2 = col_sumsq<NI>(x);
+    be2 = col_sumsq<NI>(y);
+  }
+  al = al2;
+  be = be2;
   return 1;
 }
 
@@ -159,9 +177,18 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   cluster.sync();
 
   // ---- sweeps ---------------------------------------------------------------
+  // Squared column norms are cached next to the slots (recomputed at the start
+  // of every sweep, updated by each rotation, moved with their columns).
+  float* nrm = esm + 4 * slot;  // [buffer][slot][b]
   int sweep = 0, cur = 0, done = 0;
   for (; sweep < a.max_sweeps && !done; ++sweep) {
     if (tid == 0) { s_count = 0; s_off = 0u; }
+    for (int c = warp; c < 2 * b; c += EIG_WARPS) {  // zero columns give zero norms
+      float4 x[NI];
+      col_load<NI>(esm, 2 * slot * cur + (c < b ? c * kp : slot + (c - b) * kp), x, lane);
+      const float n2 = col_sumsq<NI>(x);
+      if (lane == 0) nrm[(2 * cur + (c < b ? 0 : 1)) * b + (c < b ? c : c - b)] = n2;
+    }
     __syncthreads();
     float off2 = 0.0f;
     for (int t = 0; t < nb - 1; ++t) {
@@ -170,6 +197,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
       const int bb = max(0, min(k, blkB * b + b) - blkB * b);
       const int top = 2 * slot * cur;
       const int bot = top + slot;
+      float* ntop = nrm + 2 * cur * b;
+      float* nbot = ntop + b;
       int cnt = 0;
       if (t == 0) {  // every pair among the ba + bb local columns
         const int n2 = ba + bb, m2 = n2 + (n2 & 1);
@@ -179,19 +208,73 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
             if (u < n2 && v < n2) {
               const int cu = u < ba ? top + u * kp : bot + (u - ba) * kp;
               const int cv = v < ba ? top + v * kp : bot + (v - ba) * kp;
-              cnt += jacobi_pair<NI>(esm, cu, cv, a.tol, off2, lane);
+              float* nu = u < ba ? ntop + u : nbot + (u - ba);
+              float* nv = v < ba ? ntop + v : nbot + (v - ba);
+              float4 x[NI], y[NI];
+              col_load<NI>(esm, cu, x, lane);
+              col_load<NI>(esm, cv, y, lane);
+              float al = *nu, be = *nv;
+              if (jacobi_rot<NI>(x, y, al, be, a.tol, off2)) {
+                col_store<NI>(esm, cu, x, lane);
+                col_store<NI>(esm, cv, y, lane);
+                if (lane == 0) { *nu = al; *nv = be; }
+                ++cnt;
+              }
             }
           }
           __syncthreads();
         }
       } else {  // the ba x bb cross pairs, max(ba, bb) disjoint pairs per inner round
         const int bmax = max(ba, bb);
-        for (int r = 0; r < bmax; ++r) {
-          for (int i = warp; i < bmax; i += EIG_WARPS) {
-            int j = (i + r) % bmax;
-            if (i < ba && j < bb) cnt += jacobi_pair<NI>(esm, top + i * kp, bot + j * kp, a.tol, off2, lane);
+        if (bmax <= EIG_WARPS) {
+          // Warp i keeps top column i in registers for the whole block-round;
+          // the bottom columns pass from warp to warp through shared memory.
+          const int i = warp;
+          const bool has_top = i < ba;
+          float4 x[NI];
+          float al = 0.0f;
+          if (has_top) {
+            col_load<NI>(esm, top + i * kp, x, lane);
+            al = ntop[i];
+          }
+          for (int r = 0; r < bmax; ++r) {
+            const int j = (i + r) % bmax;
+            if (has_top && j < bb) {
+              float4 y[NI];
+              col_load<NI>(esm, bot + j * kp, y, lane);
+              float be = nbot[j];
+              if (jacobi_rot<NI>(x, y, al, be, a.tol, off2)) {
+                col_store<NI>(esm, bot + j * kp, y, lane);
+                if (lane == 0) nbot[j] = be;
+                ++cnt;
+              }
+            }
+            __syncthreads();
+          }
+          if (has_top) {
+            col_store<NI>(esm, top + i * kp, x, lane);
+            if (lane == 0) ntop[i] = al;
           }
           __syncthreads();
+        } else {  // more pairs than warps: both columns through shared memory
+          for (int r = 0; r < bmax; ++r) {
+            for (int i = warp; i < bmax; i += EIG_WARPS) {
+              const int j = (i + r) % bmax;
+              if (i < ba && j < bb) {
+                float4 x[NI], y[NI];
+                col_load<NI>(esm, top + i * kp, x, lane);
+                col_load<NI>(esm, bot + j * kp, y, lane);
+                float al = ntop[i], be = nbot[j];
+                if (jacobi_rot<NI>(x, y, al, be, a.tol, off2)) {
+                  col_store<NI>(esm, top + i * kp, x, lane);
+                  col_store<NI>(esm, bot + j * kp, y, lane);
+                  if (lane == 0) { ntop[i] = al; nbot[j] = be; }
+                  ++cnt;
+                }
+              }
+            }
+            __syncthreads();
+          }
         }
       }
       if (lane == 0 && cnt) atomicAdd(&s_count, cnt);
@@ -214,6 +297,10 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
         for (int e = tid; e < n4; e += EIG_THREADS) {
           d1[e] = s1[e];
           d2[e] = s2[e];
+        }
+        if (tid < b) {
+          *cluster.map_shared_rank(nrm + (2 * nxt + ds_top) * b + tid, dq_top) = ntop[tid];
+          *cluster.map_shared_rank(nrm + (2 * nxt + ds_bot) * b + tid, dq_bot) = nbot[tid];
         }
         cluster.sync();
         cur = nxt;
@@ -444,7 +531,7 @@ cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_swe
   nc = nc < 1 ? 1 : (nc > EIG_MAX_NC ? EIG_MAX_NC : nc);
   const int b = (k + 2 * nc - 1) / (2 * nc);
   const int kp = (k + 127) / 128 * 128;  // float4 per lane, 32 lanes
-  const size_t smem = sizeof(float) * 4 * (size_t)b * kp;  // 2 buffers x 2 slots
+  const size_t smem = sizeof(float) * 4 * ((size_t)b * kp + b);  // 2 buffers x 2 slots, with their column norms
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
   EigArgs a = {gscratch, shift, k, max_sweeps, tol, X, lam, flags, stats, b, kp, stop_tol};
   switch (kp / 128) {

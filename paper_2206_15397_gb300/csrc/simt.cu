@@ -133,19 +133,29 @@ __global__ void __launch_bounds__(256) k_gemm_t16(GemmDesc<T> g) {
   }
 }
 
+// Sum of the split-K partials of entry (i, j) with Neumaier's compensated
+// summation in FP32 (the FP64 pipe issues at ~1/64 of the FP32 rate on this
+// part): s + c carries the sum to about FP64 accuracy for same-sign terms and
+// to ~2u |sum| + nu^2 sum|x| in general.
+__device__ __forceinline__ double sum_partials(const float* __restrict__ p, int nsplit, long long zstride) {
+  float s = 0.0f, c = 0.0f;
+  for (int z = 0; z < nsplit; ++z) {
+    const float x = p[z * zstride];
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  return (double)s + (double)c;
+}
+
 __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
                                 double* __restrict__ out, int ldo, int symmetrize, float* __restrict__ out32,
                                 int* flags) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * n) return;
-  int i = (int)(idx / n), j = (int)(idx % n);
-  double s = 0.0;
-  for (int z = 0; z < nsplit; ++z) s += (double)part[z * zstride + (long long)i * ldp + j];
-  if (symmetrize) {
-    double t = 0.0;
-    for (int z = 0; z < nsplit; ++z) t += (double)part[z * zstride + (long long)j * ldp + i];
-    s = 0.5 * (s + t);
-  }
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // n * n < 2^31
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  double s = sum_partials(part + (long long)i * ldp + j, nsplit, zstride);
+  if (symmetrize) s = 0.5 * (s + sum_partials(part + (long long)j * ldp + i, nsplit, zstride));
   if (!isfinite(s)) raise_flag(flags, KFAC_FLAG_NONFINITE);
   out[(long long)i * ldo + j] = s;
   if (out32) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
