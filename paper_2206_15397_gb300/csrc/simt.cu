@@ -137,15 +137,73 @@ __global__ void __launch_bounds__(256) k_gemm_t16(GemmDesc<T> g) {
 // summation in FP32 (the FP64 pipe issues at ~1/64 of the FP32 rate on this
 // part): s + c carries the sum to about FP64 accuracy for same-sign terms and
 // to ~2u |sum| + nu^2 sum|x| in general.
+// Loads go out eight at a time (each waits out the L2 latency otherwise).
 __device__ __forceinline__ double sum_partials(const float* __restrict__ p, int nsplit, long long zstride) {
   float s = 0.0f, c = 0.0f;
-  for (int z = 0; z < nsplit; ++z) {
-    const float x = p[z * zstride];
-    const float t = s + x;
-    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
-    s = t;
+  for (int z0 = 0; z0 < nsplit; z0 += 8) {
+    float x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = z0 + q < nsplit ? p[(z0 + q) * zstride] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float t = s + x[q];
+      c += (fabsf(s) >= fabsf(x[q])) ? (s - t) + x[q] : (x[q] - t) + s;
+      s = t;
+    }
   }
   return (double)s + (double)c;
+}
+
+// FP32 16 x 16-tile product for K <= kT16MaxK: both K-panels are staged in
+// shared memory with all loads in flight at once, then one barrier (the
+// per-16-column stepping of k_gemm_t16 waits out the global latency ~K/16 times).
+constexpr int kT16MaxK = 256;
+__global__ void __launch_bounds__(256) k_gemm_t16_wholek(GemmDesc<float> g) {
+  __shared__ float As[16][kT16MaxK + 1];
+  __shared__ float Bs[16][kT16MaxK + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int mb = blockIdx.y * 16, nb = blockIdx.x * 16;
+  const int tot = 16 * g.K;
+  for (int e0 = 0; e0 < tot; e0 += 8 * 256) {  // eight loads of each operand in flight per thread
+    float va[8], vb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * 256 + tid;
+      va[q] = vb[q] = 0.0f;
+      if (e < tot) {
+        int r, kk;
+        if (g.sak == 1) { r = e / g.K; kk = e - r * g.K; } else { kk = e >> 4; r = e & 15; }  // coalesced either way
+        if (mb + r < g.M) va[q] = g.A[(long long)(mb + r) * g.sam + (long long)kk * g.sak];
+        int rb, kb;
+        if (g.sbk == 1) { rb = e / g.K; kb = e - rb * g.K; } else { kb = e >> 4; rb = e & 15; }
+        if (nb + rb < g.N) vb[q] = g.B[(long long)(nb + rb) * g.sbn + (long long)kb * g.sbk];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * 256 + tid;
+      if (e < tot) {
+        int r, kk;
+        if (g.sak == 1) { r = e / g.K; kk = e - r * g.K; } else { kk = e >> 4; r = e & 15; }
+        As[r][kk] = va[q];
+        int rb, kb;
+        if (g.sbk == 1) { rb = e / g.K; kb = e - rb * g.K; } else { kb = e >> 4; rb = e & 15; }
+        Bs[rb][kb] = vb[q];
+      }
+    }
+  }
+  __syncthreads();
+  const int m = mb + ty, n = nb + tx;
+  float acc = 0.0f;
+#pragma unroll 8
+  for (int kk = 0; kk < g.K; ++kk) acc = fmaf(As[ty][kk], Bs[tx][kk], acc);
+  if (m < g.M && n < g.N) {
+    float v = acc * g.alpha;
+    if (g.rowscale) v *= g.rowscale[m];
+    if (g.colscale) v *= g.colscale[n];
+    if (g.beta != 0.0f) v = fmaf(g.beta, g.C0[g.c0_trans ? (long long)n * g.ldc + m : (long long)m * g.ldc + n], v);
+    g.D[g.d_trans ? (long long)n * g.ldd + m : (long long)m * g.ldd + n] = v;
+  }
 }
 
 __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
@@ -154,11 +212,26 @@ __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // n * n < 2^31
   if (idx >= n * n) return;
   const int i = idx / n, j = idx - i * n;
-  double s = sum_partials(part + (long long)i * ldp + j, nsplit, zstride);
-  if (symmetrize) s = 0.5 * (s + sum_partials(part + (long long)j * ldp + i, nsplit, zstride));
+  const double s = sum_partials(part + (long long)i * ldp + j, nsplit, zstride);
   if (!isfinite(s)) raise_flag(flags, KFAC_FLAG_NONFINITE);
   out[(long long)i * ldo + j] = s;
-  if (out32) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
+  if (out32 && !symmetrize) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
+}
+
+// out <- (out + out^T) / 2 in place, one thread per pair i <= j (the summed
+// matrix is read twice, not the split-K partials), with the FP32 copy.
+__global__ void k_symmetrize(double* __restrict__ out, int n, int ldo, float* __restrict__ out32) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx - i * n;
+  if (j < i) return;
+  const double v = 0.5 * (out[(long long)i * ldo + j] + out[(long long)j * ldo + i]);
+  out[(long long)i * ldo + j] = v;
+  out[(long long)j * ldo + i] = v;
+  if (out32) {
+    out32[(long long)i * n + j] = (float)v;
+    out32[(long long)j * n + i] = (float)v;
+  }
 }
 
 __global__ void k_transpose(const float* __restrict__ in, long long ldi, int rows, int cols, float* __restrict__ out,
@@ -213,7 +286,11 @@ cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (g.zsplit > 1) return launch_gemm<float, Round::None>(g, s);
   dim3 grid((g.N + 15) / 16, (g.M + 15) / 16);
-  k_gemm_t16<float><<<grid, 256, 0, s>>>(g);
+  if (g.K <= kT16MaxK) {
+    k_gemm_t16_wholek<<<grid, 256, 0, s>>>(g);
+  } else {
+    k_gemm_t16<float><<<grid, 256, 0, s>>>(g);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -225,6 +302,10 @@ cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, 
   k_reduce_splitk<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, zstride, n, ldp, out, ldo, symmetrize,
                                                                   out32, flags);
   note_launch();
+  if (symmetrize) {
+    k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(out, n, ldo, out32);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 
