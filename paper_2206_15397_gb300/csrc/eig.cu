@@ -9,12 +9,13 @@
 //     matrix is stored. The sweeps run on a thread-block cluster as a block
 //     round-robin: one warp per column pair, one cluster barrier per
 //     block-round.
-//  2. eig_refine_f64: one FP64 refinement step of all eigenpairs (Ogita and
-//     Aishima, "Iterative refinement for symmetric eigenvalue decomposition",
-//     2018): from R = I - X^T X and S = X^T C X, lam_i = S_ii / (1 - R_ii) and
-//     X <- X + X E with E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) for
-//     separated pairs, R_ij / 2 otherwise. The products are FP64 GEMMs spread
-//     over many CTAs; it lifts FP32-accurate pairs to near FP64 accuracy.
+//  2. eig_refine_f32 / eig_refine_f64: one refinement step of all eigenpairs
+//     (Ogita and Aishima, "Iterative refinement for symmetric eigenvalue
+//     decomposition", 2018): from R = I - X^T X and S = X^T C X,
+//     lam_i = S_ii / (1 - R_ii) and X <- X + X E with
+//     E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) for separated pairs,
+//     R_ij / 2 otherwise. The k x k products run in FP32 (default) or FP64,
+//     spread over many CTAs; X and lam are carried in FP64.
 //  3. eig_select: descending stable sort, leading r pairs, damping coefficients.
 #include <algorithm>
 #include <cooperative_groups.h>
