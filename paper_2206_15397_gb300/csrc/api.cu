@@ -183,7 +183,7 @@ InvertLayout invert_layout(int d, int k, int r) {
   L.g = b.take<double>((size_t)k * k);
   L.g32 = b.take<float>((size_t)k * k);
   L.l32 = b.take<float>((size_t)k * k);
-  L.dinv = b.take<float>((size_t)((k + 31) / 32) * 1024);
+  L.dinv = b.take<float>(trsm_ws_floats(k));
   L.c = b.take<double>((size_t)k * k);
   L.c32 = b.take<float>((size_t)k * k);
   L.x = b.take<double>((size_t)k * k);

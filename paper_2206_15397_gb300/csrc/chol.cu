@@ -670,7 +670,11 @@ constexpr int TR_COLS = 32, TR_RB = 32, TR_THREADS = 256;
 __global__ void __launch_bounds__(32) k_diag_block_inv(const float* __restrict__ L, int k, float* __restrict__ Dinv) {
   __shared__ float Lb[TR_RB][TR_RB + 1];
   const int blk = blockIdx.x, i0 = blk * TR_RB, ib = min(TR_RB, k - i0), c = threadIdx.x;
-  for (int a = 0; a < TR_RB; ++a) Lb[a][c] = (a < ib && c < ib) ? L[(size_t)(i0 + a) * k + i0 + c] : (a == c ? 1.f : 0.f);
+  float lv[TR_RB];  // all 32 loads in flight (one at a time each waits out the L2 latency)
+#pragma unroll
+  for (int a = 0; a < TR_RB; ++a) lv[a] = (a < ib && c < ib) ? L[(size_t)(i0 + a) * k + i0 + c] : (a == c ? 1.f : 0.f);
+#pragma unroll
+  for (int a = 0; a < TR_RB; ++a) Lb[a][c] = lv[a];
   __syncwarp();
   float x[TR_RB];  // column c of the block inverse
 #pragma unroll
@@ -742,6 +746,52 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restri
     __syncthreads();
   }
 }
+// Packs L for k_trsm_lower_smem once per solve (instead of every CTA
+// gathering it with 4-byte copies): block row I of 32 rows at offset
+// 1024 I (I+1) / 2 with row width 32 (I+1), the off-diagonal blocks copied
+// from L and the diagonal block replaced by its inverse (warp 0, as
+// k_diag_block_inv). One CTA per block row.
+__global__ void __launch_bounds__(256) k_trsm_pack(const float* __restrict__ L, int k, float* __restrict__ Lp) {
+  __shared__ float Lb[TR_RB][TR_RB + 1];
+  const int I = blockIdx.x, i0 = I * TR_RB, ib = min(TR_RB, k - i0), tid = threadIdx.x;
+  const int width = 32 * (I + 1);
+  float* dst = Lp + (size_t)512 * I * (I + 1);
+  // off-diagonal part, eight loads in flight per thread
+  const int tot = 32 * 32 * I;
+  for (int e0 = 0; e0 < tot; e0 += 8 * 256) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * 256 + tid, a = e / (32 * I), cc = e - a * 32 * I;
+      v[q] = (e < tot && a < ib) ? L[(size_t)(i0 + a) * k + cc] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * 256 + tid, a = e / (32 * I), cc = e - a * 32 * I;
+      if (e < tot) dst[(size_t)a * width + cc] = v[q];
+    }
+  }
+  if (tid < 32) {  // diagonal block inverse, lane c = column c
+    const int c = tid;
+    float lv[TR_RB];
+#pragma unroll
+    for (int a = 0; a < TR_RB; ++a) lv[a] = (a < ib && c < ib) ? L[(size_t)(i0 + a) * k + i0 + c] : (a == c ? 1.f : 0.f);
+#pragma unroll
+    for (int a = 0; a < TR_RB; ++a) Lb[a][c] = lv[a];
+    __syncwarp();
+    float x[TR_RB];
+#pragma unroll
+    for (int i = 0; i < TR_RB; ++i) {
+      float v = (i == c) ? 1.0f : 0.0f;
+#pragma unroll
+      for (int u = 0; u < i; ++u) v = fmaf(-Lb[i][u], x[u], v);
+      x[i] = (i >= c) ? v * __frcp_rn(Lb[i][i]) : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < TR_RB; ++i) dst[(size_t)i * width + 32 * I + c] = x[i];
+  }
+}
+
 // The same solve with the whole lower factor resident in shared memory (for
 // k <= 32 * TS_MAXT): the 32-row block rows of L are packed once (their
 // diagonal blocks replaced by the block inverses) and the CTA's 32 columns of
@@ -754,8 +804,7 @@ __host__ __device__ inline size_t trsm_smem_floats(int T) {
   return (size_t)1024 * T * (T + 1) / 2 + (size_t)32 * (32 * T + 4) + 32 * 33;
 }
 
-__global__ void __launch_bounds__(TR_THREADS) k_trsm_lower_smem(const float* __restrict__ L,
-                                                                 const float* __restrict__ Dinv, int k, int T,
+__global__ void __launch_bounds__(TR_THREADS) k_trsm_lower_smem(const float* __restrict__ Lpk, int k, int T,
                                                                  const float* __restrict__ Yt, long long ldy,
                                                                  float* __restrict__ Qt, long long ldq, int d) {
   extern __shared__ __align__(16) float tsm[];
@@ -765,16 +814,9 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower_smem(const float* __r
   float* Ts = Xc + (size_t)32 * xs;                    // [32][33]: one block of partial sums
   const int tid = threadIdx.x, c = tid & 31, w = tid >> 5;  // w: rows 4w..4w+3 of a block
   const int col0 = blockIdx.x * TR_COLS, col = col0 + c;
-  for (int I = 0; I < T; ++I) {
-    const int width = 32 * (I + 1);
-    float* Lb = Lp + (size_t)512 * I * (I + 1);
-    for (int a = w; a < 32; a += TR_THREADS / 32) {  // warp per row, lanes along the row
-      const int row = 32 * I + a;
-      for (int cc = c; cc < width; cc += 32) {
-        if (cc >= 32 * I) cp_async4(Lb + (size_t)a * width + cc, Dinv + (size_t)I * 1024 + a * 32 + (cc - 32 * I), true);
-        else cp_async4(Lb + (size_t)a * width + cc, L + (size_t)(row < k ? row : 0) * k + cc, row < k);
-      }
-    }
+  {  // the packed factor (k_trsm_pack), 16 bytes per copy
+    const int n4 = 128 * T * (T + 1);  // 512 T (T+1) floats
+    for (int e = tid; e < n4; e += TR_THREADS) cp_async16(Lp + 4 * e, Lpk + 4 * e);
   }
   for (int i = w; i < kpad; i += TR_THREADS / 32) {  // warp per row of Yt, lanes over the 32 columns
     const bool ok = i < k && col < d;
@@ -833,8 +875,6 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  k_diag_block_inv<<<(k + TR_RB - 1) / TR_RB, 32, 0, s>>>(L, k, dinv_ws);
-  note_launch();
   const int T = kpad / TR_RB;
   if (T <= TS_MAXT) {
     static bool attr_smem = false;
@@ -845,12 +885,16 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
     }
     const size_t smem_all = sizeof(float) * trsm_smem_floats(T);
     if (smem_all <= (size_t)kSmemOptin) {
-      k_trsm_lower_smem<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem_all, s>>>(L, dinv_ws, k, T, Yt, ldy, Qt,
-                                                                                  ldq, d);
+      k_trsm_pack<<<T, 256, 0, s>>>(L, k, dinv_ws);
+      note_launch();
+      k_trsm_lower_smem<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem_all, s>>>(dinv_ws, k, T, Yt, ldy, Qt, ldq,
+                                                                                  d);
       note_launch();
       return cudaGetLastError();
     }
   }
+  k_diag_block_inv<<<(k + TR_RB - 1) / TR_RB, 32, 0, s>>>(L, k, dinv_ws);
+  note_launch();
   k_trsm_lower<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem, s>>>(L, dinv_ws, k, Yt, ldy, Qt, ldq, d);
   note_launch();
   return cudaGetLastError();

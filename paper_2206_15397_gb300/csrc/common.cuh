@@ -35,6 +35,10 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src, 
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(gmem_src), "r"(valid ? 4 : 0)
                : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(gmem_src) : "memory");
@@ -124,7 +128,12 @@ cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, fl
                          const float* G32 = nullptr, long long ld32 = 0);
 
 // Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
-// dinv_ws: ceil(k/32) * 1024 floats of workspace (inverses of L's diagonal blocks).
+// dinv_ws: trsm_ws_floats(k) floats of workspace (L packed by 32-row block rows
+// with inverted diagonal blocks, or the block inverses alone for large k).
+inline size_t trsm_ws_floats(int k) {
+  const size_t T = (size_t)(k + 31) / 32;
+  return T * 1024 > 512 * T * (T + 1) ? T * 1024 : 512 * T * (T + 1);
+}
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
                            float* dinv_ws, cudaStream_t s);
 
