@@ -18,9 +18,11 @@
 // Two kernels:
 //   k_tc_gemm   TF32 products, one accumulator over the CTA's whole K range
 //               (all 8 warps share the epilogue).
-//   k_tc_gemm3  FP32-accurate products (3xTF32): warps 2-7 split every staged
-//               value in place into its TF32 head and FP32 tail (x = hi + lo
-//               exactly) and fence the writes for the async proxy; the issuer
+//   k_tc_gemm3  FP32-accurate products (3xTF32): the staged FP32 tile is the
+//               head operand as it stands (the tensor core reads it truncated
+//               to TF32); warps 2-7 write each value's tail, the rest below
+//               that truncation rounded to TF32, and fence the writes for the
+//               async proxy; the issuer
 //               puts hi*hi into one accumulator and hi*lo + lo*hi into
 //               another. The tensor core's FP32 accumulation rounds toward
 //               zero, which over a long K loop drifts every sum low (measured
@@ -189,6 +191,14 @@ __device__ __forceinline__ float tf32_head(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
+}
+
+// The tail of x below the TF32 the tensor core reads from an FP32 operand (it
+// drops the 13 low mantissa bits), rounded to nearest TF32: x - trunc(x) is
+// exact in FP32 and below 2^-10 |x|, so x ~ trunc(x) + tail to 2^-21 |x|,
+// without a sign bias.
+__device__ __forceinline__ float tf32_tail(float x) {
+  return tf32_head(x - __uint_as_float(__float_as_uint(x) & 0xffffe000u));
 }
 
 template <int BN>
@@ -489,11 +499,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     mma_commit(accb);  // every issued MMA has completed (also when nothing was issued)
   } else if (warp >= 2) {
-    // ---- warps 2-7: 3xTF32 split of stage kb; warps 4-7 then drain pair kb-1 --
-    // hi = x rounded to TF32, lo = x - hi is exact in FP32 and |lo| <= 2^-11 |x|;
-    // the tensor core reads lo at TF32 precision, so hi*hi + hi*lo + lo*hi
-    // carries x*y to ~2^-21 relative. All waits here are warp-uniform so the
-    // warp stays converged for tcgen05.ld.
+    // ---- warps 2-7: 3xTF32 split of stage kb; warps 4-7 then drain pairs ------
+    // hi is the staged FP32 value itself, which the tensor core reads truncated
+    // to TF32; lo = RN_tf32(x - trunc(x)) goes to the second half of the stage,
+    // so hi*hi + hi*lo + lo*hi carries x*y to ~2^-21 relative, unbiased. All
+    // waits here are warp-uniform so the warp stays converged for tcgen05.ld.
     const int t = tid - 64;
     const bool drainer = warp >= 4;
     const uint32_t lrow = (uint32_t)(32 * (warp & 3)) << 16;
@@ -506,18 +516,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int s = kb % C::STAGES;
         const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
         if (!mbar_wait_warp(full0 + 8 * s, ph, p.flags, lane)) { drained = false; break; }
-        float4* raw = reinterpret_cast<float4*>(smem + s * C::STAGE);
+        const float4* raw = reinterpret_cast<const float4*>(smem + s * C::STAGE);
         float4* lo = reinterpret_cast<float4*>(smem + s * C::STAGE + C::RAW);
 #pragma unroll 2
         for (int e = t; e < C::RAW / 16; e += kSplitThreads) {
-          const float4 x = raw[e];
-          float4 h, l;
-          h.x = tf32_head(x.x); l.x = x.x - h.x;
-          h.y = tf32_head(x.y); l.y = x.y - h.y;
-          h.z = tf32_head(x.z); l.z = x.z - h.z;
-          h.w = tf32_head(x.w); l.w = x.w - h.w;
-          raw[e] = h;
-          lo[e] = l;
+          const float4 x = raw[e];  // read as hi by the tensor core (its TF32 truncation)
+          lo[e] = make_float4(tf32_tail(x.x), tf32_tail(x.y), tf32_tail(x.z), tf32_tail(x.w));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(split0 + 8 * s);
