@@ -496,19 +496,21 @@ __device__ __forceinline__ void cta_panel_solve(float* A, int ks, int k, int j0,
   }
 }
 
-// A[i][c] -= sum_t A[i][j0+t] A[c][j0+t] for i in [r0, r1), c in [r0, c1),
-// c <= i, t < jb. Warps [w0, w0 + nw); each warp takes groups of 8 x 4 tiles
-// (32 rows x 16 columns), a lane one 4 x 4 tile.
-__device__ __forceinline__ void cta_rank_update(float* A, int ks, int k, int j0, int jb, int r0, int r1, int c1,
-                                                int w0, int nw, int warp, int lane) {
-  if (warp < w0 || r1 <= r0 || c1 <= r0) return;
-  const int GR = (r1 - r0 + 31) / 32, GC = (c1 - r0 + 15) / 16;
+// A[i][c] -= sum_t A[i][j0+t] A[c][j0+t] for i in [r0, r1), c in [cb, c1),
+// c <= i, t < jb (cb <= r0). Warps [w0, w0 + nw); each warp takes groups of
+// 8 x 4 tiles (32 rows x 16 columns), a lane one 4 x 4 tile.
+__device__ __forceinline__ void cta_rank_update(float* A, int ks, int k, int j0, int jb, int r0, int r1, int cb,
+                                                int c1, int w0, int nw, int warp, int lane) {
+  if (warp < w0 || r1 <= r0 || c1 <= cb) return;
+  const int GR = (r1 - r0 + 31) / 32, GC = (c1 - cb + 15) / 16;
+  // groups of row band gr that reach the diagonal: cb + 16 gc <= r0 + 32 gr + 31
+  auto per_row = [&](int gr) { return min(GC, (r0 - cb + 32 * gr + 31) / 16 + 1); };
   int ngroups = 0;
-  for (int gr = 0; gr < GR; ++gr) ngroups += min(GC, 2 * gr + 2);
+  for (int gr = 0; gr < GR; ++gr) ngroups += per_row(gr);
   for (int grp = warp - w0; grp < ngroups; grp += nw) {
     int gr = 0, rem = grp;
-    while (rem >= min(GC, 2 * gr + 2)) { rem -= min(GC, 2 * gr + 2); ++gr; }
-    const int i0 = r0 + 32 * gr + 4 * (lane >> 2), c0 = r0 + 16 * rem + 4 * (lane & 3);
+    while (rem >= per_row(gr)) { rem -= per_row(gr); ++gr; }
+    const int i0 = r0 + 32 * gr + 4 * (lane >> 2), c0 = cb + 16 * rem + 4 * (lane & 3);
     if (i0 >= r1 || c0 >= c1 || c0 > i0 + 3) continue;
     float acc[4][4];
 #pragma unroll
@@ -599,11 +601,17 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
       const int jb1 = min(PW, k - first);
       cta_panel_solve(A, ks, k, j0, jb, Xi, warp, lane);
       __syncthreads();
-      // next block column (its diagonal block and the rows below it)
-      cta_rank_update(A, ks, k, j0, jb, first, k, first + jb1, 0, CTA_WARPS, warp, lane);
-      __syncthreads();
-      if (warp == 0) cta_factor_diag(A, ks, first, jb1, rinv, Xi, G, k, shift, pfloor, sflag, lane);
-      else cta_rank_update(A, ks, k, j0, jb, first + jb1, k, k, 1, CTA_WARPS - 1, warp, lane);
+      // Warp 1 applies the panel to the next diagonal block and releases warp 0
+      // (named barrier 1), which factors it; meanwhile warps 1-15 update every
+      // row below it, from the next block column to the diagonal.
+      if (warp == 0) {
+        asm volatile("bar.sync 1, %0;" ::"n"(CTA_THREADS) : "memory");
+        cta_factor_diag(A, ks, first, jb1, rinv, Xi, G, k, shift, pfloor, sflag, lane);
+      } else {
+        cta_rank_update(A, ks, k, j0, jb, first, first + jb1, first, first + jb1, 1, 1, warp, lane);
+        asm volatile("bar.arrive 1, %0;" ::"n"(CTA_THREADS) : "memory");
+        cta_rank_update(A, ks, k, j0, jb, first + jb1, k, first, k, 1, CTA_WARPS - 1, warp, lane);
+      }
       __syncthreads();
     }
     if (!sflag[0]) {
