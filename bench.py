@@ -204,7 +204,7 @@ def stage_work(stage: str, w, q: int, steps: int):
 # summarised under profiles/, same kernels as built here). The Cholesky stage
 # runs the FP32 single-CTA kernel, which reads the k x k Gram once; the Jacobi
 # kernel reads the k x k FP32 factor once.
-NCU_TRAFFIC_PER_LAUNCH = {"cholqr_chol": 266240.0, "eig_jacobi": 198656.0, "sketch_gemm": 72325632.0}
+NCU_TRAFFIC_PER_LAUNCH = {"cholqr_chol": 255488.0, "eig_jacobi": 198656.0, "sketch_gemm": 72325632.0}
 
 
 def load_peaks():
