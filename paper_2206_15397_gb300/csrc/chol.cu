@@ -323,13 +323,9 @@ size_t chol_smem_bytes(int k, int nloc, int B, size_t elt) {
 template <typename T>
 cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, int* flags,
                         unsigned long long* stats, cudaStream_t s, double* shift_out) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_chol_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  {
+    cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cluster<T>), kSmemOptin, true);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_chol_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   int nc = (k + 15) / 16;
   if (nc > 16) nc = 16;
@@ -650,12 +646,8 @@ cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, fl
                          long long ld32) {
   if (k <= 0) return cudaSuccess;
   if (!fp64 && k <= CTA_KMAX && cta_smem_bytes(k) <= (size_t)kSmemOptin) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_chol_cta_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cta_f32), kSmemOptin, false);
+    if (e != cudaSuccess) return e;
     k_chol_cta_f32<<<1, CTA_THREADS, cta_smem_bytes(k), s>>>(G, G32, ld32, k, shift_rel, L32, flags, stats,
                                                                shift_out);
     note_launch();
@@ -877,20 +869,14 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
   const int kpad = (k + TR_RB - 1) / TR_RB * TR_RB;  // X rows incl. the padded tail block
   size_t smem = sizeof(float) * ((size_t)kpad * TR_COLS + TR_RB * (TR_RB + 1));
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_trsm_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
+  {
+    cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_trsm_lower), kSmemOptin, false);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const int T = kpad / TR_RB;
   if (T <= TS_MAXT) {
-    static bool attr_smem = false;
-    if (!attr_smem) {
-      cudaError_t e = cudaFuncSetAttribute(k_trsm_lower_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemOptin);
-      if (e != cudaSuccess) return e;
-      attr_smem = true;
-    }
+    cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_trsm_lower_smem), kSmemOptin, false);
+    if (e != cudaSuccess) return e;
     const size_t smem_all = sizeof(float) * trsm_smem_floats(T);
     if (smem_all <= (size_t)kSmemOptin) {
       k_trsm_pack<<<T, 256, 0, s>>>(L, k, dinv_ws);

@@ -102,6 +102,11 @@ struct GemmDesc {
 // ---- launchers (host) --------------------------------------------------------
 cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s);
 cudaError_t gemm_simt_f64(const GemmDesc<double>& g, cudaStream_t s);
+// Kernel attributes belong to a kernel on one device: set the dynamic shared
+// memory limit (and, for cluster kernels, non-portable cluster sizes) once per
+// kernel and device, on the current device.
+cudaError_t set_kernel_attrs_once(const void* fn, int max_dyn_smem, bool nonportable_cluster);
+
 // FP32 product with 16 x 16 output tiles (plain FP32 FMA), for k x k matrices.
 cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s);
 // out[i, j] = sum_z part[z][i, j] in FP64 (n x n), optionally symmetrised as

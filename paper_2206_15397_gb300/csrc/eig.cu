@@ -496,14 +496,9 @@ __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ 
 
 template <int NI, int EIG_THREADS>
 static cudaError_t launch_eig(const EigArgs& a, int nc, size_t smem, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_eig_cluster<NI, EIG_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemOptin);
+  {
+    cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_eig_cluster<NI, EIG_THREADS>), kSmemOptin, true);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_eig_cluster<NI, EIG_THREADS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nc, 1, 1);

@@ -1,5 +1,9 @@
 // SIMT kernels: strided GEMM (FP32 with optional operand rounding, FP64),
 // split-K reduction to FP64, transpose and widening copies.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "common.cuh"
 
 namespace kfac {
@@ -260,6 +264,23 @@ __global__ void k_convert(const float* __restrict__ in, long long ldi, int rows,
 }
 
 }  // namespace
+
+cudaError_t set_kernel_attrs_once(const void* fn, int max_dyn_smem, bool nonportable_cluster) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({fn, dev})) return cudaSuccess;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem)) != cudaSuccess)
+    return e;
+  if (nonportable_cluster &&
+      (e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+    return e;
+  done.insert({fn, dev});
+  return cudaSuccess;
+}
 
 static unsigned long long g_launches = 0;
 void note_launch(unsigned n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }

@@ -752,12 +752,11 @@ bool make_map(CUtensorMap* map, const float* ptr, int rows, int cols, long long 
 }
 
 template <typename Kern>
-cudaError_t launch_kernel(Kern kern, int smem, int bn, bool& attr, const TcArgs& a, const float* A, long long lda,
+cudaError_t launch_kernel(Kern kern, int smem, int bn, const TcArgs& a, const float* A, long long lda,
                           const float* B, long long ldb, int zsplit, cudaStream_t s) {
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  {
+    cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(kern), smem, false);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, bn)) return cudaErrorInvalidValue;
@@ -777,11 +776,10 @@ bool eligible(const float* A, long long lda, const float* B, long long ldb, int 
 
 cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
                  Mode mode, cudaStream_t s) {
-  static bool attr3 = false, attr256 = false, attr128 = false, attr16 = false;
-  if (mode == Mode::Fp32) return launch_kernel(k_tc_gemm3, Cfg3::SMEM, BN3, attr3, a, A, lda, B, ldb, zsplit, s);
-  if (mode == Mode::Bf16) return launch_kernel(k_tc_gemm16, Cfg16::SMEM, BN16, attr16, a, A, lda, B, ldb, zsplit, s);
-  if (a.N > 128) return launch_kernel(k_tc_gemm<256>, Cfg<256>::SMEM, 256, attr256, a, A, lda, B, ldb, zsplit, s);
-  return launch_kernel(k_tc_gemm<128>, Cfg<128>::SMEM, 128, attr128, a, A, lda, B, ldb, zsplit, s);
+  if (mode == Mode::Fp32) return launch_kernel(k_tc_gemm3, Cfg3::SMEM, BN3, a, A, lda, B, ldb, zsplit, s);
+  if (mode == Mode::Bf16) return launch_kernel(k_tc_gemm16, Cfg16::SMEM, BN16, a, A, lda, B, ldb, zsplit, s);
+  if (a.N > 128) return launch_kernel(k_tc_gemm<256>, Cfg<256>::SMEM, 256, a, A, lda, B, ldb, zsplit, s);
+  return launch_kernel(k_tc_gemm<128>, Cfg<128>::SMEM, 128, a, A, lda, B, ldb, zsplit, s);
 }
 
 }  // namespace tc
