@@ -111,10 +111,6 @@ T* at(kfac_ctx* ctx, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(ctx->ws) + off);
 }
 
-Round to_round(kfac_precision p) {
-  return p == KFAC_PREC_BF16 ? Round::BF16 : (p == KFAC_PREC_TF32 ? Round::TF32 : Round::None);
-}
-
 #define CK(expr)                                   \
   do {                                             \
     cudaError_t e_ = (expr);                       \
