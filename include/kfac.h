@@ -58,9 +58,10 @@ typedef enum {
 } kfac_status;
 
 /* Arithmetic of the large GEMMs (EA SYRK, sketch / power / projection, apply).
- * The orthonormalisation and the eigensolve keep their own precision (FP32
- * tensor/SIMT products with FP64 Cholesky and FP64 eigen-refinement) in every
- * mode. */
+ * The orthonormalisation and the eigensolve keep their own precision in every
+ * mode: FP32-accurate Grams summed with compensation into FP64, FP32 Cholesky,
+ * FP32 Jacobi and an eigen-refinement with FP32 products and FP64 carriers
+ * (KFAC_OPT_CHOLQR_FP32_PASSES and KFAC_OPT_EIG_REFINE_FP64 select FP64). */
 typedef enum {
   KFAC_PREC_FP32 = 0,  /* FP32-accurate products (3xTF32 split on tensor cores)  */
   KFAC_PREC_TF32 = 1,  /* single-pass TF32 tensor-core products, FP32 accumulate */
@@ -278,13 +279,13 @@ typedef enum {
                                        later pass squares the orthogonality error, and the
                                        basis polish (KFAC_OPT_BASIS_POLISH) squares what is
                                        left */
-  KFAC_OPT_EIG_STOP_TOL = 9         /* [3e-3]: Jacobi also stops after a sweep in which
+  KFAC_OPT_EIG_STOP_TOL = 9,        /* [3e-3]: Jacobi also stops after a sweep in which
                                        every pair cosine, taken before its rotation, was <= v;
                                        cyclic Jacobi converges quadratically, so that sweep
-                                       leaves them near v^2, and the FP64 refinement that
-                                       follows squares the remaining error again. 0: sweep
-                                       until a sweep rotates no pair (every pair cosine <=
-                                       KFAC_OPT_EIG_TOL) */,
+                                       leaves them near v^2, and the refinement that follows
+                                       squares the remaining error again. 0: sweep until a
+                                       sweep rotates no pair (every pair cosine <=
+                                       KFAC_OPT_EIG_TOL) */
   KFAC_OPT_EIG_REFINE_FP64 = 10     /* 0 [default]: the eigen-refinement and basis-polish
                                        k x k products run in FP32 (FP64 carries the matrices
                                        between steps); their rounding, ~6e-8 of ||C||, is at
