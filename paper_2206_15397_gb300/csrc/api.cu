@@ -195,7 +195,8 @@ InvertLayout invert_layout(int d, int k, int r) {
 }
 
 // Gram-type product out = A A'^T (k x k, K = d) for two k x d row-major
-// operands, split over K with FP32 partials reduced (and symmetrised) in FP64.
+// operands, split over K with FP32 partials summed with compensation (and
+// symmetrised) into FP64.
 kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const float* Bm, long long ld, int k,
                      int d, kfac_precision prec, double* out, int stage, float* out32) {
   GemmDesc<float> g = {};
