@@ -1,7 +1,13 @@
-// FP64 Cholesky of the CholeskyQR Gram matrix on one thread-block cluster.
+// Cholesky factorisations of the CholeskyQR Grams and of the eigensolver's
+// shifted projected matrix, and the triangular solve Q^T = L^-1 Y^T:
+//   - k_chol_cta_f32: FP32 on one CTA with the matrix in shared memory, the
+//     default for k <= CTA_KMAX (described at the kernel);
+//   - k_chol_cluster<T>: FP32 above that size, or FP64 when the options ask
+//     for it, on one thread-block cluster (below);
+//   - k_trsm_pack / k_trsm_lower_smem / k_trsm_lower: the block solve.
 //
-// FP64 runs at about 2 FMA/clock/SM on this part, so a k x k Cholesky (k^3/3
-// FMA) is spread over up to 16 CTAs of a cluster. Rows are distributed
+// Cluster kernel. FP64 runs at about 2 FMA/clock/SM on this part, so a k x k
+// Cholesky (k^3/3 FMA) is spread over up to 16 CTAs of a cluster. Rows are distributed
 // cyclically (row i lives in CTA i % NC, in its shared memory). A blocked
 // right-looking factorisation with panel width B runs in lock-step:
 //   (a) the owners of the diagonal-block rows broadcast them into every CTA
