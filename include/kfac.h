@@ -125,8 +125,12 @@ typedef struct {
 
 /* kfac_ea_update for `count` factors (every layer's forward and backward
  * factor, Alg. 1), enqueued on up to 8 streams forked from the context stream
- * (event fork/join, graph-capturable; no workspace). All descriptors are
- * checked before anything is enqueued; factors must not alias each other. */
+ * (event fork/join, graph-capturable). A batch matrix whose base or row stride
+ * is not 16-byte aligned is first copied into the workspace with a padded
+ * stride (so that the product runs on the tensor cores); a call that does this
+ * under graph capture needs the workspace sized by an earlier call with the same
+ * shapes. All descriptors are checked before anything is enqueued; factors must
+ * not alias each other. */
 KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac_ea_desc* descs);
 
 /* Randomized low-rank eigendecomposition + damping coefficients of one
@@ -300,9 +304,9 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double valu
  * to test it directly): D = alpha * A B^T + beta * D for row-major A (M x K,
  * lda), B (N x K, ldb) and D (M x N, ldd), device pointers. prec: FP32 (3xTF32
  * tensor-core products), TF32 or BF16 (operands rounded, FP32 accumulation).
- * The tcgen05 tensor-core kernel runs when A, B are 16-byte aligned with row
- * strides that are multiples of 4 floats (TMA); otherwise a SIMT kernel with
- * the same arithmetic. D must not overlap A or B. */
+ * The products run on the tcgen05 tensor cores; an operand whose base or row
+ * stride is not 16-byte aligned (which TMA cannot read) is first copied into a
+ * padded workspace. D must not overlap A or B. */
 KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const float* A, int lda, const float* B,
                                   int ldb, float alpha, float beta, float* D, int ldd, kfac_precision prec);
 
@@ -320,6 +324,14 @@ KFAC_API kfac_status kfac_profile_read(kfac_ctx* ctx, const char** names, double
 /* Number of kernels this library has launched in the process so far (all
  * contexts). Used to count device work inside a timed region. */
 KFAC_API uint64_t kfac_kernel_launch_count(void);
+
+/* Number of large products (EA SYRK, sketch / power / projection, lift,
+ * preconditioner apply, kfac_gemm_nt) that ran on the SIMT fallback kernel
+ * instead of the tensor cores, in the process so far. Operands whose rows are
+ * not 16-byte aligned are copied to a padded workspace first, so this stays 0
+ * unless a product is degenerate or kfac_precondition_noalloc's transposed
+ * operands are used. */
+KFAC_API uint64_t kfac_simt_gemm_count(void);
 
 /* Device-side counters of the context, read after synchronising its stream and
  * then cleared: out[0] = Jacobi sweeps performed, out[1] = Jacobi solves,

@@ -41,13 +41,27 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (plain gcc, -O2, no arch flags)."""
+    """Compile oracle.c into _build/liboracle.so (plain gcc, -O2, no arch flags;
+    -fopenmp spreads independent rows over the host cores without changing any
+    sum's order; OMP_NUM_THREADS caps the threads)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Set the OpenMP thread count of later oracle calls; returns the previous maximum."""
+    lib = _load()
+    prev = lib.omp_get_max_threads()
+    lib.omp_set_num_threads(int(n))
+    return prev
+
+
+def max_threads() -> int:
+    return int(_load().omp_get_max_threads())
 
 
 def _load():
@@ -71,6 +85,8 @@ def _load():
             lib.orc_exact_apply.restype = i
             lib.orc_rank_bound.argtypes = [d, d, d, l, l]
             lib.orc_rank_bound.restype = l
+            lib.omp_get_max_threads.restype = i
+            lib.omp_set_num_threads.argtypes = [i]
             _lib = lib
     return _lib
 

@@ -6,10 +6,13 @@
  * benchmark's CPU-baseline leg may load or call this library; the product path
  * (the CUDA library) never does, and the two share no code.
  *
- * Everything here is plain, slow, sequential FP64 C: triple-loop products,
- * textbook cyclic Jacobi, textbook Householder QR. Each function cites the
- * passage of the paper whose computation it writes out. Matrices are dense,
- * row-major, with the leading dimension equal to the column count.
+ * Everything here is plain, slow FP64 C: triple-loop products, textbook
+ * cyclic Jacobi, textbook Householder QR. Each function cites the passage of
+ * the paper whose computation it writes out. Matrices are dense, row-major,
+ * with the leading dimension equal to the column count. Loops over
+ * independent rows or columns carry OpenMP pragmas (used when built with
+ * -fopenmp): every output element is still summed by one thread in the same
+ * order, so the results are bitwise those of the sequential build.
  *
  * Readings of points where the paper is silent or ambiguous (all mirrored by
  * the GPU path):
@@ -41,6 +44,7 @@
 void orc_matmul(int m, int n, int kk, const double* A, int ta, const double* B, int tb, double* C) {
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < n; ++j) C[(size_t)i * n + j] = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) if ((double)m * n * kk > 1e6)
   for (int i = 0; i < m; ++i) {
     double* c = C + (size_t)i * n;
     for (int t = 0; t < kk; ++t) {
@@ -64,6 +68,7 @@ void orc_matmul(int m, int n, int kk, const double* A, int ta, const double* B, 
 
 /* F <- rho F + (1 - rho) (1/n) X X^T, X is d x n (one column per sample). */
 void orc_ea_update(int d, int n, const double* X, double rho, double* F) {
+#pragma omp parallel for schedule(dynamic, 8) if ((double)d * d * n > 1e6)
   for (int i = 0; i < d; ++i) {
     for (int j = 0; j < d; ++j) {
       double s = 0.0;
@@ -179,6 +184,7 @@ void orc_qr(int m, int k, const double* Y, double* Q, double* R) {
     }
     if (vnorm2 == 0.0) { beta[j] = 0.0; continue; }
     beta[j] = 2.0 / vnorm2;
+#pragma omp parallel for schedule(static) if ((double)(m - j) * (k - j) > 1e5)
     for (int c = j; c < k; ++c) { /* W[j:, c] <- (I - beta v v^T) W[j:, c] */
       double s = 0.0;
       for (int i = j; i < m; ++i) s += Vh[(size_t)i * k + j] * W[(size_t)i * k + c];
@@ -193,6 +199,7 @@ void orc_qr(int m, int k, const double* Y, double* Q, double* R) {
     for (int j = 0; j < k; ++j) Q[(size_t)i * k + j] = (i == j) ? 1.0 : 0.0;
   for (int j = k - 1; j >= 0; --j) {
     if (beta[j] == 0.0) continue;
+#pragma omp parallel for schedule(static) if ((double)(m - j) * k > 1e5)
     for (int c = 0; c < k; ++c) {
       double s = 0.0;
       for (int i = j; i < m; ++i) s += Vh[(size_t)i * k + j] * Q[(size_t)i * k + c];
@@ -252,6 +259,7 @@ int orc_srevd(int d, const double* X, int k, const double* Omega, int q, int r,
       C[(size_t)j * k + i] = s;
     }
   int rc = orc_jacobi_eigh(k, C, w, P, 100, 1e-15); /* P_C D_C P_C^T = C  */
+#pragma omp parallel for schedule(static) if ((double)d * r * k > 1e6)
   for (int i = 0; i < d; ++i)                       /* U = Q P_C[:, :r]   */
     for (int j = 0; j < r; ++j) {
       double s = 0.0;
@@ -310,10 +318,11 @@ void orc_precondition(int dg, int da, const double* J, const double* Ua, const d
 void orc_precondition_cols(int dg, int da, const double* J, const double* Ua, const double* ca, int ra,
                            const double* Ug, const double* cg, int rg, double lam, int ncols, const int* cols,
                            double* S_cols) {
-  double* v = (double*)malloc(sizeof(double) * (size_t)da);
-  double* m = (double*)malloc(sizeof(double) * (size_t)dg);
-  double* t = (double*)malloc(sizeof(double) * (size_t)(rg > 0 ? rg : 1));
+#pragma omp parallel for schedule(dynamic, 1) if (ncols > 1)
   for (int jc = 0; jc < ncols; ++jc) {
+    double* v = (double*)malloc(sizeof(double) * (size_t)da);
+    double* m = (double*)malloc(sizeof(double) * (size_t)dg);
+    double* t = (double*)malloc(sizeof(double) * (size_t)(rg > 0 ? rg : 1));
     const int c = cols[jc];
     for (int i = 0; i < da; ++i) {                     /* v = U_a (c_a o U_a[c, :]) */
       double s = 0.0;
@@ -335,8 +344,8 @@ void orc_precondition_cols(int dg, int da, const double* J, const double* Ua, co
       for (int l = 0; l < rg; ++l) s += Ug[(size_t)i * rg + l] * t[l];
       S_cols[(size_t)i * ncols + jc] = s + m[i] / lam;
     }
+    free(v); free(m); free(t);
   }
-  free(v); free(m); free(t);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -145,16 +145,21 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, p32, skws, total;
-  long long dp, skws_floats;
+  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, skws, total;
+  long long dp, kp, skws_floats;
   int nsplit, kchunk;
+  bool pack_f;
 };
 
 constexpr int kSketchMaxSplit = 6;  // split-K partials of the sketch products
 
-InvertLayout invert_layout(int d, int k, int r) {
+// pack_f: F's rows are not 16-byte aligned, so the sketch products read a
+// copy of F with a padded row stride (one extra pass over F per inversion,
+// against the q + 2 passes of the products it puts on the tensor cores).
+InvertLayout invert_layout(int d, int k, int r, bool pack_f) {
   InvertLayout L = {};
   Bump b;
+  L.pack_f = pack_f;
   if (k >= d) {  // exact path
     int n = d;
     L.c = b.take<double>((size_t)n * n);
@@ -187,7 +192,10 @@ InvertLayout invert_layout(int d, int k, int r) {
   L.work = b.take<double>(eig_refine_doubles(k));
   L.jac = b.take<float>(eig_scratch_floats(k));
   L.r32 = b.take<float>(eig_refine_floats(k) + 3 * (size_t)k * k);  // refinement, then the polish's E, P, Q
-  L.p32 = b.take<float>((size_t)k * r);
+  L.kp = round_up(k, 4);
+  L.pt = b.take<float>((size_t)r * L.kp);  // P[:, :r]^T, the lift's B operand
+  L.qn = b.take<float>((size_t)d * L.kp);  // Q (d x k), the lift's A operand
+  if (pack_f) L.fp = b.take<float>((size_t)d * L.dp);
   L.skws_floats = (long long)kSketchMaxSplit * k * d;
   L.skws = b.take<float>((size_t)L.skws_floats);
   L.total = b.off;
@@ -312,9 +320,9 @@ kfac_status check_invert(const kfac_invert_desc& a, int* r_out, int* k_out) {
 kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L, size_t base) {
   const int d = a.d, r = std::min(a.rank, a.d), k = a.rank + a.oversample;
   const float* F = a.F;
-  const int ldf = a.ldf;
+  int ldf = a.ldf;
   for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
-                    &L.r32, &L.p32, &L.skws})
+                    &L.r32, &L.pt, &L.qn, &L.fp, &L.skws})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;
@@ -325,9 +333,16 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
                     at<float>(ctx, L.jac), at<float>(ctx, L.r32));
     if (st != KFAC_OK) return st;
     STAGE(ctx, ST_SELECT);
-    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), d, r, a.lambda, nullptr, a.D, a.coef, a.U, a.ldu,
-                  s));
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), d, r, a.lambda, nullptr, 0, a.D, a.coef, a.U,
+                  a.ldu, s));
     return KFAC_OK;
+  }
+  if (L.pack_f) {  // rows of F not 16-byte aligned: the tensor-core products read a padded copy
+    STAGE(ctx, ST_TRANSPOSE);
+    float* Fp = at<float>(ctx, L.fp);
+    CK(pack_rows_f32(F, ldf, d, d, Fp, L.dp, s));
+    F = Fp;
+    ldf = (int)L.dp;
   }
   // Omega^T (k x d) so that every sketch product reads K-contiguous rows.
   float* Om = at<float>(ctx, L.om);
@@ -394,19 +409,24 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     STAGE(ctx, ST_POLISH);
     CK(polish_vectors_f32(at<double>(ctx, L.x), k, pw32, s));
   }
-  float* P32 = at<float>(ctx, L.p32);
+  float* Pt = at<float>(ctx, L.pt);
   {
     STAGE(ctx, ST_SELECT);
-    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, a.lambda, P32, a.D, a.coef, nullptr, 0, s));
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, a.lambda, Pt, L.kp, a.D, a.coef, nullptr, 0,
+                  s));
   }
-  // Lift: U (d x r) = Q P[:, :r] = (Q^T)^T P32.
+  // Lift: U (d x r) = Q P[:, :r], both operands K-contiguous (Q from Q^T by a
+  // transpose, P[:, :r]^T from the selection) so the product runs on tcgen05.
+  STAGE(ctx, ST_LIFT);
+  float* Qn = at<float>(ctx, L.qn);
+  CK(transpose_f32(cur, L.dp, k, d, Qn, L.kp, s));
   GemmDesc<float> g = {};
   g.M = d; g.N = r; g.K = k;
-  g.A = cur; g.sam = 1; g.sak = L.dp;
-  g.B = P32; g.sbn = 1; g.sbk = r;
+  g.A = Qn; g.sam = L.kp; g.sak = 1;
+  g.B = Pt; g.sbn = L.kp; g.sbk = 1;
   g.D = a.U; g.ldd = a.ldu;
   g.alpha = 1.0f; g.zsplit = 1;
-  STAGE(ctx, ST_LIFT);
+  g.flags = ctx->dflags;
   CK(gemm_f32(g, KFAC_PREC_FP32, s));
   return KFAC_OK;
 }
@@ -417,15 +437,19 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
 // T2^T = M^T U_g diag(c_g) (d_a x r_g), S = U_g (T2^T)^T + M/lam, with the small
 // transposes U_a^T, U_g^T; split-K partials for the two long-K products.
 struct PrecLayout {
-  size_t uat, ugt, t, mt, t2, ws, total;
-  long long ld_uat, ld_ugt, ld_t, ld_mt, ld_t2, ws_floats;
+  size_t uat, ugt, t, mt, t2, ws, jp, uap, ugp, total;
+  long long ld_uat, ld_ugt, ld_t, ld_mt, ld_t2, ws_floats, ld_jp, ld_uap, ld_ugp;
+  bool pack_j, pack_ua, pack_ug;
 };
 
 constexpr int kApplyMaxSplit = 6;
 
-PrecLayout prec_layout(int dg, int da, int ra, int rg) {
+// pack_j / pack_ua / pack_ug: that operand's rows are not 16-byte aligned, so
+// the tensor-core products read a copy with a padded row stride.
+PrecLayout prec_layout(int dg, int da, int ra, int rg, bool pack_j, bool pack_ua, bool pack_ug) {
   PrecLayout P = {};
   Bump b;
+  P.pack_j = pack_j; P.pack_ua = pack_ua && ra > 0; P.pack_ug = pack_ug && rg > 0;
   P.ld_uat = round_up(da, 4);
   P.ld_ugt = round_up(dg, 4);
   P.ld_t = round_up(std::max(ra, 1), 4);
@@ -438,16 +462,45 @@ PrecLayout prec_layout(int dg, int da, int ra, int rg) {
   P.t2 = b.take<float>((size_t)da * P.ld_t2);
   P.ws_floats = (long long)kApplyMaxSplit * std::max((long long)dg * std::max(ra, 1), (long long)da * std::max(rg, 1));
   P.ws = b.take<float>((size_t)P.ws_floats);
+  P.ld_jp = round_up(da, 4);
+  P.ld_uap = round_up(std::max(ra, 1), 4);
+  P.ld_ugp = round_up(std::max(rg, 1), 4);
+  if (P.pack_j) P.jp = b.take<float>((size_t)dg * P.ld_jp);
+  if (P.pack_ua) P.uap = b.take<float>((size_t)da * P.ld_uap);
+  if (P.pack_ug) P.ugp = b.take<float>((size_t)dg * P.ld_ugp);
   P.total = b.off;
   return P;
+}
+
+PrecLayout prec_layout_for(int dg, int da, const float* J, int ldj, const float* U_a, int ld_ua, int ra,
+                           const float* U_g, int ld_ug, int rg) {
+  return prec_layout(dg, da, ra, rg, !tma_rows_ok(J, ldj), !tma_rows_ok(U_a, ld_ua), !tma_rows_ok(U_g, ld_ug));
 }
 
 kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, int ldj, const float* U_a, int ld_ua,
                              const float* coef_a, int r_a, const float* U_g, int ld_ug, const float* coef_g, int r_g,
                              float lambda, kfac_precision prec, float* S, int lds, PrecLayout P, size_t base) {
-  for (size_t* o : {&P.uat, &P.ugt, &P.t, &P.mt, &P.t2, &P.ws}) *o += base;
+  for (size_t* o : {&P.uat, &P.ugt, &P.t, &P.mt, &P.t2, &P.ws, &P.jp, &P.uap, &P.ugp}) *o += base;
   cudaStream_t s = ctx->stream;
   const float inv_lam = 1.0f / lambda;
+  if (P.pack_j || P.pack_ua || P.pack_ug) {  // operands whose rows TMA cannot read: padded copies
+    STAGE(ctx, ST_TRANSPOSE);
+    if (P.pack_j) {
+      CK(pack_rows_f32(J, ldj, d_g, d_a, at<float>(ctx, P.jp), P.ld_jp, s));
+      J = at<float>(ctx, P.jp);
+      ldj = (int)P.ld_jp;
+    }
+    if (P.pack_ua) {
+      CK(pack_rows_f32(U_a, ld_ua, d_a, r_a, at<float>(ctx, P.uap), P.ld_uap, s));
+      U_a = at<float>(ctx, P.uap);
+      ld_ua = (int)P.ld_uap;
+    }
+    if (P.pack_ug) {
+      CK(pack_rows_f32(U_g, ld_ug, d_g, r_g, at<float>(ctx, P.ugp), P.ld_ugp, s));
+      U_g = at<float>(ctx, P.ugp);
+      ld_ug = (int)P.ld_ugp;
+    }
+  }
   float* Uat = at<float>(ctx, P.uat);
   float* Ugt = at<float>(ctx, P.ugt);
   float* T = at<float>(ctx, P.t);
@@ -640,14 +693,14 @@ KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t m
   DeviceGuard g(ctx->device);
   size_t need = 0;
   if (d_max > 0 && k_max > 0) {
-    InvertLayout a = invert_layout(d_max, std::min(k_max, d_max - 1 > 0 ? d_max - 1 : 1), k_max);
-    InvertLayout b = invert_layout(std::min(d_max, k_max), k_max, k_max);
+    InvertLayout a = invert_layout(d_max, std::min(k_max, d_max - 1 > 0 ? d_max - 1 : 1), k_max, true);
+    InvertLayout b = invert_layout(std::min(d_max, k_max), k_max, k_max, true);
     need = std::max(a.total, b.total);
   }
-  if (mn_max > 0) {  // preconditioner apply: M^T plus thin intermediates and split-K partials
+  if (mn_max > 0) {  // preconditioner apply: M^T (and a padded copy of J) plus thin intermediates and split-K partials
     const size_t dk = (size_t)std::max(d_max, 1) * (std::max(k_max, 1) + 4);
-    size_t p = sizeof(float) * ((size_t)mn_max + 4 * (size_t)std::max(d_max, 1) + (4 + kApplyMaxSplit) * dk) +
-               8 * 256;
+    const size_t mn_pad = (size_t)mn_max + 4 * (size_t)std::max(d_max, 1);
+    size_t p = sizeof(float) * (2 * mn_pad + (6 + kApplyMaxSplit) * dk) + 12 * 256;
     need = std::max(need, p);
   }
   return ensure_ws(ctx, need);
@@ -661,15 +714,31 @@ KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const floa
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   const long long ws_floats = std::min<long long>(6LL * M * N, 1LL << 24);
-  kfac_status st = ensure_ws(ctx, (size_t)ws_floats * sizeof(float));
+  const long long kp = round_up(K, 4);
+  const bool pack_a = K > 0 && !tma_rows_ok(A, lda), pack_b = K > 0 && !tma_rows_ok(B, ldb);
+  Bump b;
+  const size_t o_ws = b.take<float>((size_t)ws_floats);
+  const size_t o_a = pack_a ? b.take<float>((size_t)M * kp) : 0;
+  const size_t o_b = pack_b ? b.take<float>((size_t)N * kp) : 0;
+  kfac_status st = ensure_ws(ctx, b.off);
   if (st != KFAC_OK) return st;
+  if (pack_a) {  // rows TMA cannot read: the tensor-core kernel reads padded copies
+    CK(pack_rows_f32(A, lda, M, K, at<float>(ctx, o_a), kp, ctx->stream));
+    A = at<float>(ctx, o_a);
+    lda = (int)kp;
+  }
+  if (pack_b) {
+    CK(pack_rows_f32(B, ldb, N, K, at<float>(ctx, o_b), kp, ctx->stream));
+    B = at<float>(ctx, o_b);
+    ldb = (int)kp;
+  }
   GemmDesc<float> g = {};
   g.M = M; g.N = N; g.K = K;
   g.A = A; g.sam = lda; g.sak = 1;
   g.B = B; g.sbn = ldb; g.sbk = 1;
   g.D = D; g.ldd = ldd;
   g.alpha = alpha; g.beta = beta; g.C0 = D; g.ldc = ldd;
-  g.zsplit = 1; g.ws = at<float>(ctx, 0); g.ws_floats = ws_floats; g.flags = ctx->dflags;
+  g.zsplit = 1; g.ws = at<float>(ctx, o_ws); g.ws_floats = ws_floats; g.flags = ctx->dflags;
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
 }
@@ -690,6 +759,28 @@ KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags) {
   return KFAC_OK;
 }
 
+// Workspace bytes of one EA update: a padded copy of X when TMA cannot read its rows.
+static size_t ea_ws_bytes(int d, int n, const float* X, int ldx) {
+  if (n == 0 || tma_rows_ok(X, ldx)) return 0;
+  return sizeof(float) * (size_t)d * (size_t)round_up(n, 4) + 256;
+}
+
+// One EA update on ctx->stream; a ragged X is first packed at byte offset `base`
+// of the workspace.
+static kfac_status ea_run(kfac_ctx* ctx, int d, int n, const float* X, int ldx, float rho, kfac_precision prec,
+                          float* F, int ldf, size_t base) {
+  STAGE(ctx, ST_EA);
+  if (n > 0 && !tma_rows_ok(X, ldx)) {
+    float* Xp = at<float>(ctx, (base + 255) & ~size_t(255));
+    const long long ldp = round_up(n, 4);
+    CK(pack_rows_f32(X, ldx, d, n, Xp, ldp, ctx->stream));
+    X = Xp;
+    ldx = (int)ldp;
+  }
+  CK(ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags));
+  return KFAC_OK;
+}
+
 KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X, int ldx, float rho,
                                     kfac_precision prec, float* F, int ldf) {
   if (!ctx || d < 0 || n < 0 || ldf < d || (d > 0 && !F) || (n > 0 && (!X || ldx < n))) return KFAC_ERR_INVALID_ARG;
@@ -697,8 +788,9 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
   if (d == 0) return KFAC_OK;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  STAGE(ctx, ST_EA);
-  return ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags) == cudaSuccess ? KFAC_OK : KFAC_ERR_CUDA;
+  kfac_status st = ensure_ws(ctx, ea_ws_bytes(d, n, X, ldx));
+  if (st != KFAC_OK) return st;
+  return ea_run(ctx, d, n, X, ldx, rho, prec, F, ldf, 0);
 }
 
 static kfac_status check_ea(const kfac_ea_desc& a) {
@@ -719,7 +811,14 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   const int ns = std::min(count, kMaxSideStreams);
-  kfac_status st;
+  std::vector<size_t> base(ns + 1, 0);  // per-stream workspace slices (padded copies of ragged X)
+  for (int q = 0; q < ns; ++q) {
+    size_t m = 0;
+    for (int f = q; f < count; f += ns) m = std::max(m, ea_ws_bytes(descs[f].d, descs[f].n, descs[f].X, descs[f].ldx));
+    base[q + 1] = base[q] + ((m + 255) & ~size_t(255));
+  }
+  kfac_status st = ensure_ws(ctx, base[ns]);
+  if (st != KFAC_OK) return st;
   if (ns > 1 && (st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
   cudaStream_t main_s = ctx->stream;
   if (ns > 1) {
@@ -731,9 +830,7 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
     const kfac_ea_desc& a = descs[f];
     if (a.d == 0) continue;
     ctx->stream = ns > 1 ? ctx->side[f % ns] : main_s;
-    STAGE(ctx, ST_EA);
-    if (ea_syrk(ctx->stream, a.d, a.n, a.X, a.ldx, a.rho, a.prec, a.F, a.ldf, ctx->dflags) != cudaSuccess)
-      first_err = KFAC_ERR_CUDA;
+    first_err = ea_run(ctx, a.d, a.n, a.X, a.ldx, a.rho, a.prec, a.F, a.ldf, base[f % ns]);
   }
   ctx->stream = main_s;
   if (ns > 1) {
@@ -755,7 +852,7 @@ KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int 
   if (st != KFAC_OK) return st;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  InvertLayout L = invert_layout(d, k, r);
+  InvertLayout L = invert_layout(d, k, r, !tma_rows_ok(F, ldf));
   if ((st = ensure_ws(ctx, L.total)) != KFAC_OK) return st;
   return invert_run(ctx, a, L, 0);
 }
@@ -768,7 +865,7 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
     int r = 0, k = 0;
     kfac_status st = check_invert(descs[f], &r, &k);
     if (st != KFAC_OK) return st;
-    lay[f] = invert_layout(descs[f].d, k, r);
+    lay[f] = invert_layout(descs[f].d, k, r, !tma_rows_ok(descs[f].F, descs[f].ldf));
   }
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
@@ -811,7 +908,7 @@ KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const fl
   if (r_g > 0 && (!U_g || ld_ug < r_g || !coef_g)) return KFAC_ERR_INVALID_ARG;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  PrecLayout P = prec_layout(d_g, d_a, r_a, r_g);
+  PrecLayout P = prec_layout_for(d_g, d_a, J, ldj, U_a, ld_ua, r_a, U_g, ld_ug, r_g);
   kfac_status st = ensure_ws(ctx, P.total);
   if (st != KFAC_OK) return st;
   return precondition_run(ctx, d_g, d_a, J, ldj, U_a, ld_ua, coef_a, r_a, U_g, ld_ug, coef_g, r_g, lambda, prec, S,
@@ -838,7 +935,10 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   std::vector<PrecLayout> lay(count);
-  for (int f = 0; f < count; ++f) lay[f] = prec_layout(descs[f].d_g, descs[f].d_a, descs[f].r_a, descs[f].r_g);
+  for (int f = 0; f < count; ++f) {
+    const kfac_precond_desc& a = descs[f];
+    lay[f] = prec_layout_for(a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.r_a, a.U_g, a.ld_ug, a.r_g);
+  }
   const int ns = std::min(count, kMaxSideStreams);
   std::vector<size_t> base(ns + 1, 0);
   for (int q = 0; q < ns; ++q) {
@@ -873,6 +973,8 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
 }
 
 KFAC_API uint64_t kfac_kernel_launch_count(void) { return (uint64_t)launch_count(); }
+
+KFAC_API uint64_t kfac_simt_gemm_count(void) { return (uint64_t)simt_gemm_count(); }
 
 KFAC_API kfac_status kfac_stats_read(kfac_ctx* ctx, int64_t* out, int n) {
   if (!ctx || n < 0 || (n > 0 && !out)) return KFAC_ERR_INVALID_ARG;

@@ -21,6 +21,10 @@ constexpr int kMaxSketch = 576;
 // Process-wide count of kernel launches issued by this library.
 void note_launch(unsigned n = 1);
 unsigned long long launch_count();
+// Process-wide count of products that gemm_f32 sent to the SIMT kernel
+// instead of the tensor cores (K > 0; see kfac_simt_gemm_count).
+void note_simt_gemm();
+unsigned long long simt_gemm_count();
 
 // Device-side counters (see kfac_stats_read): sweeps, solves, Cholesky, retries.
 enum { STAT_SWEEPS = 0, STAT_EIG_SOLVES = 1, STAT_CHOL = 2, STAT_CHOL_RETRY = 3, STAT_COUNT = 4 };
@@ -118,6 +122,17 @@ cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, fl
                           cudaStream_t s);
 cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int cols, double* out, long long ldo,
                                int* flags, cudaStream_t s);
+// dst (rows x cols, row stride ldd: a multiple of 4 floats, 16-byte aligned
+// base) <- src (any row stride lds); the pad columns are zeroed. Gives the
+// tensor-core kernels (whose TMA loads need 16-byte row strides) a copy of an
+// operand whose rows are not 16-byte aligned.
+cudaError_t pack_rows_f32(const float* src, long long lds, int rows, int cols, float* dst, long long ldd,
+                          cudaStream_t s);
+// True when TMA can read a row-major FP32 matrix at p with row stride ld as is
+// (16-byte aligned base and row stride).
+inline bool tma_rows_ok(const void* p, long long ld) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (ld & 3) == 0;
+}
 
 // Cholesky of (G + shift I) on a thread-block cluster, factorised in FP64
 // (fp64) or FP32 from the FP64 Gram G; writes the lower factor L as FP32 (k x k
@@ -175,9 +190,10 @@ cudaError_t polish_projected_f32(const double* G, double* C, float* C32, int k, 
 cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s);
 
 // Sort eigenpairs descending (stable by index), emit the r leading ones:
-// P32 (k x r FP32, columns = eigenvectors), D and coef (FP32, Eq. (13)), and
-// optionally Uout (k x r into a strided FP32 matrix, for the k >= d path).
-cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* P32, float* D,
-                       float* coef, float* Uout, long long ldu, cudaStream_t s);
+// Pt (r x k FP32, row stride ldpt, row t = eigenvector t; optional), D and coef
+// (FP32, Eq. (13)), and optionally Uout (k x r into a strided FP32 matrix, for
+// the k >= d path).
+cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* Pt, long long ldpt,
+                       float* D, float* coef, float* Uout, long long ldu, cudaStream_t s);
 
 }  // namespace kfac

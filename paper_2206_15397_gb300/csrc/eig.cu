@@ -448,9 +448,10 @@ __global__ void __launch_bounds__(REF_THREADS) k_refine_E(const double* __restri
 }
 
 __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ X, const double* __restrict__ lam,
-                                                      int k, int r, float lambda, float* __restrict__ P32,
-                                                      float* __restrict__ D, float* __restrict__ coef,
-                                                      float* __restrict__ Uout, long long ldu) {
+                                                      int k, int r, float lambda, float* __restrict__ Pt,
+                                                      long long ldpt, float* __restrict__ D,
+                                                      float* __restrict__ coef, float* __restrict__ Uout,
+                                                      long long ldu) {
   // Every CTA ranks the k eigenvalues (from shared memory) and copies its
   // slice of the selected columns; CTA 0 also writes D and the coefficients.
   // Ranking compares order-preserving integer keys of the FP64 values (an
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ 
   for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < total; e += step) {
     int row = (int)(e / r), t = (int)(e % r);
     float v = (float)X[(size_t)row * k + order[t]];
-    if (P32) P32[e] = v;
+    if (Pt) Pt[(long long)t * ldpt + row] = v;
     if (Uout) Uout[(long long)row * ldu + t] = v;
   }
 }
@@ -744,14 +745,14 @@ cudaError_t convert_f64_to_f32(const double* in, long long n, float* out, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* P32, float* D,
-                       float* coef, float* Uout, long long ldu, cudaStream_t s) {
+cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* Pt, long long ldpt,
+                       float* D, float* coef, float* Uout, long long ldu, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   const long long total = (long long)k * r;
   int grid = (int)((total + 4095) / 4096);
   grid = grid < 1 ? 1 : (grid > 152 ? 152 : grid);
-  k_eig_select<<<grid, 1024, (sizeof(double) + sizeof(int)) * k + 8, s>>>(X, lam, k, r, lambda, P32, D, coef, Uout,
-                                                                           ldu);
+  k_eig_select<<<grid, 1024, (sizeof(double) + sizeof(int)) * k + 8, s>>>(X, lam, k, r, lambda, Pt, ldpt, D, coef,
+                                                                           Uout, ldu);
   note_launch();
   return cudaGetLastError();
 }

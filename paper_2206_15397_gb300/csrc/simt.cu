@@ -1,5 +1,6 @@
 // SIMT kernels: strided GEMM (FP32 with optional operand rounding, FP64),
 // split-K reduction to FP64, transpose and widening copies.
+#include <algorithm>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -253,6 +254,26 @@ __global__ void k_transpose(const float* __restrict__ in, long long ldi, int row
   }
 }
 
+// dst (rows x ldd, ldd a multiple of 4, 16-byte aligned) <- src (rows x cols,
+// any row stride); columns cols..ldd-1 are zeroed. Each thread writes one
+// 16-byte group, so the stores are vector stores whatever the source stride.
+__global__ void k_pack_rows(const float* __restrict__ src, long long lds, int rows, int cols,
+                            float* __restrict__ dst, long long ldd) {
+  const long long groups = ldd >> 2, total = (long long)rows * groups;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long r = g / groups;
+    const int c = (int)(g - r * groups) * 4;
+    const float* s = src + r * lds;
+    float4 v;
+    v.x = c < cols ? s[c] : 0.0f;
+    v.y = c + 1 < cols ? s[c + 1] : 0.0f;
+    v.z = c + 2 < cols ? s[c + 2] : 0.0f;
+    v.w = c + 3 < cols ? s[c + 3] : 0.0f;
+    *reinterpret_cast<float4*>(dst + r * ldd + c) = v;
+  }
+}
+
 __global__ void k_convert(const float* __restrict__ in, long long ldi, int rows, int cols, double* __restrict__ out,
                           long long ldo, int* flags) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -285,6 +306,9 @@ cudaError_t set_kernel_attrs_once(const void* fn, int max_dyn_smem, bool nonport
 static unsigned long long g_launches = 0;
 void note_launch(unsigned n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+static unsigned long long g_simt_gemms = 0;
+void note_simt_gemm() { __atomic_fetch_add(&g_simt_gemms, 1ull, __ATOMIC_RELAXED); }
+unsigned long long simt_gemm_count() { return __atomic_load_n(&g_simt_gemms, __ATOMIC_RELAXED); }
 
 cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s) {
   switch (rnd) {
@@ -335,6 +359,16 @@ cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, fl
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   dim3 grid((cols + 31) / 32, (rows + 31) / 32);
   k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, ldi, rows, cols, out, ldo);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t pack_rows_f32(const float* src, long long lds, int rows, int cols, float* dst, long long ldd,
+                          cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const long long total = (long long)rows * (ldd >> 2);
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
+  k_pack_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, rows, cols, dst, ldd);
   note_launch();
   return cudaGetLastError();
 }

@@ -77,6 +77,7 @@ def lib():
         L.kfac_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d), ctypes.POINTER(i), i,
                                         ctypes.POINTER(i)]
         L.kfac_kernel_launch_count.restype = ctypes.c_uint64
+        L.kfac_simt_gemm_count.restype = ctypes.c_uint64
         L.kfac_rsvd_invert_grouped.argtypes = [vp, i, ctypes.POINTER(InvertDesc)]
         L.kfac_ea_update_grouped.argtypes = [vp, i, ctypes.POINTER(EaDesc)]
         L.kfac_ea_update_grouped.restype = i
@@ -236,6 +237,11 @@ def kfac_profile_read(ctx: Context) -> dict:
 
 def kfac_kernel_launch_count() -> int:
     return int(lib().kfac_kernel_launch_count())
+
+
+def kfac_simt_gemm_count() -> int:
+    """Large products that ran on the SIMT fallback instead of the tensor cores (process total)."""
+    return int(lib().kfac_simt_gemm_count())
 
 
 def kfac_stats_read(ctx: Context) -> dict:

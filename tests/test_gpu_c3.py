@@ -65,6 +65,7 @@ def run_c3(kf, ctx, w, prec):
         for side in ("a", "g"):
             items.append(dict(F=cuda(L["f" + side]), rank=L["r_" + side], oversample=p, power_iters=q, lam=lam,
                               omega=cuda(L["om_" + side]), prec=prec))
+    n_simt = kf.kfac_simt_gemm_count()
     outs = kf.kfac_rsvd_invert_grouped(ctx, items)
     pitems = []
     for li, L in enumerate(w["layers"]):
@@ -74,6 +75,8 @@ def run_c3(kf, ctx, w, prec):
     torch.cuda.synchronize()
     st, flags = kf.kfac_get_status(ctx)
     assert st == 0 and set(flags) <= {"CHOL_SHIFTED", "EIG_SHIFTED"}, (st, flags)
+    # unpadded tensors (A factors 28 ... 4609 wide): every product on the tensor cores
+    assert kf.kfac_simt_gemm_count() == n_simt
     return items, outs, S
 
 

@@ -1,7 +1,8 @@
-"""The GEMM engine under the entry points (tcgen05 tensor-core kernel where the
-operands are TMA-addressable, SIMT otherwise), through the kfac_gemm_nt utility
-of the C ABI, against FP64 products. Tolerances: FP32-accurate 3xTF32 1e-5,
-TF32 5e-3 and BF16 2e-2 relative Frobenius."""
+"""The GEMM engine under the entry points (the tcgen05 tensor-core kernels;
+operands whose rows TMA cannot address are first copied with a padded stride),
+through the kfac_gemm_nt utility of the C ABI, against FP64 products.
+Tolerances: FP32-accurate 3xTF32 1e-5, TF32 5e-3 and BF16 2e-2 relative
+Frobenius."""
 import numpy as np
 import pytest
 
@@ -38,7 +39,8 @@ def padded(rows, cols, pad, seed):
     (130, 230, 97, 3),       # ragged M, N, K; row strides 100 / 100 floats
     (1000, 230, 4097, 3),    # few tiles, long K: split-K with the reducing epilogue
     (300, 64, 1024, 0),
-    (77, 5, 9, 0),           # K not a multiple of 4: SIMT path
+    (77, 5, 9, 0),           # K not a multiple of 4: operands copied to a padded stride
+    (65, 33, 577, 0),        # row stride 577 floats (a VGG16 conv factor's width)
 ])
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 def test_gemm_nt(kf, ctx, M, N, K, pad, prec):
@@ -46,7 +48,9 @@ def test_gemm_nt(kf, ctx, M, N, K, pad, prec):
     B = padded(N, K, pad, 2)
     D0 = torch.randn(M, N, device="cuda")
     D = D0.clone()
+    n_simt = kf.kfac_simt_gemm_count()
     kf.kfac_gemm_nt(ctx, A, B, D, alpha=0.7, beta=0.3, prec=prec)
+    assert kf.kfac_simt_gemm_count() == n_simt   # every stride runs on the tensor cores
     ref = 0.7 * (A.double() @ B.double().T) + 0.3 * D0.double()
     st, flags = kf.kfac_get_status(ctx)
     assert st == 0, flags

@@ -190,6 +190,42 @@ def test_c1_end_to_end(kf, ctx, prec, lam_rule):
     assert rel_fro(host(S), s_or) <= S_TOL[prec], rel_fro(host(S), s_or)
 
 
+# ----------------------------------------------------------------------------- ragged row strides
+
+def test_ragged_strides_stay_on_tensor_cores(kf, ctx):
+    """Contiguous factors, batches and gradients whose row strides are not
+    multiples of 4 floats (a VGG16 conv layer: A 577 = 64*9 + 1, n = 17, G 130)
+    go through EA, inversion and apply on the tensor cores (no SIMT product)
+    and match the oracle."""
+    da, dg, n, r, p, q, lam = 577, 130, 17, 40, 10, 1, 0.1
+    xa = inputs.activation_batches(41, da - 1, n, 3, alpha=1.0, bias=True, salt=1)
+    xg = inputs.activation_batches(41, dg, n, 3, alpha=1.0, salt=2)
+    j = inputs.gradient(41, dg, da, std=0.1)
+    om_a, om_g = inputs.omega(41, da, r + p, 1), inputs.omega(41, dg, r + p, 2)
+    n_simt = kf.kfac_simt_gemm_count()
+    Fa = torch.zeros((da, da), device="cuda")
+    Fg = torch.zeros((dg, dg), device="cuda")
+    for x in xa:
+        kf.kfac_ea_update(ctx, cuda(x), Fa, 0.95)
+    kf.kfac_ea_update_grouped(ctx, [dict(X=cuda(x), F=Fg, rho=0.95) for x in xg[:1]])
+    for x in xg[1:]:
+        kf.kfac_ea_update(ctx, cuda(x), Fg, 0.95)
+    Ua, Da, ca = kf.kfac_rsvd_invert(ctx, Fa, r, p, q, lam, cuda(om_a))
+    Ug, Dg, cg = kf.kfac_rsvd_invert(ctx, Fg, r, p, q, lam, cuda(om_g))
+    S = kf.kfac_precondition(ctx, cuda(j), Ua, ca, Ug, cg, lam)
+    assert_status_ok(kf, ctx)
+    assert kf.kfac_simt_gemm_count() == n_simt
+    fa, fg = workloads.ea_factor(xa), workloads.ea_factor(xg)
+    assert np.abs(host(Fa) - fa).max() <= 2e-6 * np.abs(fa).max()
+    assert np.abs(host(Fg) - fg).max() <= 2e-6 * np.abs(fg).max()
+    ua, d_a, c_a = oracle.invert(host(Fa), om_a.astype(np.float64), r, q, lam)
+    ug, d_g, c_g = oracle.invert(host(Fg), om_g.astype(np.float64), r, q, lam)
+    assert np.abs(host(Da) - d_a).max() / d_a[0] <= EIG_TOL
+    assert np.abs(host(Dg) - d_g).max() / d_g[0] <= EIG_TOL
+    want = oracle.precondition(j.astype(np.float64), ua, c_a, ug, c_g, lam)
+    assert rel_fro(host(S), want) <= S_TOL["fp32"], rel_fro(host(S), want)
+
+
 # ----------------------------------------------------------------------------- grouped calls
 
 def test_invert_grouped_matches_single_calls(kf, ctx):
