@@ -1,34 +1,46 @@
 #!/usr/bin/env python
-"""Benchmark of the randomized K-FAC hot path on one wide fully-connected layer.
+"""Benchmark of the randomized K-FAC hot path on one GB300: per step, the EA
+update of every factor, the randomized inversion of every factor and the
+preconditioner apply of every layer (T_KU = T_KI = 1).
 
-Workload (one layer, the wide-FC configuration): forward factor A 4097 x 4097
-(4096 inputs + bias), backward factor G 4096 x 4096, batch n = 256 activations
-a = z diag(s) V^T with s_i = i^-1.5 and V Haar, rho = 0.95, rank r = 220,
-oversampling p = 10, power iterations q = 1 (set with --power-iters), lambda = 0.1,
-gradient J 4096 x 4097 ~ N(0, 1e-2). Inputs are synthetic (seeded Philox draws).
+Workloads (--workload; synthetic, seeded, built on the device):
+  c5 (default, the headline): the batching-stress set. 64 factors with
+     d ~ U{256..8192}, activation spectra s_i = i^-alpha with alpha ~ U[0.8, 2]
+     (factor eigenvalues i^-2alpha over the 640 leading directions), ranks
+     r in {64, 128, 256, 512} capped at d, p = 10, q = 1, lambda = 0.1. Factors
+     2i and 2i+1 are the A and G factors of layer i (32 layers, gradient
+     J ~ N(0, 1e-2) of shape d_G x d_A). EA batches of n = 256 columns.
+  c3: the VGG16_bn-on-32x32 factor set (13 conv layers, A = C_in*9 + 1 and
+     G = C_out, plus the 513 -> 10 FC layer), n = 128, s_i = i^-1 over 512
+     directions, r = min(d, 220), p = 10, q = 1.
+  c2: one wide FC layer, A 4097 (4096 + bias), G 4096, n = 256, s_i = i^-1.5,
+     r = 220, p = 10, q = 1 (--power-iters).
 
-One step = one EA update of each factor with a fresh batch + the randomized
-inversion of both factors + the preconditioner apply (T_KU = T_KI = 1).
-Metric: ms/step (lower is better), device-timed with CUDA events over K steps
-after W warm-up steps, inputs resident in HBM. The working set touched per step
-(two 67 MB factors, J, M and S) is several times the 129 MB L2, so no explicit
-L2 flush is used.
+Every step is captured once in a CUDA graph (grouped EA, grouped inversion on
+forked streams, grouped apply) and replayed; the metric is ms/step (lower is
+better), device-timed with CUDA events over K replays after W warm-up replays,
+inputs resident in HBM. Matrices are allocated with row strides rounded up to
+16 bytes (the layout the tensor-core loads read without a copy). Per step the
+workload touches several GB (c5), far beyond the 129 MB L2, so no flush is
+used. Per-stage device times come from a separate eager pass with the
+library's stage events on, outside the timed region.
 
-Also reported: the end-to-end time through the public API with host buffers
-(pinned H2D of the step's inputs and D2H of S inside the timed region), the
-full-eigendecomposition path on the same GPU (torch.linalg.eigh + truncated
-apply) with the accuracy of both paths against the exact damped inverse, the
-roofline of the dominant kernel group (per-stage CUDA events inside the timed
-region), and the FP64 CPU oracle on a bounded sample projected to a full step.
+Also reported: the same step end to end through the public API with host
+buffers (pinned H2D of the step's batches, gradients and test matrices, D2H of
+the preconditioned gradients, inside the timed region); the full-eigendecomposition
+path on the same GPU (torch.linalg.eigh + the same apply) with both paths'
+errors against the exact damped inverse on sampled layers; the roofline of the
+dominant kernel group and of the sketch products; extra lines for the other
+precisions and workloads; and the FP64 CPU oracle timed on the host cores on a
+bounded sample of the step, scaled to a whole step by each stage's work.
 
-`--impl reference` times the CPU oracle (the plain FP64 restatement of the
-method) as the reference arm, each step a bounded sample projected to a step.
+`--impl reference` times that CPU oracle as the reference arm (each step a
+bounded sample of the workload's step, scaled the same way).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -40,14 +52,43 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(d_in=4096, bias=True, d_out=4096, n=256, alpha=1.5, rho=0.95, r=220, p=10, lam=0.1,
-                j_std=0.1, init_steps=10, seed=0)
+METRIC = "K-factor RSVD-invert+precondition ms/step"
+
+# VGG16_bn on 32x32 images: (C_in, C_out) of the 13 conv layers (3x3 kernels).
+VGG16_CONV = [(3, 64), (64, 64), (64, 128), (128, 128), (128, 256), (256, 256), (256, 256), (256, 512), (512, 512),
+              (512, 512), (512, 512), (512, 512), (512, 512)]
 
 
-def workload_name(w, q):
-    return (f"one wide FC layer: A {w['d_in'] + w['bias']}x{w['d_in'] + w['bias']} (bias), "
-            f"G {w['d_out']}x{w['d_out']}, n={w['n']}, s_i=i^-{w['alpha']}, rho={w['rho']}, "
-            f"r={w['r']}, p={w['p']}, q={q}, lambda={w['lam']}")
+def workload_spec(name: str, q: int = 1, seed: int = 0) -> dict:
+    """Factor and layer shapes of a workload (no arithmetic, no tensors)."""
+    from paper_2206_15397_gb300 import inputs as I
+    if name == "c5":
+        shapes = I.batching_stress_shapes(seed, 64)
+        factors = [dict(d=s["d"], alpha=s["alpha"], r=s["r"], bias=False) for s in shapes]
+        layers = [(2 * i, 2 * i + 1) for i in range(32)]
+        return dict(name=name, factors=factors, layers=layers, n=256, p=10, q=q, lam=0.1, rho=0.95, m_cap=640,
+                    seed=seed, j_std=0.1,
+                    workload=("batching stress: 64 factors, d ~ U{256..8192} (seeded), eigenvalues i^-2alpha, "
+                              "alpha ~ U[0.8,2], r in {64,128,256,512} capped at d, p=10, q=%d, lambda=0.1; "
+                              "32 layers (factor pairs), EA batch n=256" % q))
+    if name == "c3":
+        factors, layers = [], []
+        for ci, co in VGG16_CONV + [(None, 10)]:
+            da = ci * 9 + 1 if ci is not None else 513
+            factors.append(dict(d=da, alpha=1.0, r=min(da, 220), bias=True))
+            factors.append(dict(d=co, alpha=1.0, r=min(co, 220), bias=False))
+            layers.append((len(factors) - 2, len(factors) - 1))
+        return dict(name=name, factors=factors, layers=layers, n=128, p=10, q=q, lam=0.1, rho=0.95, m_cap=512,
+                    seed=seed, j_std=0.1,
+                    workload=("VGG16_bn on 32x32 factor set: 13 conv layers (A = C_in*9+1, G = C_out) + FC 513/10, "
+                              "n=128, s_i=i^-1 over 512 directions, r=min(d,220), p=10, q=%d, lambda=0.1" % q))
+    if name == "c2":
+        factors = [dict(d=4097, alpha=1.5, r=220, bias=True), dict(d=4096, alpha=1.5, r=220, bias=False)]
+        return dict(name=name, factors=factors, layers=[(0, 1)], n=256, p=10, q=q, lam=0.1, rho=0.95, m_cap=None,
+                    seed=seed, j_std=0.1,
+                    workload=("one wide FC layer: A 4097x4097 (bias), G 4096x4096, n=256, s_i=i^-1.5, rho=0.95, "
+                              "r=220, p=10, q=%d, lambda=0.1" % q))
+    raise ValueError(name)
 
 
 # ----------------------------------------------------------------------------- distributed helpers
@@ -135,76 +176,78 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# ----------------------------------------------------------------------------- synthetic inputs
+# ----------------------------------------------------------------------------- work model
 
-def make_inputs(w, nbatch: int):
-    """Host-side FP32 inputs: initial-state batches, per-step batches, J, Omega."""
-    from paper_2206_15397_gb300 import inputs as I
-    seed = w["seed"]
-    va = I.haar(seed, w["d_in"], salt=11)
-    vg = I.haar(seed, w["d_out"], salt=12)
-    tot = w["init_steps"] + nbatch
-    xa = I.activation_batches(seed, w["d_in"], w["n"], tot, alpha=w["alpha"], bias=w["bias"], salt=11, v=va)
-    xg = I.activation_batches(seed, w["d_out"], w["n"], tot, alpha=w["alpha"], salt=12, v=vg)
-    da = w["d_in"] + int(w["bias"])
-    dg = w["d_out"]
-    k = w["r"] + w["p"]
-    js = [I.gradient(seed, dg, da, std=w["j_std"], salt=20 + t) for t in range(2)]
-    oa = [I.omega(seed, da, k, salt=30 + t) for t in range(2)]
-    og = [I.omega(seed, dg, k, salt=40 + t) for t in range(2)]
-    return dict(xa_init=xa[:w["init_steps"]], xg_init=xg[:w["init_steps"]], xa=xa[w["init_steps"]:],
-                xg=xg[w["init_steps"]:], j=js, om_a=oa, om_g=og, da=da, dg=dg, k=k)
+def sketched(f, p):
+    return f["r"] + p < f["d"]
 
 
-# ----------------------------------------------------------------------------- roofline bookkeeping
-
-def stage_work(stage: str, w, q: int, steps: int):
-    """Algorithmic (flops, bytes) of one stage summed over `steps` steps."""
-    da, dg, n, r, k = w["d_in"] + int(w["bias"]), w["d_out"], w["n"], w["r"], w["r"] + w["p"]
-    dims = (da, dg)
-    f, b = 0.0, 0.0
+def stage_work(stage: str, spec: dict):
+    """Algorithmic (flops, bytes) of one stage over one step of the workload."""
+    p, q, n = spec["p"], spec["q"], spec["n"]
+    F = spec["factors"]
+    fl, by = 0.0, 0.0
     if stage == "sketch_gemm":
-        for d in dims:
-            f += (q + 2) * 2.0 * k * d * d
-            b += (q + 2) * 4.0 * (d * d + 2 * k * d)
+        for f in F:
+            if sketched(f, p):
+                d, k = f["d"], f["r"] + p
+                fl += (q + 2) * 2.0 * k * d * d
+                by += (q + 2) * 4.0 * (d * d + 2 * k * d)
     elif stage == "ea_syrk":
-        for d in dims:
-            f += 2.0 * d * d * n
-            b += 4.0 * (2 * d * d + d * n)
-    elif stage == "apply_T":
-        f, b = 2.0 * dg * da * r, 4.0 * (dg * da + da * r + dg * r)
-    elif stage == "apply_M":
-        f, b = 2.0 * dg * da * r, 4.0 * (2 * dg * da + da * r + dg * r)
-    elif stage == "apply_T2":
-        f, b = 2.0 * dg * da * r, 4.0 * (dg * da + dg * r + da * r)
-    elif stage == "apply_S":
-        f, b = 2.0 * dg * da * r, 4.0 * (2 * dg * da + dg * r + da * r)
-    elif stage in ("cholqr_gram", "projection_gram"):
-        npass = 3 * (q + 1) if stage == "cholqr_gram" else 1
-        for d in dims:
-            f += npass * 2.0 * k * k * d
-            b += npass * 4.0 * k * d
+        for f in F:
+            d = f["d"]
+            fl += 1.0 * d * (d + 1) * n   # the triangle, two flops per term
+            by += 4.0 * (2 * d * d + d * n)
+    elif stage in ("cholqr_gram", "projection_gram", "basis_polish"):
+        npass = {"cholqr_gram": 3 * (q + 1), "projection_gram": 1, "basis_polish": 1}[stage]
+        for f in F:
+            if sketched(f, p):
+                d, k = f["d"], f["r"] + p
+                fl += npass * 2.0 * k * k * d
+                by += npass * 4.0 * (k * d if stage != "projection_gram" else 2 * k * d)
     elif stage == "cholqr_trsm":
-        for d in dims:
-            f += 3 * (q + 1) * 1.0 * k * k * d
-            b += 3 * (q + 1) * 8.0 * k * d
-    elif stage == "cholqr_chol":
-        f = 2 * 3 * (q + 1) * (2.0 * k ** 3 / 3.0)
-    elif stage == "eig_refine":
-        f = 2 * 8.0 * k ** 3
+        for f in F:
+            if sketched(f, p):
+                d, k = f["d"], f["r"] + p
+                fl += 3 * (q + 1) * 1.0 * k * k * d
+                by += 3 * (q + 1) * 8.0 * k * d
     elif stage == "lift_gemm":
-        for d in dims:
-            f += 2.0 * d * k * r
-            b += 4.0 * (d * k + d * r)
-    return f * steps, b * steps
+        for f in F:
+            if sketched(f, p):
+                d, k, r = f["d"], f["r"] + p, f["r"]
+                fl += 2.0 * d * k * r
+                by += 4.0 * (2 * d * k + d * r)
+    elif stage.startswith("apply_"):
+        for a, g in spec["layers"]:
+            da, dg, ra, rg = F[a]["d"], F[g]["d"], min(F[a]["r"], F[a]["d"]), min(F[g]["r"], F[g]["d"])
+            if stage == "apply_T":
+                fl += 2.0 * dg * da * ra
+                by += 4.0 * (dg * da + da * ra + dg * ra)
+            elif stage == "apply_M":
+                fl += 2.0 * dg * da * ra
+                by += 4.0 * (2 * dg * da + da * ra + dg * ra)
+            elif stage == "apply_T2":
+                fl += 2.0 * dg * da * rg
+                by += 4.0 * (dg * da + dg * rg + da * rg)
+            elif stage == "apply_S":
+                fl += 2.0 * dg * da * rg
+                by += 4.0 * (2 * dg * da + dg * rg + da * rg)
+    return fl, by
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each
-# stage's kernels from one ncu capture of this bench on a GB300 (the captures
-# summarised under profiles/, same kernels as built here). The Cholesky stage
-# runs the FP32 single-CTA kernel, which reads the k x k Gram once; the Jacobi
-# kernel reads the k x k FP32 factor once.
-NCU_TRAFFIC_PER_LAUNCH = {"cholqr_chol": 255488.0, "eig_jacobi": 198656.0, "sketch_gemm": 72325632.0}
+def bytes_touched(spec: dict) -> float:
+    """Bytes of the step's large operands (factors, batches, gradients, outputs)."""
+    F, n = spec["factors"], spec["n"]
+    b = sum(4.0 * (f["d"] * f["d"] + f["d"] * n) for f in F)
+    b += sum(8.0 * F[a]["d"] * F[g]["d"] for a, g in spec["layers"])
+    return b
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernels from ncu captures of this bench's kernels on a GB300 (the
+# summaries under profiles/), keyed by (workload, stage); None where no capture
+# of the current kernel exists.
+NCU_TRAFFIC_PER_LAUNCH = {}
 
 
 def load_peaks():
@@ -218,169 +261,457 @@ def load_peaks():
             "fallback"
 
 
-def roofline(profile: dict, w, q: int, steps: int, stats: dict, traffic=None):
-    """Roofline of the dominant kernel group of the timed region."""
+def tensor_peak(prec: str, pk: dict, sustained: bool):
+    """FP32-equivalent tensor peak of a product precision: BF16 measured; TF32 =
+    BF16 x 1/2 (nominal ratio); FP32-accurate 3xTF32 issues three TF32 products."""
+    bf16 = pk["bf16_tflops_sustained" if sustained else "bf16_tflops"]
+    tf32 = bf16 / 2.0
+    if prec == "fp32":
+        return tf32 / 3.0, "bf16_tflops%s x 1/2 (TF32) x 1/3 (3xTF32 products)" % ("_sustained" if sustained else "")
+    if prec == "tf32":
+        return tf32, "bf16_tflops%s x 1/2 (TF32)" % ("_sustained" if sustained else "")
+    return bf16, "bf16_tflops%s" % ("_sustained" if sustained else "")
+
+
+def stage_roofline(stage: str, ms: float, launches: int, spec: dict, prec: str, sweeps: float = 0.0):
+    """Roofline of one stage's kernels: achieved = algorithmic work per step /
+    device time per step (CUDA events around the stage's launches)."""
     pk, src = load_peaks()
     sm_hz = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     fp32_alu = 152 * 128 * 2 * sm_hz / 1e12   # TFLOP/s, FFMA units x clock
-    fp64_alu = 152 * 2 * 2 * sm_hz / 1e12     # TFLOP/s, ~2 DFMA/clk/SM on this part
-    stage, (ms, launches) = max(profile.items(), key=lambda kv: kv[1][0])
+    sec = ms * 1e-3
     if stage == "eig_jacobi":
-        kk = w["r"] + w["p"]
-        flops = stats.get("jacobi_sweeps", 0) * 6.0 * kk * kk * (kk - 1)  # 3 dots + 1 rotation per pair
-        out = {"kernel": stage, "bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_alu,
-               "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
-    elif stage in ("cholqr_chol", "eig_refine"):
-        flops, _ = stage_work(stage, w, q, steps)
-        out = {"kernel": stage, "bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp64_alu,
-               "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x max SM clock"}
+        p = spec["p"]
+        flops = 0.0
+        for f in spec["factors"]:
+            k = f["r"] + p if sketched(f, p) else f["d"]
+            flops += 6.0 * k * k * (k - 1) * sweeps   # 3 dots + 1 rotation per pair and sweep
+        out = {"kernel": stage, "bound": "alu", "achieved": flops / sec / 1e12, "peak": fp32_alu, "unit": "TFLOP/s",
+               "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+    elif stage == "cholqr_chol":
+        p, q = spec["p"], spec["q"]
+        flops = sum((2.0 * (3 * (q + 1)) + 2.0) * (f["r"] + p) ** 3 / 3.0 for f in spec["factors"] if sketched(f, p))
+        out = {"kernel": stage, "bound": "alu", "achieved": flops / sec / 1e12, "peak": fp32_alu, "unit": "TFLOP/s",
+               "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
     else:
-        flops, byts = stage_work(stage, w, q, steps)
-        intensity = flops / max(byts, 1.0)
-        fp32_ridge = fp32_alu * 1e12 / (pk["hbm_gbs"] * 1e9)
-        if intensity < fp32_ridge:
-            out = {"kernel": stage, "bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
-                   "unit": "GB/s", "peak_source": f"{src} hbm_gbs"}
+        flops, byts = stage_work(stage, spec)
+        peak_t, tsrc = tensor_peak(prec, pk, sustained=True)
+        ridge = peak_t * 1e12 / (pk["hbm_gbs"] * 1e9)
+        if flops > 0 and flops / max(byts, 1.0) >= ridge:
+            out = {"kernel": stage, "bound": "tensor", "achieved": flops / sec / 1e12, "peak": peak_t,
+                   "unit": "TFLOP/s", "peak_source": f"{src} {tsrc}"}
         else:
-            out = {"kernel": stage, "bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_alu,
-                   "unit": "TFLOP/s", "peak_source": "derived FP32 SIMT peak"}
+            out = {"kernel": stage, "bound": "hbm", "achieved": byts / sec / 1e9, "peak": pk["hbm_gbs"],
+                   "unit": "GB/s", "peak_source": f"{src} hbm_gbs"}
     out["frac"] = out["achieved"] / out["peak"]
-    out["traffic"] = traffic if traffic is not None else NCU_TRAFFIC_PER_LAUNCH.get(stage)
+    out["traffic"] = NCU_TRAFFIC_PER_LAUNCH.get((spec["name"], stage))
     out["avg_launch_ms"] = ms / max(launches, 1)
     out["launches"] = launches
     return out
 
 
-def sketch_roofline(profile: dict, w, q: int, steps: int, prec: str):
-    """Tensor-core roofline of the sketch / power / projection products (d^2 k
-    per pass, (q + 2) passes per factor). FP32-accurate 3xTF32 issues three TF32
-    products per FP32 product, so its FP32-equivalent peak is the TF32 peak / 3;
-    the TF32 peak is the measured BF16 burst peak x 1/2 (nominal TF32:BF16 ratio)."""
-    pk, src = load_peaks()
-    ms, launches = profile.get("sketch_gemm", (0.0, 0))
-    if ms <= 0:
-        return None
-    flops, _ = stage_work("sketch_gemm", w, q, steps)
-    tf32 = pk["bf16_tflops"] / 2.0
-    peak = tf32 / 3.0 if prec == "fp32" else (tf32 if prec == "tf32" else pk["bf16_tflops"])
-    achieved = flops / (ms * 1e-3) / 1e12
-    return {"kernel": "sketch_gemm", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": NCU_TRAFFIC_PER_LAUNCH["sketch_gemm"] if prec == "fp32" else None, "peak_source": f"{src} bf16_tflops x "
-            + ("1/2 (TF32) x 1/3 (3xTF32 products)" if prec == "fp32" else ("1/2 (TF32)" if prec == "tf32" else "1")),
-            "avg_launch_ms": ms / max(launches, 1), "launches": launches}
+# ----------------------------------------------------------------------------- device workload
+
+class DeviceWorkload:
+    """Tensors of one workload on the device: factors (EA-consistent synthetic
+    spectra), EA batches, test matrices, gradients and every output buffer."""
+
+    def __init__(self, spec: dict, dev, nb: int = 2):
+        import torch
+        self.spec, self.dev, self.nb = spec, dev, nb
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1000 + spec["seed"])
+        p, n = spec["p"], spec["n"]
+        self.F, self.X, self.Om, self.out = [], [], [], []
+        for f in spec["factors"]:
+            d, bias = f["d"], int(f["bias"])
+            m = d - bias if spec["m_cap"] is None else min(d - bias, spec["m_cap"])
+            g = torch.randn(d - bias, m, generator=gen, device=dev, dtype=torch.float64)
+            v, _ = torch.linalg.qr(g)                      # orthonormal directions (Stiefel)
+            s = torch.arange(1, m + 1, device=dev, dtype=torch.float64) ** (-f["alpha"])
+            F = self.padded(d, d)
+            F.zero_()
+            F[:d - bias, :d - bias] = ((v * s * s) @ v.T).float()   # E[x x^T] of the batches below
+            if bias:
+                F[d - 1, d - 1] = 1.0
+            self.F.append(F)
+            xs = []
+            for _ in range(nb):
+                z = torch.randn(n, m, generator=gen, device=dev, dtype=torch.float64)
+                x = ((v * s) @ z.T).float()
+                if bias:
+                    x = torch.cat([x, torch.ones(1, n, device=dev)], 0)
+                X = self.padded(d, n)
+                X.copy_(x)
+                xs.append(X)
+            self.X.append(xs)
+            k = f["r"] + p
+            self.Om.append(torch.randn(d, k, generator=gen, device=dev, dtype=torch.float32) if k < d else None)
+            r = min(f["r"], d)
+            self.out.append((self.padded(d, r), torch.empty(r, device=dev), torch.empty(r, device=dev)))
+        self.J, self.S = [], []
+        for a, gi in spec["layers"]:
+            da, dg = spec["factors"][a]["d"], spec["factors"][gi]["d"]
+            J = self.padded(dg, da)
+            J.copy_(spec["j_std"] * torch.randn(dg, da, generator=gen, device=dev))
+            self.J.append(J)
+            self.S.append(self.padded(dg, da))
+        torch.cuda.synchronize(dev)
+
+    def padded(self, rows, cols):
+        """rows x cols view of a rows x round_up(cols, 4) tensor (16-byte row stride)."""
+        import torch
+        return torch.empty((rows, (cols + 3) // 4 * 4), device=self.dev)[:, :cols]
+
+    def descriptors(self, kfac, prec: str):
+        spec = self.spec
+        ea = [kfac.ea_descs([dict(X=self.X[i][b], F=self.F[i], rho=spec["rho"], prec=prec)
+                             for i in range(len(self.F))]) for b in range(self.nb)]
+        inv, _ = kfac.invert_descs([dict(F=self.F[i], rank=f["r"], oversample=spec["p"], power_iters=spec["q"],
+                                         lam=spec["lam"], omega=self.Om[i], prec=prec, out=self.out[i])
+                                    for i, f in enumerate(spec["factors"])])
+        pre, _ = kfac.precond_descs([dict(J=self.J[li], U_a=self.out[a][0], coef_a=self.out[a][2],
+                                          U_g=self.out[g][0], coef_g=self.out[g][2], lam=spec["lam"], prec=prec,
+                                          out=self.S[li]) for li, (a, g) in enumerate(spec["layers"])])
+        return ea, inv, pre
 
 
-# ----------------------------------------------------------------------------- CPU oracle sample
+def run_step(kfac, ctx, descs, b):
+    ea, inv, pre = descs
+    kfac.call_grouped(ctx, "ea", ea[b])
+    kfac.call_grouped(ctx, "invert", inv)
+    kfac.call_grouped(ctx, "precondition", pre)
 
-def oracle_step_sample(w, q: int, fa: np.ndarray, fg: np.ndarray, j: np.ndarray, om_g: np.ndarray,
-                       xa: np.ndarray, frac: int):
-    """Time the FP64 oracle on a bounded sample of one step and project to a step.
 
-    Row-separable stages (EA rows, sketch / power / projection product rows, lift
-    rows, the preconditioner's column blocks) are timed on 1/frac of their rows or
-    columns and scaled by frac; the orthonormalisation (Householder QR of the full
-    d x k basis) and the Jacobi eigensolve of the full k x k matrix are timed at
-    full size. Returns (projected ms per step, seconds actually spent)."""
+def capture_graphs(kfac, ctx, wl, descs, stream):
+    """One CUDA graph per batch buffer; returns (graphs, library launches per step)."""
+    import torch
+    graphs, launches = [], 0
+    for b in range(wl.nb):
+        g = torch.cuda.CUDAGraph()
+        n0 = kfac.kfac_kernel_launch_count()
+        with torch.cuda.graph(g, stream=stream):
+            run_step(kfac, ctx, descs, b)
+        launches = kfac.kfac_kernel_launch_count() - n0
+        graphs.append(g)
+    return graphs, launches
+
+
+def time_graphs(graphs, stream, steps, warmup):
+    import torch
+    with torch.cuda.stream(stream):
+        for i in range(warmup):
+            graphs[i % len(graphs)].replay()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            graphs[i % len(graphs)].replay()
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def profile_stages(kfac, ctx, descs, stream, steps):
+    """Eager steps with the library's stage events on: {stage: (ms/step, launches/step)}."""
+    import torch
+    with torch.cuda.stream(stream):
+        kfac.kfac_stats_read(ctx)
+        kfac.kfac_profile_enable(ctx, True)
+        n_simt = kfac.kfac_simt_gemm_count()
+        for i in range(steps):
+            run_step(kfac, ctx, descs, i % len(descs[0]))
+        prof = kfac.kfac_profile_read(ctx)
+        kfac.kfac_profile_enable(ctx, False)
+        stats = kfac.kfac_stats_read(ctx)
+        simt = kfac.kfac_simt_gemm_count() - n_simt
+    stages = {k: (v[0] / steps, v[1] / steps) for k, v in prof.items() if v[1] > 0}
+    sweeps = stats["jacobi_sweeps"] / max(stats["jacobi_solves"], 1)
+    return stages, sweeps, simt
+
+
+def sample_layers(spec, count):
+    """Layers with the smallest d_A d_G (their exact inverses are cheap in FP64)."""
+    F = spec["factors"]
+    order = sorted(range(len(spec["layers"])), key=lambda li: F[spec["layers"][li][0]]["d"] * F[spec["layers"][li][1]]["d"])
+    return order[:count]
+
+
+def exact_errors(wl, S_list, layers):
+    """Relative Frobenius error of S against the exact damped inverse apply
+    (G + lam I)^-1 J (A + lam I)^-1 (FP64 eigendecompositions on the device)."""
+    import torch
+    spec = wl.spec
+    lam = spec["lam"]
+    errs = []
+    for li in layers:
+        a, g = spec["layers"][li]
+        fa, fg = wl.F[a].double(), wl.F[g].double()
+        wa, va = torch.linalg.eigh(fa)
+        wg, vg = torch.linalg.eigh(fg)
+        jd = wl.J[li].double()
+        m = ((jd @ va) / (wa.clamp(min=0) + lam)[None, :]) @ va.T
+        s_exact = vg @ ((vg.T @ m) / (wg.clamp(min=0) + lam)[:, None])
+        errs.append(float(torch.linalg.norm(S_list[li].double() - s_exact) / torch.linalg.norm(s_exact)))
+    return errs
+
+
+def evd_comparison(kfac, ctx, wl, stream, prec, n_sample):
+    """Full-EVD path on the same GPU: torch.linalg.eigh (cuSOLVER, FP32) of every
+    factor, top-r truncation, Eq. (13) coefficients and the same grouped apply.
+    Timed once (one step, EA excluded); errors of both paths against the exact
+    damped inverse on the sampled layers."""
+    import torch
+    spec = wl.spec
+    lam = spec["lam"]
+    with torch.cuda.stream(stream):
+        torch.linalg.eigh(wl.F[0][:8, :8].contiguous())   # solver set-up outside the timing
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        us = []
+        for i, f in enumerate(spec["factors"]):
+            r = min(f["r"], f["d"])
+            w, v = torch.linalg.eigh(wl.F[i])
+            u = v[:, -r:].flip(1).contiguous()
+            dv = w[-r:].flip(0)
+            us.append((u, (1.0 / (dv.clamp(min=0) + lam) - 1.0 / lam).contiguous()))
+        items = [dict(J=wl.J[li], U_a=us[a][0], coef_a=us[a][1], U_g=us[g][0], coef_g=us[g][1], lam=lam, prec=prec)
+                 for li, (a, g) in enumerate(spec["layers"])]
+        s_evd = kfac.kfac_precondition_grouped(ctx, items)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        layers = sample_layers(spec, n_sample)
+        err_evd = exact_errors(wl, s_evd, layers)
+        err_rand = exact_errors(wl, wl.S, layers)
+        between = [float(torch.linalg.norm(wl.S[li].double() - s_evd[li].double()) / torch.linalg.norm(s_evd[li].double()))
+                   for li in layers]
+        stream.synchronize()
+    return {"impl": "torch.linalg.eigh (cuSOLVER syevd, FP32) of every factor + top-r Eq. (13) apply",
+            "ms_per_step_excl_ea": ms, "sampled_layers": layers,
+            "err_vs_exact_inverse": max(err_evd), "randomized_err_vs_exact_inverse": max(err_rand),
+            "randomized_vs_truncated_evd": max(between)}
+
+
+def e2e_measure(kfac, ctx, wl, graphs, stream, steps):
+    """The captured step end to end with host buffers: per step, pinned H2D of
+    every factor's EA batch and test matrix and every layer's gradient, the
+    graph replay, and D2H of every preconditioned gradient."""
+    import torch
+    base = lambda t: t._base if t._base is not None else t
+    dev_in = [base(wl.X[i][0]) for i in range(len(wl.F))] + [o for o in wl.Om if o is not None] + \
+             [base(j) for j in wl.J]
+    dev_out = [base(s) for s in wl.S]
+    host_in = [t.cpu().pin_memory() for t in dev_in]
+    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in dev_out]
+    h2d = sum(t.numel() * 4 for t in host_in)
+    d2h = sum(t.numel() * 4 for t in host_out)
+
+    def one():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        graphs[0].replay()
+        for d, h in zip(dev_out, host_out):
+            h.copy_(d, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            one()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            one()
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / steps, h2d, d2h
+
+
+# ----------------------------------------------------------------------------- CPU oracle on a sample
+
+def host_layer(spec: dict, li: int, seed_salt: int = 0):
+    """Host FP32 inputs of one layer of the workload (same recipe as the device
+    workload, drawn with the seeded Philox generator)."""
+    from paper_2206_15397_gb300 import inputs as I
+    a, g = spec["layers"][li]
+    out = {}
+    for side, fi in (("a", a), ("g", g)):
+        f = spec["factors"][fi]
+        d, bias = f["d"], int(f["bias"])
+        m = d - bias if spec["m_cap"] is None else min(d - bias, spec["m_cap"])
+        v = I.stiefel(spec["seed"], d - bias, m, salt=900 + 2 * li + (side == "g"))
+        s = I.power_spectrum(m, f["alpha"])
+        fac = np.zeros((d, d))
+        fac[:d - bias, :d - bias] = (v * (s * s)[None, :]) @ v.T
+        if bias:
+            fac[d - 1, d - 1] = 1.0
+        x = I.activation_batches(spec["seed"], d - bias, spec["n"], 1, alpha=f["alpha"], bias=bool(bias),
+                                 salt=950 + 2 * li + (side == "g"), v=v, rank_cap=m)[0]
+        k = f["r"] + spec["p"]
+        out[side] = dict(F=fac.astype(np.float32), X=x, r=min(f["r"], d), k=k,
+                         omega=I.omega(spec["seed"], d, k, salt=980 + 2 * li + (side == "g")) if k < d else None)
+    da, dg = spec["factors"][a]["d"], spec["factors"][g]["d"]
+    out["J"] = I.gradient(spec["seed"], dg, da, std=spec["j_std"], salt=990 + li)
+    return out
+
+
+def oracle_layer_times(spec: dict, layer: dict) -> dict:
+    """Time the FP64 oracle's steps on one layer: EA update of both factors,
+    Alg. 3 with power iterations (products, Householder QR, projection, Jacobi,
+    lift) for both factors, Eq. (13) and the Alg. 4 apply. {stage: seconds}."""
     import oracle
-    t_all = time.perf_counter()
-    dg, da = j.shape
-    k = om_g.shape[1]
-    r = w["r"]
-    R = max(1, dg // frac)
-    tm = {}
+    q, lam, rho = spec["q"], spec["lam"], spec["rho"]
+    t = dict(ea=0.0, prod=0.0, qr=0.0, proj=0.0, jacobi=0.0, lift=0.0, apply=0.0)
 
     def clock(name, fn, *a):
         t0 = time.perf_counter()
-        out = fn(*a)
-        tm[name] = time.perf_counter() - t0
-        return out
+        res = fn(*a)
+        t[name] += time.perf_counter() - t0
+        return res
 
-    # EA on a row block of A's factor (rows i of F depend only on rows i of X).
-    rows = max(1, da // frac)
-    clock("ea", oracle.matmul, xa[:rows].astype(np.float64), xa.astype(np.float64), False, True)
-    # Sketch product row block of G's factor.
-    fg64 = fg.astype(np.float64)
-    om64 = om_g.astype(np.float64)
-    clock("sketch", oracle.matmul, fg64[:R], om64)
-    # Orthonormalisation of the full d x k basis.
-    y = fg64 @ om64
-    q_basis, _ = clock("qr", oracle.qr, y)
-    # Projection C = Q^T (F Q): the contraction over d split in frac blocks.
-    z = fg64 @ q_basis
-    clock("proj", oracle.matmul, q_basis[:R], z[:R], True, False)
-    c = q_basis.T @ z
-    c = 0.5 * (c + c.T)
-    _, p_eig, _ = clock("jacobi", oracle.jacobi_eigh, c)
-    clock("lift", oracle.matmul, q_basis[:R], np.ascontiguousarray(p_eig[:, :r]))
-    # Preconditioner: T = J U_a on a row block, then a column block of M, T2, S.
-    ua = np.linalg.qr(np.asarray(fa[:, :r], dtype=np.float64))[0]
-    ug = np.linalg.qr(np.asarray(fg[:, :r], dtype=np.float64))[0]
-    ca = -np.linspace(1.0, 0.1, r)
-    cg = -np.linspace(1.0, 0.1, r)
-    j64 = j.astype(np.float64)
-    clock("apply_T", oracle.matmul, j64[:R], ua)
-    t_full = j64 @ ua
-    Ra = max(1, da // frac)
-    cols = slice(0, Ra)
+    res = {}
+    for side in ("a", "g"):
+        L = layer[side]
+        f = clock("ea", oracle.ea_update, L["F"].astype(np.float64), L["X"].astype(np.float64), rho)
+        r, k = L["r"], L["k"]
+        if L["omega"] is None:   # k >= d: the factor itself is diagonalised
+            w, v, _ = clock("jacobi", oracle.jacobi_eigh, f)
+            u, dd = v[:, :r], w[:r]
+        else:
+            y = clock("prod", oracle.matmul, f, L["omega"].astype(np.float64))
+            qb, _ = clock("qr", oracle.qr, y)
+            for _ in range(q):
+                y = clock("prod", oracle.matmul, f, qb)
+                qb, _ = clock("qr", oracle.qr, y)
+            y = clock("prod", oracle.matmul, f, qb)
+            c = clock("proj", oracle.matmul, qb, y, True, False)
+            c = 0.5 * (c + c.T)
+            w, p, _ = clock("jacobi", oracle.jacobi_eigh, c)
+            u = clock("lift", oracle.matmul, qb, np.ascontiguousarray(p[:, :r]))
+            dd = w[:r]
+        res[side] = (u, oracle.damped_coef(dd, lam))
+    (ua, ca), (ug, cg) = res["a"], res["g"]
+    clock("apply", oracle.precondition, layer["J"].astype(np.float64), ua, ca, ug, cg, lam)
+    return t
 
-    def apply_cols():
-        m = oracle.matmul(t_full * ca[None, :], np.ascontiguousarray(ua[cols]), False, True)
-        m = m + j64[:, cols] / w["lam"]
-        t2 = oracle.matmul(ug, m, True, False) * cg[:, None]
-        return oracle.matmul(ug, t2) + m / w["lam"]
 
-    clock("apply_cols", apply_cols)
-    spent = time.perf_counter() - t_all
-    ps = q + 2
-    per_factor = (ps * tm["sketch"] * frac + (q + 1) * tm["qr"] + tm["proj"] * frac + tm["jacobi"]
-                  + tm["lift"] * frac)
-    step = 2 * per_factor + 2 * tm["ea"] * frac + tm["apply_T"] * frac + tm["apply_cols"] * frac
-    return step * 1e3, spent
+def oracle_stage_work(spec: dict, layers) -> dict:
+    """Work of each oracle stage (multiply-adds) over the given layers."""
+    F, p, q, n = spec["factors"], spec["p"], spec["q"], spec["n"]
+    w = dict(ea=0.0, prod=0.0, qr=0.0, proj=0.0, jacobi=0.0, lift=0.0, apply=0.0)
+    for li in layers:
+        a, g = spec["layers"][li]
+        for fi in (a, g):
+            f = F[fi]
+            d, r, k = f["d"], min(f["r"], f["d"]), f["r"] + p
+            w["ea"] += float(d) * d * n
+            if k >= d:
+                w["jacobi"] += float(d) ** 3
+                continue
+            w["prod"] += (q + 2) * float(d) * d * k
+            w["qr"] += (q + 1) * float(d) * k * k
+            w["proj"] += float(d) * k * k
+            w["jacobi"] += float(k) ** 3
+            w["lift"] += float(d) * k * r
+        da, dg = F[a]["d"], F[g]["d"]
+        w["apply"] += 2.0 * da * dg * (min(F[a]["r"], da) + min(F[g]["r"], dg))
+    return w
+
+
+def oracle_projected_step(spec: dict, li: int, threads: int):
+    """The oracle on layer li with `threads` OpenMP threads, each stage's time
+    scaled by the ratio of its work over the whole step to its work on that
+    layer. Returns (ms per step, seconds spent, stage seconds)."""
+    import oracle
+    oracle.build()
+    prev = oracle.set_threads(threads)
+    try:
+        layer = host_layer(spec, li)
+        t0 = time.perf_counter()
+        times = oracle_layer_times(spec, layer)
+        spent = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(prev)
+    full = oracle_stage_work(spec, range(len(spec["layers"])))
+    part = oracle_stage_work(spec, [li])
+    step = sum(times[s] * full[s] / part[s] for s in times if part[s] > 0)
+    return step * 1e3, spent, times
+
+
+def pick_layer(spec: dict, threads: int, target_s: float) -> int:
+    """The layer whose oracle run is expected to take the longest within
+    target_s seconds (rough model: ~1e9 multiply-adds per second and thread for
+    the row-parallel stages, ~15 k^3 sequential multiply-adds per Jacobi solve),
+    else the cheapest layer."""
+    def est(li):
+        w = oracle_stage_work(spec, [li])
+        par = sum(v for k, v in w.items() if k != "jacobi")
+        return par / (1e9 * threads) + 15.0 * w["jacobi"] / 1e9
+    order = sorted(range(len(spec["layers"])), key=est)
+    fit = [li for li in order if est(li) <= target_s]
+    return fit[-1] if fit else order[0]
 
 
 # ----------------------------------------------------------------------------- reference arm
 
-def run_reference(args, w):
+def run_reference(args):
     world, rank, _ = dist_env()
     if world > 1 and rank != 0:
         return 0
-    from paper_2206_15397_gb300 import inputs as I
-    import oracle
-    oracle.build()
-    da, dg, k = w["d_in"] + int(w["bias"]), w["d_out"], w["r"] + w["p"]
-    # Host-side factors with the workload's spectrum (the GPU builds them by EA;
-    # the sample only needs their shapes and decay).
-    xa = I.activation_batches(w["seed"], w["d_in"], w["n"], 1, alpha=w["alpha"], bias=w["bias"], salt=11)[0]
-    v = I.haar(w["seed"], dg, salt=12)
-    s2 = I.power_spectrum(dg, 2 * w["alpha"])
-    fg = ((v * s2[None, :]) @ v.T).astype(np.float32)
-    fa = np.zeros((da, da), dtype=np.float32)
-    fa[:dg, :dg] = fg
-    fa[dg:, dg:] = 1.0
-    j = I.gradient(w["seed"], dg, da, std=w["j_std"], salt=20)
-    om_g = I.omega(w["seed"], dg, k, salt=40)
-    frac = 32
-    times = []
+    spec = workload_spec(args.workload, args.power_iters)
+    cores = os.cpu_count() or 1
+    li = pick_layer(spec, cores, 4.0)
+    times, spent_all = [], 0.0
     for it in range(args.warmup + args.steps):
-        ms, _ = oracle_step_sample(w, args.power_iters, fa, fg, j, om_g, xa, frac)
+        ms, spent, _ = oracle_projected_step(spec, li, cores)
+        spent_all += spent
         if it >= args.warmup:
             times.append(ms)
     val = statistics.mean(times)
-    line = {"impl": "reference", "metric": "K-factor RSVD-invert+precondition ms/step", "value": val,
-            "unit": "ms/step", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": val,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded Philox)",
-            "config": {"workload": workload_name(w, args.power_iters), "parallelism": "replicas"},
-            "cpu_baseline": {"value": val, "unit": "ms/step", "cores": 1, "kind": "oracle",
-                             "sample": f"FP64 C oracle, 1 thread; row/column-separable stages on 1/{frac} of rows "
-                                       f"(scaled by {frac}), QR of the d x k basis and Jacobi of the k x k matrix "
-                                       f"at full size; projected to one step"},
+    a, g = spec["layers"][li]
+    sample = (f"FP64 C oracle (OpenMP, {cores} threads) on layer {li} of the step (A {spec['factors'][a]['d']}, "
+              f"G {spec['factors'][g]['d']}): EA, Alg. 3 + power iterations and the Alg. 4 apply, each stage's time "
+              f"scaled by its work over all {len(spec['layers'])} layers; {spent_all / len(times + [0] * args.warmup):.1f} s "
+              f"of wall time per sampled step")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "ms/step", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)",
+            "config": {"workload": spec["workload"], "parallelism": "single GPU" if world == 1 else "replicas"},
+            "cpu_baseline": {"value": val, "unit": "ms/step", "cores": cores, "kind": "oracle", "sample": sample},
+            "sampled": {"wall_s_per_sampled_step": spent_all / (args.warmup + args.steps),
+                        "projected_ms_per_step": val},
             "e2e": {"value": val, "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-# ----------------------------------------------------------------------------- main (ours)
+# ----------------------------------------------------------------------------- our arm
+
+def log(msg: str):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+def bench_workload(kfac, ctx, wl, stream, prec, steps, warmup, clocks=None, profile_steps=3):
+    """Capture and time one workload at one precision. Returns a result dict."""
+    import torch
+    log(f"{wl.spec['name']} {prec}: eager warm-up, capture, {steps} timed replays")
+    descs = wl.descriptors(kfac, prec)
+    with torch.cuda.stream(stream):
+        for b in range(2):            # eager: sizes the workspace and creates the side streams
+            run_step(kfac, ctx, descs, b % wl.nb)
+        stream.synchronize()
+    graphs, launches = capture_graphs(kfac, ctx, wl, descs, stream)
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
+    ms = time_graphs(graphs, stream, steps, warmup)
+    clk = clocks.stop() if clocks is not None else None
+    st, flags = kfac.kfac_get_status(ctx)
+    stages, sweeps, simt = profile_stages(kfac, ctx, descs, stream, profile_steps)
+    return dict(ms=ms, graphs=graphs, launches=launches, clocks=clk, status=(st, flags), stages=stages,
+                sweeps=sweeps, simt=simt)
+
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -388,15 +719,15 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c5", "c3", "c2"], default="c5")
     ap.add_argument("--power-iters", type=int, default=1)
     ap.add_argument("--prec", choices=["fp32", "tf32", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-evd", action="store_true")
-    ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the dominant kernel")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args(argv)
-    w = dict(WORKLOAD)
     if args.impl == "reference":
-        return run_reference(args, w)
+        return run_reference(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
 
@@ -412,147 +743,108 @@ def main(argv=None):
         kbuild.build()
     from paper_2206_15397_gb300 import kfac
 
-    q = args.power_iters
-    nb = 4
-    host = make_inputs(w, nb)
-    da, dg, k, r, lam = host["da"], host["dg"], host["k"], w["r"], w["lam"]
+    spec = workload_spec(args.workload, args.power_iters)
     stream = torch.cuda.Stream(dev)
     ctx = kfac.Context(local, stream)
-    kfac.kfac_reserve(ctx, max(da, dg), k, da * dg)
-    def padded(rows, cols):
-        """rows x cols view with a row stride rounded up to 4 floats (16 bytes): the
-        tensor-core kernels read operands through TMA, which needs 16-byte strides."""
-        return torch.zeros((rows, (cols + 3) // 4 * 4), device=dev)[:, :cols]
+    log(f"building workload {args.workload} on {dev}")
+    wl = DeviceWorkload(spec, dev)
 
-    with torch.cuda.stream(stream):
-        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, non_blocking=False)
-        TP = lambda a: padded(*a.shape).copy_(T(a))
-        XA = [T(x) for x in host["xa"]]
-        XG = [T(x) for x in host["xg"]]
-        J = [TP(x) for x in host["j"]]
-        OA = [T(x) for x in host["om_a"]]
-        OG = [T(x) for x in host["om_g"]]
-        Fa = padded(da, da)
-        Fg = padded(dg, dg)
-        for x in host["xa_init"]:
-            kfac.kfac_ea_update(ctx, T(x), Fa, w["rho"])
-        for x in host["xg_init"]:
-            kfac.kfac_ea_update(ctx, T(x), Fg, w["rho"])
-        Ua = torch.empty((da, r), device=dev); Da = torch.empty(r, device=dev); Ca = torch.empty(r, device=dev)
-        Ug = torch.empty((dg, r), device=dev); Dg = torch.empty(r, device=dev); Cg = torch.empty(r, device=dev)
-        S = padded(dg, da)
-    stream.synchronize()
-
-    def step(i, xa=None, xg=None, j=None, oa=None, og=None):
-        kfac.kfac_ea_update_grouped(ctx, [
-            dict(X=XA[i % nb] if xa is None else xa, F=Fa, rho=w["rho"], prec=args.prec),
-            dict(X=XG[i % nb] if xg is None else xg, F=Fg, rho=w["rho"], prec=args.prec)])
-        kfac.kfac_rsvd_invert_grouped(ctx, [
-            dict(F=Fa, rank=r, oversample=w["p"], power_iters=q, lam=lam, omega=OA[i % 2] if oa is None else oa,
-                 prec=args.prec, out=(Ua, Da, Ca)),
-            dict(F=Fg, rank=r, oversample=w["p"], power_iters=q, lam=lam, omega=OG[i % 2] if og is None else og,
-                 prec=args.prec, out=(Ug, Dg, Cg))])
-        kfac.kfac_precondition(ctx, J[i % 2] if j is None else j, Ua, Ca, Ug, Cg, lam, args.prec, out=S)
-
-    # ---- device-timed region -------------------------------------------------
-    for i in range(args.warmup):
-        step(i)
-    st, flags = kfac.kfac_get_status(ctx)
-    kfac.kfac_stats_read(ctx)
     barrier(world, dev)
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(dev.index)
-    clocks.start()
-    time.sleep(0.3)
-    kfac.kfac_profile_enable(ctx, True)
-    n0 = kfac.kfac_kernel_launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-    e1.record(stream)
-    e1.synchronize()
-    launches = kfac.kfac_kernel_launch_count() - n0
+    res = bench_workload(kfac, ctx, wl, stream, args.prec, args.steps, args.warmup, clocks=clocks)
     torch.cuda.synchronize(dev)
     barrier(world, dev)
-    clk = clocks.stop()
-    ms_step = e0.elapsed_time(e1) / args.steps
-    prof = kfac.kfac_profile_read(ctx)
-    kfac.kfac_profile_enable(ctx, False)
-    stats = kfac.kfac_stats_read(ctx)
-    st, flags = kfac.kfac_get_status(ctx)
-    ms_step_max = reduce_max(ms_step, world, dev)
-
-    # ---- end to end through the public API with host buffers --------------------
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    hxa = [pin(x) for x in host["xa"][:2]]
-    hxg = [pin(x) for x in host["xg"][:2]]
-    hj = [pin(x) for x in host["j"]]
-    hoa = [pin(x) for x in host["om_a"]]
-    hog = [pin(x) for x in host["om_g"]]
-    hs = torch.empty((dg, da), dtype=torch.float32).pin_memory()
-    dxa = torch.empty_like(XA[0]); dxg = torch.empty_like(XG[0]); dj = padded(dg, da)
-    doa = torch.empty_like(OA[0]); dog = torch.empty_like(OG[0])
-    h2d = sum(t.numel() * 4 for t in (hxa[0], hxg[0], hj[0], hoa[0], hog[0]))
-    d2h = hs.numel() * 4
-
-    def e2e_step(i):
-        with torch.cuda.stream(stream):
-            dxa.copy_(hxa[i % 2], non_blocking=True)
-            dxg.copy_(hxg[i % 2], non_blocking=True)
-            dj.copy_(hj[i % 2], non_blocking=True)
-            doa.copy_(hoa[i % 2], non_blocking=True)
-            dog.copy_(hog[i % 2], non_blocking=True)
-            step(i, dxa, dxg, dj, doa, dog)
-            hs.copy_(S, non_blocking=True)
-
-    e2e_steps = max(3, min(args.steps, 10))
-    for i in range(2):
-        e2e_step(i)
-    stream.synchronize()
-    e0.record(stream)
-    for i in range(e2e_steps):
-        e2e_step(i)
-    e1.record(stream)
-    e1.synchronize()
-    e2e_ms = reduce_max(e0.elapsed_time(e1) / e2e_steps, world, dev)
+    ms_step = reduce_max(res["ms"], world, dev)
+    log("end to end with host buffers")
+    e2e_ms, h2d, d2h = e2e_measure(kfac, ctx, wl, res["graphs"], stream, max(3, min(args.steps, 10)))
+    e2e_ms = reduce_max(e2e_ms, world, dev)
 
     result = None
     if rank == 0:
-        result = {"metric": "K-factor RSVD-invert+precondition ms/step", "value": ms_step_max, "unit": "ms/step",
-                  "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
-                  "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.prec.replace(
-                      "fp32", "f32"), "data": "synthetic (seeded Philox draws, Haar V, power-law spectra)",
-                  "config": {"workload": workload_name(w, q), "steps_per_layer": 1,
-                             "l2": "no flush: >0.4 GB of inputs/outputs touched per step (L2 129 MB)",
-                             "parallelism": "replicas" if world > 1 else "single GPU",
-                             "precision": args.prec},
+        stages = res["stages"]
+        st, flags = res["status"]
+        dom = max(stages.items(), key=lambda kv: kv[1][0])[0]
+        result = {"metric": METRIC, "value": ms_step * 1.0, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+                  "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+                  "vs_baseline": None, "dtype": args.prec.replace("fp32", "f32"),
+                  "data": "synthetic (seeded device draws: orthonormal directions, power-law spectra, Gaussian "
+                          "batches, gradients and test matrices)",
+                  "config": {"workload": spec["workload"], "steps_per_layer": 1, "precision": args.prec,
+                             "graph": "one CUDA graph per step (grouped EA, inversion on forked streams, apply)",
+                             "layout": "row strides rounded up to 16 bytes",
+                             "l2": "no flush: %.1f GB of factors, batches, gradients and outputs per step (L2 129 MB)"
+                                   % (bytes_touched(spec) / 1e9),
+                             "parallelism": "replicas" if world > 1 else "single GPU"},
                   "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                  "gpu_launches": launches, "clocks": clk, "status": {"code": st, "flags": flags},
-                  "stage_ms_per_step": {kname: round(v[0] / args.steps, 4) for kname, v in prof.items()},
-                  "jacobi_sweeps_per_solve": stats["jacobi_sweeps"] / max(stats["jacobi_solves"], 1)}
-        result["roofline"] = roofline(prof, w, q, args.steps, stats, args.traffic)
-        result["roofline_sketch_gemm"] = sketch_roofline(prof, w, q, args.steps, args.prec)
+                  "gpu_launches": res["launches"] * args.steps, "clocks": res["clocks"],
+                  "status": {"code": st, "flags": flags},
+                  "stage_ms_per_step": {k: round(v[0], 4) for k, v in sorted(stages.items())},
+                  "stage_pass": "eager steps with per-stage CUDA events, outside the timed region; stages on "
+                                "forked streams overlap, so their sum exceeds ms/step",
+                  "simt_products_per_step": res["simt"] / 3.0,
+                  "jacobi_sweeps_per_solve": res["sweeps"]}
+        result["roofline"] = stage_roofline(dom, stages[dom][0], int(round(stages[dom][1])), spec, args.prec,
+                                            res["sweeps"])
+        if "sketch_gemm" in stages:
+            result["roofline_sketch_gemm"] = stage_roofline("sketch_gemm", stages["sketch_gemm"][0],
+                                                            int(round(stages["sketch_gemm"][1])), spec, args.prec)
 
-    # ---- full-EVD comparator on the same GPU and accuracy at equal rank -----------
+    # ---- full-EVD comparator on the same GPU, accuracy at equal rank -------------
     if rank == 0 and not args.no_evd:
-        cmp_ = evd_comparison(kfac, ctx, stream, Fa, Fg, J[0], OA[0], OG[0], w, q, args.prec, ms_step_max)
+        log("full-EVD comparator")
+        cmp_ = evd_comparison(kfac, ctx, wl, stream, args.prec, 3)
         ea_ms = result["stage_ms_per_step"].get("ea_syrk", 0.0)
-        cmp_["evd_comparator"]["ms_per_step"] = cmp_["evd_comparator"]["ms_per_step_excl_ea"] + ea_ms
-        cmp_["speedup_vs_evd"] = cmp_["evd_comparator"]["ms_per_step"] / ms_step_max
-        result.update(cmp_)
+        cmp_["ms_per_step"] = cmp_["ms_per_step_excl_ea"] + ea_ms
+        result["evd_comparator"] = cmp_
+        result["speedup_vs_evd"] = cmp_["ms_per_step"] / ms_step
 
-    # ---- FP64 CPU oracle on a bounded sample --------------------------------------
+    # ---- other precisions and workloads (short runs) -------------------------------
+    if rank == 0 and not args.no_extras:
+        extras = {}
+        for prec in ("tf32", "bf16"):
+            if prec == args.prec:
+                continue
+            r2 = bench_workload(kfac, ctx, wl, stream, prec, 10, 3, profile_steps=1)
+            errs = exact_errors(wl, wl.S, sample_layers(spec, 3))
+            sk = r2["stages"].get("sketch_gemm")
+            extras[f"{args.workload}_{prec}"] = {
+                "ms_per_step": r2["ms"], "err_vs_exact_inverse_sampled": max(errs),
+                "roofline_sketch_gemm": stage_roofline("sketch_gemm", sk[0], int(round(sk[1])), spec, prec)
+                if sk else None}
+            del r2
+        for other in ("c3", "c2"):
+            if other == args.workload:
+                continue
+            spec2 = workload_spec(other, args.power_iters)
+            wl2 = DeviceWorkload(spec2, dev)
+            for prec in (args.prec, "bf16"):
+                r2 = bench_workload(kfac, ctx, wl2, stream, prec, 10, 3, profile_steps=1)
+                errs = exact_errors(wl2, wl2.S, sample_layers(spec2, 2))
+                extras[f"{other}_{prec}"] = {"workload": spec2["workload"], "ms_per_step": r2["ms"],
+                                             "err_vs_exact_inverse_sampled": max(errs),
+                                             "stage_ms_per_step": {k: round(v[0], 4) for k, v in r2["stages"].items()}}
+                del r2
+            del wl2
+            torch.cuda.empty_cache()
+        result["extras"] = extras
+
+    # ---- FP64 CPU oracle on a bounded sample -----------------------------------------
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        frac = 4
-        ms_cpu, spent = oracle_step_sample(w, q, Fa.cpu().numpy(), Fg.cpu().numpy(), host["j"][0], host["om_g"][0],
-                                           host["xa"][0], frac)
-        result["cpu_baseline"] = {"value": ms_cpu, "unit": "ms/step", "cores": 1, "kind": "oracle",
-                                  "sample": f"FP64 C oracle, 1 thread, {spent:.1f} s: row/column-separable stages on "
-                                            f"1/{frac} of rows (scaled by {frac}); Householder QR of the d x k basis "
-                                            f"and Jacobi of the k x k matrix at full size; projected to one step"}
+        log("CPU oracle baseline")
+        cores = os.cpu_count() or 1
+        li = pick_layer(spec, cores, 20.0)
+        ms_cpu, spent, _ = oracle_projected_step(spec, li, cores)
+        li1 = pick_layer(spec, 1, 10.0)
+        ms_cpu1, spent1, _ = oracle_projected_step(spec, li1, 1)
+        a, g = spec["layers"][li]
+        result["cpu_baseline"] = {
+            "value": ms_cpu, "unit": "ms/step", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 C oracle, OpenMP {cores} threads, {spent:.1f} s on layer {li} (A {spec['factors'][a]['d']}, "
+                       f"G {spec['factors'][g]['d']}): EA, Alg. 3 + power iterations, Alg. 4 apply; each stage's "
+                       f"time scaled by its work over the whole step"),
+            "value_1thread": ms_cpu1,
+            "sample_1thread": f"1 thread, {spent1:.1f} s on layer {li1}, scaled the same way"}
     if rank == 0:
         print(json.dumps(result))
     ctx.close()
@@ -560,58 +852,6 @@ def main(argv=None):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
-
-
-def evd_comparison(kfac, ctx, stream, Fa, Fg, J, OA, OG, w, q, prec, ms_rand):
-    """torch.linalg.eigh (cuSOLVER) of both factors + truncated Eq. (13) apply,
-    timed per step without the EA updates (the caller adds the measured EA time,
-    common to both paths), and the preconditioned-gradient error of both paths
-    against the exact damped inverse."""
-    import torch
-    r, lam = w["r"], w["lam"]
-    dev = Fa.device
-    with torch.cuda.stream(stream):
-        fa, fg = Fa, Fg  # read-only here: eigh and the inversion do not modify their input
-
-        def evd_path():
-            wa, va = torch.linalg.eigh(fa)
-            wg, vg = torch.linalg.eigh(fg)
-            ua, da = va[:, -r:].flip(1).contiguous(), wa[-r:].flip(0)
-            ug, dgv = vg[:, -r:].flip(1).contiguous(), wg[-r:].flip(0)
-            ca = (1.0 / (da.clamp(min=0) + lam) - 1.0 / lam).contiguous()
-            cg = (1.0 / (dgv.clamp(min=0) + lam) - 1.0 / lam).contiguous()
-            return kfac.kfac_precondition(ctx, J, ua, ca, ug, cg, lam, "fp32"), (wa, va, wg, vg)
-
-        evd_path()
-        stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
-        e0.record(stream)
-        for _ in range(reps):
-            s_evd, full = evd_path()
-        e1.record(stream)
-        e1.synchronize()
-        ms_evd = e0.elapsed_time(e1) / reps
-        # EA updates are common to both paths: add the measured EA time of the randomized step.
-        Ua, Da, Ca = kfac.kfac_rsvd_invert(ctx, fa, r, w["p"], q, lam, OA, prec)
-        Ug, Dg, Cg = kfac.kfac_rsvd_invert(ctx, fg, r, w["p"], q, lam, OG, prec)
-        s_rand = kfac.kfac_precondition(ctx, J, Ua, Ca, Ug, Cg, lam, prec)
-        wa, va, wg, vg = (x.double() for x in full)
-        # exact damped inverse in FP64 from the full eigendecompositions
-        jd = J.double()
-        m = ((jd @ va) / (wa.clamp(min=0) + lam)[None, :]) @ va.T
-        s_exact = vg @ (((vg.T @ m)) / (wg.clamp(min=0) + lam)[:, None])
-        rel = lambda a, b: float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))
-        err_rand, err_evd = rel(s_rand, s_exact), rel(s_evd, s_exact)
-        err_between = rel(s_rand, s_evd.double())
-        lam_top = float(wa[-1])
-        stream.synchronize()
-    return {"evd_comparator": {"impl": "torch.linalg.eigh (cuSOLVER syevd, FP32) x2 + truncated Eq. (13) apply",
-                               "ms_per_step_excl_ea": ms_evd,
-                               "err_vs_exact_inverse": err_evd},
-            "randomized_err_vs_exact_inverse": err_rand,
-            "randomized_vs_truncated_evd": err_between,
-            "lambda_max_A": lam_top}
 
 
 if __name__ == "__main__":

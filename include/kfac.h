@@ -125,7 +125,8 @@ typedef struct {
 
 /* kfac_ea_update for `count` factors (every layer's forward and backward
  * factor, Alg. 1), enqueued on up to 8 streams forked from the context stream
- * (event fork/join, graph-capturable). A batch matrix whose base or row stride
+ * (event fork/join, graph-capturable; factors taken largest first, each on the
+ * stream with the least work so far). A batch matrix whose base or row stride
  * is not 16-byte aligned is first copied into the workspace with a padded
  * stride (so that the product runs on the tensor cores); a call that does this
  * under graph capture needs the workspace sized by an earlier call with the same
@@ -170,8 +171,9 @@ typedef struct {
 
 /* kfac_rsvd_invert for `count` independent factors (the per-layer loop of
  * Alg. 4/5). The factors' pipelines are enqueued on up to 8 streams forked
- * from the context stream (event fork/join, graph-capturable), each with its
- * own workspace slice, so the latency-bound small-matrix steps of different
+ * from the context stream (event fork/join, graph-capturable; the costliest
+ * factor first, each on the stream with the least estimated work so far), each
+ * stream with its own workspace slice, so the latency-bound small-matrix steps of different
  * factors overlap on the GPU. Arguments of every descriptor are checked before
  * anything is enqueued; the host array may be reused once the call returns. */
 KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kfac_invert_desc* descs);

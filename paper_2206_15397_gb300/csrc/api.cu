@@ -555,6 +555,41 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
   return KFAC_OK;
 }
 
+// Stream assignment of a grouped call: jobs are taken longest first and each
+// goes to the stream with the least estimated work so far (longest processing
+// time first). order: enqueue order (longest first); slot[f]: stream of job f.
+void lpt_schedule(const std::vector<double>& cost, int ns, std::vector<int>& order, std::vector<int>& slot) {
+  const int n = (int)cost.size();
+  order.resize(n);
+  slot.assign(n, 0);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> load(std::max(ns, 1), 0.0);
+  for (int f : order) {
+    const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    slot[f] = q;
+    load[q] += cost[f];
+  }
+}
+
+// Per-stream workspace bases for a grouped call: stream q gets a slice as large
+// as the largest job assigned to it.
+std::vector<size_t> stream_bases(const std::vector<size_t>& need, const std::vector<int>& slot, int ns) {
+  std::vector<size_t> m(ns, 0), base(ns + 1, 0);
+  for (size_t f = 0; f < need.size(); ++f) m[slot[f]] = std::max(m[slot[f]], need[f]);
+  for (int q = 0; q < ns; ++q) base[q + 1] = base[q] + ((m[q] + 255) & ~size_t(255));
+  return base;
+}
+
+// Estimated device seconds of one randomized inversion: the large products at
+// ~100 TFLOP/s plus the latency-bound k x k chain (~3 ms at k = 230, growing
+// as k^2).
+double invert_cost(const kfac_invert_desc& a) {
+  const double d = a.d, k = (double)a.rank + a.oversample;
+  if (k >= d) return 1e-3 * (d / 230.0) * (d / 230.0);
+  return (a.power_iters + 2) * 2.0 * d * d * k / 1e14 + 3e-3 * (k / 230.0) * (k / 230.0);
+}
+
 kfac_status ensure_side_streams(kfac_ctx* ctx, int n) {
   if (!ctx->fork_ev && cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess)
     return KFAC_ERR_CUDA;
@@ -811,12 +846,16 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   const int ns = std::min(count, kMaxSideStreams);
-  std::vector<size_t> base(ns + 1, 0);  // per-stream workspace slices (padded copies of ragged X)
-  for (int q = 0; q < ns; ++q) {
-    size_t m = 0;
-    for (int f = q; f < count; f += ns) m = std::max(m, ea_ws_bytes(descs[f].d, descs[f].n, descs[f].X, descs[f].ldx));
-    base[q + 1] = base[q] + ((m + 255) & ~size_t(255));
+  std::vector<double> cost(count);
+  std::vector<size_t> need(count);  // padded copies of ragged X
+  for (int f = 0; f < count; ++f) {
+    const kfac_ea_desc& a = descs[f];
+    cost[f] = (double)a.d * a.d * (a.n + 8);
+    need[f] = ea_ws_bytes(a.d, a.n, a.X, a.ldx);
   }
+  std::vector<int> order, slot;
+  lpt_schedule(cost, ns, order, slot);
+  const std::vector<size_t> base = stream_bases(need, slot, ns);
   kfac_status st = ensure_ws(ctx, base[ns]);
   if (st != KFAC_OK) return st;
   if (ns > 1 && (st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
@@ -826,11 +865,12 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
     for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(ctx->side[q], ctx->fork_ev, 0));
   }
   kfac_status first_err = KFAC_OK;
-  for (int f = 0; f < count && first_err == KFAC_OK; ++f) {
+  for (int i = 0; i < count && first_err == KFAC_OK; ++i) {
+    const int f = order[i];
     const kfac_ea_desc& a = descs[f];
     if (a.d == 0) continue;
-    ctx->stream = ns > 1 ? ctx->side[f % ns] : main_s;
-    first_err = ea_run(ctx, a.d, a.n, a.X, a.ldx, a.rho, a.prec, a.F, a.ldf, base[f % ns]);
+    ctx->stream = ns > 1 ? ctx->side[slot[f]] : main_s;
+    first_err = ea_run(ctx, a.d, a.n, a.X, a.ldx, a.rho, a.prec, a.F, a.ldf, base[slot[f]]);
   }
   ctx->stream = main_s;
   if (ns > 1) {
@@ -870,12 +910,15 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   const int ns = std::min(count, kMaxSideStreams);
-  std::vector<size_t> base(ns + 1, 0);
-  for (int q = 0; q < ns; ++q) {
-    size_t m = 0;
-    for (int f = q; f < count; f += ns) m = std::max(m, lay[f].total);
-    base[q + 1] = base[q] + ((m + 255) & ~size_t(255));
+  std::vector<double> cost(count);
+  std::vector<size_t> need(count);
+  for (int f = 0; f < count; ++f) {
+    cost[f] = invert_cost(descs[f]);
+    need[f] = lay[f].total;
   }
+  std::vector<int> order, slot;
+  lpt_schedule(cost, ns, order, slot);
+  const std::vector<size_t> base = stream_bases(need, slot, ns);
   kfac_status st = ensure_ws(ctx, base[ns]);
   if (st != KFAC_OK) return st;
   if (count == 1) return invert_run(ctx, descs[0], lay[0], 0);
@@ -884,9 +927,10 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
   CK(cudaEventRecord(ctx->fork_ev, main_s));
   for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(ctx->side[q], ctx->fork_ev, 0));
   kfac_status first_err = KFAC_OK;
-  for (int f = 0; f < count && first_err == KFAC_OK; ++f) {
-    ctx->stream = ctx->side[f % ns];
-    first_err = invert_run(ctx, descs[f], lay[f], base[f % ns]);
+  for (int i = 0; i < count && first_err == KFAC_OK; ++i) {
+    const int f = order[i];
+    ctx->stream = ctx->side[slot[f]];
+    first_err = invert_run(ctx, descs[f], lay[f], base[slot[f]]);
   }
   ctx->stream = main_s;
   for (int q = 0; q < ns; ++q) {
@@ -940,12 +984,16 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
     lay[f] = prec_layout_for(a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.r_a, a.U_g, a.ld_ug, a.r_g);
   }
   const int ns = std::min(count, kMaxSideStreams);
-  std::vector<size_t> base(ns + 1, 0);
-  for (int q = 0; q < ns; ++q) {
-    size_t m = 0;
-    for (int f = q; f < count; f += ns) m = std::max(m, lay[f].total);
-    base[q + 1] = base[q] + ((m + 255) & ~size_t(255));
+  std::vector<double> cost(count);
+  std::vector<size_t> need(count);
+  for (int f = 0; f < count; ++f) {
+    const kfac_precond_desc& a = descs[f];
+    cost[f] = (double)a.d_g * a.d_a * (a.r_a + a.r_g + 8);
+    need[f] = lay[f].total;
   }
+  std::vector<int> order, slot;
+  lpt_schedule(cost, ns, order, slot);
+  const std::vector<size_t> base = stream_bases(need, slot, ns);
   kfac_status st = ensure_ws(ctx, base[ns]);
   if (st != KFAC_OK) return st;
   auto run = [&](int f, size_t off) -> kfac_status {
@@ -960,9 +1008,10 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
   CK(cudaEventRecord(ctx->fork_ev, main_s));
   for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(ctx->side[q], ctx->fork_ev, 0));
   kfac_status first_err = KFAC_OK;
-  for (int f = 0; f < count && first_err == KFAC_OK; ++f) {
-    ctx->stream = ctx->side[f % ns];
-    first_err = run(f, base[f % ns]);
+  for (int i = 0; i < count && first_err == KFAC_OK; ++i) {
+    const int f = order[i];
+    ctx->stream = ctx->side[slot[f]];
+    first_err = run(f, base[slot[f]]);
   }
   ctx->stream = main_s;
   for (int q = 0; q < ns; ++q) {

@@ -276,10 +276,11 @@ def kfac_precondition_noalloc(J: torch.Tensor, U_a: torch.Tensor, coef_a: torch.
     return S
 
 
-def kfac_rsvd_invert_grouped(ctx: Context, items):
-    """Grouped kfac_rsvd_invert. items: sequence of dicts with keys F, rank,
-    oversample, power_iters, lam, omega, prec (optional) and out (optional
-    (U, D, coef)). Returns the list of (U, D, coef)."""
+def invert_descs(items):
+    """kfac_invert_desc array for a grouped inversion. items: sequence of dicts
+    with keys F, rank, oversample, power_iters, lam, omega, prec (optional) and
+    out (optional (U, D, coef)). Returns (descs, [(U, D, coef), ...]); the array
+    can be passed to call_grouped() any number of times."""
     descs = (InvertDesc * len(items))()
     outs = []
     for it, dsc in zip(items, descs):
@@ -304,13 +305,12 @@ def kfac_rsvd_invert_grouped(ctx: Context, items):
         dsc.U, dsc.ldu = pu.value, ldu
         dsc.D, dsc.coef = _vec(D, "D", r).value, _vec(coef, "coef", r).value
         outs.append((U, D, coef))
-    _check(lib().kfac_rsvd_invert_grouped(ctx.handle, len(items), descs), "kfac_rsvd_invert_grouped")
-    return outs
+    return descs, outs
 
 
-def kfac_ea_update_grouped(ctx: Context, items):
-    """Grouped kfac_ea_update. items: sequence of dicts with keys X (d x n),
-    F (d x d, updated in place), rho and prec (optional)."""
+def ea_descs(items):
+    """kfac_ea_desc array for a grouped EA update. items: sequence of dicts with
+    keys X (d x n), F (d x d, updated in place), rho and prec (optional)."""
     descs = (EaDesc * len(items))()
     for it, dsc in zip(items, descs):
         F, X = it["F"], it["X"]
@@ -319,14 +319,13 @@ def kfac_ea_update_grouped(ctx: Context, items):
         pf, ldf = _mat(F, "F", d, d)
         dsc.d, dsc.n, dsc.X, dsc.ldx = d, n, px.value, ldx
         dsc.rho, dsc.prec, dsc.F, dsc.ldf = float(it["rho"]), PRECISION[it.get("prec", "fp32")], pf.value, ldf
-    _check(lib().kfac_ea_update_grouped(ctx.handle, len(items), descs), "kfac_ea_update_grouped")
-    return [it["F"] for it in items]
+    return descs
 
 
-def kfac_precondition_grouped(ctx: Context, items):
-    """Grouped kfac_precondition. items: sequence of dicts with keys J, U_a,
-    coef_a, U_g, coef_g, lam, prec (optional) and out (optional S). Returns the
-    list of S."""
+def precond_descs(items):
+    """kfac_precond_desc array for a grouped apply. items: sequence of dicts with
+    keys J, U_a, coef_a, U_g, coef_g, lam, prec (optional) and out (optional S).
+    Returns (descs, [S, ...])."""
     descs = (PrecondDesc * len(items))()
     outs = []
     for it, dsc in zip(items, descs):
@@ -343,7 +342,36 @@ def kfac_precondition_grouped(ctx: Context, items):
         dsc.U_g, dsc.ld_ug, dsc.coef_g, dsc.r_g = pug.value, ldug, _vec(it["coef_g"], "coef_g", rg).value, rg
         dsc.lam, dsc.prec, dsc.S, dsc.lds = float(it["lam"]), PRECISION[it.get("prec", "fp32")], ps.value, lds
         outs.append(S)
-    _check(lib().kfac_precondition_grouped(ctx.handle, len(items), descs), "kfac_precondition_grouped")
+    return descs, outs
+
+
+_GROUPED = {"ea": "kfac_ea_update_grouped", "invert": "kfac_rsvd_invert_grouped",
+            "precondition": "kfac_precondition_grouped"}
+
+
+def call_grouped(ctx: Context, kind: str, descs):
+    """Issue a grouped call ("ea", "invert" or "precondition") on a prepared descriptor array."""
+    name = _GROUPED[kind]
+    _check(getattr(lib(), name)(ctx.handle, len(descs), descs), name)
+
+
+def kfac_rsvd_invert_grouped(ctx: Context, items):
+    """Grouped kfac_rsvd_invert (items as invert_descs). Returns the list of (U, D, coef)."""
+    descs, outs = invert_descs(items)
+    call_grouped(ctx, "invert", descs)
+    return outs
+
+
+def kfac_ea_update_grouped(ctx: Context, items):
+    """Grouped kfac_ea_update (items as ea_descs)."""
+    call_grouped(ctx, "ea", ea_descs(items))
+    return [it["F"] for it in items]
+
+
+def kfac_precondition_grouped(ctx: Context, items):
+    """Grouped kfac_precondition (items as precond_descs). Returns the list of S."""
+    descs, outs = precond_descs(items)
+    call_grouped(ctx, "precondition", descs)
     return outs
 
 
