@@ -412,10 +412,13 @@ def time_graphs(graphs, stream, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def profile_stages(kfac, ctx, descs, stream, steps):
-    """Eager steps with the library's stage events on: {stage: (ms/step, launches/step)}."""
+def profile_stages(kfac, ctx, descs, stream, steps, streams):
+    """Eager steps with the library's stage events on and every grouped item in
+    turn on one stream, so each stage's time is its kernels' own device time
+    (not stretched by items running beside it): {stage: (ms/step, launches/step)}."""
     import torch
     with torch.cuda.stream(stream):
+        kfac.kfac_set_option(ctx, "group_streams", 1)
         kfac.kfac_stats_read(ctx)
         kfac.kfac_profile_enable(ctx, True)
         n_simt = kfac.kfac_simt_gemm_count()
@@ -423,6 +426,7 @@ def profile_stages(kfac, ctx, descs, stream, steps):
             run_step(kfac, ctx, descs, i % len(descs[0]))
         prof = kfac.kfac_profile_read(ctx)
         kfac.kfac_profile_enable(ctx, False)
+        kfac.kfac_set_option(ctx, "group_streams", streams)
         stats = kfac.kfac_stats_read(ctx)
         simt = kfac.kfac_simt_gemm_count() - n_simt
     stages = {k: (v[0] / steps, v[1] / steps) for k, v in prof.items() if v[1] > 0}
@@ -692,11 +696,12 @@ def log(msg: str):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
-def bench_workload(kfac, ctx, wl, stream, prec, steps, warmup, clocks=None, profile_steps=3):
+def bench_workload(kfac, ctx, wl, stream, prec, steps, warmup, streams, clocks=None, profile_steps=3):
     """Capture and time one workload at one precision. Returns a result dict."""
     import torch
     log(f"{wl.spec['name']} {prec}: eager warm-up, capture, {steps} timed replays")
     descs = wl.descriptors(kfac, prec)
+    kfac.kfac_set_option(ctx, "group_streams", streams)
     with torch.cuda.stream(stream):
         for b in range(2):            # eager: sizes the workspace and creates the side streams
             run_step(kfac, ctx, descs, b % wl.nb)
@@ -708,7 +713,8 @@ def bench_workload(kfac, ctx, wl, stream, prec, steps, warmup, clocks=None, prof
     ms = time_graphs(graphs, stream, steps, warmup)
     clk = clocks.stop() if clocks is not None else None
     st, flags = kfac.kfac_get_status(ctx)
-    stages, sweeps, simt = profile_stages(kfac, ctx, descs, stream, profile_steps)
+    stages, sweeps, simt = profile_stages(kfac, ctx, descs, stream, profile_steps, streams) if profile_steps else \
+        ({}, 0.0, 0)
     return dict(ms=ms, graphs=graphs, launches=launches, clocks=clk, status=(st, flags), stages=stages,
                 sweeps=sweeps, simt=simt)
 
@@ -725,6 +731,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-evd", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--streams", type=int, default=16, help="streams a grouped call forks (1..32)")
+    ap.add_argument("--profile-steps", type=int, default=3, help="eager steps of the per-stage pass (0: none)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -752,7 +760,8 @@ def main(argv=None):
     barrier(world, dev)
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(dev.index)
-    res = bench_workload(kfac, ctx, wl, stream, args.prec, args.steps, args.warmup, clocks=clocks)
+    res = bench_workload(kfac, ctx, wl, stream, args.prec, args.steps, args.warmup, args.streams, clocks=clocks,
+                         profile_steps=args.profile_steps)
     torch.cuda.synchronize(dev)
     barrier(world, dev)
     ms_step = reduce_max(res["ms"], world, dev)
@@ -762,7 +771,7 @@ def main(argv=None):
 
     result = None
     if rank == 0:
-        stages = res["stages"]
+        stages = res["stages"] or {"none": (0.0, 0)}
         st, flags = res["status"]
         dom = max(stages.items(), key=lambda kv: kv[1][0])[0]
         result = {"metric": METRIC, "value": ms_step * 1.0, "unit": "ms/step", "n_gpus": world, "steps": args.steps,
@@ -772,6 +781,7 @@ def main(argv=None):
                           "batches, gradients and test matrices)",
                   "config": {"workload": spec["workload"], "steps_per_layer": 1, "precision": args.prec,
                              "graph": "one CUDA graph per step (grouped EA, inversion on forked streams, apply)",
+                             "streams": args.streams,
                              "layout": "row strides rounded up to 16 bytes",
                              "l2": "no flush: %.1f GB of factors, batches, gradients and outputs per step (L2 129 MB)"
                                    % (bytes_touched(spec) / 1e9),
@@ -780,12 +790,13 @@ def main(argv=None):
                   "gpu_launches": res["launches"] * args.steps, "clocks": res["clocks"],
                   "status": {"code": st, "flags": flags},
                   "stage_ms_per_step": {k: round(v[0], 4) for k, v in sorted(stages.items())},
-                  "stage_pass": "eager steps with per-stage CUDA events, outside the timed region; stages on "
-                                "forked streams overlap, so their sum exceeds ms/step",
-                  "simt_products_per_step": res["simt"] / 3.0,
+                  "stage_pass": "eager steps outside the timed region, every item in turn on one stream, CUDA "
+                                "events around each stage's launches: the kernels' own device time (the timed "
+                                "step overlaps items on forked streams, so it is shorter than the sum)",
+                  "simt_products_per_step": res["simt"] / max(args.profile_steps, 1),
                   "jacobi_sweeps_per_solve": res["sweeps"]}
-        result["roofline"] = stage_roofline(dom, stages[dom][0], int(round(stages[dom][1])), spec, args.prec,
-                                            res["sweeps"])
+        result["roofline"] = None if not res["stages"] else stage_roofline(
+            dom, stages[dom][0], int(round(stages[dom][1])), spec, args.prec, res["sweeps"])
         if "sketch_gemm" in stages:
             result["roofline_sketch_gemm"] = stage_roofline("sketch_gemm", stages["sketch_gemm"][0],
                                                             int(round(stages["sketch_gemm"][1])), spec, args.prec)
@@ -805,7 +816,7 @@ def main(argv=None):
         for prec in ("tf32", "bf16"):
             if prec == args.prec:
                 continue
-            r2 = bench_workload(kfac, ctx, wl, stream, prec, 10, 3, profile_steps=1)
+            r2 = bench_workload(kfac, ctx, wl, stream, prec, 10, 3, args.streams, profile_steps=1)
             errs = exact_errors(wl, wl.S, sample_layers(spec, 3))
             sk = r2["stages"].get("sketch_gemm")
             extras[f"{args.workload}_{prec}"] = {
@@ -819,7 +830,7 @@ def main(argv=None):
             spec2 = workload_spec(other, args.power_iters)
             wl2 = DeviceWorkload(spec2, dev)
             for prec in (args.prec, "bf16"):
-                r2 = bench_workload(kfac, ctx, wl2, stream, prec, 10, 3, profile_steps=1)
+                r2 = bench_workload(kfac, ctx, wl2, stream, prec, 10, 3, args.streams, profile_steps=1)
                 errs = exact_errors(wl2, wl2.S, sample_layers(spec2, 2))
                 extras[f"{other}_{prec}"] = {"workload": spec2["workload"], "ms_per_step": r2["ms"],
                                              "err_vs_exact_inverse_sampled": max(errs),

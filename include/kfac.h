@@ -124,7 +124,7 @@ typedef struct {
 } kfac_ea_desc;
 
 /* kfac_ea_update for `count` factors (every layer's forward and backward
- * factor, Alg. 1), enqueued on up to 8 streams forked from the context stream
+ * factor, Alg. 1), enqueued on up to KFAC_OPT_GROUP_STREAMS streams forked from the context stream
  * (event fork/join, graph-capturable; factors taken largest first, each on the
  * stream with the least work so far). A batch matrix whose base or row stride
  * is not 16-byte aligned is first copied into the workspace with a padded
@@ -170,7 +170,7 @@ typedef struct {
 } kfac_invert_desc;
 
 /* kfac_rsvd_invert for `count` independent factors (the per-layer loop of
- * Alg. 4/5). The factors' pipelines are enqueued on up to 8 streams forked
+ * Alg. 4/5). The factors' pipelines are enqueued on up to KFAC_OPT_GROUP_STREAMS streams forked
  * from the context stream (event fork/join, graph-capturable; the costliest
  * factor first, each on the stream with the least estimated work so far), each
  * stream with its own workspace slice, so the latency-bound small-matrix steps of different
@@ -212,7 +212,7 @@ typedef struct {
 } kfac_precond_desc;
 
 /* kfac_precondition for `count` layers (the per-layer loop of Alg. 4),
- * enqueued on up to 8 streams forked from the context stream, each stream with
+ * enqueued on up to KFAC_OPT_GROUP_STREAMS streams forked from the context stream, each stream with
  * its own workspace slice (graph-capturable once kfac_reserve or an earlier
  * call has sized the workspace). All descriptors are checked first. */
 KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const kfac_precond_desc* descs);
@@ -225,8 +225,12 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
  * allocates) and never calls cudaMalloc, cudaFree or any allocating library
  * routine.
  *
- * Same inputs, output and arithmetic as kfac_precondition, on `stream` (a
- * cudaStream_t as void*; NULL = legacy default stream) of the CURRENT device.
+ * Same inputs and output as kfac_precondition, with results that agree with it
+ * to within rounding (the products are formed in another order: T and the
+ * final product read U_a / U_g transposed and T2 reads M through S, so those
+ * three run on the SIMT kernel, only M = T U_a^T + J / lambda on the tensor
+ * cores), on `stream` (a cudaStream_t as void*; NULL = legacy default stream)
+ * of the CURRENT device.
  * The caller's S doubles as the staging area of M. The two thin intermediates
  * T = J U_a diag(coef_a) (d_g x r_a) and T2 = diag(coef_g) U_g^T M
  * (r_g x d_a) take turns in a static device array of KFAC_NOALLOC_SCRATCH_FLOATS
@@ -241,7 +245,9 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
  * call, so nothing needs clearing); calls whose work overlaps on the GPU (two
  * streams, or two host threads) race on it and must be serialised by the
  * caller. Argument errors return KFAC_ERR_INVALID_ARG; launch errors
- * KFAC_ERR_CUDA. There is no device status word: NaN/Inf propagate to S. */
+ * KFAC_ERR_CUDA. There is no device status word: NaN/Inf propagate to S, and a
+ * bounded wait of the tensor-core product that runs out (~2 s; not expected in
+ * practice) is not reported by this entry point and leaves S undefined. */
 #define KFAC_NOALLOC_SCRATCH_FLOATS (2 * 1024 * 1024)
 KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, const float* J, int ldj,
                                                const float* U_a, int ld_ua, const float* coef_a, int r_a,
@@ -249,9 +255,19 @@ KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, c
                                                float lambda, kfac_precision prec, float* S, int lds);
 
 /* Synchronise the context's stream, return KFAC_OK or the most severe device
- * condition recorded since the last call, store the raw KFAC_FLAG_* bits in
- * *flags (may be NULL) and clear them. */
+ * condition recorded since the last call (by any entry point, grouped items
+ * included), store the raw KFAC_FLAG_* bits in *flags (may be NULL) and clear
+ * them, the per-item words of kfac_get_item_status included. */
 KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags);
+
+/* Per-item attribution of device conditions in grouped calls: item i of a
+ * grouped EA update, inversion or apply raises its KFAC_FLAG_* bits in word i
+ * of a per-context array, so a breakdown can be traced to its factor or layer.
+ * Synchronises the context's stream and stores words 0..count-1 in
+ * item_flags (0 for items no grouped call has used); does not clear them.
+ * The words accumulate over grouped calls until kfac_get_status clears them,
+ * so read them after each grouped call whose items should be told apart. */
+KFAC_API kfac_status kfac_get_item_status(kfac_ctx* ctx, int count, int* item_flags);
 
 /* Tunables (defaults in brackets). Returns KFAC_ERR_INVALID_ARG for an unknown
  * option or an out-of-range value. */
@@ -292,6 +308,21 @@ typedef enum {
                                        squares the remaining error again. 0: sweep until a
                                        sweep rotates no pair (every pair cosine <=
                                        KFAC_OPT_EIG_TOL) */
+  KFAC_OPT_GROUP_STREAMS = 12,      /* [16]: streams a grouped call forks from the context
+                                       stream, 1..32 (1 = every item in turn on the context
+                                       stream). More streams overlap more of the items'
+                                       latency-bound k x k steps; each stream has its own
+                                       workspace slice */
+  KFAC_OPT_WAIT_CYCLES = 11,        /* [4e9, ~2 s]: limit, in SM clock cycles, of every wait
+                                       in which one role of a tensor-core kernel waits for
+                                       another (loads for the issuer, the issuer for free
+                                       stages, ...), 1..1e12. A wait that runs out raises
+                                       KFAC_FLAG_TIMEOUT (kfac_get_status then returns
+                                       KFAC_ERR_TIMEOUT); the kernel still waits for its own
+                                       copies and tensor-core operations in flight (with the
+                                       default limit), writes zeros for the products it could
+                                       not finish and returns. Small values exist to exercise
+                                       that path */
   KFAC_OPT_EIG_REFINE_FP64 = 10     /* 0 [default]: the eigen-refinement and basis-polish
                                        k x k products run in FP32 (FP64 carries the matrices
                                        between steps); their rounding, ~6e-8 of ||C||, is at

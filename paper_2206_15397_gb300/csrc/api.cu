@@ -34,7 +34,7 @@ struct Profiler {
 };
 }  // namespace
 
-constexpr int kMaxSideStreams = 8;
+constexpr int kMaxSideStreams = 32;
 
 struct kfac_ctx {
   Profiler prof;
@@ -45,7 +45,10 @@ struct kfac_ctx {
   cudaStream_t stream = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
-  int* dflags = nullptr;  // device status word
+  int* dflags = nullptr;  // device status word the kernels being enqueued raise flags in
+  int* dglobal = nullptr;  // the context's own status word (dflags outside grouped calls)
+  int* ditems = nullptr;   // per-item status words of grouped calls (item_cap of them)
+  int item_cap = 0, item_used = 0;
   unsigned long long* dstats = nullptr;  // STAT_COUNT device counters
   // options
   int cholqr_passes = 3;
@@ -59,6 +62,8 @@ struct kfac_ctx {
   double eig_tol = 2e-6;
   double eig_stop_tol = 3e-3;
   int eig_refine_fp64 = 0;
+  long long wait_cycles = kfac::kDefaultWaitCycles;
+  int group_streams = 16;  // side streams a grouped call may fork (KFAC_OPT_GROUP_STREAMS)
 };
 
 namespace {
@@ -214,7 +219,7 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.D = at<float>(ctx, L.part); g.ldd = k;
   g.alpha = 1.0f;
   g.zsplit = L.nsplit; g.kchunk = L.kchunk; g.zstride = (long long)k * k;
-  g.flags = ctx->dflags;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
   StageScope sc(ctx, stage);
   CK(gemm_f32(g, prec, ctx->stream));
   CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, 1, ctx->dflags, ctx->stream,
@@ -235,7 +240,7 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
   g.D = out; g.ldd = ldo; g.d_trans = 1;
   g.alpha = 1.0f; g.zsplit = 1;
   g.ws = at<float>(ctx, L.skws); g.ws_floats = L.skws_floats;
-  g.flags = ctx->dflags;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
   STAGE(ctx, ST_SKETCH);
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
@@ -426,7 +431,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   g.B = Pt; g.sbn = L.kp; g.sbk = 1;
   g.D = a.U; g.ldd = a.ldu;
   g.alpha = 1.0f; g.zsplit = 1;
-  g.flags = ctx->dflags;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
   CK(gemm_f32(g, KFAC_PREC_FP32, s));
   return KFAC_OK;
 }
@@ -515,7 +520,8 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.B = Uat; g.sbn = P.ld_uat; g.sbk = 1;
     g.D = T; g.ldd = P.ld_t;
     g.alpha = 1.0f; g.colscale = coef_a; g.zsplit = 1;
-    g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats; g.flags = ctx->dflags;
+    g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
     CK(gemm_f32(g, prec, s));
   }
   {  // M^T = U_a T^T + J^T / lambda
@@ -526,7 +532,7 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.B = T; g.sbn = P.ld_t; g.sbk = 1;
     g.D = Mt; g.ldd = P.ld_mt;
     g.alpha = 1.0f; g.beta = inv_lam; g.C0 = J; g.ldc = ldj; g.c0_trans = 1; g.zsplit = 1;
-    g.flags = ctx->dflags;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
     CK(gemm_f32(g, prec, s));
   }
   if (r_g > 0) {  // T2^T = M^T U_g diag(c_g), through U_g^T
@@ -538,7 +544,8 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.B = Ugt; g.sbn = P.ld_ugt; g.sbk = 1;
     g.D = T2t; g.ldd = P.ld_t2;
     g.alpha = 1.0f; g.colscale = coef_g; g.zsplit = 1;
-    g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats; g.flags = ctx->dflags;
+    g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
     CK(gemm_f32(g, prec, s));
   }
   {  // S = U_g T2 + M / lambda  (M read through M^T)
@@ -549,7 +556,7 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.B = T2t; g.sbn = P.ld_t2; g.sbk = 1;
     g.D = S; g.ldd = lds;
     g.alpha = 1.0f; g.beta = inv_lam; g.C0 = Mt; g.ldc = P.ld_mt; g.c0_trans = 1; g.zsplit = 1;
-    g.flags = ctx->dflags;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
     CK(gemm_f32(g, prec, s));
   }
   return KFAC_OK;
@@ -588,6 +595,29 @@ double invert_cost(const kfac_invert_desc& a) {
   const double d = a.d, k = (double)a.rank + a.oversample;
   if (k >= d) return 1e-3 * (d / 230.0) * (d / 230.0);
   return (a.power_iters + 2) * 2.0 * d * d * k / 1e14 + 3e-3 * (k / 230.0) * (k / 230.0);
+}
+
+// Per-item status words for a grouped call of `count` items (allocated before
+// anything is enqueued, so a captured grouped call needs an earlier call with
+// at least as many items).
+kfac_status ensure_items(kfac_ctx* ctx, int count) {
+  if (count > ctx->item_cap) {
+    if (ctx->ditems) {
+      if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+      cudaFree(ctx->ditems);
+      ctx->ditems = nullptr;
+      ctx->item_cap = 0;
+    }
+    const int cap = std::max(count, 64);
+    if (cudaMalloc(&ctx->ditems, sizeof(int) * (size_t)cap) != cudaSuccess) {
+      cudaGetLastError();
+      return KFAC_ERR_OOM;
+    }
+    if (cudaMemset(ctx->ditems, 0, sizeof(int) * (size_t)cap) != cudaSuccess) return KFAC_ERR_CUDA;
+    ctx->item_cap = cap;
+  }
+  ctx->item_used = std::max(ctx->item_used, count);
+  return KFAC_OK;
 }
 
 kfac_status ensure_side_streams(kfac_ctx* ctx, int n) {
@@ -641,6 +671,7 @@ KFAC_API kfac_status kfac_create(kfac_ctx** out, int device, void* stream) {
     delete ctx;
     return KFAC_ERR_OOM;
   }
+  ctx->dglobal = ctx->dflags;
   ctx->dstats = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->dflags) + 32);
   if (cudaMemset(ctx->dflags, 0, 64) != cudaSuccess) {
     cudaFree(ctx->dflags);
@@ -661,7 +692,8 @@ KFAC_API kfac_status kfac_destroy(kfac_ctx* ctx) {
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->ws) cudaFree(ctx->ws);
-  if (ctx->dflags) cudaFree(ctx->dflags);
+  if (ctx->ditems) cudaFree(ctx->ditems);
+  if (ctx->dglobal) cudaFree(ctx->dglobal);
   delete ctx;
   return KFAC_OK;
 }
@@ -719,6 +751,14 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->eig_refine_fp64 = (int)v;
       return KFAC_OK;
+    case KFAC_OPT_GROUP_STREAMS:
+      if (v < 1 || v > kMaxSideStreams) return KFAC_ERR_INVALID_ARG;
+      ctx->group_streams = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_WAIT_CYCLES:
+      if (!(v >= 1 && v <= 1e12)) return KFAC_ERR_INVALID_ARG;
+      ctx->wait_cycles = (long long)v;
+      return KFAC_OK;
   }
   return KFAC_ERR_INVALID_ARG;
 }
@@ -773,7 +813,8 @@ KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const floa
   g.B = B; g.sbn = ldb; g.sbk = 1;
   g.D = D; g.ldd = ldd;
   g.alpha = alpha; g.beta = beta; g.C0 = D; g.ldc = ldd;
-  g.zsplit = 1; g.ws = at<float>(ctx, o_ws); g.ws_floats = ws_floats; g.flags = ctx->dflags;
+  g.zsplit = 1; g.ws = at<float>(ctx, o_ws); g.ws_floats = ws_floats;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
 }
@@ -782,10 +823,18 @@ KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags) {
   if (!ctx) return KFAC_ERR_INVALID_ARG;
   DeviceGuard g(ctx->device);
   int h = 0;
-  if (cudaMemcpyAsync(&h, ctx->dflags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+  std::vector<int> items((size_t)ctx->item_used);
+  if (cudaMemcpyAsync(&h, ctx->dglobal, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    return KFAC_ERR_CUDA;
+  if (ctx->item_used > 0 && cudaMemcpyAsync(items.data(), ctx->ditems, sizeof(int) * items.size(),
+                                            cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
     return KFAC_ERR_CUDA;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
-  if (cudaMemsetAsync(ctx->dflags, 0, sizeof(int), ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  if (cudaMemsetAsync(ctx->dglobal, 0, sizeof(int), ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  if (ctx->item_used > 0 &&
+      cudaMemsetAsync(ctx->ditems, 0, sizeof(int) * (size_t)ctx->item_used, ctx->stream) != cudaSuccess)
+    return KFAC_ERR_CUDA;
+  for (int v : items) h |= v;
   if (flags) *flags = h;
   if (h & KFAC_FLAG_NONFINITE) return KFAC_ERR_NONFINITE;
   if (h & KFAC_FLAG_CHOL_FAILED) return KFAC_ERR_CHOLESKY;
@@ -812,7 +861,19 @@ static kfac_status ea_run(kfac_ctx* ctx, int d, int n, const float* X, int ldx, 
     X = Xp;
     ldx = (int)ldp;
   }
-  CK(ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags));
+  CK(ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags, ctx->wait_cycles));
+  return KFAC_OK;
+}
+
+KFAC_API kfac_status kfac_get_item_status(kfac_ctx* ctx, int count, int* item_flags) {
+  if (!ctx || count < 0 || (count > 0 && !item_flags)) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  for (int i = 0; i < count; ++i) item_flags[i] = 0;
+  const int n = std::min(count, ctx->item_used);
+  if (n > 0 && cudaMemcpyAsync(item_flags, ctx->ditems, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost,
+                               ctx->stream) != cudaSuccess)
+    return KFAC_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
   return KFAC_OK;
 }
 
@@ -845,7 +906,7 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
   if (count == 0) return KFAC_OK;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  const int ns = std::min(count, kMaxSideStreams);
+  const int ns = std::min(count, ctx->group_streams);
   std::vector<double> cost(count);
   std::vector<size_t> need(count);  // padded copies of ragged X
   for (int f = 0; f < count; ++f) {
@@ -858,6 +919,7 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
   const std::vector<size_t> base = stream_bases(need, slot, ns);
   kfac_status st = ensure_ws(ctx, base[ns]);
   if (st != KFAC_OK) return st;
+  if ((st = ensure_items(ctx, count)) != KFAC_OK) return st;
   if (ns > 1 && (st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
   cudaStream_t main_s = ctx->stream;
   if (ns > 1) {
@@ -870,8 +932,10 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
     const kfac_ea_desc& a = descs[f];
     if (a.d == 0) continue;
     ctx->stream = ns > 1 ? ctx->side[slot[f]] : main_s;
+    ctx->dflags = ctx->ditems + f;
     first_err = ea_run(ctx, a.d, a.n, a.X, a.ldx, a.rho, a.prec, a.F, a.ldf, base[slot[f]]);
   }
+  ctx->dflags = ctx->dglobal;
   ctx->stream = main_s;
   if (ns > 1) {
     for (int q = 0; q < ns; ++q) {
@@ -909,7 +973,7 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
   }
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  const int ns = std::min(count, kMaxSideStreams);
+  const int ns = std::min(count, ctx->group_streams);
   std::vector<double> cost(count);
   std::vector<size_t> need(count);
   for (int f = 0; f < count; ++f) {
@@ -921,7 +985,13 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
   const std::vector<size_t> base = stream_bases(need, slot, ns);
   kfac_status st = ensure_ws(ctx, base[ns]);
   if (st != KFAC_OK) return st;
-  if (count == 1) return invert_run(ctx, descs[0], lay[0], 0);
+  if ((st = ensure_items(ctx, count)) != KFAC_OK) return st;
+  if (count == 1) {
+    ctx->dflags = ctx->ditems;
+    st = invert_run(ctx, descs[0], lay[0], 0);
+    ctx->dflags = ctx->dglobal;
+    return st;
+  }
   if ((st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
   cudaStream_t main_s = ctx->stream;
   CK(cudaEventRecord(ctx->fork_ev, main_s));
@@ -930,8 +1000,10 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
   for (int i = 0; i < count && first_err == KFAC_OK; ++i) {
     const int f = order[i];
     ctx->stream = ctx->side[slot[f]];
+    ctx->dflags = ctx->ditems + f;
     first_err = invert_run(ctx, descs[f], lay[f], base[slot[f]]);
   }
+  ctx->dflags = ctx->dglobal;
   ctx->stream = main_s;
   for (int q = 0; q < ns; ++q) {
     CK(cudaEventRecord(ctx->join_ev[q], ctx->side[q]));
@@ -983,7 +1055,7 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
     const kfac_precond_desc& a = descs[f];
     lay[f] = prec_layout_for(a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.r_a, a.U_g, a.ld_ug, a.r_g);
   }
-  const int ns = std::min(count, kMaxSideStreams);
+  const int ns = std::min(count, ctx->group_streams);
   std::vector<double> cost(count);
   std::vector<size_t> need(count);
   for (int f = 0; f < count; ++f) {
@@ -1002,7 +1074,13 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
     return precondition_run(ctx, a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.coef_a, a.r_a, a.U_g, a.ld_ug,
                             a.coef_g, a.r_g, a.lambda, a.prec, a.S, a.lds, lay[f], off);
   };
-  if (count == 1) return run(0, 0);
+  if ((st = ensure_items(ctx, count)) != KFAC_OK) return st;
+  if (count == 1) {
+    ctx->dflags = ctx->ditems;
+    st = run(0, 0);
+    ctx->dflags = ctx->dglobal;
+    return st;
+  }
   if ((st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
   cudaStream_t main_s = ctx->stream;
   CK(cudaEventRecord(ctx->fork_ev, main_s));
@@ -1011,8 +1089,10 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
   for (int i = 0; i < count && first_err == KFAC_OK; ++i) {
     const int f = order[i];
     ctx->stream = ctx->side[slot[f]];
+    ctx->dflags = ctx->ditems + f;
     first_err = run(f, base[slot[f]]);
   }
+  ctx->dflags = ctx->dglobal;
   ctx->stream = main_s;
   for (int q = 0; q < ns; ++q) {
     CK(cudaEventRecord(ctx->join_ev[q], ctx->side[q]));

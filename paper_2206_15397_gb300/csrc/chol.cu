@@ -95,14 +95,19 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
     __syncthreads();
     if (tid < 32) {  // fixed summation order: lane-strided partial sums, then a fixed shuffle tree
       double t = 0.0;
-      for (int i = tid; i < k; i += 32) t += dg[i];
+      for (int i = tid; i < k; i += 32) t += fabs(dg[i]);
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (tid == 0) s_trace = t;
     }
     __syncthreads();
   }
   const double trace = s_trace;
+  // trace: sum of |G_ii| (the trace of a PSD matrix; a scale for the shifts and
+  // the floor of any symmetric one). A zero diagonal means the zero matrix
+  // (the Gram of a zero sketch, or a zero projected matrix): it is factored
+  // exactly as G + 1 I = I I^T (L = I, shift 1).
   const bool finite_in = isfinite(trace) && trace > 0.0;
+  const bool zero_in = trace == 0.0;
   // Pivot floor. A pivot below it (the column is, to the Gram's FP32
   // accuracy, in the span of the previous ones) is replaced by the column's
   // original diagonal G_jj + shift (at least the floor): the factor is then
@@ -298,10 +303,11 @@ __global__ void __launch_bounds__(CHOL_THREADS, 1) k_chol_cluster(const double* 
 
   if (!ok) {
     if (rank == 0 && tid == 0) {
-      raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : KFAC_FLAG_NONFINITE);
-      if (shift_out) *shift_out = 0.0;
+      raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : (zero_in ? KFAC_FLAG_CHOL_SHIFTED : KFAC_FLAG_NONFINITE));
+      if (shift_out) *shift_out = zero_in ? 1.0 : 0.0;
     }
-    // Keep downstream finite: L = diag(sqrt(max(G_ii, tiny))).
+    // Keep downstream finite: L = diag(sqrt(G_ii)), 1 where G_ii is not
+    // positive and finite (L = I for the zero matrix).
     for (int li = 0; li < nloc; ++li) {
       int i = li * NC + rank;
       if (i >= k) continue;
@@ -561,13 +567,18 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
 
   if (warp == 0) {  // fixed-order trace
     double t = 0.0;
-    for (int i = lane; i < k; i += 32) t += G[(size_t)i * k + i];
+    for (int i = lane; i < k; i += 32) t += fabs(G[(size_t)i * k + i]);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) s_trace = t;
   }
   __syncthreads();
   const double trace = s_trace;
+  // trace: sum of |G_ii| (the trace of a PSD matrix; a scale for the shifts and
+  // the floor of any symmetric one). A zero diagonal means the zero matrix
+  // (the Gram of a zero sketch, or a zero projected matrix): it is factored
+  // exactly as G + 1 I = I I^T (L = I, shift 1).
   const bool finite_in = isfinite(trace) && trace > 0.0;
+  const bool zero_in = trace == 0.0;
   const float pfloor = (float)fmax(1e-9 * trace, 1e-6 * trace / k);
   double shift = shift_rel > 0.0 ? shift_rel * trace : (shift_rel < 0.0 ? -shift_rel * trace / k : 0.0);
   int ok = 0;
@@ -628,8 +639,8 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
   }
   if (!ok) {
     if (tid == 0) {
-      raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : KFAC_FLAG_NONFINITE);
-      if (shift_out) *shift_out = 0.0;
+      raise_flag(flags, finite_in ? KFAC_FLAG_CHOL_FAILED : (zero_in ? KFAC_FLAG_CHOL_SHIFTED : KFAC_FLAG_NONFINITE));
+      if (shift_out) *shift_out = zero_in ? 1.0 : 0.0;
     }
     for (int i = warp; i < k; i += CTA_WARPS) {
       const double g = G[(size_t)i * k + i];

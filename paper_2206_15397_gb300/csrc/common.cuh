@@ -101,7 +101,12 @@ struct GemmDesc {
   T* ws;
   long long ws_floats;
   int* flags;  // device status word for bounded-wait timeouts (may be null)
+  long long wait_cycles;  // limit of the tensor-core kernels' waits on each other's progress (0: default)
 };
+
+// Default limit of a tensor-core kernel's wait for another role's progress:
+// ~2 s at 2 GHz, far beyond any legitimate wait (KFAC_OPT_WAIT_CYCLES).
+constexpr long long kDefaultWaitCycles = 4000000000LL;
 
 // ---- launchers (host) --------------------------------------------------------
 cudaError_t gemm_simt_f32(const GemmDesc<float>& g, Round rnd, cudaStream_t s);

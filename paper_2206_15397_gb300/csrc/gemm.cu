@@ -52,6 +52,7 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
   a.C0 = g.C0; a.ldc = g.ldc; a.c0_trans = g.c0_trans;
   a.D = g.D; a.ldd = g.ldd; a.d_trans = g.d_trans;
   a.sym = g.sym; a.flags = g.flags;
+  a.wait_cycles = g.wait_cycles > 0 ? g.wait_cycles : kDefaultWaitCycles;
   if (g.zsplit > 1) {  // caller-managed raw partials
     a.partial = 1; a.kchunk = g.kchunk; a.zstride = g.zstride;
     return tc::gemm(a, g.A, g.sam, g.B, g.sbn, g.zsplit, mode, s);
@@ -82,7 +83,7 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
 }
 
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,
-                    int ldf, int* flags) {
+                    int ldf, int* flags, long long wait_cycles) {
   GemmDesc<float> g = {};
   g.M = d; g.N = d; g.K = n;
   g.A = X; g.sam = ldx; g.sak = 1;
@@ -94,6 +95,7 @@ cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float
   g.zsplit = 1;
   g.sym = 1;  // upper tiles computed once, mirrored: the factor stays exactly symmetric
   g.flags = flags;
+  g.wait_cycles = wait_cycles;
   if (rho == 0.0f) g.beta = 0.0f;
   return gemm_f32(g, prec, s);
 }

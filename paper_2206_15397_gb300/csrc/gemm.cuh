@@ -13,6 +13,6 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
 
 // F <- rho F + (1 - rho)/n X X^T (Alg. 1 EA updates), exactly symmetric result.
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,
-                    int ldf, int* flags);
+                    int ldf, int* flags, long long wait_cycles = 0);
 
 }  // namespace kfac

@@ -56,7 +56,12 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 32;  // FP32 columns per stage (128 bytes)
 constexpr int THREADS = 256;
-constexpr long long kDeadlineCycles = 4000000000LL;  // ~2 s at 2 GHz
+// Limit of the waits for this CTA's own work in flight (its TMA copies landing,
+// its MMAs completing): those always finish, so the limit is long (~2 s at
+// 2 GHz) and independent of TcArgs::wait_cycles, which bounds the waits for
+// another role's progress. A CTA whose peer wait gave up therefore still
+// exits only after its copies and MMAs have completed.
+constexpr long long kDrainCycles = 4000000000LL;
 constexpr int BN3 = 128;            // tile width of the FP32-accurate kernel
 constexpr int kSplitThreads = 192;  // warps 2-7 split the staged tiles (3xTF32)
 
@@ -81,12 +86,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Wait for the phase of `bar` with the given parity to complete, or give up
-// after the deadline (raising the timeout flag). Returns true on completion.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* flags) {
+// after `limit` clock cycles (raising the timeout flag). Returns true on
+// completion.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* flags, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kDeadlineCycles) {
+    if (clock64() - t0 > limit) {
       raise_flag(flags, KFAC_FLAG_TIMEOUT);
       return false;
     }
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags)) break;
+      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) break;
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       mbar_expect_tx(full0 + 8 * s, C::RAW);
       tma_load_2d(st, &tmA, kb0 + kb * BK, m0, full0 + 8 * s);
@@ -357,14 +363,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     // Drain: every issued copy has landed before this CTA may exit (the MMA
     // issuer consumes them in the normal path; this matters after a timeout).
     for (int kb = (issued > C::STAGES ? issued - C::STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags);
+      mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags, kDrainCycles);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----------------------------------------------------------
     constexpr uint32_t idesc = idesc_tf32(BM, BN);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (!mbar_wait(full0 + 8 * s, ph, p.flags)) break;
+      if (!mbar_wait(full0 + 8 * s, ph, p.flags, p.wait_cycles)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncwarp();
 
   // ---- epilogue ----------------------------------------------------------------
-  const bool acc_ok = mbar_wait(accb, 0, p.flags);
+  const bool acc_ok = mbar_wait(accb, 0, p.flags, kDrainCycles);  // every issued MMA has completed
   tc_fence_after();
   float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // per-warp 32 x 33 staging
   float* const Dz = p.D + (p.partial ? (long long)blockIdx.z * p.zstride : 0LL);  // split-K slice
@@ -408,9 +414,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // Warp-uniform bounded wait: lane 0 polls, the verdict is broadcast.
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* flags, int lane) {
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* flags, int lane, long long limit) {
   int ok = 1;
-  if (lane == 0) ok = mbar_wait(bar, parity, flags) ? 1 : 0;
+  if (lane == 0) ok = mbar_wait(bar, parity, flags, limit) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
@@ -463,7 +469,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags)) break;
+      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) break;
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       mbar_expect_tx(full0 + 8 * s, C::RAW);
       tma_load_2d(st, &tmA, kb0 + kb * BK, m0, full0 + 8 * s);
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       ++issued;
     }
     for (int kb = (issued > C::STAGES ? issued - C::STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags);
+      mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags, kDrainCycles);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: stages 2m, 2m+1 -> TMEM pair m & 1 ------------------------
     constexpr uint32_t idesc = idesc_tf32(BM, BN3);
@@ -479,8 +485,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int s = kb % C::STAGES, m = kb >> 1, b = m & 1;
       const bool first = (kb & 1) == 0, last = (kb & 1) == 1 || kb == nk - 1;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (first && m >= 2 && !mbar_wait(tempty0 + 8 * b, (uint32_t)((m >> 1) - 1) & 1u, p.flags)) break;
-      if (!mbar_wait(split0 + 8 * s, ph, p.flags)) break;
+      if (first && m >= 2 && !mbar_wait(tempty0 + 8 * b, (uint32_t)((m >> 1) - 1) & 1u, p.flags, p.wait_cycles)) break;
+      if (!mbar_wait(split0 + 8 * s, ph, p.flags, p.wait_cycles)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
@@ -515,7 +521,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (kb < nk) {
         const int s = kb % C::STAGES;
         const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-        if (!mbar_wait_warp(full0 + 8 * s, ph, p.flags, lane)) { drained = false; break; }
+        if (!mbar_wait_warp(full0 + 8 * s, ph, p.flags, lane, p.wait_cycles)) { drained = false; break; }
         const float4* raw = reinterpret_cast<const float4*>(smem + s * C::STAGE);
         float4* lo = reinterpret_cast<float4*>(smem + s * C::STAGE + C::RAW);
 #pragma unroll 2
@@ -528,7 +534,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (drainer && kb >= 1 && (((kb - 1) & 1) == 1 || kb == nk)) {  // pair of stages ending at kb - 1
         const int m = (kb - 1) >> 1, b = m & 1;
-        if (!mbar_wait_warp(tfull0 + 8 * b, (uint32_t)(m >> 1) & 1u, p.flags, lane)) { drained = false; break; }
+        if (!mbar_wait_warp(tfull0 + 8 * b, (uint32_t)(m >> 1) & 1u, p.flags, lane, p.wait_cycles)) { drained = false; break; }
         tc_fence_after();
 #pragma unroll
         for (int c = 0; c < BN3 / 32; ++c) {
@@ -548,7 +554,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncwarp();
 
   // ---- epilogue (warps 4-7, from the register sums) ---------------------------
-  const bool acc_ok = mbar_wait_warp(accb, 0, p.flags, lane);
+  const bool acc_ok = mbar_wait_warp(accb, 0, p.flags, lane, kDrainCycles);  // every issued MMA has completed
   tc_fence_after();
   if (warp >= 4) {
     float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);
@@ -625,7 +631,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::RAW_STAGES;
       const uint32_t ph = (uint32_t)(kb / C::RAW_STAGES) & 1u;
-      if (kb >= C::RAW_STAGES && !mbar_wait(rempty0 + 8 * s, ph ^ 1u, p.flags)) break;
+      if (kb >= C::RAW_STAGES && !mbar_wait(rempty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) break;
       const uint32_t st = smem_u32(raw0 + s * C::RAW);
       const int kx = kb0 + kb * BK16;
       mbar_expect_tx(rfull0 + 8 * s, C::RAW);
@@ -636,14 +642,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       ++issued;
     }
     for (int kb = (issued > C::RAW_STAGES ? issued - C::RAW_STAGES : 0); kb < issued; ++kb)
-      mbar_wait(rfull0 + 8 * (kb % C::RAW_STAGES), (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags);
+      mbar_wait(rfull0 + 8 * (kb % C::RAW_STAGES), (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags, kDrainCycles);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: 4 x (K = 16) per BF16 stage -----------------------------
     constexpr uint32_t idesc = idesc_bf16(BM, BN16);
     for (int kb = 0; kb < nk; ++kb) {
       const int h = kb % C::H_STAGES;
       const uint32_t ph = (uint32_t)(kb / C::H_STAGES) & 1u;
-      if (!mbar_wait(hfull0 + 8 * h, ph, p.flags)) break;
+      if (!mbar_wait(hfull0 + 8 * h, ph, p.flags, p.wait_cycles)) break;
       tc_fence_after();
       const uint32_t hb = smem_u32(half0 + h * C::HALF);
       const uint64_t ad = sdesc_k128(hb), bd = sdesc_k128(hb + C::A_H);
@@ -663,9 +669,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int t = tid - 64;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::RAW_STAGES, h = kb % C::H_STAGES;
-      if (!mbar_wait_warp(rfull0 + 8 * s, (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags, lane)) break;
+      if (!mbar_wait_warp(rfull0 + 8 * s, (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags, lane, p.wait_cycles)) break;
       if (kb >= C::H_STAGES &&
-          !mbar_wait_warp(hempty0 + 8 * h, ((uint32_t)(kb / C::H_STAGES) & 1u) ^ 1u, p.flags, lane))
+          !mbar_wait_warp(hempty0 + 8 * h, ((uint32_t)(kb / C::H_STAGES) & 1u) ^ 1u, p.flags, lane, p.wait_cycles))
         break;
       const uint8_t* rs = raw0 + s * C::RAW;
       uint8_t* hs = half0 + h * C::HALF;
@@ -692,7 +698,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncwarp();
 
   // ---- epilogue (all 8 warps, as the TF32 kernel) --------------------------------
-  const bool acc_ok = mbar_wait(accb, 0, p.flags);
+  const bool acc_ok = mbar_wait(accb, 0, p.flags, kDrainCycles);  // every issued MMA has completed
   tc_fence_after();
   float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);
   float* const Dz = p.D + (p.partial ? (long long)blockIdx.z * p.zstride : 0LL);

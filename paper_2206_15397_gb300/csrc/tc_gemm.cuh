@@ -23,6 +23,7 @@ struct TcArgs {
   long long zstride;
   int sym;       // write only m <= n, plus the mirror (n, m); tiles below the diagonal exit
   int* flags;
+  long long wait_cycles;  // limit (clock cycles, > 0) of each wait for another role's progress
 };
 
 // True when A (M x K, row stride lda) and B (N x K, row stride ldb) can be read

@@ -19,7 +19,8 @@ _lib = None
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
 OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_sweeps": 3, "eig_tol": 4,
            "cholqr_inner_passes": 5, "cholqr_fp32_passes": 6,
-           "basis_polish": 7, "cholqr_inner_fp32": 8, "eig_stop_tol": 9, "eig_refine_fp64": 10}
+           "basis_polish": 7, "cholqr_inner_fp32": 8, "eig_stop_tol": 9, "eig_refine_fp64": 10, "wait_cycles": 11,
+           "group_streams": 12}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
@@ -70,6 +71,8 @@ def lib():
         L.kfac_reserve.argtypes = [vp, i, i, i64]
         L.kfac_set_option.argtypes = [vp, i, d]
         L.kfac_get_status.argtypes = [vp, ctypes.POINTER(i)]
+        L.kfac_get_item_status.argtypes = [vp, i, ctypes.POINTER(i)]
+        L.kfac_get_item_status.restype = i
         L.kfac_ea_update.argtypes = [vp, i, i, vp, i, f, i, vp, i]
         L.kfac_rsvd_invert.argtypes = [vp, i, vp, i, i, i, i, f, vp, i, i, vp, i, vp, vp]
         L.kfac_precondition.argtypes = [vp, i, i, vp, i, vp, i, vp, i, vp, i, vp, i, f, i, vp, i]
@@ -168,6 +171,13 @@ def kfac_get_status(ctx: Context):
     f = ctypes.c_int(0)
     st = lib().kfac_get_status(ctx.handle, ctypes.byref(f))
     return st, [n for b, n in FLAGS.items() if f.value & b]
+
+
+def kfac_get_item_status(ctx: Context, count: int):
+    """Per-item flag names of grouped calls since the last kfac_get_status (does not clear)."""
+    arr = (ctypes.c_int * max(count, 1))()
+    _check(lib().kfac_get_item_status(ctx.handle, int(count), arr), "kfac_get_item_status")
+    return [[n for b, n in FLAGS.items() if arr[i] & b] for i in range(count)]
 
 
 def kfac_ea_update(ctx: Context, X: torch.Tensor, F: torch.Tensor, rho: float, prec: str = "fp32"):

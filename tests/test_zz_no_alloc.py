@@ -30,13 +30,13 @@ def test_noalloc_rejects_oversized_requests_before_any_work():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 def test_noalloc_matches_precondition_twice(prec):
     torch = pytest.importorskip("torch")
     kf = _lib()
     dev = torch.device("cuda", 0)
     with kf.Context(0) as ctx:
-        for call, (dg, da, rg, ra) in enumerate([(300, 513, 40, 64), (257, 130, 17, 0)]):
+        for call, (dg, da, rg, ra) in enumerate([(300, 513, 40, 64), (257, 130, 17, 0), (96, 200, 0, 30)]):
             rng = np.random.default_rng(100 + call)
             ua = np.linalg.qr(rng.standard_normal((da, max(ra, 1))))[0][:, :ra].astype(np.float32)
             ug = np.linalg.qr(rng.standard_normal((dg, max(rg, 1))))[0][:, :rg].astype(np.float32)
@@ -53,4 +53,4 @@ def test_noalloc_matches_precondition_twice(prec):
             a, b = s_new.double().cpu().numpy(), s_ref.double().cpu().numpy()
             assert np.isfinite(a).all()
             rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-            assert rel <= (1e-5 if prec == "fp32" else 2e-2), rel
+            assert rel <= {"fp32": 1e-5, "tf32": 5e-3, "bf16": 2e-2}[prec], rel
