@@ -15,6 +15,8 @@ Functions and the passages they follow:
   jacobi_eigh      "eig" of Alg. 1 / "Eigen_decomp" of Alg. 3 (cyclic Jacobi)
   qr               "QR_decomp" of Alg. 2 / Alg. 3 (Householder)
   srevd            Alg. 3 with the power iteration of Sec. 2.2
+  svd_jacobi       the "full SVD" of Alg. 2 (one-sided Hestenes Jacobi)
+  rsvd             Alg. 2 with the power iteration of Sec. 2.2, returning V~ (RS-KFAC, Alg. 4)
   damped_coef      Eq. (13), the diagonal (D + lam I)^-1 - I/lam
   precondition     Alg. 4, the M and S updates (Alg. 5 supplies U~ for V~)
   precondition_cols  the same S, selected columns only (full-size sampled checks)
@@ -78,6 +80,10 @@ def _load():
             lib.orc_srevd.argtypes = [i, _dp, i, _dp, i, i, _dp, _dp, _dp, _dp]
             lib.orc_srevd.restype = i
             lib.orc_damped_coef.argtypes = [i, _dp, d, _dp]
+            lib.orc_svd_jacobi.argtypes = [i, i, _dp, _dp, _dp, _dp, i, d]
+            lib.orc_svd_jacobi.restype = i
+            lib.orc_rsvd.argtypes = [i, _dp, i, _dp, i, i, _dp, _dp, _dp]
+            lib.orc_rsvd.restype = i
             lib.orc_precondition.argtypes = [i, i, _dp, _dp, _dp, i, _dp, _dp, i, d, _dp]
             ip = ctypes.POINTER(ctypes.c_int)
             lib.orc_precondition_cols.argtypes = [i, i, _dp, _dp, _dp, i, _dp, _dp, i, d, i, ip, _dp]
@@ -158,6 +164,42 @@ def srevd(factor, omega, power_iters: int, rank: int, return_basis: bool = False
     if return_basis:
         return u, dd, qb, cb
     return u, dd
+
+
+def svd_jacobi(a, max_sweeps: int = 100, tol: float = 1e-15):
+    """One-sided Jacobi thin SVD of a (m x n, m >= n): returns (U, s descending, V, sweeps)."""
+    a = _c(a)
+    m, n = a.shape
+    assert m >= n
+    u = np.empty((m, n))
+    s = np.empty(n)
+    v = np.empty((n, n))
+    sweeps = _load().orc_svd_jacobi(m, n, _p(a), _p(u), _p(s), _p(v), int(max_sweeps), float(tol))
+    return u, s, v, sweeps
+
+
+def rsvd(factor, omega, power_iters: int, rank: int, return_u: bool = False):
+    """Alg. 2 + power iterations on a symmetric PSD factor: returns (V~ d x r, S~ r)
+    [, U~ d x r when return_u]."""
+    f = _c(factor)
+    om = _c(omega)
+    d = f.shape[0]
+    k = om.shape[1]
+    r = min(rank, d)
+    v = np.empty((d, r))
+    s = np.empty(r)
+    u = np.empty((d, r)) if return_u else None
+    rc = _load().orc_rsvd(d, _p(f), k, _p(om), int(power_iters), int(rank), _p(v), _p(s),
+                          _p(u) if u is not None else None)
+    if rc < 0:
+        raise RuntimeError("oracle Jacobi did not converge")
+    return (v, s, u) if return_u else (v, s)
+
+
+def invert_rsvd(factor, omega, rank: int, power_iters: int, lam: float):
+    """The RS-KFAC inversion (Alg. 2 for V~ and S~, Eq. (13) coefficients): (V~, S~, coef)."""
+    v, s = rsvd(factor, omega, power_iters, rank)
+    return v, s, damped_coef(s, lam)
 
 
 def damped_coef(dvals, lam: float) -> np.ndarray:

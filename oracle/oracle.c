@@ -274,6 +274,143 @@ int orc_srevd(int d, const double* X, int k, const double* Omega, int q, int r,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Thin SVD by one-sided (Hestenes) Jacobi: the "full SVD of B^T" step of    */
+/* Alg. 2.                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* A (m x n, m >= n) = U diag(s) V^T with s descending, U (m x n) orthonormal
+ * columns (a zero singular value leaves a zero column), V (n x n) orthogonal.
+ * Column pairs (p, q) of a working copy W of A are rotated, W <- W J, until
+ * every pair is orthogonal to tol relative to the product of their norms;
+ * J is the plane rotation that zeroes the (p, q) entry of W^T W (the same 2x2
+ * symmetric Schur step as the two-sided Jacobi above). At the end s_j = |w_j|,
+ * U_j = w_j / s_j and V = the accumulated rotations. Returns the number of
+ * sweeps, or -1 if max_sweeps was reached first. */
+int orc_svd_jacobi(int m, int n, const double* A, double* U, double* s, double* V, int max_sweeps, double tol) {
+  double* W = (double*)malloc(sizeof(double) * (size_t)m * n);
+  memcpy(W, A, sizeof(double) * (size_t)m * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[(size_t)i * n + j] = (i == j) ? 1.0 : 0.0;
+  int sweeps = 0, converged = 0;
+  while (sweeps < max_sweeps) {
+    int rotated = 0;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = 0; i < m; ++i) {
+          const double wp = W[(size_t)i * n + p], wq = W[(size_t)i * n + q];
+          a += wp * wp;
+          b += wq * wq;
+          c += wp * wq;
+        }
+        if (a == 0.0 || b == 0.0 || fabs(c) <= tol * sqrt(a * b)) continue;
+        rotated = 1;
+        double zeta = (b - a) / (2.0 * c);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        for (int i = 0; i < m; ++i) { /* W <- W J */
+          const double wp = W[(size_t)i * n + p], wq = W[(size_t)i * n + q];
+          W[(size_t)i * n + p] = cs * wp - sn * wq;
+          W[(size_t)i * n + q] = sn * wp + cs * wq;
+        }
+        for (int i = 0; i < n; ++i) { /* V <- V J */
+          const double vp = V[(size_t)i * n + p], vq = V[(size_t)i * n + q];
+          V[(size_t)i * n + p] = cs * vp - sn * vq;
+          V[(size_t)i * n + q] = sn * vp + cs * vq;
+        }
+      }
+    }
+    ++sweeps;
+    if (!rotated) { converged = 1; break; }
+  }
+  for (int j = 0; j < n; ++j) {
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += W[(size_t)i * n + j] * W[(size_t)i * n + j];
+    s[j] = sqrt(nrm);
+    for (int i = 0; i < m; ++i) U[(size_t)i * n + j] = s[j] > 0.0 ? W[(size_t)i * n + j] / s[j] : 0.0;
+  }
+  /* stable descending order of s, applied to the columns of U and V */
+  int* idx = (int*)malloc(sizeof(int) * (size_t)n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  for (int i = 1; i < n; ++i) {
+    int v = idx[i], j = i - 1;
+    while (j >= 0 && s[idx[j]] < s[v]) { idx[j + 1] = idx[j]; --j; }
+    idx[j + 1] = v;
+  }
+  double* st = (double*)malloc(sizeof(double) * (size_t)n);
+  double* Ut = (double*)malloc(sizeof(double) * (size_t)m * n);
+  double* Vt = (double*)malloc(sizeof(double) * (size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    st[j] = s[idx[j]];
+    for (int i = 0; i < m; ++i) Ut[(size_t)i * n + j] = U[(size_t)i * n + idx[j]];
+    for (int i = 0; i < n; ++i) Vt[(size_t)i * n + j] = V[(size_t)i * n + idx[j]];
+  }
+  memcpy(s, st, sizeof(double) * (size_t)n);
+  memcpy(U, Ut, sizeof(double) * (size_t)m * n);
+  memcpy(V, Vt, sizeof(double) * (size_t)n * n);
+  free(idx); free(st); free(Ut); free(Vt); free(W);
+  return converged ? sweeps : -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Randomized SVD of a symmetric PSD factor: Alg. 2 (RSVD) with the power    */
+/* iterations of Sec. 2.2, as RS-KFAC (Alg. 4) uses it, returning V~.        */
+/* ------------------------------------------------------------------------ */
+
+/* X: d x d symmetric PSD factor; Omega: d x k (k = r + p). Steps: Y = X Omega;
+ * Q R = QR(Y); q times: Y = X Q, Q R = QR(Y); B = Q^T X (k x d); full SVD of
+ * B^T = U' diag(s) W'^T (one-sided Jacobi), so B = W' diag(s) U'^T: the left
+ * singular vectors of B are U_B = W' and its right singular vectors are
+ * V_B = U'. Outputs V~ = V_B[:, :r] (d x r), S~ = s[:r] and, when Ut is not
+ * NULL, U~ = Q U_B[:, :r] (d x r). When k >= d the factor is diagonalised
+ * directly (V~ = U~ = its leading eigenvectors, S~ = its eigenvalues). Returns
+ * r_eff = min(r, d), or -1 if a Jacobi solve did not converge. */
+int orc_rsvd(int d, const double* X, int k, const double* Omega, int q, int r, double* Vr, double* S, double* Ut) {
+  if (r > d) r = d;
+  if (k >= d) {
+    double* w = (double*)malloc(sizeof(double) * (size_t)d);
+    double* E = (double*)malloc(sizeof(double) * (size_t)d * d);
+    int rc = orc_jacobi_eigh(d, X, w, E, 100, 1e-15);
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < r; ++j) {
+        Vr[(size_t)i * r + j] = E[(size_t)i * d + j];
+        if (Ut) Ut[(size_t)i * r + j] = E[(size_t)i * d + j];
+      }
+    for (int j = 0; j < r; ++j) S[j] = w[j];
+    free(w); free(E);
+    return rc < 0 ? -1 : r;
+  }
+  double* Y = (double*)malloc(sizeof(double) * (size_t)d * k);
+  double* Q = (double*)malloc(sizeof(double) * (size_t)d * k);
+  double* R = (double*)malloc(sizeof(double) * (size_t)k * k);
+  double* Bt = (double*)malloc(sizeof(double) * (size_t)d * k);
+  double* Us = (double*)malloc(sizeof(double) * (size_t)d * k);
+  double* s = (double*)malloc(sizeof(double) * (size_t)k);
+  double* Ws = (double*)malloc(sizeof(double) * (size_t)k * k);
+  orc_matmul(d, k, d, X, 0, Omega, 0, Y);            /* Y = X Omega          */
+  orc_qr(d, k, Y, Q, R);                             /* Q R = QR_decomp(Y)   */
+  for (int it = 0; it < q; ++it) {                   /* power iterations     */
+    orc_matmul(d, k, d, X, 0, Q, 0, Y);
+    orc_qr(d, k, Y, Q, R);
+  }
+  orc_matmul(d, k, d, X, 1, Q, 0, Bt);               /* B^T = X^T Q (d x k)  */
+  int rc = orc_svd_jacobi(d, k, Bt, Us, s, Ws, 100, 1e-15);
+  for (int i = 0; i < d; ++i)                        /* V~ = V_B[:, :r]      */
+    for (int j = 0; j < r; ++j) Vr[(size_t)i * r + j] = Us[(size_t)i * k + j];
+  for (int j = 0; j < r; ++j) S[j] = s[j];
+  if (Ut) {                                          /* U~ = Q U_B[:, :r]    */
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < r; ++j) {
+        double acc = 0.0;
+        for (int t = 0; t < k; ++t) acc += Q[(size_t)i * k + t] * Ws[(size_t)t * k + j];
+        Ut[(size_t)i * r + j] = acc;
+      }
+  }
+  free(Y); free(Q); free(R); free(Bt); free(Us); free(s); free(Ws);
+  return rc < 0 ? -1 : r;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Damped low-rank inverse, Eq. (13): (U D U^T + lam I)^-1 = U diag(c) U^T + */
 /* I / lam with c_i = 1/(D_i + lam) - 1/lam.                                 */
 /* ------------------------------------------------------------------------ */

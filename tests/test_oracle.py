@@ -366,3 +366,99 @@ def test_qr_near_identity_stability():
     q, r = oracle.qr(y)
     np.testing.assert_allclose(q.T @ q, np.eye(k), atol=1e-14)
     np.testing.assert_allclose(q @ r, y, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- one-sided Jacobi SVD (Alg. 2)
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 2), (9, 4), (40, 17), (120, 60)])
+def test_svd_jacobi_vs_library(m, n):
+    """Singular values against LAPACK, the reconstruction U diag(s) V^T = A,
+    orthonormal U and V, and each singular triple A v_j = s_j u_j."""
+    a = rng(m * 100 + n).standard_normal((m, n))
+    u, s, v, sweeps = oracle.svd_jacobi(a)
+    assert sweeps > 0
+    np.testing.assert_allclose(s, np.linalg.svd(a, compute_uv=False), rtol=1e-12, atol=1e-13)
+    assert np.all(np.diff(s) <= 0)
+    np.testing.assert_allclose((u * s) @ v.T, a, atol=1e-12)
+    np.testing.assert_allclose(u.T @ u, np.eye(n), atol=1e-12)
+    np.testing.assert_allclose(v.T @ v, np.eye(n), atol=1e-12)
+    np.testing.assert_allclose(a @ v, u * s, atol=1e-12)
+
+
+def test_svd_jacobi_prescribed_and_degenerate():
+    """A = U0 diag(s0) V0^T with Haar factors gives back s0 (distinct values)
+    and the right singular subspaces; a zero column gives a zero singular value
+    and a zero left vector, without breaking the others."""
+    s0 = np.array([5.0, 2.0, 1.0, 0.5, 1e-3])
+    u0 = inputs.haar(3, 30)[:, :5]
+    v0 = inputs.haar(4, 5)
+    u, s, v, _ = oracle.svd_jacobi((u0 * s0) @ v0.T)
+    np.testing.assert_allclose(s, s0, rtol=1e-12)
+    np.testing.assert_allclose(np.abs(v.T @ v0), np.eye(5), atol=1e-10)   # same vectors up to sign
+    a = rng(5).standard_normal((12, 4))
+    a[:, 2] = 0.0
+    u, s, v, _ = oracle.svd_jacobi(a)
+    assert s[-1] == 0.0 and np.all(u[:, -1] == 0.0)
+    np.testing.assert_allclose(s[:3], np.linalg.svd(a, compute_uv=False)[:3], rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------- RSVD (Alg. 2, RS-KFAC)
+
+def test_rsvd_exact_recovery_low_rank():
+    """rank(X) <= r: the singular values, the V~ subspace and the rank-r
+    reconstruction V~ S~ V~^T are exact (no truncation and no projection error)."""
+    s_true = np.array([4.0, 2.0, 1.0, 0.3, 0.05])
+    x, v_true, _ = inputs.low_rank_factor(21, 90, s_true)
+    om = inputs.gaussian(21, (90, 9))
+    v, s = oracle.rsvd(x, om, 0, 5)
+    np.testing.assert_allclose(s, s_true, rtol=1e-12)
+    np.testing.assert_allclose(v @ v.T, v_true @ v_true.T, atol=1e-12)
+    np.testing.assert_allclose((v * s) @ v.T, x, atol=1e-12)
+
+
+def test_rsvd_singular_values_match_library_svd_of_b():
+    """S~ are the leading singular values of B = Q^T X for the basis Q the
+    oracle's own QR gives (LAPACK SVD of that B), and with k >= d the RSVD is
+    the full eigendecomposition of the PSD factor."""
+    x = rand_psd(60, 22, rank=40)
+    om = inputs.gaussian(22, (60, 14))
+    q, _ = oracle.qr(oracle.matmul(x, om))
+    q, _ = oracle.qr(oracle.matmul(x, q))
+    b = q.T @ x
+    _, s = oracle.rsvd(x, om, 1, 10)
+    np.testing.assert_allclose(s, np.linalg.svd(b, compute_uv=False)[:10], rtol=1e-11)
+    v, s = oracle.rsvd(x[:12, :12], inputs.gaussian(22, (12, 14)), 1, 12)
+    w = np.linalg.eigvalsh(x[:12, :12])[::-1]
+    np.testing.assert_allclose(s, w, rtol=1e-11, atol=1e-13)
+
+
+def test_rsvd_v_is_more_accurate_than_u_and_srevd():
+    """Sec. 2.3: V~ approximates the leading eigenvectors better than U~ = Q U_B
+    and better than SREVD's Q P_C (mean subspace error over seeds, decaying
+    spectrum, no power iteration so the difference is not hidden)."""
+    d, r, p = 120, 8, 4
+    spec = np.arange(1, d + 1, dtype=float) ** -1.0
+    x, v_all, _ = inputs.low_rank_factor(23, d, spec)
+    vr = v_all[:, :r]
+    err_v, err_u, err_sre = [], [], []
+    for seed in range(12):
+        om = inputs.gaussian(100 + seed, (d, r + p))
+        v, s, u = oracle.rsvd(x, om, 0, r, return_u=True)
+        us, _ = oracle.srevd(x, om, 0, r)
+        proj = lambda m: np.linalg.norm(m @ m.T - vr @ vr.T)
+        err_v.append(proj(v)); err_u.append(proj(u)); err_sre.append(proj(us))
+    assert np.mean(err_v) < 0.8 * np.mean(err_u)
+    assert np.mean(err_v) < 0.8 * np.mean(err_sre)
+
+
+def test_rsvd_truncation_dominates_projection_error():
+    """Sec. 2.3.1: with V~ the reconstruction error ||X - V~ S~ V~^T||_F is close
+    to the truncation error of the exact rank-r eigendecomposition (the
+    projection error is small), for a fast-decaying spectrum."""
+    d, r = 100, 10
+    spec = np.arange(1, d + 1, dtype=float) ** -2.0
+    x, _, _ = inputs.low_rank_factor(24, d, spec)
+    trunc = np.sqrt(np.sum(spec[r:] ** 2))
+    v, s = oracle.rsvd(x, inputs.gaussian(24, (d, r + 10)), 1, r)
+    err = np.linalg.norm(x - (v * s) @ v.T)
+    assert trunc <= err <= 1.05 * trunc
