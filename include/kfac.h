@@ -308,6 +308,16 @@ typedef enum {
                                        squares the remaining error again. 0: sweep until a
                                        sweep rotates no pair (every pair cosine <=
                                        KFAC_OPT_EIG_TOL) */
+  KFAC_OPT_INVERT_METHOD = 13,      /* [0]: 0 = SREVD (Alg. 3, SRE-KFAC): U = Q P from the
+                                       eigendecomposition of C = Q^T F Q; 1 = RSVD (Alg. 2, as
+                                       RS-KFAC's Alg. 4 uses it): U = V~, the leading right
+                                       singular vectors of B = Q^T F, and D = its singular
+                                       values (Sec. 2.3: V~ carries a much smaller projection
+                                       error than SREVD's U). B^T is orthonormalised by the same
+                                       shifted CholeskyQR (B^T = Q2 R2) and R2 = Q2^T B^T is
+                                       factored by one-sided Jacobi, so B B^T is never formed.
+                                       Both apply to kfac_rsvd_invert and its grouped form; the
+                                       direct path (k >= d) is the same for both */
   KFAC_OPT_GROUP_STREAMS = 12,      /* [16]: streams a grouped call forks from the context
                                        stream, 1..32 (1 = every item in turn on the context
                                        stream). More streams overlap more of the items'

@@ -64,6 +64,7 @@ struct kfac_ctx {
   int eig_refine_fp64 = 0;
   long long wait_cycles = kfac::kDefaultWaitCycles;
   int group_streams = 16;  // side streams a grouped call may fork (KFAC_OPT_GROUP_STREAMS)
+  int invert_method = 0;   // KFAC_OPT_INVERT_METHOD: 0 SREVD (Alg. 3), 1 RSVD V~ (Alg. 2, RS-KFAC)
 };
 
 namespace {
@@ -211,7 +212,7 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f) {
 // operands, split over K with FP32 partials summed with compensation (and
 // symmetrised) into FP64.
 kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const float* Bm, long long ld, int k,
-                     int d, kfac_precision prec, double* out, int stage, float* out32) {
+                     int d, kfac_precision prec, double* out, int stage, float* out32, int symmetrize = 1) {
   GemmDesc<float> g = {};
   g.M = k; g.N = k; g.K = d;
   g.A = A; g.sam = ld; g.sak = 1;
@@ -222,8 +223,8 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
   StageScope sc(ctx, stage);
   CK(gemm_f32(g, prec, ctx->stream));
-  CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, 1, ctx->dflags, ctx->stream,
-                       out32));
+  CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, symmetrize, ctx->dflags,
+                       ctx->stream, out32));
   return KFAC_OK;
 }
 
@@ -320,6 +321,60 @@ kfac_status check_invert(const kfac_invert_desc& a, int* r_out, int* k_out) {
   return KFAC_OK;
 }
 
+// Lift U (d x r) = Qb P[:, :r] from the basis Qb^T (k x d, row stride L.dp) and
+// P[:, :r]^T in L.pt: Qb transposed into L.qn, then a tcgen05 product with both
+// operands K-contiguous.
+kfac_status lift(kfac_ctx* ctx, const InvertLayout& L, const float* Qbt, const kfac_invert_desc& a, int d, int k,
+                 int r) {
+  STAGE(ctx, ST_LIFT);
+  float* Qn = at<float>(ctx, L.qn);
+  CK(transpose_f32(Qbt, L.dp, k, d, Qn, L.kp, ctx->stream));
+  GemmDesc<float> g = {};
+  g.M = d; g.N = r; g.K = k;
+  g.A = Qn; g.sam = L.kp; g.sak = 1;
+  g.B = at<float>(ctx, L.pt); g.sbn = L.kp; g.sbk = 1;
+  g.D = a.U; g.ldd = a.ldu;
+  g.alpha = 1.0f; g.zsplit = 1;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+  CK(gemm_f32(g, KFAC_PREC_FP32, ctx->stream));
+  return KFAC_OK;
+}
+
+// RS-KFAC's inverse factors (Alg. 2 with the power iterations of Sec. 2.2, as
+// Alg. 4 uses them), from the final basis Q^T (in cur): B = Q^T F (k x d, held
+// as B^T's columns in the rows of Z^T); B^T = Q2 R2 by the same shifted
+// CholeskyQR (Q2 orthonormal, d x k); R2 = Q2^T B^T (k x k, FP32-accurate
+// product kept in FP64); the SVD R2 = U_R diag(s) W^T by one-sided Jacobi, so
+// B^T = (Q2 U_R) diag(s) W^T and the right singular vectors of B are
+// V_B = Q2 U_R. Outputs V~ = (Q2 U_R)[:, :r] in U, D = s[:r] and the Eq. (13)
+// coefficients from s. The SVD of the triangular-like R2 never forms B B^T,
+// so the singular values keep an absolute error ~u s_1 (not u s_1^2 / s_i).
+kfac_status rsvd_tail(kfac_ctx* ctx, const kfac_invert_desc& a, const InvertLayout& L, float* cur, float* other, int d,
+                      int k, int r, const float* F, int ldf) {
+  cudaStream_t s = ctx->stream;
+  kfac_status st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);  // Z^T = Q^T F = B
+  if (st != KFAC_OK) return st;
+  float* c1 = at<float>(ctx, L.om);  // Omega^T is dead: B^T's basis is built there and in cur
+  CK(cudaMemcpyAsync(c1, other, sizeof(float) * (size_t)k * L.dp, cudaMemcpyDeviceToDevice, s));
+  st = orthonormalise(ctx, L, c1, cur, k, d, ctx->cholqr_passes, true);  // Q2^T in c1
+  if (st != KFAC_OK) return st;
+  st = gram_f64(ctx, L, c1, other, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.c), ST_PROJ, at<float>(ctx, L.c32),
+                0);  // R2 = Q2^T B^T, not symmetric
+  if (st != KFAC_OK) return st;
+  {
+    STAGE(ctx, ST_EIG);
+    CK(svd_jacobi_f32(at<float>(ctx, L.c32), k, ctx->eig_max_sweeps, (float)ctx->eig_tol, (float)ctx->eig_stop_tol,
+                      at<double>(ctx, L.x), at<double>(ctx, L.lam), at<float>(ctx, L.jac), ctx->dflags, ctx->dstats,
+                      s));
+  }
+  {
+    STAGE(ctx, ST_SELECT);
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, a.lambda, at<float>(ctx, L.pt), L.kp, a.D,
+                  a.coef, nullptr, 0, s, /*singular=*/1));
+  }
+  return lift(ctx, L, c1, a, d, k, r);
+}
+
 // The randomized inversion of one factor, enqueued on ctx->stream, with its
 // workspace slices offset by `base` bytes.
 kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L, size_t base) {
@@ -369,6 +424,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     if (st != KFAC_OK) return st;
     std::swap(cur, other);
   }
+  if (ctx->invert_method == 1) return rsvd_tail(ctx, a, L, cur, other, d, k, r, F, ldf);
   // Newton-Schulz polish of the final basis, in the k x k space: M = (3I - Q^T Q)/2
   // makes Q M orthonormal to second order; the Rayleigh-Ritz step below uses
   // Q M (C <- M C M, X <- M X) without touching the d x k basis.
@@ -414,26 +470,14 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     STAGE(ctx, ST_POLISH);
     CK(polish_vectors_f32(at<double>(ctx, L.x), k, pw32, s));
   }
-  float* Pt = at<float>(ctx, L.pt);
   {
     STAGE(ctx, ST_SELECT);
-    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, a.lambda, Pt, L.kp, a.D, a.coef, nullptr, 0,
-                  s));
+    CK(eig_select(at<double>(ctx, L.x), at<double>(ctx, L.lam), k, r, a.lambda, at<float>(ctx, L.pt), L.kp, a.D,
+                  a.coef, nullptr, 0, s));
   }
   // Lift: U (d x r) = Q P[:, :r], both operands K-contiguous (Q from Q^T by a
   // transpose, P[:, :r]^T from the selection) so the product runs on tcgen05.
-  STAGE(ctx, ST_LIFT);
-  float* Qn = at<float>(ctx, L.qn);
-  CK(transpose_f32(cur, L.dp, k, d, Qn, L.kp, s));
-  GemmDesc<float> g = {};
-  g.M = d; g.N = r; g.K = k;
-  g.A = Qn; g.sam = L.kp; g.sak = 1;
-  g.B = Pt; g.sbn = L.kp; g.sbk = 1;
-  g.D = a.U; g.ldd = a.ldu;
-  g.alpha = 1.0f; g.zsplit = 1;
-  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
-  CK(gemm_f32(g, KFAC_PREC_FP32, s));
-  return KFAC_OK;
+  return lift(ctx, L, cur, a, d, k, r);
 }
 
 
@@ -750,6 +794,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
     case KFAC_OPT_EIG_REFINE_FP64:
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->eig_refine_fp64 = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_INVERT_METHOD:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->invert_method = (int)v;
       return KFAC_OK;
     case KFAC_OPT_GROUP_STREAMS:
       if (v < 1 || v > kMaxSideStreams) return KFAC_ERR_INVALID_ARG;

@@ -171,6 +171,18 @@ cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_swe
                            double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
                            cudaStream_t s, const float* C32 = nullptr, long long ld32 = 0);
 
+// One-sided Jacobi on the columns of the k x k FP32 matrix held in gscratch
+// (row-major; the factor eig_jacobi_f32 writes there), with the device scalar
+// `shift`: writes X (column j = unit column j after the rotations) and
+// lam_j = |w_j|^2 - shift (unsorted).
+cudaError_t jacobi_columns(int k, int max_sweeps, float tol, float stop_tol, double* X, double* lam, float* gscratch,
+                           const double* shift, int* flags, unsigned long long* stats, cudaStream_t s);
+// Thin SVD of a k x k FP32 matrix W (row-major, dense) by one-sided Jacobi:
+// W = U diag(sigma) V^T; writes X = U (column j = left singular vector j) and
+// lam_j = sigma_j^2 (unsorted). gscratch: eig_scratch_floats(k) floats.
+cudaError_t svd_jacobi_f32(const float* W32, int k, int max_sweeps, float tol, float stop_tol, double* X, double* lam,
+                           float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s);
+
 // G <- (3 I - G) / 2 in place (k x k FP64): one Newton-Schulz step towards
 // G^-1/2 for a Gram G = Q^T Q near I, so Q (3I - G)/2 is orthonormal to
 // second order in ||G - I||.
@@ -198,7 +210,8 @@ cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s);
 // Pt (r x k FP32, row stride ldpt, row t = eigenvector t; optional), D and coef
 // (FP32, Eq. (13)), and optionally Uout (k x r into a strided FP32 matrix, for
 // the k >= d path).
+// singular != 0: lam holds squared singular values; D = sqrt(max(lam, 0)).
 cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* Pt, long long ldpt,
-                       float* D, float* coef, float* Uout, long long ldu, cudaStream_t s);
+                       float* D, float* coef, float* Uout, long long ldu, cudaStream_t s, int singular = 0);
 
 }  // namespace kfac

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ 
                                                       int k, int r, float lambda, float* __restrict__ Pt,
                                                       long long ldpt, float* __restrict__ D,
                                                       float* __restrict__ coef, float* __restrict__ Uout,
-                                                      long long ldu) {
+                                                      long long ldu, int singular) {
   // Every CTA ranks the k eigenvalues (from shared memory) and copies its
   // slice of the selected columns; CTA 0 also writes D and the coefficients.
   // Ranking compares order-preserving integer keys of the FP64 values (an
@@ -479,6 +479,7 @@ __global__ void __launch_bounds__(1024) k_eig_select(const double* __restrict__ 
   if (blockIdx.x == 0) {
     for (int t = tid; t < r; t += blockDim.x) {
       double v = lam[order[t]];
+      if (singular) v = sqrt(v > 0.0 ? v : 0.0);  // singular value from its square
       double dv = v > 0.0 ? v : 0.0;
       if (D) D[t] = (float)v;
       if (coef) coef[t] = (float)(1.0 / (dv + (double)lambda) - 1.0 / (double)lambda);
@@ -526,6 +527,21 @@ cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_swe
   double* shift = reinterpret_cast<double*>(gscratch + (((size_t)k * k + 1) & ~(size_t)1));
   cudaError_t e = chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift, C32, ld32);
   if (e != cudaSuccess) return e;
+  return jacobi_columns(k, max_sweeps, tol, stop_tol, X, lam, gscratch, shift, flags, stats, s);
+}
+
+cudaError_t svd_jacobi_f32(const float* W32, int k, int max_sweeps, float tol, float stop_tol, double* X, double* lam,
+                           float* gscratch, int* flags, unsigned long long* stats, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  double* shift = reinterpret_cast<double*>(gscratch + (((size_t)k * k + 1) & ~(size_t)1));
+  cudaError_t e = cudaMemcpyAsync(gscratch, W32, sizeof(float) * (size_t)k * k, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(shift, 0, sizeof(double), s)) != cudaSuccess) return e;
+  return jacobi_columns(k, max_sweeps, tol, stop_tol, X, lam, gscratch, shift, flags, stats, s);
+}
+
+cudaError_t jacobi_columns(int k, int max_sweeps, float tol, float stop_tol, double* X, double* lam, float* gscratch,
+                           const double* shift, int* flags, unsigned long long* stats, cudaStream_t s) {
   // b = ceil(k / 2nc) <= 8 where the cluster allows it: a cross round's b pairs
   // then leave each sub-partition at most two busy warps.
   int nc = (k + 15) / 16;
@@ -545,6 +561,12 @@ cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_swe
       default: return cudaErrorInvalidValue;
     }
   }
+  // Blocks of 17 or 18 columns (k in (512, 576] on the 16-CTA limit): one warp
+  // per pair needs 17-18 warps, so every column pair of an inner round runs at
+  // once with the top column in registers (16 warps would take two passes with
+  // both columns through shared memory).
+  if (kp / 128 == 5 && b == 17) return launch_eig<5, 17 * 32>(a, nc, smem, s);
+  if (kp / 128 == 5 && b == 18) return launch_eig<5, 18 * 32>(a, nc, smem, s);
   switch (kp / 128) {
     case 1: return launch_eig<1, EIG_THREADS_MAX>(a, nc, smem, s);
     case 2: return launch_eig<2, EIG_THREADS_MAX>(a, nc, smem, s);
@@ -746,13 +768,13 @@ cudaError_t convert_f64_to_f32(const double* in, long long n, float* out, cudaSt
 }
 
 cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* Pt, long long ldpt,
-                       float* D, float* coef, float* Uout, long long ldu, cudaStream_t s) {
+                       float* D, float* coef, float* Uout, long long ldu, cudaStream_t s, int singular) {
   if (k <= 0) return cudaSuccess;
   const long long total = (long long)k * r;
   int grid = (int)((total + 4095) / 4096);
   grid = grid < 1 ? 1 : (grid > 152 ? 152 : grid);
   k_eig_select<<<grid, 1024, (sizeof(double) + sizeof(int)) * k + 8, s>>>(X, lam, k, r, lambda, Pt, ldpt, D, coef,
-                                                                           Uout, ldu);
+                                                                           Uout, ldu, singular);
   note_launch();
   return cudaGetLastError();
 }
