@@ -254,6 +254,23 @@ KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, c
                                                const float* U_g, int ld_ug, const float* coef_g, int r_g,
                                                float lambda, kfac_precision prec, float* S, int lds);
 
+/* Autotuner of a grouped inversion's schedule on this GPU: the number of
+ * streams a grouped call forks (KFAC_OPT_GROUP_STREAMS), the cluster size of
+ * the multi-CTA Cholesky (KFAC_OPT_CHOL_CLUSTER; only when a sketch width
+ * exceeds the one-CTA kernel's 236) and the CTA count split-K products may
+ * fill (KFAC_OPT_SPLIT_TARGET). Runs kfac_rsvd_invert_grouped(ctx, count,
+ * descs) once plus twice timed (CUDA events on the context stream) per
+ * candidate of a coordinate descent from the current settings, writing the
+ * descriptors' outputs as a call would, and keeps the fastest settings in the
+ * context. cache_path (may be NULL): a text file of earlier results, one line
+ * per device name and shape signature (the factors' d, k, power iterations
+ * and precision, and the inversion method); a hit is applied without timing,
+ * a new result is appended. chosen (may be NULL, 4 ints) receives the streams,
+ * cluster size, split target and 1 if the result came from the cache. Not
+ * during stream capture (it synchronises). */
+KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_invert_desc* descs,
+                                          const char* cache_path, int* chosen);
+
 /* Synchronise the context's stream, return KFAC_OK or the most severe device
  * condition recorded since the last call (by any entry point, grouped items
  * included), store the raw KFAC_FLAG_* bits in *flags (may be NULL) and clear
@@ -308,6 +325,16 @@ typedef enum {
                                        squares the remaining error again. 0: sweep until a
                                        sweep rotates no pair (every pair cosine <=
                                        KFAC_OPT_EIG_TOL) */
+  KFAC_OPT_SPLIT_TARGET = 15,       /* [0 = 152]: a tensor-core product with fewer output tiles
+                                       than 4/5 of this many CTAs and K >= 1024 splits K into
+                                       chunks of at least 512 so that up to this many CTAs
+                                       share it, summed by a reducing epilogue; -1 = never */
+  KFAC_OPT_CHOL_CLUSTER = 14,       /* [0 = automatic]: CTAs of the multi-CTA FP32/FP64
+                                       Cholesky used where the one-CTA kernel's shared memory
+                                       cannot hold the k x k Gram (k > 236), 1..16; raised to
+                                       the fewest CTAs that hold their rows. Fewer CTAs take
+                                       fewer cluster barriers and broadcasts per panel and
+                                       leave SMs to the other factors of a grouped call */
   KFAC_OPT_INVERT_METHOD = 13,      /* [0]: 0 = SREVD (Alg. 3, SRE-KFAC): U = Q P from the
                                        eigendecomposition of C = Q^T F Q; 1 = RSVD (Alg. 2, as
                                        RS-KFAC's Alg. 4 uses it): U = V~, the leading right

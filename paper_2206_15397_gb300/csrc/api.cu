@@ -1,5 +1,6 @@
 // C ABI of libkfac: context, workspace, argument checks and the orchestration
 // of the kernels that make up each entry point.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -65,6 +66,8 @@ struct kfac_ctx {
   long long wait_cycles = kfac::kDefaultWaitCycles;
   int group_streams = 16;  // side streams a grouped call may fork (KFAC_OPT_GROUP_STREAMS)
   int invert_method = 0;   // KFAC_OPT_INVERT_METHOD: 0 SREVD (Alg. 3), 1 RSVD V~ (Alg. 2, RS-KFAC)
+  int chol_cluster = 0;    // KFAC_OPT_CHOL_CLUSTER: CTAs of the multi-CTA Cholesky (0 = automatic)
+  int split_target = 0;    // KFAC_OPT_SPLIT_TARGET: CTAs a split-K product may fill (0 = 152, -1 = no split)
 };
 
 namespace {
@@ -220,7 +223,7 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.D = at<float>(ctx, L.part); g.ldd = k;
   g.alpha = 1.0f;
   g.zsplit = L.nsplit; g.kchunk = L.kchunk; g.zstride = (long long)k * k;
-  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   StageScope sc(ctx, stage);
   CK(gemm_f32(g, prec, ctx->stream));
   CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, symmetrize, ctx->dflags,
@@ -241,7 +244,7 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
   g.D = out; g.ldd = ldo; g.d_trans = 1;
   g.alpha = 1.0f; g.zsplit = 1;
   g.ws = at<float>(ctx, L.skws); g.ws_floats = L.skws_floats;
-  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   STAGE(ctx, ST_SKETCH);
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
@@ -268,7 +271,7 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       const bool fp64 = (final_basis || !ctx->cholqr_inner_fp32) &&
                         (pass >= ctx->cholqr_fp32_passes || (pass + 1 == passes && ctx->cholqr_fp32_passes < passes));
       CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
-                      ctx->stream, nullptr, at<float>(ctx, L.g32), k));
+                      ctx->stream, nullptr, at<float>(ctx, L.g32), k, ctx->chol_cluster));
     }
     {
       STAGE(ctx, ST_TRSM);
@@ -284,7 +287,7 @@ kfac_status eigensolve(kfac_ctx* ctx, const double* C, const float* C32, long lo
   {
     STAGE(ctx, ST_EIG);
     CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, (float)ctx->eig_stop_tol, X, lam, jac,
-                      ctx->dflags, ctx->dstats, ctx->stream, C32, ld32));
+                      ctx->dflags, ctx->dstats, ctx->stream, C32, ld32, ctx->chol_cluster));
   }
   STAGE(ctx, ST_REFINE);
   for (int it = 0; it < ctx->eig_refine; ++it) {
@@ -335,7 +338,7 @@ kfac_status lift(kfac_ctx* ctx, const InvertLayout& L, const float* Qbt, const k
   g.B = at<float>(ctx, L.pt); g.sbn = L.kp; g.sbk = 1;
   g.D = a.U; g.ldd = a.ldu;
   g.alpha = 1.0f; g.zsplit = 1;
-  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   CK(gemm_f32(g, KFAC_PREC_FP32, ctx->stream));
   return KFAC_OK;
 }
@@ -363,9 +366,10 @@ kfac_status rsvd_tail(kfac_ctx* ctx, const kfac_invert_desc& a, const InvertLayo
   if (st != KFAC_OK) return st;
   {
     STAGE(ctx, ST_EIG);
-    CK(svd_jacobi_f32(at<float>(ctx, L.c32), k, ctx->eig_max_sweeps, (float)ctx->eig_tol, (float)ctx->eig_stop_tol,
-                      at<double>(ctx, L.x), at<double>(ctx, L.lam), at<float>(ctx, L.jac), ctx->dflags, ctx->dstats,
-                      s));
+    // Swept to full convergence (every pair cosine <= KFAC_OPT_EIG_TOL): no
+    // refinement step follows here to square away an early stop's residue.
+    CK(svd_jacobi_f32(at<float>(ctx, L.c32), k, ctx->eig_max_sweeps, (float)ctx->eig_tol, 0.0f, at<double>(ctx, L.x),
+                      at<double>(ctx, L.lam), at<float>(ctx, L.jac), ctx->dflags, ctx->dstats, s));
   }
   {
     STAGE(ctx, ST_SELECT);
@@ -565,7 +569,7 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.D = T; g.ldd = P.ld_t;
     g.alpha = 1.0f; g.colscale = coef_a; g.zsplit = 1;
     g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats;
-    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
     CK(gemm_f32(g, prec, s));
   }
   {  // M^T = U_a T^T + J^T / lambda
@@ -576,7 +580,7 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.B = T; g.sbn = P.ld_t; g.sbk = 1;
     g.D = Mt; g.ldd = P.ld_mt;
     g.alpha = 1.0f; g.beta = inv_lam; g.C0 = J; g.ldc = ldj; g.c0_trans = 1; g.zsplit = 1;
-    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
     CK(gemm_f32(g, prec, s));
   }
   if (r_g > 0) {  // T2^T = M^T U_g diag(c_g), through U_g^T
@@ -589,7 +593,7 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.D = T2t; g.ldd = P.ld_t2;
     g.alpha = 1.0f; g.colscale = coef_g; g.zsplit = 1;
     g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats;
-    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
     CK(gemm_f32(g, prec, s));
   }
   {  // S = U_g T2 + M / lambda  (M read through M^T)
@@ -600,7 +604,7 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.B = T2t; g.sbn = P.ld_t2; g.sbk = 1;
     g.D = S; g.ldd = lds;
     g.alpha = 1.0f; g.beta = inv_lam; g.C0 = Mt; g.ldc = P.ld_mt; g.c0_trans = 1; g.zsplit = 1;
-    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+    g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
     CK(gemm_f32(g, prec, s));
   }
   return KFAC_OK;
@@ -795,6 +799,14 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->eig_refine_fp64 = (int)v;
       return KFAC_OK;
+    case KFAC_OPT_SPLIT_TARGET:
+      if (v < -1 || v > 4096) return KFAC_ERR_INVALID_ARG;
+      ctx->split_target = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_CHOL_CLUSTER:
+      if (v < 0 || v > 16) return KFAC_ERR_INVALID_ARG;
+      ctx->chol_cluster = (int)v;
+      return KFAC_OK;
     case KFAC_OPT_INVERT_METHOD:
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->invert_method = (int)v;
@@ -862,7 +874,7 @@ KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const floa
   g.D = D; g.ldd = ldd;
   g.alpha = alpha; g.beta = beta; g.C0 = D; g.ldc = ldd;
   g.zsplit = 1; g.ws = at<float>(ctx, o_ws); g.ws_floats = ws_floats;
-  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles;
+  g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
 }
@@ -1058,6 +1070,132 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
     CK(cudaStreamWaitEvent(main_s, ctx->join_ev[q], 0));
   }
   return first_err;
+}
+
+// ---- autotuner ----------------------------------------------------------------
+
+// Shape signature of a grouped inversion (order-independent): factor count and
+// a hash of every factor's (d, k, power iterations, precision), plus the
+// inversion method.
+static unsigned long long invert_signature(const kfac_ctx* ctx, int count, const kfac_invert_desc* descs) {
+  std::vector<unsigned long long> keys(count);
+  for (int f = 0; f < count; ++f) {
+    const kfac_invert_desc& a = descs[f];
+    keys[f] = ((unsigned long long)a.d << 32) ^ ((unsigned long long)(a.rank + a.oversample) << 12) ^
+              ((unsigned long long)a.power_iters << 4) ^ (unsigned long long)a.prec;
+  }
+  std::sort(keys.begin(), keys.end());
+  unsigned long long h = 1469598103934665603ull ^ (unsigned long long)count ^ ((unsigned long long)ctx->invert_method << 40);
+  for (unsigned long long k : keys) {  // FNV-1a over the sorted keys
+    for (int b = 0; b < 8; ++b) {
+      h ^= (k >> (8 * b)) & 0xffull;
+      h *= 1099511628211ull;
+    }
+  }
+  return h;
+}
+
+// Looks for "<device> <signature> <streams> <chol_cluster> <split_target> <ms>"
+// in the cache file; fills cfg[3] and returns true when found.
+static bool cache_lookup(const char* path, const char* dev, unsigned long long sig, int* cfg) {
+  FILE* fp = fopen(path, "r");
+  if (!fp) return false;
+  char line[512];
+  bool found = false;
+  while (fgets(line, sizeof line, fp)) {
+    char name[256];
+    unsigned long long s = 0;
+    int a = 0, b = 0, c = 0;
+    double ms = 0.0;
+    if (sscanf(line, "%255[^|]|%llx %d %d %d %lf", name, &s, &a, &b, &c, &ms) == 6 && s == sig &&
+        strcmp(name, dev) == 0) {
+      cfg[0] = a; cfg[1] = b; cfg[2] = c;
+      found = true;  // the last entry for this key wins
+    }
+  }
+  fclose(fp);
+  return found;
+}
+
+KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_invert_desc* descs,
+                                          const char* cache_path, int* chosen) {
+  if (!ctx || count <= 0 || !descs) return KFAC_ERR_INVALID_ARG;
+  for (int f = 0; f < count; ++f) {
+    int r = 0, k = 0;
+    kfac_status st = check_invert(descs[f], &r, &k);
+    if (st != KFAC_OK) return st;
+  }
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, ctx->device));
+  for (char* c = prop.name; *c; ++c)
+    if (*c == '|' || *c == '\n') *c = ' ';
+  const unsigned long long sig = invert_signature(ctx, count, descs);
+  int cfg[3] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target};
+  bool cached = cache_path && cache_lookup(cache_path, prop.name, sig, cfg);
+  double best_ms = 0.0;
+  if (!cached) {
+    bool big_k = false;
+    for (int f = 0; f < count; ++f) {
+      const int k = descs[f].rank + descs[f].oversample;
+      if (k > 236 && k < descs[f].d) big_k = true;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return KFAC_ERR_CUDA; }
+    // One warm-up and two timed grouped inversions per candidate.
+    auto run = [&](const int* c, double* ms) -> kfac_status {
+      ctx->group_streams = c[0]; ctx->chol_cluster = c[1]; ctx->split_target = c[2];
+      kfac_status st = kfac_rsvd_invert_grouped(ctx, count, descs);
+      if (st != KFAC_OK) return st;
+      if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+      for (int it = 0; it < 2 && st == KFAC_OK; ++it) st = kfac_rsvd_invert_grouped(ctx, count, descs);
+      if (st != KFAC_OK) return st;
+      if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        return KFAC_ERR_CUDA;
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return KFAC_ERR_CUDA;
+      *ms = t / 2.0;
+      return KFAC_OK;
+    };
+    // Coordinate descent over the three knobs, from the current settings.
+    const int streams_c[] = {4, 8, 16, 32};
+    const int chol_c[] = {0, 8, 12};
+    const int split_c[] = {0, 304, -1};
+    kfac_status st = run(cfg, &best_ms);
+    for (int dim = 0; dim < 3 && st == KFAC_OK; ++dim) {
+      const int* cand = dim == 0 ? streams_c : (dim == 1 ? chol_c : split_c);
+      const int n = dim == 0 ? 4 : 3;
+      if (dim == 1 && !big_k) continue;  // no factor uses the multi-CTA Cholesky
+      for (int i = 0; i < n && st == KFAC_OK; ++i) {
+        if (cand[i] == cfg[dim]) continue;
+        int trial[3] = {cfg[0], cfg[1], cfg[2]};
+        trial[dim] = cand[i];
+        double ms = 0.0;
+        st = run(trial, &ms);
+        if (st == KFAC_OK && ms < best_ms) {
+          best_ms = ms;
+          cfg[dim] = cand[i];
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != KFAC_OK) return st;
+    if (cache_path) {
+      FILE* fp = fopen(cache_path, "a");
+      if (fp) {
+        fprintf(fp, "%s|%llx %d %d %d %.4f\n", prop.name, sig, cfg[0], cfg[1], cfg[2], best_ms);
+        fclose(fp);
+      }
+    }
+  }
+  ctx->group_streams = cfg[0];
+  ctx->chol_cluster = cfg[1];
+  ctx->split_target = cfg[2];
+  if (chosen) { chosen[0] = cfg[0]; chosen[1] = cfg[1]; chosen[2] = cfg[2]; chosen[3] = cached ? 1 : 0; }
+  return KFAC_OK;
 }
 
 KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const float* J, int ldj,

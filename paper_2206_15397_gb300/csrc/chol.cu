@@ -332,22 +332,27 @@ size_t chol_smem_bytes(int k, int nloc, int B, size_t elt) {
   return elt * ((size_t)nloc * k + 2 * (size_t)B * B + B + 2 * (size_t)k * B) + 16;
 }
 
+// Cluster size nc_pref > 0 asks for that many CTAs (raised to the fewest whose
+// shared memory holds the rows); 0 = one CTA per 16 rows, at most 16.
 template <typename T>
 cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, int* flags,
-                        unsigned long long* stats, cudaStream_t s, double* shift_out) {
+                        unsigned long long* stats, cudaStream_t s, double* shift_out, int nc_pref) {
   {
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cluster<T>), kSmemOptin, true);
     if (e != cudaSuccess) return e;
   }
-  int nc = (k + 15) / 16;
+  int nc = nc_pref > 0 ? nc_pref : (k + 15) / 16;
   if (nc > 16) nc = 16;
   if (nc < 1) nc = 1;
-  int B = 16;
-  int nloc = (k + nc - 1) / nc;
-  size_t smem = chol_smem_bytes(k, nloc, B, sizeof(T));
-  while (smem > (size_t)kSmemOptin && B > 4) {
-    B /= 2;
-    smem = chol_smem_bytes(k, nloc, B, sizeof(T));
+  int B = 16, nloc = 0;
+  size_t smem = 0;
+  for (;; ++nc) {  // fewest CTAs from nc up whose rows fit (panel width 16, else 8, else 4)
+    nloc = (k + nc - 1) / nc;
+    for (B = 16; B >= 4; B /= 2) {
+      smem = chol_smem_bytes(k, nloc, B, sizeof(T));
+      if (smem <= (size_t)kSmemOptin) break;
+    }
+    if (smem <= (size_t)kSmemOptin || nc >= 16) break;
   }
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
@@ -660,7 +665,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
 
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
                          unsigned long long* stats, cudaStream_t s, double* shift_out, const float* G32,
-                         long long ld32) {
+                         long long ld32, int nc_pref) {
   if (k <= 0) return cudaSuccess;
   if (!fp64 && k <= CTA_KMAX && cta_smem_bytes(k) <= (size_t)kSmemOptin) {
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cta_f32), kSmemOptin, false);
@@ -670,8 +675,8 @@ cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, fl
     note_launch();
     return cudaGetLastError();
   }
-  return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s, shift_out)
-              : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s, shift_out);
+  return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref)
+              : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref);
 }
 
 // ---------------------------------------------------------------------------
@@ -706,61 +711,91 @@ __global__ void __launch_bounds__(32) k_diag_block_inv(const float* __restrict__
   for (int i = 0; i < TR_RB; ++i) out[i * TR_RB + c] = x[i];
 }
 
+// The tiles of L this CTA multiplies by arrive through a two-slot ring of
+// cp.async copies issued one tile ahead: tile s of the sequence L(I, 0), ...,
+// L(I, I-1), Dinv(I) over the block rows I (s = I (I+1) / 2 + M) is copied
+// while tile s - 1 is used, so the loop waits on L2 once per block row of the
+// ring instead of once per tile.
+__device__ __forceinline__ void trsm_tile_async(float* dst, const float* __restrict__ L, const float* __restrict__ Dinv,
+                                                int k, int I, int M, int tid) {
+  const int i0 = I * TR_RB, ib = min(TR_RB, k - i0);
+  if (M < I) {  // off-diagonal tile of L: rows i0.., columns 32 M..
+    for (int e = tid; e < TR_RB * TR_RB; e += TR_THREADS) {
+      const int a = e / TR_RB, b = e % TR_RB;
+      const bool ok = a < ib;
+      cp_async4(dst + a * (TR_RB + 1) + b, L + (ok ? (size_t)(i0 + a) * k + (size_t)TR_RB * M + b : 0), ok);
+    }
+  } else {      // the block inverse of the diagonal block
+    const float* Di = Dinv + (size_t)I * TR_RB * TR_RB;
+    for (int e = tid; e < TR_RB * TR_RB; e += TR_THREADS)
+      cp_async4(dst + (e / TR_RB) * (TR_RB + 1) + e % TR_RB, Di + e, true);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restrict__ L, const float* __restrict__ Dinv,
                                                             int k, const float* __restrict__ Yt, long long ldy,
                                                             float* __restrict__ Qt, long long ldq, int d) {
   extern __shared__ __align__(16) float tsm[];
   float* X = tsm;                          // kpad x TR_COLS
   const int kpad = (k + TR_RB - 1) / TR_RB * TR_RB;
-  float* Lt = X + (size_t)kpad * TR_COLS;  // TR_RB x (TR_RB + 1), after the padded tail rows of X
+  const int T = kpad / TR_RB;
+  float* ring = X + (size_t)kpad * TR_COLS;  // 2 x TR_RB x (TR_RB + 1)
+  constexpr int TILE = TR_RB * (TR_RB + 1);
   const int tid = threadIdx.x, c = tid & 31, r0 = tid >> 5;  // 8 row groups
   const int col0 = blockIdx.x * TR_COLS;
   const int col = col0 + c;
-  for (int i0 = 0; i0 < k; i0 += TR_RB) {
-    const int ib = min(TR_RB, k - i0);
+  int s = 0;                                // tile sequence index of the tile in use
+  trsm_tile_async(ring, L, Dinv, k, 0, 0, tid);
+  for (int I = 0; I < T; ++I) {
+    const int i0 = I * TR_RB, ib = min(TR_RB, k - i0);
     float acc[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       int ri = r0 + 8 * u;
       acc[u] = (ri < ib && col < d) ? Yt[(long long)(i0 + ri) * ldy + col] : 0.0f;
     }
-    for (int m0 = 0; m0 < i0; m0 += TR_RB) {
-      for (int e = tid; e < TR_RB * TR_RB; e += TR_THREADS) {
-        int a = e / TR_RB, b = e % TR_RB;
-        Lt[a * (TR_RB + 1) + b] = (a < ib) ? L[(size_t)(i0 + a) * k + m0 + b] : 0.0f;
+    for (int M = 0; M <= I; ++M, ++s) {
+      // prefetch the next tile of the sequence into the other slot, then wait for this one
+      const int nI = (M < I) ? I : I + 1, nM = (M < I) ? M + 1 : 0;
+      if (nI < T) {
+        trsm_tile_async(ring + ((s + 1) & 1) * TILE, L, Dinv, k, nI, nM, tid);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
       }
       __syncthreads();
+      const float* Lt = ring + (s & 1) * TILE;
+      if (M < I) {  // acc -= L(I, M) X_M
 #pragma unroll 8
-      for (int mm = 0; mm < TR_RB; ++mm) {
-        float x = X[(size_t)(m0 + mm) * TR_COLS + c];
+        for (int mm = 0; mm < TR_RB; ++mm) {
+          float x = X[(size_t)(TR_RB * M + mm) * TR_COLS + c];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fmaf(-Lt[(r0 + 8 * u) * (TR_RB + 1) + mm], x, acc[u]);
-      }
-      __syncthreads();
-    }
-    // X_I = Dinv_I * acc: stage acc, load the block inverse, multiply.
+          for (int u = 0; u < 4; ++u) acc[u] = fmaf(-Lt[(r0 + 8 * u) * (TR_RB + 1) + mm], x, acc[u]);
+        }
+      } else {      // X_I = Dinv_I * acc: stage acc, then multiply by the block inverse
 #pragma unroll
-    for (int u = 0; u < 4; ++u) X[(size_t)(i0 + r0 + 8 * u) * TR_COLS + c] = (r0 + 8 * u < ib) ? acc[u] : 0.0f;
-    const float* Di = Dinv + (size_t)(i0 / TR_RB) * TR_RB * TR_RB;
-    for (int e = tid; e < TR_RB * TR_RB; e += TR_THREADS) Lt[(e / TR_RB) * (TR_RB + 1) + e % TR_RB] = Di[e];
-    __syncthreads();
-    float out[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int u = 0; u < 4; ++u) X[(size_t)(i0 + r0 + 8 * u) * TR_COLS + c] = (r0 + 8 * u < ib) ? acc[u] : 0.0f;
+        __syncthreads();
+        float out[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
-    for (int u = 0; u < TR_RB; ++u) {
-      const float x = X[(size_t)(i0 + u) * TR_COLS + c];
+        for (int u = 0; u < TR_RB; ++u) {
+          const float x = X[(size_t)(i0 + u) * TR_COLS + c];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) out[v] = fmaf(Lt[(r0 + 8 * v) * (TR_RB + 1) + u], x, out[v]);
-    }
-    __syncthreads();
+          for (int v = 0; v < 4; ++v) out[v] = fmaf(Lt[(r0 + 8 * v) * (TR_RB + 1) + u], x, out[v]);
+        }
+        __syncthreads();
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int ri = r0 + 8 * v;
-      if (ri < ib) {
-        X[(size_t)(i0 + ri) * TR_COLS + c] = out[v];
-        if (col < d) Qt[(long long)(i0 + ri) * ldq + col] = out[v];
+        for (int v = 0; v < 4; ++v) {
+          const int ri = r0 + 8 * v;
+          if (ri < ib) {
+            X[(size_t)(i0 + ri) * TR_COLS + c] = out[v];
+            if (col < d) Qt[(long long)(i0 + ri) * ldq + col] = out[v];
+          }
+        }
       }
+      __syncthreads();  // the slot just used is refilled by the next iteration's prefetch
     }
-    __syncthreads();
   }
 }
 // Packs L for k_trsm_lower_smem once per solve (instead of every CTA
@@ -884,7 +919,7 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
                            float* dinv_ws, cudaStream_t s) {
   if (k <= 0 || d <= 0) return cudaSuccess;
   const int kpad = (k + TR_RB - 1) / TR_RB * TR_RB;  // X rows incl. the padded tail block
-  size_t smem = sizeof(float) * ((size_t)kpad * TR_COLS + TR_RB * (TR_RB + 1));
+  size_t smem = sizeof(float) * ((size_t)kpad * TR_COLS + 2 * TR_RB * (TR_RB + 1));
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
   {
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_trsm_lower), kSmemOptin, false);

@@ -102,6 +102,7 @@ struct GemmDesc {
   long long ws_floats;
   int* flags;  // device status word for bounded-wait timeouts (may be null)
   long long wait_cycles;  // limit of the tensor-core kernels' waits on each other's progress (0: default)
+  int split_target;       // split K of a product with few tiles up to this many CTAs (0: 152, < 0: never)
 };
 
 // Default limit of a tensor-core kernel's wait for another role's progress:
@@ -148,9 +149,11 @@ inline bool tma_rows_ok(const void* p, long long ld) {
 // shift_out (optional, device) receives the shift the successful attempt used.
 // G32 (optional, row stride ld32): an FP32 copy of G that the FP32 path reads
 // instead of converting G (a conversion runs on the FP64 pipe).
+// nc_pref: cluster size of the multi-CTA kernel (0 = one CTA per 16 rows, at
+// most 16; raised to the fewest CTAs whose shared memory holds the rows).
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
                          unsigned long long* stats, cudaStream_t s, double* shift_out = nullptr,
-                         const float* G32 = nullptr, long long ld32 = 0);
+                         const float* G32 = nullptr, long long ld32 = 0, int nc_pref = 0);
 
 // Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
 // dinv_ws: trsm_ws_floats(k) floats of workspace (L packed by 32-row block rows
@@ -169,14 +172,15 @@ inline size_t eig_scratch_floats(int k) { return (((size_t)k * k + 1) & ~(size_t
 // stop_tol > 0 ends the sweeps after one whose largest pair cosine was below it.
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, float stop_tol,
                            double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
-                           cudaStream_t s, const float* C32 = nullptr, long long ld32 = 0);
+                           cudaStream_t s, const float* C32 = nullptr, long long ld32 = 0, int chol_nc = 0);
 
 // One-sided Jacobi on the columns of the k x k FP32 matrix held in gscratch
 // (row-major; the factor eig_jacobi_f32 writes there), with the device scalar
 // `shift`: writes X (column j = unit column j after the rotations) and
-// lam_j = |w_j|^2 - shift (unsorted).
+// lam_j = |w_j|^2 - shift (unsorted). full = 0 reads only the lower triangle
+// (a Cholesky factor), 1 the whole matrix.
 cudaError_t jacobi_columns(int k, int max_sweeps, float tol, float stop_tol, double* X, double* lam, float* gscratch,
-                           const double* shift, int* flags, unsigned long long* stats, cudaStream_t s);
+                           const double* shift, int* flags, unsigned long long* stats, cudaStream_t s, int full);
 // Thin SVD of a k x k FP32 matrix W (row-major, dense) by one-sided Jacobi:
 // W = U diag(sigma) V^T; writes X = U (column j = left singular vector j) and
 // lam_j = sigma_j^2 (unsorted). gscratch: eig_scratch_floats(k) floats.

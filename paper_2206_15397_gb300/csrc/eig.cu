@@ -133,6 +133,7 @@ struct EigArgs {
   int b;   // columns per block (the cluster holds 2 * NC blocks)
   int kp;  // padded column length in shared memory (multiple of 128)
   float stop_tol;  // > 0: stop after a sweep whose largest pair cosine was below it
+  int full;        // 0: L is lower triangular (only i >= j is read); 1: a full matrix
 };
 
 // One-sided Jacobi on the columns of L = chol(C + sI), spread over a cluster.
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
       const int dst = sl * slot;
       for (int e = tid; e < b * kp; e += EIG_THREADS) {
         const int c = e / kp, i = e % kp;
-        const bool ok = c < nc && i < k && i >= c0 + c;
+        const bool ok = c < nc && i < k && (a.full || i >= c0 + c);
         cp_async4(esm + dst + e, a.L + (ok ? (size_t)i * k + c0 + c : 0), ok);
       }
     }
@@ -520,14 +521,14 @@ static cudaError_t launch_eig(const EigArgs& a, int nc, size_t smem, cudaStream_
 
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, float stop_tol,
                            double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
-                           cudaStream_t s, const float* C32, long long ld32) {
+                           cudaStream_t s, const float* C32, long long ld32, int chol_nc) {
   if (k <= 0) return cudaSuccess;
   // W = L with L L^T = C + sI, factorised on a cluster in FP32; the shift it
   // used (grown on breakdown) is stored after the factor.
   double* shift = reinterpret_cast<double*>(gscratch + (((size_t)k * k + 1) & ~(size_t)1));
-  cudaError_t e = chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift, C32, ld32);
+  cudaError_t e = chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift, C32, ld32, chol_nc);
   if (e != cudaSuccess) return e;
-  return jacobi_columns(k, max_sweeps, tol, stop_tol, X, lam, gscratch, shift, flags, stats, s);
+  return jacobi_columns(k, max_sweeps, tol, stop_tol, X, lam, gscratch, shift, flags, stats, s, 0);
 }
 
 cudaError_t svd_jacobi_f32(const float* W32, int k, int max_sweeps, float tol, float stop_tol, double* X, double* lam,
@@ -537,11 +538,11 @@ cudaError_t svd_jacobi_f32(const float* W32, int k, int max_sweeps, float tol, f
   cudaError_t e = cudaMemcpyAsync(gscratch, W32, sizeof(float) * (size_t)k * k, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(shift, 0, sizeof(double), s)) != cudaSuccess) return e;
-  return jacobi_columns(k, max_sweeps, tol, stop_tol, X, lam, gscratch, shift, flags, stats, s);
+  return jacobi_columns(k, max_sweeps, tol, stop_tol, X, lam, gscratch, shift, flags, stats, s, 1);
 }
 
 cudaError_t jacobi_columns(int k, int max_sweeps, float tol, float stop_tol, double* X, double* lam, float* gscratch,
-                           const double* shift, int* flags, unsigned long long* stats, cudaStream_t s) {
+                           const double* shift, int* flags, unsigned long long* stats, cudaStream_t s, int full) {
   // b = ceil(k / 2nc) <= 8 where the cluster allows it: a cross round's b pairs
   // then leave each sub-partition at most two busy warps.
   int nc = (k + 15) / 16;
@@ -550,7 +551,7 @@ cudaError_t jacobi_columns(int k, int max_sweeps, float tol, float stop_tol, dou
   const int kp = (k + 127) / 128 * 128;  // float4 per lane, 32 lanes
   const size_t smem = sizeof(float) * 4 * ((size_t)b * kp + b);  // 2 buffers x 2 slots, with their column norms
   if (smem > (size_t)kSmemOptin) return cudaErrorInvalidValue;
-  EigArgs a = {gscratch, shift, k, max_sweeps, tol, X, lam, flags, stats, b, kp, stop_tol};
+  EigArgs a = {gscratch, shift, k, max_sweeps, tol, X, lam, flags, stats, b, kp, stop_tol, full};
   if (b <= 8) {
     switch (kp / 128) {
       case 1: return launch_eig<1, 256>(a, nc, smem, s);

@@ -62,8 +62,9 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
   if (g.sym) tiles = (tiles + 1) / 2;
   const long long rows = g.d_trans ? g.N : g.M, cols = g.d_trans ? g.M : g.N;
   int z = 1;
-  if (g.ws && !g.sym && tiles < 120 && g.K >= 1024) {  // split K, but stay within one wave of 152 SMs
-    z = (int)std::min<long long>(152 / tiles, g.K / 512);
+  const int target = g.split_target == 0 ? 152 : g.split_target;  // CTAs a split product may fill
+  if (g.ws && !g.sym && target > 0 && tiles < (target * 4) / 5 && g.K >= 1024) {
+    z = (int)std::min<long long>(target / tiles, g.K / 512);
     while (z > 1 && (long long)z * rows * cols > g.ws_floats) --z;
   }
   if (z > 1) {

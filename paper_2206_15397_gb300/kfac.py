@@ -20,7 +20,8 @@ PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
 OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_sweeps": 3, "eig_tol": 4,
            "cholqr_inner_passes": 5, "cholqr_fp32_passes": 6,
            "basis_polish": 7, "cholqr_inner_fp32": 8, "eig_stop_tol": 9, "eig_refine_fp64": 10, "wait_cycles": 11,
-           "group_streams": 12, "invert_method": 13}
+           "group_streams": 12, "invert_method": 13,
+           "chol_cluster": 14, "split_target": 15}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
@@ -71,6 +72,8 @@ def lib():
         L.kfac_reserve.argtypes = [vp, i, i, i64]
         L.kfac_set_option.argtypes = [vp, i, d]
         L.kfac_get_status.argtypes = [vp, ctypes.POINTER(i)]
+        L.kfac_autotune_invert.argtypes = [vp, i, ctypes.POINTER(InvertDesc), ctypes.c_char_p, ctypes.POINTER(i)]
+        L.kfac_autotune_invert.restype = i
         L.kfac_get_item_status.argtypes = [vp, i, ctypes.POINTER(i)]
         L.kfac_get_item_status.restype = i
         L.kfac_ea_update.argtypes = [vp, i, i, vp, i, f, i, vp, i]
@@ -171,6 +174,15 @@ def kfac_get_status(ctx: Context):
     f = ctypes.c_int(0)
     st = lib().kfac_get_status(ctx.handle, ctypes.byref(f))
     return st, [n for b, n in FLAGS.items() if f.value & b]
+
+
+def kfac_autotune_invert(ctx: Context, descs, cache_path: str | None = None) -> dict:
+    """Tune the grouped inversion's schedule for a prepared descriptor array
+    (invert_descs); returns the chosen settings."""
+    out = (ctypes.c_int * 4)()
+    _check(lib().kfac_autotune_invert(ctx.handle, len(descs), descs,
+                                      cache_path.encode() if cache_path else None, out), "kfac_autotune_invert")
+    return {"group_streams": out[0], "chol_cluster": out[1], "split_target": out[2], "cached": bool(out[3])}
 
 
 def kfac_get_item_status(ctx: Context, count: int):
