@@ -325,6 +325,15 @@ typedef enum {
                                        squares the remaining error again. 0: sweep until a
                                        sweep rotates no pair (every pair cosine <=
                                        KFAC_OPT_EIG_TOL) */
+  KFAC_OPT_WARM_START = 16,         /* [0]: 1 = subspace iteration across inversions (a variant
+                                       beyond the paper): the sketch matrix is [U_prev | omega'],
+                                       U_prev being what the call's U buffer holds on entry (the
+                                       previous inversion of the same factor, same d and r) and
+                                       omega' the first k - r columns of omega. The EA factor moves
+                                       little between inversions, so C = Q^T F Q starts nearly
+                                       diagonal and the Jacobi solve stops after fewer sweeps; one
+                                       power iteration or none may then do. Only for calls whose U
+                                       holds such a result (not the first inversion) */
   KFAC_OPT_SPLIT_TARGET = 15,       /* [0 = 152]: a tensor-core product with fewer output tiles
                                        than 4/5 of this many CTAs and K >= 1024 splits K into
                                        chunks of at least 512 so that up to this many CTAs

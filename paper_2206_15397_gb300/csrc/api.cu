@@ -68,6 +68,7 @@ struct kfac_ctx {
   int invert_method = 0;   // KFAC_OPT_INVERT_METHOD: 0 SREVD (Alg. 3), 1 RSVD V~ (Alg. 2, RS-KFAC)
   int chol_cluster = 0;    // KFAC_OPT_CHOL_CLUSTER: CTAs of the multi-CTA Cholesky (0 = automatic)
   int split_target = 0;    // KFAC_OPT_SPLIT_TARGET: CTAs a split-K product may fill (0 = 152, -1 = no split)
+  int warm_start = 0;      // KFAC_OPT_WARM_START: previous U seeds the sketch
 };
 
 namespace {
@@ -364,12 +365,29 @@ kfac_status rsvd_tail(kfac_ctx* ctx, const kfac_invert_desc& a, const InvertLayo
   st = gram_f64(ctx, L, c1, other, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.c), ST_PROJ, at<float>(ctx, L.c32),
                 0);  // R2 = Q2^T B^T, not symmetric
   if (st != KFAC_OK) return st;
+  // Newton-Schulz polish of Q2 (as for SREVD's basis): with E = Q2^T Q2 - I and
+  // M = I - E/2, Q2 M is orthonormal to second order and B^T = (Q2 M)(M R2) to
+  // first order, so the SVD is taken of M R2 and V~ = Q2 (M U_R).
+  float* pw32 = at<float>(ctx, L.r32) + eig_refine_floats(k);
+  const bool polish = ctx->basis_polish != 0;
+  if (polish) {
+    st = gram_f64(ctx, L, c1, c1, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_POLISH, nullptr);
+    if (st != KFAC_OK) return st;
+    STAGE(ctx, ST_POLISH);
+    CK(polish_E_f32(at<double>(ctx, L.g), k, pw32, s));
+    CK(polish_vectors_f32(at<double>(ctx, L.c), k, pw32, s));  // R2 <- M R2
+    CK(convert_f64_to_f32(at<double>(ctx, L.c), (long long)k * k, at<float>(ctx, L.c32), s));
+  }
   {
     STAGE(ctx, ST_EIG);
     // Swept to full convergence (every pair cosine <= KFAC_OPT_EIG_TOL): no
     // refinement step follows here to square away an early stop's residue.
     CK(svd_jacobi_f32(at<float>(ctx, L.c32), k, ctx->eig_max_sweeps, (float)ctx->eig_tol, 0.0f, at<double>(ctx, L.x),
                       at<double>(ctx, L.lam), at<float>(ctx, L.jac), ctx->dflags, ctx->dstats, s));
+  }
+  if (polish) {
+    STAGE(ctx, ST_POLISH);
+    CK(polish_vectors_f32(at<double>(ctx, L.x), k, pw32, s));  // U_R <- M U_R
   }
   {
     STAGE(ctx, ST_SELECT);
@@ -414,7 +432,15 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   float* other = at<float>(ctx, L.q);
   {
     STAGE(ctx, ST_TRANSPOSE);
-    CK(transpose_f32(a.omega, a.ldo, d, k, Om, L.dp, s));
+    if (ctx->warm_start) {
+      // Subspace iteration across inversions: the previous inversion's U (the
+      // caller's U buffer, read before this call overwrites it) seeds the
+      // first r sketch columns, omega's first k - r columns the rest.
+      CK(transpose_f32(a.U, a.ldu, d, r, Om, L.dp, s));
+      CK(transpose_f32(a.omega, a.ldo, d, k - r, Om + (size_t)r * L.dp, L.dp, s));
+    } else {
+      CK(transpose_f32(a.omega, a.ldo, d, k, Om, L.dp, s));
+    }
   }
   st = sketch_product(ctx, L, Om, L.dp, F, ldf, k, d, a.prec, cur, L.dp);  // Y^T = Omega^T F
   if (st != KFAC_OK) return st;
@@ -798,6 +824,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
     case KFAC_OPT_EIG_REFINE_FP64:
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->eig_refine_fp64 = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_WARM_START:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->warm_start = (int)v;
       return KFAC_OK;
     case KFAC_OPT_SPLIT_TARGET:
       if (v < -1 || v > 4096) return KFAC_ERR_INVALID_ARG;

@@ -209,6 +209,8 @@ cudaError_t eig_refine_f32(const float* C32, long long ldc32, int k, double* X, 
 // 3 k^2 floats of w32 for polish_vectors_f32, which applies X <- M X.
 cudaError_t polish_projected_f32(const double* G, double* C, float* C32, int k, float* w32, cudaStream_t s);
 cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s);
+// E = G - I (FP32, k x k) into the first k^2 floats of w32, for polish_vectors_f32.
+cudaError_t polish_E_f32(const double* G, int k, float* w32, cudaStream_t s);
 
 // Sort eigenpairs descending (stable by index), emit the r leading ones:
 // Pt (r x k FP32, row stride ldpt, row t = eigenvector t; optional), D and coef

@@ -842,6 +842,13 @@ cudaError_t polish_projected_f32(const double* G, double* C, float* C32, int k, 
   return cudaGetLastError();
 }
 
+cudaError_t polish_E_f32(const double* G, int k, float* w32, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_polish_E32<<<row_grid(k), 256, 0, s>>>(G, k, w32);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   const size_t kk = (size_t)k * k;

@@ -21,7 +21,7 @@ OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_swee
            "cholqr_inner_passes": 5, "cholqr_fp32_passes": 6,
            "basis_polish": 7, "cholqr_inner_fp32": 8, "eig_stop_tol": 9, "eig_refine_fp64": 10, "wait_cycles": 11,
            "group_streams": 12, "invert_method": 13,
-           "chol_cluster": 14, "split_target": 15}
+           "chol_cluster": 14, "split_target": 15, "warm_start": 16}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 

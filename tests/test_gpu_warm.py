@@ -1,0 +1,54 @@
+"""Warm-started subspace iteration (KFAC_OPT_WARM_START, a variant beyond the
+paper): after one EA step the factor moves little, so seeding the sketch with
+the previous inversion's U gives the same leading eigenpairs as the oracle's
+Alg. 3 on the same seed matrix [U_prev | Omega_p] (U_prev the oracle's own
+previous result), with no power iteration and fewer Jacobi sweeps than a cold
+start."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_15397_gb300 import inputs
+from tests import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_2206_15397_gb300 import build, kfac
+    build.build()
+    return kfac
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("d,r,p,alpha", [(400, 40, 10, 1.0), (1025, 120, 10, 1.5)])
+def test_warm_start_matches_oracle_and_saves_sweeps(kf, d, r, p, alpha):
+    xs = inputs.activation_batches(91, d - 1, 96, 8, alpha=alpha, bias=True, salt=3)
+    f1 = workloads.ea_factor(xs[:7]).astype(np.float32)
+    f2 = workloads.ea_factor(xs).astype(np.float32)          # one more EA step
+    om = inputs.omega(91, d, r + p, salt=4)
+    u1_o, _ = oracle.srevd(f1.astype(np.float64), om.astype(np.float64), 1, r)
+    seed = np.hstack([u1_o, om[:, :p].astype(np.float64)])
+    u2_o, d2_o = oracle.srevd(f2.astype(np.float64), seed, 0, r)
+    with kf.Context(0) as ctx:
+        U = torch.empty(d, r, device="cuda")
+        D = torch.empty(r, device="cuda")
+        c = torch.empty(r, device="cuda")
+        kf.kfac_stats_read(ctx)
+        kf.kfac_rsvd_invert(ctx, cuda(f1), r, p, 1, 0.1, cuda(om), out=(U, D, c))   # cold, q = 1
+        cold = kf.kfac_stats_read(ctx)["jacobi_sweeps"]
+        kf.kfac_set_option(ctx, "warm_start", 1)
+        kf.kfac_rsvd_invert(ctx, cuda(f2), r, p, 0, 0.1, cuda(om), out=(U, D, c))   # warm, q = 0
+        warm = kf.kfac_stats_read(ctx)["jacobi_sweeps"]
+        st, flags = kf.kfac_get_status(ctx)
+        assert st == 0 and set(flags) <= {"CHOL_SHIFTED", "EIG_SHIFTED"}, (st, flags)
+        dd, u = D.double().cpu().numpy(), U.double().cpu().numpy()
+    assert np.abs(dd - d2_o).max() <= 1e-5 * d2_o[0]
+    rec, rec_o = (u * dd) @ u.T, (u2_o * d2_o) @ u2_o.T
+    assert np.linalg.norm(rec - rec_o) <= 1e-4 * np.linalg.norm(rec_o)
+    assert warm < cold, (warm, cold)
