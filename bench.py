@@ -498,6 +498,31 @@ def evd_comparison(kfac, ctx, wl, stream, prec, n_sample):
             "randomized_vs_truncated_evd": max(between)}
 
 
+def phase_times(kfac, ctx, descs, stream, reps=5):
+    """Device ms of the step's three phases, each captured in a graph of its own
+    and replayed: the grouped EA update, the grouped inversion, the grouped apply."""
+    import torch
+    ea, inv, pre = descs
+    out = {}
+    for name, fn in (("ea", lambda: kfac.call_grouped(ctx, "ea", ea[0])),
+                     ("invert", lambda: kfac.call_grouped(ctx, "invert", inv)),
+                     ("apply", lambda: kfac.call_grouped(ctx, "precondition", pre))):
+        with torch.cuda.stream(stream):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                fn()
+            g.replay()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
+            e1.synchronize()
+        out[name] = e0.elapsed_time(e1) / reps
+    return out
+
+
 def e2e_measure(kfac, ctx, wl, graphs, stream, steps):
     """The captured step end to end with host buffers: per step, pinned H2D of
     every factor's EA batch and test matrix and every layer's gradient, the
@@ -724,7 +749,7 @@ def bench_workload(kfac, ctx, wl, stream, prec, steps, warmup, streams, clocks=N
     stages, sweeps, simt = profile_stages(kfac, ctx, descs, stream, profile_steps, streams) if profile_steps else \
         ({}, 0.0, 0)
     return dict(ms=ms, graphs=graphs, launches=launches, clocks=clk, status=(st, flags), stages=stages,
-                sweeps=sweeps, simt=simt, tuned=tuned)
+                sweeps=sweeps, simt=simt, tuned=tuned, descs=descs)
 
 
 def main(argv=None):
@@ -810,6 +835,14 @@ def main(argv=None):
         if "sketch_gemm" in stages:
             result["roofline_sketch_gemm"] = stage_roofline("sketch_gemm", stages["sketch_gemm"][0],
                                                             int(round(stages["sketch_gemm"][1])), spec, args.prec)
+
+    # ---- the paper's amortised schedule (Sec. 5: T_KU = 10, T_KI = 50) -----------
+    if rank == 0:
+        ph = phase_times(kfac, ctx, res["descs"], stream)
+        result["amortised"] = {"T_KU": 10, "T_KI": 50, "phase_ms": {k: round(v, 4) for k, v in ph.items()},
+                               "ms_per_step": ph["apply"] + ph["ea"] / 10.0 + ph["invert"] / 50.0,
+                               "note": "apply every step, EA every T_KU steps, inversion every T_KI steps; phases "
+                                       "timed as separate graph replays"}
 
     # ---- full-EVD comparator on the same GPU, accuracy at equal rank -------------
     if rank == 0 and not args.no_evd:

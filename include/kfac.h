@@ -112,6 +112,19 @@ KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t m
 KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X, int ldx, float rho,
                                     kfac_precision prec, float* F, int ldf);
 
+/* The same EA update from a batch in the layout a layer sees it: A is n x cols
+ * row-major (one sample per row, row stride lda >= cols), e.g. a linear
+ * layer's input activations or its output gradients. The factor is
+ * d x d with d = cols + append_one: with append_one != 0 the homogeneous
+ * coordinate 1 is appended last to every sample (the bias column of Mat(g)).
+ * Every sample is multiplied by `scale` first (e.g. the batch size for the
+ * gradients of a batch-mean loss, so that they are per-sample gradients):
+ *     F <- rho F + (1 - rho) / n * scale^2 * Abar^T Abar,   Abar = [A, 1].
+ * The batch is transposed into the context workspace (one kernel) and the
+ * product runs as kfac_ea_update. */
+KFAC_API kfac_status kfac_ea_update_rows(kfac_ctx* ctx, int n, int cols, const float* A, int lda, int append_one,
+                                         float scale, float rho, kfac_precision prec, float* F, int ldf);
+
 /* One factor of a grouped EA update (arguments as kfac_ea_update). */
 typedef struct {
   int d, n;

@@ -979,6 +979,26 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
   return ea_run(ctx, d, n, X, ldx, rho, prec, F, ldf, 0);
 }
 
+KFAC_API kfac_status kfac_ea_update_rows(kfac_ctx* ctx, int n, int cols, const float* A, int lda, int append_one,
+                                         float scale, float rho, kfac_precision prec, float* F, int ldf) {
+  const int d = cols + (append_one ? 1 : 0);
+  if (!ctx || n < 0 || cols < 0 || d == 0 || ldf < d || !F || (n > 0 && cols > 0 && (!A || lda < cols)))
+    return KFAC_ERR_INVALID_ARG;
+  if (!(rho >= 0.0f && rho <= 1.0f) || !(scale == scale) || prec < KFAC_PREC_FP32 || prec > KFAC_PREC_BF16)
+    return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  const long long ldx = round_up(std::max(n, 1), 4);
+  kfac_status st = ensure_ws(ctx, sizeof(float) * (size_t)d * (size_t)ldx);
+  if (st != KFAC_OK) return st;
+  float* X = at<float>(ctx, 0);
+  {
+    STAGE(ctx, ST_TRANSPOSE);
+    CK(rows_to_cols_f32(A, lda, n, cols, append_one ? 1 : 0, scale, X, ldx, ctx->stream));
+  }
+  return ea_run(ctx, d, n, X, (int)ldx, rho, prec, F, ldf, 0);
+}
+
 static kfac_status check_ea(const kfac_ea_desc& a) {
   if (a.d < 0 || a.n < 0 || a.ldf < a.d || (a.d > 0 && !a.F) || (a.n > 0 && (!a.X || a.ldx < a.n)))
     return KFAC_ERR_INVALID_ARG;

@@ -134,6 +134,10 @@ cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int col
 // operand whose rows are not 16-byte aligned.
 cudaError_t pack_rows_f32(const float* src, long long lds, int rows, int cols, float* dst, long long ldd,
                           cudaStream_t s);
+// X (d x ldx, d = cols + append_one, ldx >= n) <- scale * A^T for a row-major
+// batch A (n x cols), plus a last row of ones when append_one; pad columns zeroed.
+cudaError_t rows_to_cols_f32(const float* A, long long lda, int n, int cols, int append_one, float scale, float* X,
+                             long long ldx, cudaStream_t s);
 // True when TMA can read a row-major FP32 matrix at p with row stride ld as is
 // (16-byte aligned base and row stride).
 inline bool tma_rows_ok(const void* p, long long ld) {

@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   const int slot = b * kp;  // floats per slot; buffer x starts at offset 2 * slot * x (top slot, then bottom)
   __shared__ int s_count, s_total;
   __shared__ unsigned s_off, s_offmax;  // largest squared pair cosine of a sweep (FP32 bits, >= 0)
-  if (tid == 0) { s_total = 0; s_offmax = 0u; }
+  __shared__ unsigned s_absmax;         // largest |w_ij| of the CTA's blocks, then of the cluster (FP32 bits)
+  if (tid == 0) { s_total = 0; s_offmax = 0u; s_absmax = 0u; }
 
   // ---- initial blocks (round 0 positions) from the factor ------------------
   // (asynchronous copies, all in flight at once; zero outside the factor)
@@ -178,7 +179,26 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
     }
     cp_async_wait_all();
   }
-  // Every CTA has its blocks before the first distributed shared memory store.
+  // Exact power-of-two rescaling so that the largest entry is in [0.5, 1):
+  // products of squared column norms of a tiny-scale matrix (the R factor of
+  // a factor scaled 1e-6, say) would otherwise underflow in the pair tests.
+  // Rotations are scale-invariant, so the columns' directions are unchanged.
+  __syncthreads();
+  {
+    float m = 0.0f;
+    for (int e = tid; e < 2 * slot; e += EIG_THREADS) m = fmaxf(m, fabsf(esm[e]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0.0f) atomicMax(&s_absmax, __float_as_uint(m));
+  }
+  cluster.sync();  // every CTA's blocks are loaded and its maximum taken
+  if (tid == 0 && s_absmax) atomicMax(cluster.map_shared_rank(&s_absmax, 0), s_absmax);
+  cluster.sync();
+  const float wmax = __uint_as_float(*cluster.map_shared_rank(&s_absmax, 0));
+  int wexp = 0;
+  frexpf(wmax, &wexp);  // wmax = f 2^wexp, f in [0.5, 1) (wexp = 0 for a zero matrix)
+  const float wscale = ldexpf(1.0f, -wexp);
+  for (int e = tid; e < 2 * slot; e += EIG_THREADS) esm[e] *= wscale;
+  // Every CTA has its blocks (rescaled) before the first distributed shared memory store.
   cluster.sync();
 
   // ---- sweeps ---------------------------------------------------------------
@@ -338,6 +358,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
   // ---- eigenpairs of the blocks held here: lam_j = |w_j|^2 - s, x_j = w_j / |w_j|
   // After a whole number of sweeps the blocks are back at their round-0 positions.
   const double sh = *a.shift;
+  const double unscale = ldexp(1.0, 2 * wexp);  // |w_j|^2 back in the input's units
   const int blk[2] = {rr_player(rank, 0, nb), rr_player(nb - 1 - rank, 0, nb)};
   for (int sl = 0; sl < 2; ++sl) {
     const int c0 = blk[sl] * b;
@@ -352,7 +373,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
       n2 = __shfl_sync(0xffffffffu, n2, 0);
       double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
       for (int i = lane; i < k; i += 32) a.X[(size_t)i * k + j] = (double)wj[i] * inv;
-      if (lane == 0) a.lam[j] = n2 - sh;
+      if (lane == 0) a.lam[j] = n2 * unscale - sh;
     }
   }
   cluster.sync();  // no CTA leaves while others may still address its shared memory

@@ -274,6 +274,26 @@ __global__ void k_pack_rows(const float* __restrict__ src, long long lds, int ro
   }
 }
 
+// X (d x ldx, d = cols + append_one) <- scale * A^T for a row-major batch A
+// (n x cols, row stride lda), with a last row of ones when append_one; the pad
+// columns n..ldx-1 are zeroed. 32 x 32 tiles through shared memory so that both
+// the reads of A and the writes of X are coalesced.
+__global__ void k_rows_to_cols(const float* __restrict__ A, long long lda, int n, int cols, int append_one,
+                               float scale, float* __restrict__ X, long long ldx) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.y * 32, t0 = blockIdx.x * 32;  // feature (row of X) and sample (column of X) blocks
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int t = t0 + y, c = c0 + threadIdx.x;
+    tile[y][threadIdx.x] = (t < n && c < cols) ? scale * A[(long long)t * lda + c] : 0.0f;
+  }
+  __syncthreads();
+  const int d = cols + append_one;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int c = c0 + y, t = t0 + threadIdx.x;  // X[c][t] = A[t][c]
+    if (c < d && t < ldx) X[(long long)c * ldx + t] = (t >= n) ? 0.0f : (c < cols ? tile[threadIdx.x][y] : 1.0f);
+  }
+}
+
 __global__ void k_convert(const float* __restrict__ in, long long ldi, int rows, int cols, double* __restrict__ out,
                           long long ldo, int* flags) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -369,6 +389,16 @@ cudaError_t pack_rows_f32(const float* src, long long lds, int rows, int cols, f
   const long long total = (long long)rows * (ldd >> 2);
   const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
   k_pack_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, rows, cols, dst, ldd);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t rows_to_cols_f32(const float* A, long long lda, int n, int cols, int append_one, float scale, float* X,
+                             long long ldx, cudaStream_t s) {
+  const int d = cols + append_one;
+  if (d <= 0 || ldx <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((ldx + 31) / 32), (unsigned)((d + 31) / 32));
+  k_rows_to_cols<<<grid, dim3(32, 8), 0, s>>>(A, lda, n, cols, append_one, scale, X, ldx);
   note_launch();
   return cudaGetLastError();
 }

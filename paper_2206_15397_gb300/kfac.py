@@ -72,6 +72,8 @@ def lib():
         L.kfac_reserve.argtypes = [vp, i, i, i64]
         L.kfac_set_option.argtypes = [vp, i, d]
         L.kfac_get_status.argtypes = [vp, ctypes.POINTER(i)]
+        L.kfac_ea_update_rows.argtypes = [vp, i, i, vp, i, i, f, f, i, vp, i]
+        L.kfac_ea_update_rows.restype = i
         L.kfac_autotune_invert.argtypes = [vp, i, ctypes.POINTER(InvertDesc), ctypes.c_char_p, ctypes.POINTER(i)]
         L.kfac_autotune_invert.restype = i
         L.kfac_get_item_status.argtypes = [vp, i, ctypes.POINTER(i)]
@@ -198,6 +200,18 @@ def kfac_ea_update(ctx: Context, X: torch.Tensor, F: torch.Tensor, rho: float, p
     px, ldx = _mat(X, "X", d, n)
     pf, ldf = _mat(F, "F", d, d)
     _check(lib().kfac_ea_update(ctx.handle, d, n, px, ldx, float(rho), PRECISION[prec], pf, ldf), "kfac_ea_update")
+    return F
+
+
+def kfac_ea_update_rows(ctx: Context, A: torch.Tensor, F: torch.Tensor, rho: float, append_one: bool = False,
+                        scale: float = 1.0, prec: str = "fp32"):
+    """F <- rho F + (1 - rho)/n scale^2 [A, 1]^T [A, 1] in place for a batch A of shape (n, cols)."""
+    n, cols = A.shape
+    d = cols + int(bool(append_one))
+    pa, lda = _mat(A, "A", n, cols)
+    pf, ldf = _mat(F, "F", d, d)
+    _check(lib().kfac_ea_update_rows(ctx.handle, n, cols, pa, lda, int(bool(append_one)), float(scale), float(rho),
+                                     PRECISION[prec], pf, ldf), "kfac_ea_update_rows")
     return F
 
 
