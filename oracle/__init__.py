@@ -12,6 +12,7 @@ and returns float64 numpy arrays, row-major.
 
 Functions and the passages they follow:
   ea_update        Alg. 1, EA update of the forward/backward K-factors; Eq. (6)
+  ea_update_conv   the same for a conv layer, from patch statistics (Sec. 2.1's conv K-factors)
   jacobi_eigh      "eig" of Alg. 1 / "Eigen_decomp" of Alg. 3 (cyclic Jacobi)
   qr               "QR_decomp" of Alg. 2 / Alg. 3 (Householder)
   srevd            Alg. 3 with the power iteration of Sec. 2.2
@@ -80,6 +81,7 @@ def _load():
             lib.orc_srevd.argtypes = [i, _dp, i, _dp, i, i, _dp, _dp, _dp, _dp]
             lib.orc_srevd.restype = i
             lib.orc_damped_coef.argtypes = [i, _dp, d, _dp]
+            lib.orc_ea_update_conv.argtypes = [i, i, i, i, _dp, i, i, i, i, i, i, i, d, d, _dp]
             lib.orc_svd_jacobi.argtypes = [i, i, _dp, _dp, _dp, _dp, i, d]
             lib.orc_svd_jacobi.restype = i
             lib.orc_rsvd.argtypes = [i, _dp, i, _dp, i, i, _dp, _dp, _dp]
@@ -122,6 +124,20 @@ def ea_update(factor, x, rho: float) -> np.ndarray:
     d, n = x.shape
     assert f.shape == (d, d)
     _load().orc_ea_update(d, n, _p(x), float(rho), _p(f))
+    return f
+
+
+def ea_update_conv(factor, x, kernel, stride=(1, 1), pad=(0, 0), rho: float = 0.95, append_one: bool = False,
+                   scale: float = 1.0) -> np.ndarray:
+    """EA update of a conv layer's factor from the patch statistics of x (n, c, h, w)."""
+    f = _c(factor).copy()
+    x = _c(x)
+    n, c, h, w = x.shape
+    kh, kw = kernel
+    d = c * kh * kw + int(append_one)
+    assert f.shape == (d, d)
+    _load().orc_ea_update_conv(n, c, h, w, _p(x), kh, kw, stride[0], stride[1], pad[0], pad[1], int(append_one),
+                               float(scale), float(rho), _p(f))
     return f
 
 

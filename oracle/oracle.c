@@ -79,6 +79,45 @@ void orc_ea_update(int d, int n, const double* X, double rho, double* F) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* EA update of a convolutional layer's K-factor from patch statistics: the  */
+/* factor A A^T of Eq. (4) for a conv layer (the paper defers its exact form */
+/* to KFC, Sec. 2.1), with A's columns the input patches at every sample and */
+/* output position. Reading: the batch product is the mean over samples and  */
+/* positions, patches are zero-padded, entries ordered (channel, kernel row, */
+/* kernel column) as a conv weight flattens, with the homogeneous 1 last.    */
+/* ------------------------------------------------------------------------ */
+
+/* x: n x c x h x w (NCHW). Patch of sample i at output position (oy, ox):
+ * p[(ch * kh + r) * kw + t] = x[i, ch, oy * sh + r - ph, ox * sw + t - pw]
+ * (0 outside the image), followed by 1 when append_one. Each patch is scaled
+ * by `scale`, and F <- rho F + (1 - rho) / (n * ho * wo) * sum_patches p p^T. */
+void orc_ea_update_conv(int n, int c, int h, int w, const double* x, int kh, int kw, int sh, int sw, int ph,
+                        int pw, int append_one, double scale, double rho, double* F) {
+  const int ho = (h + 2 * ph - kh) / sh + 1, wo = (w + 2 * pw - kw) / sw + 1;
+  const int d = c * kh * kw + (append_one ? 1 : 0);
+  double* S = (double*)calloc((size_t)d * d, sizeof(double));
+  double* p = (double*)malloc(sizeof(double) * (size_t)d);
+  for (int i = 0; i < n; ++i)
+    for (int oy = 0; oy < ho; ++oy)
+      for (int ox = 0; ox < wo; ++ox) {
+        for (int ch = 0; ch < c; ++ch)
+          for (int r = 0; r < kh; ++r)
+            for (int t = 0; t < kw; ++t) {
+              const int y = oy * sh + r - ph, xx = ox * sw + t - pw;
+              const int idx = (ch * kh + r) * kw + t;
+              p[idx] = (y >= 0 && y < h && xx >= 0 && xx < w)
+                           ? scale * x[(((size_t)i * c + ch) * h + y) * w + xx] : 0.0;
+            }
+        if (append_one) p[d - 1] = scale;
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) S[(size_t)a * d + b] += p[a] * p[b];
+      }
+  const double m = (double)n * ho * wo;
+  for (size_t e = 0; e < (size_t)d * d; ++e) F[e] = rho * F[e] + (1.0 - rho) * S[e] / m;
+  free(S); free(p);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Symmetric eigendecomposition by the cyclic-by-row Jacobi method: the      */
 /* "eig" of Alg. 1 and the "Eigen_decomp" of Alg. 3.                         */
 /* ------------------------------------------------------------------------ */

@@ -462,3 +462,48 @@ def test_rsvd_truncation_dominates_projection_error():
     v, s = oracle.rsvd(x, inputs.gaussian(24, (d, r + 10)), 1, r)
     err = np.linalg.norm(x - (v * s) @ v.T)
     assert trunc <= err <= 1.05 * trunc
+
+
+# ----------------------------------------------------------------------------- conv K-factors (patch statistics)
+
+def _unfold(x, kh, kw, sh, sw, ph, pw):
+    """Patch matrix (d x n*ho*wo) by numpy slicing of the zero-padded input."""
+    n, c, h, w = x.shape
+    xp = np.zeros((n, c, h + 2 * ph, w + 2 * pw))
+    xp[:, :, ph:ph + h, pw:pw + w] = x
+    ho, wo = (h + 2 * ph - kh) // sh + 1, (w + 2 * pw - kw) // sw + 1
+    cols = np.empty((c, kh, kw, n, ho, wo))
+    for r in range(kh):
+        for t in range(kw):
+            cols[:, r, t] = xp[:, :, r:r + sh * ho:sh, t:t + sw * wo:sw].transpose(1, 0, 2, 3)
+    return cols.reshape(c * kh * kw, n * ho * wo)
+
+
+@pytest.mark.parametrize("shape,kernel,stride,pad", [((2, 3, 5, 6), (3, 3), (1, 1), (1, 1)),
+                                                      ((3, 2, 7, 7), (3, 2), (2, 1), (0, 1)),
+                                                      ((1, 4, 4, 4), (1, 1), (1, 1), (0, 0))])
+def test_ea_conv_matches_unfolded_product(shape, kernel, stride, pad):
+    """Patch statistics equal the EA update of the explicitly unfolded patch
+    matrix (numpy slicing of the zero-padded input), with the bias row."""
+    x = rng(sum(shape)).standard_normal(shape)
+    a = _unfold(x, *kernel, *stride, *pad)
+    abar = np.vstack([a, np.ones((1, a.shape[1]))])
+    f0 = rand_psd(abar.shape[0], 3)
+    got = oracle.ea_update_conv(f0, x, kernel, stride, pad, 0.9, append_one=True)
+    want = 0.9 * f0 + 0.1 * abar @ abar.T / a.shape[1]
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-13)
+
+
+def test_ea_conv_special_cases():
+    """A kernel covering the whole unpadded image gives one patch per sample
+    (the FC factor of the flattened images); a 1 x 1 kernel gives the
+    per-position channel covariance; a scale s multiplies the increment by s^2."""
+    x = rng(4).standard_normal((5, 2, 3, 4))
+    flat = x.reshape(5, -1).T
+    got = oracle.ea_update_conv(np.zeros((24, 24)), x, (3, 4), rho=0.5)
+    np.testing.assert_allclose(got, oracle.ea_update(np.zeros((24, 24)), flat, 0.5), rtol=1e-12)
+    got = oracle.ea_update_conv(np.zeros((2, 2)), x, (1, 1), rho=0.0)
+    chan = x.transpose(1, 0, 2, 3).reshape(2, -1)
+    np.testing.assert_allclose(got, chan @ chan.T / chan.shape[1], rtol=1e-12)
+    g3 = oracle.ea_update_conv(np.zeros((2, 2)), x, (1, 1), rho=0.0, scale=3.0)
+    np.testing.assert_allclose(g3, 9.0 * got, rtol=1e-12)
