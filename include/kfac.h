@@ -125,6 +125,26 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
 KFAC_API kfac_status kfac_ea_update_rows(kfac_ctx* ctx, int n, int cols, const float* A, int lda, int append_one,
                                          float scale, float rho, kfac_precision prec, float* F, int ldf);
 
+/* EA update of a convolutional layer's K-factor from patch statistics (the
+ * conv K-factors of Eq. (4), which the paper takes from KFC): the columns of
+ * the batch matrix are the layer's input patches at every sample and output
+ * position,
+ *     F <- rho F + (1 - rho) / (n ho wo) * sum_{i, oy, ox} p p^T,
+ *     p[(ch kh + r) kw + t] = scale * x[i, ch, oy sh + r - ph, ox sw + t - pw]
+ * (zero outside the image; with append_one the entry `scale` is appended last
+ * for the bias), so F is d x d with d = c kh kw + append_one, ordered as a
+ * PyTorch conv weight (C_out, C_in, kh, kw) flattens per output channel.
+ * x: n x c x h x w input activations (NCHW, contiguous, device memory);
+ * ho = (h + 2 ph - kh) / sh + 1, wo likewise. The backward factor of the same
+ * layer is this call on the output gradients (n x C_out x ho x wo) with a 1 x 1
+ * kernel, stride 1, no padding, append_one 0 and scale = n for a batch-mean
+ * loss. The patch matrix is built in the context workspace in chunks of whole
+ * samples of at most KFAC_OPT_CONV_CHUNK floats, each chunk accumulated by the
+ * tensor-core SYRK of kfac_ea_update. */
+KFAC_API kfac_status kfac_ea_update_conv(kfac_ctx* ctx, int n, int c, int h, int w, const float* x, int kh, int kw,
+                                         int stride_h, int stride_w, int pad_h, int pad_w, int append_one, float scale,
+                                         float rho, kfac_precision prec, float* F, int ldf);
+
 /* One factor of a grouped EA update (arguments as kfac_ea_update). */
 typedef struct {
   int d, n;
@@ -338,6 +358,9 @@ typedef enum {
                                        squares the remaining error again. 0: sweep until a
                                        sweep rotates no pair (every pair cosine <=
                                        KFAC_OPT_EIG_TOL) */
+  KFAC_OPT_CONV_CHUNK = 17,         /* [32 Mi]: floats of one chunk of the patch matrix that
+                                       kfac_ea_update_conv builds in the workspace (whole
+                                       samples per chunk, at least one) */
   KFAC_OPT_WARM_START = 16,         /* [0]: 1 = subspace iteration across inversions (a variant
                                        beyond the paper): the sketch matrix is [U_prev | omega'],
                                        U_prev being what the call's U buffer holds on entry (the

@@ -69,6 +69,7 @@ struct kfac_ctx {
   int chol_cluster = 0;    // KFAC_OPT_CHOL_CLUSTER: CTAs of the multi-CTA Cholesky (0 = automatic)
   int split_target = 0;    // KFAC_OPT_SPLIT_TARGET: CTAs a split-K product may fill (0 = 152, -1 = no split)
   int warm_start = 0;      // KFAC_OPT_WARM_START: previous U seeds the sketch
+  long long conv_chunk = 32LL << 20;  // KFAC_OPT_CONV_CHUNK: floats of one patch-matrix chunk
 };
 
 namespace {
@@ -155,10 +156,10 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, skws, total;
-  long long dp, kp, skws_floats;
+  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, total;
+  long long dp, kp, dpb, skws_floats;
   int nsplit, kchunk;
-  bool pack_f;
+  bool pack_f, bf16;
 };
 
 constexpr int kSketchMaxSplit = 6;  // split-K partials of the sketch products
@@ -166,10 +167,13 @@ constexpr int kSketchMaxSplit = 6;  // split-K partials of the sketch products
 // pack_f: F's rows are not 16-byte aligned, so the sketch products read a
 // copy of F with a padded row stride (one extra pass over F per inversion,
 // against the q + 2 passes of the products it puts on the tensor cores).
-InvertLayout invert_layout(int d, int k, int r, bool pack_f) {
+// bf16: the BF16 products read a BF16 copy of F (made once per inversion) and
+// of each product's k x d operand, which TMA feeds to the tensor cores as is.
+InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false) {
   InvertLayout L = {};
   Bump b;
   L.pack_f = pack_f;
+  L.bf16 = bf16 && k < d;
   if (k >= d) {  // exact path
     int n = d;
     L.c = b.take<double>((size_t)n * n);
@@ -206,6 +210,11 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f) {
   L.pt = b.take<float>((size_t)r * L.kp);  // P[:, :r]^T, the lift's B operand
   L.qn = b.take<float>((size_t)d * L.kp);  // Q (d x k), the lift's A operand
   if (pack_f) L.fp = b.take<float>((size_t)d * L.dp);
+  L.dpb = round_up(d, 8);
+  if (L.bf16) {
+    L.fb = b.take<uint16_t>((size_t)d * L.dpb);
+    L.xb = b.take<uint16_t>((size_t)k * L.dpb);
+  }
   L.skws_floats = (long long)kSketchMaxSplit * k * d;
   L.skws = b.take<float>((size_t)L.skws_floats);
   L.total = b.off;
@@ -242,6 +251,13 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
   g.M = d; g.N = k; g.K = d;
   g.A = F; g.sam = ldf; g.sak = 1;
   g.B = Xt; g.sbn = ldx; g.sbk = 1;
+  if (L.bf16 && prec == KFAC_PREC_BF16) {  // BF16 copies: F's made once per inversion, Xt's here
+    STAGE(ctx, ST_TRANSPOSE);
+    CK(to_bf16_f32(Xt, ldx, k, d, at<uint16_t>(ctx, L.xb), L.dpb, ctx->stream));
+    g.A = reinterpret_cast<const float*>(at<uint16_t>(ctx, L.fb)); g.sam = L.dpb;
+    g.B = reinterpret_cast<const float*>(at<uint16_t>(ctx, L.xb)); g.sbn = L.dpb;
+    g.ab_bf16 = 1;
+  }
   g.D = out; g.ldd = ldo; g.d_trans = 1;
   g.alpha = 1.0f; g.zsplit = 1;
   g.ws = at<float>(ctx, L.skws); g.ws_floats = L.skws_floats;
@@ -404,7 +420,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const float* F = a.F;
   int ldf = a.ldf;
   for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
-                    &L.r32, &L.pt, &L.qn, &L.fp, &L.skws})
+                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;
@@ -425,6 +441,10 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
     CK(pack_rows_f32(F, ldf, d, d, Fp, L.dp, s));
     F = Fp;
     ldf = (int)L.dp;
+  }
+  if (L.bf16) {  // F rounded to BF16 once, for the sketch, power and projection products
+    STAGE(ctx, ST_TRANSPOSE);
+    CK(to_bf16_f32(F, ldf, d, d, at<uint16_t>(ctx, L.fb), L.dpb, s));
   }
   // Omega^T (k x d) so that every sketch product reads K-contiguous rows.
   float* Om = at<float>(ctx, L.om);
@@ -825,6 +845,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->eig_refine_fp64 = (int)v;
       return KFAC_OK;
+    case KFAC_OPT_CONV_CHUNK:
+      if (!(v >= 1 && v <= 1e10)) return KFAC_ERR_INVALID_ARG;
+      ctx->conv_chunk = (long long)v;
+      return KFAC_OK;
     case KFAC_OPT_WARM_START:
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->warm_start = (int)v;
@@ -858,7 +882,7 @@ KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t m
   DeviceGuard g(ctx->device);
   size_t need = 0;
   if (d_max > 0 && k_max > 0) {
-    InvertLayout a = invert_layout(d_max, std::min(k_max, d_max - 1 > 0 ? d_max - 1 : 1), k_max, true);
+    InvertLayout a = invert_layout(d_max, std::min(k_max, d_max - 1 > 0 ? d_max - 1 : 1), k_max, true, true);
     InvertLayout b = invert_layout(std::min(d_max, k_max), k_max, k_max, true);
     need = std::max(a.total, b.total);
   }
@@ -999,6 +1023,46 @@ KFAC_API kfac_status kfac_ea_update_rows(kfac_ctx* ctx, int n, int cols, const f
   return ea_run(ctx, d, n, X, (int)ldx, rho, prec, F, ldf, 0);
 }
 
+KFAC_API kfac_status kfac_ea_update_conv(kfac_ctx* ctx, int n, int c, int h, int w, const float* x, int kh, int kw,
+                                         int stride_h, int stride_w, int pad_h, int pad_w, int append_one, float scale,
+                                         float rho, kfac_precision prec, float* F, int ldf) {
+  if (!ctx || n < 0 || c <= 0 || h <= 0 || w <= 0 || kh <= 0 || kw <= 0 || stride_h <= 0 || stride_w <= 0 ||
+      pad_h < 0 || pad_w < 0 || kh > h + 2 * pad_h || kw > w + 2 * pad_w)
+    return KFAC_ERR_INVALID_ARG;
+  const long long dl = (long long)c * kh * kw + (append_one ? 1 : 0);
+  if (!F || ldf < dl || (n > 0 && !x)) return KFAC_ERR_INVALID_ARG;
+  if (dl > 65535) return KFAC_ERR_UNSUPPORTED;  // one grid row of the patch kernel per factor row
+  if (!(rho >= 0.0f && rho <= 1.0f) || !(scale == scale) || prec < KFAC_PREC_FP32 || prec > KFAC_PREC_BF16)
+    return KFAC_ERR_INVALID_ARG;
+  const int d = (int)dl;
+  const int ho = (h + 2 * pad_h - kh) / stride_h + 1, wo = (w + 2 * pad_w - kw) / stride_w + 1;
+  const long long pos = (long long)ho * wo;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  // Samples per chunk: the patch matrix of a chunk fits KFAC_OPT_CONV_CHUNK floats.
+  long long per = std::max<long long>(1, ctx->conv_chunk / std::max<long long>(1, (long long)d * pos));
+  per = std::min<long long>(per, std::max(n, 1));
+  while (per > 1 && per * pos > (1LL << 30)) per /= 2;
+  const long long ldx = round_up(per * pos, 4);
+  kfac_status st = ensure_ws(ctx, sizeof(float) * (size_t)d * (size_t)ldx);
+  if (st != KFAC_OK) return st;
+  float* X = at<float>(ctx, 0);
+  const float alpha = n > 0 ? (1.0f - rho) / (float)((double)n * pos) : 0.0f;
+  STAGE(ctx, ST_EA);
+  if (n == 0) {
+    CK(syrk_update(ctx->stream, d, 0, X, (int)ldx, 0.0f, rho, prec, F, ldf, ctx->dflags, ctx->wait_cycles));
+    return KFAC_OK;
+  }
+  for (int i0 = 0; i0 < n; i0 += (int)per) {
+    const int ns = (int)std::min<long long>(per, n - i0);
+    CK(im2col_f32(x, c, h, w, kh, kw, stride_h, stride_w, pad_h, pad_w, i0, ns, append_one ? 1 : 0, scale, X, ldx,
+                  ctx->stream));
+    CK(syrk_update(ctx->stream, d, (int)(ns * pos), X, (int)ldx, alpha, i0 == 0 ? rho : 1.0f, prec, F, ldf,
+                   ctx->dflags, ctx->wait_cycles));
+  }
+  return KFAC_OK;
+}
+
 static kfac_status check_ea(const kfac_ea_desc& a) {
   if (a.d < 0 || a.n < 0 || a.ldf < a.d || (a.d > 0 && !a.F) || (a.n > 0 && (!a.X || a.ldx < a.n)))
     return KFAC_ERR_INVALID_ARG;
@@ -1066,7 +1130,7 @@ KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int 
   if (st != KFAC_OK) return st;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  InvertLayout L = invert_layout(d, k, r, !tma_rows_ok(F, ldf));
+  InvertLayout L = invert_layout(d, k, r, !tma_rows_ok(F, ldf), prec == KFAC_PREC_BF16);
   if ((st = ensure_ws(ctx, L.total)) != KFAC_OK) return st;
   return invert_run(ctx, a, L, 0);
 }
@@ -1079,7 +1143,7 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
     int r = 0, k = 0;
     kfac_status st = check_invert(descs[f], &r, &k);
     if (st != KFAC_OK) return st;
-    lay[f] = invert_layout(descs[f].d, k, r, !tma_rows_ok(descs[f].F, descs[f].ldf));
+    lay[f] = invert_layout(descs[f].d, k, r, !tma_rows_ok(descs[f].F, descs[f].ldf), descs[f].prec == KFAC_PREC_BF16);
   }
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;

@@ -103,6 +103,7 @@ struct GemmDesc {
   int* flags;  // device status word for bounded-wait timeouts (may be null)
   long long wait_cycles;  // limit of the tensor-core kernels' waits on each other's progress (0: default)
   int split_target;       // split K of a product with few tiles up to this many CTAs (0: 152, < 0: never)
+  int ab_bf16;            // A and B point to BF16 data (K-major, strides in elements; tensor cores only)
 };
 
 // Default limit of a tensor-core kernel's wait for another role's progress:
@@ -138,6 +139,14 @@ cudaError_t pack_rows_f32(const float* src, long long lds, int rows, int cols, f
 // batch A (n x cols), plus a last row of ones when append_one; pad columns zeroed.
 cudaError_t rows_to_cols_f32(const float* A, long long lda, int n, int cols, int append_one, float scale, float* X,
                              long long ldx, cudaStream_t s);
+// Patch matrix (d x ldx, d = c kh kw + append_one) of samples [i0, i0 + ns) of
+// an NCHW convolution input: column (sample, output position), row (channel,
+// kernel row, kernel column), zero padding, times `scale`; pad columns zeroed.
+cudaError_t im2col_f32(const float* x, int c, int h, int w, int kh, int kw, int sh, int sw, int ph, int pw, int i0,
+                       int ns, int append_one, float scale, float* X, long long ldx, cudaStream_t s);
+// dst (rows x cols BF16, row stride ldd a multiple of 8, 16-byte aligned) <-
+// src (FP32, row stride lds) rounded to nearest even; pad columns zeroed.
+cudaError_t to_bf16_f32(const float* src, long long lds, int rows, int cols, void* dst, long long ldd, cudaStream_t s);
 // True when TMA can read a row-major FP32 matrix at p with row stride ld as is
 // (16-byte aligned base and row stride).
 inline bool tma_rows_ok(const void* p, long long ld) {

@@ -179,26 +179,28 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_cluster(EigArgs a) {
     }
     cp_async_wait_all();
   }
-  // Exact power-of-two rescaling so that the largest entry is in [0.5, 1):
-  // products of squared column norms of a tiny-scale matrix (the R factor of
-  // a factor scaled 1e-6, say) would otherwise underflow in the pair tests.
-  // Rotations are scale-invariant, so the columns' directions are unchanged.
-  __syncthreads();
-  {
+  // SVD input (a.full): exact power-of-two rescaling so that the largest entry
+  // is in [0.5, 1), since products of squared column norms of a tiny-scale
+  // matrix (the R factor of a factor scaled 1e-6, say) would otherwise
+  // underflow in the pair tests. The eigensolver's Cholesky factor is used as
+  // loaded (its validated path). a.full is uniform over the cluster, so every
+  // CTA takes the same barriers.
+  int wexp = 0;
+  if (a.full) {
+    __syncthreads();
     float m = 0.0f;
     for (int e = tid; e < 2 * slot; e += EIG_THREADS) m = fmaxf(m, fabsf(esm[e]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0 && m > 0.0f) atomicMax(&s_absmax, __float_as_uint(m));
+    cluster.sync();  // every CTA's blocks are loaded and its maximum taken
+    if (tid == 0 && s_absmax) atomicMax(cluster.map_shared_rank(&s_absmax, 0), s_absmax);
+    cluster.sync();
+    const float wmax = __uint_as_float(*cluster.map_shared_rank(&s_absmax, 0));
+    frexpf(wmax, &wexp);  // wmax = f 2^wexp, f in [0.5, 1) (wexp = 0 for a zero matrix)
+    const float wscale = ldexpf(1.0f, -wexp);
+    for (int e = tid; e < 2 * slot; e += EIG_THREADS) esm[e] *= wscale;
   }
-  cluster.sync();  // every CTA's blocks are loaded and its maximum taken
-  if (tid == 0 && s_absmax) atomicMax(cluster.map_shared_rank(&s_absmax, 0), s_absmax);
-  cluster.sync();
-  const float wmax = __uint_as_float(*cluster.map_shared_rank(&s_absmax, 0));
-  int wexp = 0;
-  frexpf(wmax, &wexp);  // wmax = f 2^wexp, f in [0.5, 1) (wexp = 0 for a zero matrix)
-  const float wscale = ldexpf(1.0f, -wexp);
-  for (int e = tid; e < 2 * slot; e += EIG_THREADS) esm[e] *= wscale;
-  // Every CTA has its blocks (rescaled) before the first distributed shared memory store.
+  // Every CTA has its blocks before the first distributed shared memory store.
   cluster.sync();
 
   // ---- sweeps ---------------------------------------------------------------

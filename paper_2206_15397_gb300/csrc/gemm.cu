@@ -37,13 +37,21 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
   const bool kmajor = g.sak == 1 && g.sbk == 1;
   const tc::Mode mode = prec == KFAC_PREC_FP32 ? tc::Mode::Fp32 : (prec == KFAC_PREC_TF32 ? tc::Mode::Tf32 : tc::Mode::Bf16);
   const int kalign = tc::k_step(mode);  // a K-chunk must cover whole K-steps of the kernel
-  const bool tc_ok = kmajor && g.K > 0 &&
+  const bool bf16d = g.ab_bf16 != 0;     // operands already BF16: only the direct tensor-core kernel reads them
+  if (bf16d && (!kmajor || g.K <= 0 || prec != KFAC_PREC_BF16 || g.sym || !tma_rows_ok(g.A, 2 * g.sam) ||
+                !tma_rows_ok(g.B, 2 * g.sbn) || (g.sam & 7) || (g.sbn & 7) || g.sam < g.K || g.sbn < g.K ||
+                (g.zsplit > 1 && g.kchunk % 64 != 0)))
+    return cudaErrorInvalidValue;
+  const bool tc_ok = bf16d || (kmajor && g.K > 0 &&
                      tc::eligible(g.A, g.sam, g.B, g.sbn, g.M, g.N, g.K) &&
-                     (g.zsplit <= 1 || g.kchunk % kalign == 0) && !(g.sym && g.zsplit > 1);
+                     (g.zsplit <= 1 || g.kchunk % kalign == 0) && !(g.sym && g.zsplit > 1));
   if (!tc_ok) {
     if (g.K > 0) note_simt_gemm();
     return gemm_simt_f32(g, round_of(prec), s);
   }
+  auto launch = [&](const tc::TcArgs& a, int zsplit) {
+    return bf16d ? tc::gemm_bf16(a, g.A, g.sam, g.B, g.sbn, zsplit, s) : tc::gemm(a, g.A, g.sam, g.B, g.sbn, zsplit, mode, s);
+  };
 
   tc::TcArgs a = {};
   a.M = g.M; a.N = g.N; a.K = g.K;
@@ -55,9 +63,9 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
   a.wait_cycles = g.wait_cycles > 0 ? g.wait_cycles : kDefaultWaitCycles;
   if (g.zsplit > 1) {  // caller-managed raw partials
     a.partial = 1; a.kchunk = g.kchunk; a.zstride = g.zstride;
-    return tc::gemm(a, g.A, g.sam, g.B, g.sbn, g.zsplit, mode, s);
+    return launch(a, g.zsplit);
   }
-  const int bn = tc::tile_n(g.N, mode);
+  const int bn = bf16d ? (g.N > 128 ? 256 : 128) : tc::tile_n(g.N, mode);
   long long tiles = cdiv(g.M, 128) * cdiv(g.N, bn);
   if (g.sym) tiles = (tiles + 1) / 2;
   const long long rows = g.d_trans ? g.N : g.M, cols = g.d_trans ? g.M : g.N;
@@ -71,7 +79,7 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
     const int kchunk = (int)(cdiv(cdiv(g.K, z), kalign) * kalign);
     z = (int)cdiv(g.K, kchunk);
     a.partial = 1; a.kchunk = kchunk; a.D = g.ws; a.ldd = cols; a.zstride = rows * cols;
-    cudaError_t e = tc::gemm(a, g.A, g.sam, g.B, g.sbn, z, mode, s);
+    cudaError_t e = launch(a, z);
     if (e != cudaSuccess) return e;
     const long long tot = rows * cols;
     k_reduce_epilogue<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(g.ws, z, rows * cols, (int)rows, (int)cols, g);
@@ -80,7 +88,24 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
   }
   a.partial = 0;
   a.kchunk = (int)(cdiv(g.K, kalign) * kalign);
-  return tc::gemm(a, g.A, g.sam, g.B, g.sbn, 1, mode, s);
+  return launch(a, 1);
+}
+
+cudaError_t syrk_update(cudaStream_t s, int d, int K, const float* X, int ldx, float alpha, float beta,
+                        kfac_precision prec, float* F, int ldf, int* flags, long long wait_cycles) {
+  GemmDesc<float> g = {};
+  g.M = d; g.N = d; g.K = K;
+  g.A = X; g.sam = ldx; g.sak = 1;
+  g.B = X; g.sbn = ldx; g.sbk = 1;
+  g.D = F; g.ldd = ldf;
+  g.C0 = F; g.ldc = ldf;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.zsplit = 1;
+  g.sym = 1;
+  g.flags = flags;
+  g.wait_cycles = wait_cycles;
+  return gemm_f32(g, prec, s);
 }
 
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,

@@ -15,4 +15,8 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,
                     int ldf, int* flags, long long wait_cycles = 0);
 
+// F <- beta F + alpha X X^T (exactly symmetric), X d x K with row stride ldx.
+cudaError_t syrk_update(cudaStream_t s, int d, int K, const float* X, int ldx, float alpha, float beta,
+                        kfac_precision prec, float* F, int ldf, int* flags, long long wait_cycles = 0);
+
 }  // namespace kfac

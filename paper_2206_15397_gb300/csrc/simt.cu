@@ -294,6 +294,53 @@ __global__ void k_rows_to_cols(const float* __restrict__ A, long long lda, int n
   }
 }
 
+// Patch matrix of a convolution input for samples [i0, i0 + ns): row
+// (ch * kh + r) * kw + t, column (i - i0) * ho * wo + oy * wo + ox holds
+// scale * x[i, ch, oy * sh + r - ph, ox * sw + t - pw] (0 outside the image);
+// with append_one a last row of `scale`; columns past ns * ho * wo zeroed. One
+// thread per column and row: consecutive threads take consecutive output
+// positions, so the writes are coalesced and the reads strided by sw.
+__global__ void k_im2col(const float* __restrict__ x, int c, int h, int w, int kh, int kw, int sh, int sw, int ph,
+                         int pw, int ho, int wo, int i0, int ns, int append_one, float scale, float* __restrict__ X,
+                         long long ldx) {
+  const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (col >= ldx) return;
+  const long long pos = (long long)ho * wo, ncols = (long long)ns * pos;
+  float v = 0.0f;
+  if (col < ncols) {
+    if (append_one && row == c * kh * kw) {
+      v = scale;
+    } else {
+      const int i = i0 + (int)(col / pos);
+      const int q = (int)(col % pos), oy = q / wo, ox = q % wo;
+      const int ch = row / (kh * kw), rt = row % (kh * kw), r = rt / kw, t = rt % kw;
+      const int y = oy * sh + r - ph, xx = ox * sw + t - pw;
+      if (y >= 0 && y < h && xx >= 0 && xx < w) v = scale * x[(((long long)i * c + ch) * h + y) * w + xx];
+    }
+  }
+  X[(long long)row * ldx + col] = v;
+}
+
+// BF16 copy with a padded row stride: one thread per 8 outputs (a 16-byte store).
+__global__ void k_to_bf16(const float* __restrict__ src, long long lds, int rows, int cols,
+                          uint4* __restrict__ dst, long long ldd8) {
+  const long long total = (long long)rows * ldd8;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long r = g / ldd8;
+    const int c = (int)(g - r * ldd8) * 8;
+    const float* sr = src + r * lds;
+    unsigned u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float a = c + 2 * q < cols ? sr[c + 2 * q] : 0.0f, b = c + 2 * q + 1 < cols ? sr[c + 2 * q + 1] : 0.0f;
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u[q]) : "f"(b), "f"(a));
+    }
+    dst[g] = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+}
+
 __global__ void k_convert(const float* __restrict__ in, long long ldi, int rows, int cols, double* __restrict__ out,
                           long long ldo, int* flags) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -389,6 +436,26 @@ cudaError_t pack_rows_f32(const float* src, long long lds, int rows, int cols, f
   const long long total = (long long)rows * (ldd >> 2);
   const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
   k_pack_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, rows, cols, dst, ldd);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t to_bf16_f32(const float* src, long long lds, int rows, int cols, void* dst, long long ldd, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const long long total = (long long)rows * (ldd / 8);
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
+  k_to_bf16<<<(unsigned)blocks, 256, 0, s>>>(src, lds, rows, cols, static_cast<uint4*>(dst), ldd / 8);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t im2col_f32(const float* x, int c, int h, int w, int kh, int kw, int sh, int sw, int ph, int pw, int i0,
+                       int ns, int append_one, float scale, float* X, long long ldx, cudaStream_t s) {
+  const int ho = (h + 2 * ph - kh) / sh + 1, wo = (w + 2 * pw - kw) / sw + 1;
+  const int d = c * kh * kw + (append_one ? 1 : 0);
+  if (d <= 0 || ldx <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((ldx + 255) / 256), (unsigned)d);
+  k_im2col<<<grid, 256, 0, s>>>(x, c, h, w, kh, kw, sh, sw, ph, pw, ho, wo, i0, ns, append_one, scale, X, ldx);
   note_launch();
   return cudaGetLastError();
 }

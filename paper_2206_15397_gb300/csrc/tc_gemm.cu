@@ -310,10 +310,15 @@ __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int
   }
 }
 
-template <int BN>
+// BF16D: A and B are BF16 in global memory (64 K-columns = 128 bytes per
+// stage row, tcgen05.mma.kind::f16 with K = 16); otherwise FP32 read as TF32
+// (32 K-columns per stage row, kind::tf32 with K = 8). The shared-memory tiles
+// have the same shape and swizzle either way.
+template <int BN, bool BF16D = false>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
   using C = Cfg<BN>;
+  constexpr int BK = BF16D ? 64 : 32;  // K elements per stage (128-byte rows)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
@@ -366,7 +371,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags, kDrainCycles);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----------------------------------------------------------
-    constexpr uint32_t idesc = idesc_tf32(BM, BN);
+    constexpr uint32_t idesc = BF16D ? idesc_bf16(BM, BN) : idesc_tf32(BM, BN);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
@@ -375,9 +380,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per instruction
+      for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction: 8 TF32 or 16 BF16
         const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4
-        mma_tf32(taddr, ad + off, bd + off, idesc, (kb | kk) ? 1u : 0u);
+        if (BF16D) mma_bf16(taddr, ad + off, bd + off, idesc, (kb | kk) ? 1u : 0u);
+        else mma_tf32(taddr, ad + off, bd + off, idesc, (kb | kk) ? 1u : 0u);
       }
       mma_commit(empty0 + 8 * s);  // stage reusable once these MMAs completed
     }
@@ -744,28 +750,31 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D map of a row-major FP32 matrix (rows x cols, row stride ld) read in
 // boxes of 32 columns x box_rows rows with the 128-byte swizzle.
-bool make_map(CUtensorMap* map, const float* ptr, int rows, int cols, long long ld, int box_rows) {
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, long long ld, int box_rows, bool bf16 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
+  const int esz = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};  // 128-byte rows
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+  CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 template <typename Kern>
-cudaError_t launch_kernel(Kern kern, int smem, int bn, const TcArgs& a, const float* A, long long lda,
-                          const float* B, long long ldb, int zsplit, cudaStream_t s) {
+cudaError_t launch_kernel(Kern kern, int smem, int bn, const TcArgs& a, const void* A, long long lda,
+                          const void* B, long long ldb, int zsplit, cudaStream_t s, bool bf16 = false) {
   {
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(kern), smem, false);
     if (e != cudaSuccess) return e;
   }
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, bn)) return cudaErrorInvalidValue;
+  if (!make_map(&ma, A, a.M, a.K, lda, BM, bf16) || !make_map(&mb, B, a.N, a.K, ldb, bn, bf16))
+    return cudaErrorInvalidValue;
   dim3 grid((a.N + bn - 1) / bn, (a.M + BM - 1) / BM, zsplit);
   kern<<<grid, THREADS, smem, s>>>(ma, mb, a);
   note_launch();
@@ -773,6 +782,12 @@ cudaError_t launch_kernel(Kern kern, int smem, int bn, const TcArgs& a, const fl
 }
 
 }  // namespace
+
+cudaError_t gemm_bf16(const TcArgs& a, const void* A, long long lda, const void* B, long long ldb, int zsplit,
+                      cudaStream_t s) {
+  if (a.N > 128) return launch_kernel(k_tc_gemm<256, true>, Cfg<256>::SMEM, 256, a, A, lda, B, ldb, zsplit, s, true);
+  return launch_kernel(k_tc_gemm<128, true>, Cfg<128>::SMEM, 128, a, A, lda, B, ldb, zsplit, s, true);
+}
 
 bool eligible(const float* A, long long lda, const float* B, long long ldb, int M, int N, int K) {
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };

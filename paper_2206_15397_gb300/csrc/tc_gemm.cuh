@@ -43,6 +43,11 @@ inline int k_step(Mode mode) { return mode == Mode::Bf16 ? 64 : 32; }
 // Launch one GEMM.
 cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
                  Mode mode, cudaStream_t s);
+// The same with A and B already BF16 in global memory (row strides lda, ldb in
+// elements, multiples of 8; 16-byte aligned bases): TMA loads the BF16 tiles
+// directly and tcgen05.mma.kind::f16 multiplies them; a.kchunk a multiple of 64.
+cudaError_t gemm_bf16(const TcArgs& a, const void* A, long long lda, const void* B, long long ldb, int zsplit,
+                      cudaStream_t s);
 
 }  // namespace tc
 }  // namespace kfac

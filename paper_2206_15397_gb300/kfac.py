@@ -21,7 +21,8 @@ OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_swee
            "cholqr_inner_passes": 5, "cholqr_fp32_passes": 6,
            "basis_polish": 7, "cholqr_inner_fp32": 8, "eig_stop_tol": 9, "eig_refine_fp64": 10, "wait_cycles": 11,
            "group_streams": 12, "invert_method": 13,
-           "chol_cluster": 14, "split_target": 15, "warm_start": 16}
+           "chol_cluster": 14, "split_target": 15, "warm_start": 16,
+           "conv_chunk": 17}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
@@ -72,6 +73,8 @@ def lib():
         L.kfac_reserve.argtypes = [vp, i, i, i64]
         L.kfac_set_option.argtypes = [vp, i, d]
         L.kfac_get_status.argtypes = [vp, ctypes.POINTER(i)]
+        L.kfac_ea_update_conv.argtypes = [vp, i, i, i, i, vp, i, i, i, i, i, i, i, f, f, i, vp, i]
+        L.kfac_ea_update_conv.restype = i
         L.kfac_ea_update_rows.argtypes = [vp, i, i, vp, i, i, f, f, i, vp, i]
         L.kfac_ea_update_rows.restype = i
         L.kfac_autotune_invert.argtypes = [vp, i, ctypes.POINTER(InvertDesc), ctypes.c_char_p, ctypes.POINTER(i)]
@@ -212,6 +215,22 @@ def kfac_ea_update_rows(ctx: Context, A: torch.Tensor, F: torch.Tensor, rho: flo
     pf, ldf = _mat(F, "F", d, d)
     _check(lib().kfac_ea_update_rows(ctx.handle, n, cols, pa, lda, int(bool(append_one)), float(scale), float(rho),
                                      PRECISION[prec], pf, ldf), "kfac_ea_update_rows")
+    return F
+
+
+def kfac_ea_update_conv(ctx: Context, x: torch.Tensor, F: torch.Tensor, kernel, rho: float, stride=(1, 1),
+                        padding=(0, 0), append_one: bool = False, scale: float = 1.0, prec: str = "fp32"):
+    """Conv-layer factor from the patch statistics of x (n, c, h, w), updated in place."""
+    if (not isinstance(x, torch.Tensor) or x.device.type != "cuda" or x.dtype != torch.float32 or x.dim() != 4
+            or not x.is_contiguous()):
+        raise KfacError("x must be a contiguous 4-D CUDA float32 tensor (NCHW)")
+    n, c, h, w = x.shape
+    kh, kw = kernel
+    d = c * kh * kw + int(bool(append_one))
+    pf, ldf = _mat(F, "F", d, d)
+    _check(lib().kfac_ea_update_conv(ctx.handle, n, c, h, w, ctypes.c_void_p(x.data_ptr()), kh, kw, stride[0],
+                                     stride[1], padding[0], padding[1], int(bool(append_one)), float(scale),
+                                     float(rho), PRECISION[prec], pf, ldf), "kfac_ea_update_conv")
     return F
 
 
