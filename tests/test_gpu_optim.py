@@ -82,6 +82,6 @@ def test_training_with_the_amortised_schedule_reduces_the_loss(optim):
         loss.backward()
         pre.step()
         sgd.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert pre.status()[0] == 0
     assert losses[-1] < 0.7 * losses[0], losses
