@@ -289,17 +289,18 @@ KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, c
 
 /* Autotuner of a grouped inversion's schedule on this GPU: the number of
  * streams a grouped call forks (KFAC_OPT_GROUP_STREAMS), the cluster size of
- * the multi-CTA Cholesky (KFAC_OPT_CHOL_CLUSTER; only when a sketch width
- * exceeds the one-CTA kernel's 236) and the CTA count split-K products may
- * fill (KFAC_OPT_SPLIT_TARGET). Runs kfac_rsvd_invert_grouped(ctx, count,
+ * the multi-CTA Cholesky and its panel width (KFAC_OPT_CHOL_CLUSTER and
+ * KFAC_OPT_CHOL_PANEL; only when a sketch width exceeds the one-CTA kernel's
+ * 236) and the CTA count split-K products may fill (KFAC_OPT_SPLIT_TARGET). Runs kfac_rsvd_invert_grouped(ctx, count,
  * descs) once plus twice timed (CUDA events on the context stream) per
  * candidate of a coordinate descent from the current settings, writing the
  * descriptors' outputs as a call would, and keeps the fastest settings in the
  * context. cache_path (may be NULL): a text file of earlier results, one line
  * per device name and shape signature (the factors' d, k, power iterations
  * and precision, and the inversion method); a hit is applied without timing,
- * a new result is appended. chosen (may be NULL, 4 ints) receives the streams,
- * cluster size, split target and 1 if the result came from the cache. Not
+ * a new result is appended. chosen (may be NULL, 5 ints) receives the streams,
+ * cluster size, split target, panel width and 1 if the result came from the
+ * cache. Not
  * during stream capture (it synchronises). */
 KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_invert_desc* descs,
                                           const char* cache_path, int* chosen);
@@ -374,6 +375,9 @@ typedef enum {
                                        than 4/5 of this many CTAs and K >= 1024 splits K into
                                        chunks of at least 512 so that up to this many CTAs
                                        share it, summed by a reducing epilogue; -1 = never */
+  KFAC_OPT_CHOL_PANEL = 18,         /* [16]: panel width of the multi-CTA Cholesky, 16 or 32
+                                       (halved while its shared memory overflows); wider panels
+                                       take half the cluster barriers and broadcasts */
   KFAC_OPT_CHOL_CLUSTER = 14,       /* [0 = automatic]: CTAs of the multi-CTA FP32/FP64
                                        Cholesky used where the one-CTA kernel's shared memory
                                        cannot hold the k x k Gram (k > 236), 1..16; raised to

@@ -67,6 +67,7 @@ struct kfac_ctx {
   int group_streams = 16;  // side streams a grouped call may fork (KFAC_OPT_GROUP_STREAMS)
   int invert_method = 0;   // KFAC_OPT_INVERT_METHOD: 0 SREVD (Alg. 3), 1 RSVD V~ (Alg. 2, RS-KFAC)
   int chol_cluster = 0;    // KFAC_OPT_CHOL_CLUSTER: CTAs of the multi-CTA Cholesky (0 = automatic)
+  int chol_panel = 16;     // KFAC_OPT_CHOL_PANEL: its panel width (16 or 32)
   int split_target = 0;    // KFAC_OPT_SPLIT_TARGET: CTAs a split-K product may fill (0 = 152, -1 = no split)
   int warm_start = 0;      // KFAC_OPT_WARM_START: previous U seeds the sketch
   long long conv_chunk = 32LL << 20;  // KFAC_OPT_CONV_CHUNK: floats of one patch-matrix chunk
@@ -288,7 +289,7 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       const bool fp64 = (final_basis || !ctx->cholqr_inner_fp32) &&
                         (pass >= ctx->cholqr_fp32_passes || (pass + 1 == passes && ctx->cholqr_fp32_passes < passes));
       CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
-                      ctx->stream, nullptr, at<float>(ctx, L.g32), k, ctx->chol_cluster));
+                      ctx->stream, nullptr, at<float>(ctx, L.g32), k, ctx->chol_cluster, ctx->chol_panel));
     }
     {
       STAGE(ctx, ST_TRSM);
@@ -304,7 +305,7 @@ kfac_status eigensolve(kfac_ctx* ctx, const double* C, const float* C32, long lo
   {
     STAGE(ctx, ST_EIG);
     CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, (float)ctx->eig_stop_tol, X, lam, jac,
-                      ctx->dflags, ctx->dstats, ctx->stream, C32, ld32, ctx->chol_cluster));
+                      ctx->dflags, ctx->dstats, ctx->stream, C32, ld32, ctx->chol_cluster, ctx->chol_panel));
   }
   STAGE(ctx, ST_REFINE);
   for (int it = 0; it < ctx->eig_refine; ++it) {
@@ -857,6 +858,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       if (v < -1 || v > 4096) return KFAC_ERR_INVALID_ARG;
       ctx->split_target = (int)v;
       return KFAC_OK;
+    case KFAC_OPT_CHOL_PANEL:
+      if (v != 16 && v != 32) return KFAC_ERR_INVALID_ARG;
+      ctx->chol_panel = (int)v;
+      return KFAC_OK;
     case KFAC_OPT_CHOL_CLUSTER:
       if (v < 0 || v > 16) return KFAC_ERR_INVALID_ARG;
       ctx->chol_cluster = (int)v;
@@ -1219,11 +1224,11 @@ static bool cache_lookup(const char* path, const char* dev, unsigned long long s
   while (fgets(line, sizeof line, fp)) {
     char name[256];
     unsigned long long s = 0;
-    int a = 0, b = 0, c = 0;
+    int a = 0, b = 0, c = 0, e = 0;
     double ms = 0.0;
-    if (sscanf(line, "%255[^|]|%llx %d %d %d %lf", name, &s, &a, &b, &c, &ms) == 6 && s == sig &&
+    if (sscanf(line, "%255[^|]|%llx %d %d %d %d %lf", name, &s, &a, &b, &c, &e, &ms) == 7 && s == sig &&
         strcmp(name, dev) == 0) {
-      cfg[0] = a; cfg[1] = b; cfg[2] = c;
+      cfg[0] = a; cfg[1] = b; cfg[2] = c; cfg[3] = e;
       found = true;  // the last entry for this key wins
     }
   }
@@ -1246,7 +1251,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
   for (char* c = prop.name; *c; ++c)
     if (*c == '|' || *c == '\n') *c = ' ';
   const unsigned long long sig = invert_signature(ctx, count, descs);
-  int cfg[3] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target};
+  int cfg[4] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target, ctx->chol_panel};
   bool cached = cache_path && cache_lookup(cache_path, prop.name, sig, cfg);
   double best_ms = 0.0;
   if (!cached) {
@@ -1260,7 +1265,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return KFAC_ERR_CUDA; }
     // One warm-up and two timed grouped inversions per candidate.
     auto run = [&](const int* c, double* ms) -> kfac_status {
-      ctx->group_streams = c[0]; ctx->chol_cluster = c[1]; ctx->split_target = c[2];
+      ctx->group_streams = c[0]; ctx->chol_cluster = c[1]; ctx->split_target = c[2]; ctx->chol_panel = c[3];
       kfac_status st = kfac_rsvd_invert_grouped(ctx, count, descs);
       if (st != KFAC_OK) return st;
       if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
@@ -1273,18 +1278,19 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
       *ms = t / 2.0;
       return KFAC_OK;
     };
-    // Coordinate descent over the three knobs, from the current settings.
+    // Coordinate descent over the four knobs, from the current settings.
     const int streams_c[] = {4, 8, 16, 32};
     const int chol_c[] = {0, 8, 12};
     const int split_c[] = {0, 304, -1};
+    const int panel_c[] = {16, 32};
     kfac_status st = run(cfg, &best_ms);
-    for (int dim = 0; dim < 3 && st == KFAC_OK; ++dim) {
-      const int* cand = dim == 0 ? streams_c : (dim == 1 ? chol_c : split_c);
-      const int n = dim == 0 ? 4 : 3;
-      if (dim == 1 && !big_k) continue;  // no factor uses the multi-CTA Cholesky
+    for (int dim = 0; dim < 4 && st == KFAC_OK; ++dim) {
+      const int* cand = dim == 0 ? streams_c : (dim == 1 ? chol_c : (dim == 2 ? split_c : panel_c));
+      const int n = dim == 0 ? 4 : (dim == 3 ? 2 : 3);
+      if ((dim == 1 || dim == 3) && !big_k) continue;  // no factor uses the multi-CTA Cholesky
       for (int i = 0; i < n && st == KFAC_OK; ++i) {
         if (cand[i] == cfg[dim]) continue;
-        int trial[3] = {cfg[0], cfg[1], cfg[2]};
+        int trial[4] = {cfg[0], cfg[1], cfg[2], cfg[3]};
         trial[dim] = cand[i];
         double ms = 0.0;
         st = run(trial, &ms);
@@ -1300,7 +1306,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     if (cache_path) {
       FILE* fp = fopen(cache_path, "a");
       if (fp) {
-        fprintf(fp, "%s|%llx %d %d %d %.4f\n", prop.name, sig, cfg[0], cfg[1], cfg[2], best_ms);
+        fprintf(fp, "%s|%llx %d %d %d %d %.4f\n", prop.name, sig, cfg[0], cfg[1], cfg[2], cfg[3], best_ms);
         fclose(fp);
       }
     }
@@ -1308,7 +1314,8 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
   ctx->group_streams = cfg[0];
   ctx->chol_cluster = cfg[1];
   ctx->split_target = cfg[2];
-  if (chosen) { chosen[0] = cfg[0]; chosen[1] = cfg[1]; chosen[2] = cfg[2]; chosen[3] = cached ? 1 : 0; }
+  ctx->chol_panel = cfg[3];
+  if (chosen) { chosen[0] = cfg[0]; chosen[1] = cfg[1]; chosen[2] = cfg[2]; chosen[3] = cfg[3]; chosen[4] = cached ? 1 : 0; }
   return KFAC_OK;
 }
 

@@ -336,7 +336,7 @@ size_t chol_smem_bytes(int k, int nloc, int B, size_t elt) {
 // shared memory holds the rows); 0 = one CTA per 16 rows, at most 16.
 template <typename T>
 cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, int* flags,
-                        unsigned long long* stats, cudaStream_t s, double* shift_out, int nc_pref) {
+                        unsigned long long* stats, cudaStream_t s, double* shift_out, int nc_pref, int panel) {
   {
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cluster<T>), kSmemOptin, true);
     if (e != cudaSuccess) return e;
@@ -346,9 +346,10 @@ cudaError_t launch_chol(const double* G, int k, double shift_rel, float* L32, in
   if (nc < 1) nc = 1;
   int B = 16, nloc = 0;
   size_t smem = 0;
-  for (;; ++nc) {  // fewest CTAs from nc up whose rows fit (panel width 16, else 8, else 4)
+  const int B0 = panel == 32 ? 32 : 16;
+  for (;; ++nc) {  // fewest CTAs from nc up whose rows fit (panel width B0, else halved down to 4)
     nloc = (k + nc - 1) / nc;
-    for (B = 16; B >= 4; B /= 2) {
+    for (B = B0; B >= 4; B /= 2) {
       smem = chol_smem_bytes(k, nloc, B, sizeof(T));
       if (smem <= (size_t)kSmemOptin) break;
     }
@@ -665,7 +666,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
 
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
                          unsigned long long* stats, cudaStream_t s, double* shift_out, const float* G32,
-                         long long ld32, int nc_pref) {
+                         long long ld32, int nc_pref, int panel) {
   if (k <= 0) return cudaSuccess;
   if (!fp64 && k <= CTA_KMAX && cta_smem_bytes(k) <= (size_t)kSmemOptin) {
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cta_f32), kSmemOptin, false);
@@ -675,8 +676,8 @@ cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, fl
     note_launch();
     return cudaGetLastError();
   }
-  return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref)
-              : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref);
+  return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref, panel)
+              : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref, panel);
 }
 
 // ---------------------------------------------------------------------------

@@ -164,9 +164,10 @@ inline bool tma_rows_ok(const void* p, long long ld) {
 // instead of converting G (a conversion runs on the FP64 pipe).
 // nc_pref: cluster size of the multi-CTA kernel (0 = one CTA per 16 rows, at
 // most 16; raised to the fewest CTAs whose shared memory holds the rows).
+// panel: its panel width, 16 or 32 (halved while the shared memory overflows).
 cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, float* L32, int* flags,
                          unsigned long long* stats, cudaStream_t s, double* shift_out = nullptr,
-                         const float* G32 = nullptr, long long ld32 = 0, int nc_pref = 0);
+                         const float* G32 = nullptr, long long ld32 = 0, int nc_pref = 0, int panel = 16);
 
 // Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
 // dinv_ws: trsm_ws_floats(k) floats of workspace (L packed by 32-row block rows
@@ -185,7 +186,8 @@ inline size_t eig_scratch_floats(int k) { return (((size_t)k * k + 1) & ~(size_t
 // stop_tol > 0 ends the sweeps after one whose largest pair cosine was below it.
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, float stop_tol,
                            double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
-                           cudaStream_t s, const float* C32 = nullptr, long long ld32 = 0, int chol_nc = 0);
+                           cudaStream_t s, const float* C32 = nullptr, long long ld32 = 0, int chol_nc = 0,
+                           int chol_panel = 16);
 
 // One-sided Jacobi on the columns of the k x k FP32 matrix held in gscratch
 // (row-major; the factor eig_jacobi_f32 writes there), with the device scalar
