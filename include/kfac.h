@@ -375,6 +375,13 @@ typedef enum {
                                        than 4/5 of this many CTAs and K >= 1024 splits K into
                                        chunks of at least 512 so that up to this many CTAs
                                        share it, summed by a reducing epilogue; -1 = never */
+  KFAC_OPT_TAIL_PLANES = 19,        /* [1]: FP32 (3xTF32) products read precomputed TF32 tails
+                                       of their large operands (the factor's once per
+                                       inversion, 4 d^2 bytes of workspace per concurrent
+                                       item; the batch's and the k x d bases' per product)
+                                       instead of every CTA forming them in shared memory;
+                                       0 = form them in the kernel (less workspace). Results
+                                       are bitwise the same either way */
   KFAC_OPT_CHOL_PANEL = 18,         /* [16]: panel width of the multi-CTA Cholesky, 16 or 32
                                        (halved while its shared memory overflows); wider panels
                                        take half the cluster barriers and broadcasts */
@@ -398,7 +405,12 @@ typedef enum {
                                        stream, 1..32 (1 = every item in turn on the context
                                        stream). More streams overlap more of the items'
                                        latency-bound k x k steps; each stream has its own
-                                       workspace slice */
+                                       workspace slice. The device runs at most
+                                       CUDA_DEVICE_MAX_CONNECTIONS streams side by side (an
+                                       environment variable read when the process creates its
+                                       CUDA context; 8 unless set, up to 32): set it to 32
+                                       for more than 8 streams to overlap (the Python binding
+                                       defaults it to 32 on import) */
   KFAC_OPT_WAIT_CYCLES = 11,        /* [4e9, ~2 s]: limit, in SM clock cycles, of every wait
                                        in which one role of a tensor-core kernel waits for
                                        another (loads for the issuer, the issuer for free
@@ -439,6 +451,19 @@ KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const floa
 KFAC_API kfac_status kfac_profile_enable(kfac_ctx* ctx, int on);
 KFAC_API kfac_status kfac_profile_read(kfac_ctx* ctx, const char** names, double* total_ms, int* launches,
                                        int max_stages, int* n_stages);
+/* The recorded stage intervals as a timeline (call before kfac_profile_read,
+ * which clears them): synchronises the context stream, sets *n_events to the
+ * number of intervals recorded since kfac_profile_enable(ctx, 1) and, for the
+ * first min(max_events, *n_events) of them in order of start time, stores the
+ * stage index (into the names kfac_profile_read reports), the grouped-call item
+ * index (-1 outside a grouped call) and the start and end in milliseconds
+ * after recording began. Any output pointer may be NULL. Intervals of items on
+ * forked streams overlap; the timeline shows how. KFAC_ERR_INVALID_ARG if
+ * recording was never enabled. */
+KFAC_API kfac_status kfac_profile_timeline(kfac_ctx* ctx, int max_events, int* stage, int* item, double* start_ms,
+                                           double* end_ms, int* n_events);
+/* Name of stage index `stage` (a static string), NULL if out of range. */
+KFAC_API const char* kfac_stage_name(int stage);
 
 /* Number of kernels this library has launched in the process so far (all
  * contexts). Used to count device work inside a timed region. */

@@ -27,10 +27,13 @@ static_assert(ST_COUNT == KFAC_NUM_STAGES, "stage table");
 struct Profiler {
   bool on = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[ST_COUNT];
+  std::vector<int> item[ST_COUNT];  // grouped-call item of each interval (-1: not in a grouped call)
   size_t used[ST_COUNT] = {};
+  cudaEvent_t base = nullptr;  // recorded on the context stream when recording starts
   ~Profiler() {
     for (auto& v : ev)
       for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    if (base) cudaEventDestroy(base);
   }
 };
 }  // namespace
@@ -71,6 +74,7 @@ struct kfac_ctx {
   int split_target = 0;    // KFAC_OPT_SPLIT_TARGET: CTAs a split-K product may fill (0 = 152, -1 = no split)
   int warm_start = 0;      // KFAC_OPT_WARM_START: previous U seeds the sketch
   long long conv_chunk = 32LL << 20;  // KFAC_OPT_CONV_CHUNK: floats of one patch-matrix chunk
+  int tail_planes = 1;                // KFAC_OPT_TAIL_PLANES: precomputed 3xTF32 tails of the large operands
 };
 
 namespace {
@@ -144,8 +148,10 @@ struct StageScope {
       if (cudaEventCreate(&a) != cudaSuccess) return;
       if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
       p.ev[st].push_back({a, b});
+      p.item[st].push_back(-1);
     }
     idx = (long long)p.used[st]++;
+    p.item[st][idx] = c->dflags == c->dglobal ? -1 : (int)(c->dflags - c->ditems);
     cudaEventRecord(p.ev[st][idx].first, c->stream);
   }
   ~StageScope() {
@@ -157,10 +163,11 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, total;
+  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, flo, xlo, xlo2,
+      total;
   long long dp, kp, dpb, skws_floats;
   int nsplit, kchunk;
-  bool pack_f, bf16;
+  bool pack_f, bf16, tails;
 };
 
 constexpr int kSketchMaxSplit = 6;  // split-K partials of the sketch products
@@ -170,11 +177,15 @@ constexpr int kSketchMaxSplit = 6;  // split-K partials of the sketch products
 // against the q + 2 passes of the products it puts on the tensor cores).
 // bf16: the BF16 products read a BF16 copy of F (made once per inversion) and
 // of each product's k x d operand, which TMA feeds to the tensor cores as is.
-InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false) {
+// tails: the FP32 (3xTF32) products read precomputed tails of their operands
+// (F's once per inversion, 4 d^2 bytes; the k x d operands' per product)
+// instead of every CTA forming them in shared memory.
+InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, bool tails = false) {
   InvertLayout L = {};
   Bump b;
   L.pack_f = pack_f;
   L.bf16 = bf16 && k < d;
+  L.tails = tails && !L.bf16 && k < d;
   if (k >= d) {  // exact path
     int n = d;
     L.c = b.take<double>((size_t)n * n);
@@ -218,6 +229,11 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false) 
   }
   L.skws_floats = (long long)kSketchMaxSplit * k * d;
   L.skws = b.take<float>((size_t)L.skws_floats);
+  if (L.tails) {
+    L.flo = b.take<float>((size_t)d * L.dp);
+    L.xlo = b.take<float>((size_t)k * L.dp);
+    L.xlo2 = b.take<float>((size_t)k * L.dp);
+  }
   L.total = b.off;
   return L;
 }
@@ -236,6 +252,12 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.zsplit = L.nsplit; g.kchunk = L.kchunk; g.zstride = (long long)k * k;
   g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   StageScope sc(ctx, stage);
+  if (L.tails && prec == KFAC_PREC_FP32) {
+    CK(tails_f32(A, ld, k, d, at<float>(ctx, L.xlo), L.dp, ctx->stream));
+    g.A_lo = at<float>(ctx, L.xlo); g.ld_alo = L.dp;
+    if (Bm != A) CK(tails_f32(Bm, ld, k, d, at<float>(ctx, L.xlo2), L.dp, ctx->stream));
+    g.B_lo = at<float>(ctx, Bm != A ? L.xlo2 : L.xlo); g.ld_blo = L.dp;
+  }
   CK(gemm_f32(g, prec, ctx->stream));
   CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, symmetrize, ctx->dflags,
                        ctx->stream, out32));
@@ -264,6 +286,11 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
   g.ws = at<float>(ctx, L.skws); g.ws_floats = L.skws_floats;
   g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   STAGE(ctx, ST_SKETCH);
+  if (L.tails && prec == KFAC_PREC_FP32) {  // F's tails were formed once per inversion
+    CK(tails_f32(Xt, ldx, k, d, at<float>(ctx, L.xlo), L.dp, ctx->stream));
+    g.A_lo = at<float>(ctx, L.flo); g.ld_alo = L.dp;
+    g.B_lo = at<float>(ctx, L.xlo); g.ld_blo = L.dp;
+  }
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
 }
@@ -421,7 +448,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const float* F = a.F;
   int ldf = a.ldf;
   for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
-                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws})
+                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;
@@ -446,6 +473,10 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   if (L.bf16) {  // F rounded to BF16 once, for the sketch, power and projection products
     STAGE(ctx, ST_TRANSPOSE);
     CK(to_bf16_f32(F, ldf, d, d, at<uint16_t>(ctx, L.fb), L.dpb, s));
+  }
+  if (L.tails && a.prec == KFAC_PREC_FP32) {  // F's 3xTF32 tails once, for the sketch, power and projection products
+    STAGE(ctx, ST_TRANSPOSE);
+    CK(tails_f32(F, ldf, d, d, at<float>(ctx, L.flo), L.dp, s));
   }
   // Omega^T (k x d) so that every sketch product reads K-contiguous rows.
   float* Om = at<float>(ctx, L.om);
@@ -537,19 +568,22 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
 // T2^T = M^T U_g diag(c_g) (d_a x r_g), S = U_g (T2^T)^T + M/lam, with the small
 // transposes U_a^T, U_g^T; split-K partials for the two long-K products.
 struct PrecLayout {
-  size_t uat, ugt, t, mt, t2, ws, jp, uap, ugp, total;
+  size_t uat, ugt, t, mt, t2, ws, jp, uap, ugp, big_lo, ua_lo, ug_lo, uat_lo, ugt_lo, t_lo, t2_lo, total;
   long long ld_uat, ld_ugt, ld_t, ld_mt, ld_t2, ws_floats, ld_jp, ld_uap, ld_ugp;
-  bool pack_j, pack_ua, pack_ug;
+  bool pack_j, pack_ua, pack_ug, tails;
 };
 
 constexpr int kApplyMaxSplit = 6;
 
 // pack_j / pack_ua / pack_ug: that operand's rows are not 16-byte aligned, so
-// the tensor-core products read a copy with a padded row stride.
-PrecLayout prec_layout(int dg, int da, int ra, int rg, bool pack_j, bool pack_ua, bool pack_ug) {
+// the tensor-core products read a copy with a padded row stride. tails: the
+// FP32 products read precomputed 3xTF32 tails of their operands (one d_g x d_a
+// plane serves J's and then M^T's).
+PrecLayout prec_layout(int dg, int da, int ra, int rg, bool pack_j, bool pack_ua, bool pack_ug, bool tails = false) {
   PrecLayout P = {};
   Bump b;
   P.pack_j = pack_j; P.pack_ua = pack_ua && ra > 0; P.pack_ug = pack_ug && rg > 0;
+  P.tails = tails;
   P.ld_uat = round_up(da, 4);
   P.ld_ugt = round_up(dg, 4);
   P.ld_t = round_up(std::max(ra, 1), 4);
@@ -568,21 +602,42 @@ PrecLayout prec_layout(int dg, int da, int ra, int rg, bool pack_j, bool pack_ua
   if (P.pack_j) P.jp = b.take<float>((size_t)dg * P.ld_jp);
   if (P.pack_ua) P.uap = b.take<float>((size_t)da * P.ld_uap);
   if (P.pack_ug) P.ugp = b.take<float>((size_t)dg * P.ld_ugp);
+  if (P.tails) {
+    P.big_lo = b.take<float>(std::max((size_t)dg * P.ld_jp, (size_t)da * P.ld_mt));
+    P.ua_lo = b.take<float>((size_t)da * P.ld_uap);
+    P.ug_lo = b.take<float>((size_t)dg * P.ld_ugp);
+    P.uat_lo = b.take<float>((size_t)std::max(ra, 1) * P.ld_uat);
+    P.ugt_lo = b.take<float>((size_t)std::max(rg, 1) * P.ld_ugt);
+    P.t_lo = b.take<float>((size_t)dg * P.ld_t);
+    P.t2_lo = b.take<float>((size_t)da * P.ld_t2);
+  }
   P.total = b.off;
   return P;
 }
 
 PrecLayout prec_layout_for(int dg, int da, const float* J, int ldj, const float* U_a, int ld_ua, int ra,
-                           const float* U_g, int ld_ug, int rg) {
-  return prec_layout(dg, da, ra, rg, !tma_rows_ok(J, ldj), !tma_rows_ok(U_a, ld_ua), !tma_rows_ok(U_g, ld_ug));
+                           const float* U_g, int ld_ug, int rg, bool tails) {
+  return prec_layout(dg, da, ra, rg, !tma_rows_ok(J, ldj), !tma_rows_ok(U_a, ld_ua), !tma_rows_ok(U_g, ld_ug), tails);
 }
 
 kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, int ldj, const float* U_a, int ld_ua,
                              const float* coef_a, int r_a, const float* U_g, int ld_ug, const float* coef_g, int r_g,
                              float lambda, kfac_precision prec, float* S, int lds, PrecLayout P, size_t base) {
-  for (size_t* o : {&P.uat, &P.ugt, &P.t, &P.mt, &P.t2, &P.ws, &P.jp, &P.uap, &P.ugp}) *o += base;
+  for (size_t* o : {&P.uat, &P.ugt, &P.t, &P.mt, &P.t2, &P.ws, &P.jp, &P.uap, &P.ugp, &P.big_lo, &P.ua_lo, &P.ug_lo,
+                    &P.uat_lo, &P.ugt_lo, &P.t_lo, &P.t2_lo})
+    *o += base;
   cudaStream_t s = ctx->stream;
   const float inv_lam = 1.0f / lambda;
+  const bool tails = P.tails && prec == KFAC_PREC_FP32;
+  // Tails of a product's operand, formed just before the product reads it.
+  auto tail = [&](GemmDesc<float>& g, bool a_side, const float* X, long long ldx, int rows, int cols, size_t plane,
+                  long long ldp) -> cudaError_t {
+    if (!tails || rows <= 0 || cols <= 0) return cudaSuccess;
+    float* lo = at<float>(ctx, plane);
+    cudaError_t e = tails_f32(X, ldx, rows, cols, lo, ldp, s);
+    if (a_side) { g.A_lo = lo; g.ld_alo = ldp; } else { g.B_lo = lo; g.ld_blo = ldp; }
+    return e;
+  };
   if (P.pack_j || P.pack_ua || P.pack_ug) {  // operands whose rows TMA cannot read: padded copies
     STAGE(ctx, ST_TRANSPOSE);
     if (P.pack_j) {
@@ -617,6 +672,8 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.alpha = 1.0f; g.colscale = coef_a; g.zsplit = 1;
     g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats;
     g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
+    CK(tail(g, true, J, ldj, d_g, d_a, P.big_lo, P.ld_jp));
+    CK(tail(g, false, Uat, P.ld_uat, r_a, d_a, P.uat_lo, P.ld_uat));
     CK(gemm_f32(g, prec, s));
   }
   {  // M^T = U_a T^T + J^T / lambda
@@ -628,6 +685,10 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.D = Mt; g.ldd = P.ld_mt;
     g.alpha = 1.0f; g.beta = inv_lam; g.C0 = J; g.ldc = ldj; g.c0_trans = 1; g.zsplit = 1;
     g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
+    if (r_a > 0) {
+      CK(tail(g, true, U_a, ld_ua, d_a, r_a, P.ua_lo, P.ld_uap));
+      CK(tail(g, false, T, P.ld_t, d_g, r_a, P.t_lo, P.ld_t));
+    }
     CK(gemm_f32(g, prec, s));
   }
   if (r_g > 0) {  // T2^T = M^T U_g diag(c_g), through U_g^T
@@ -641,6 +702,8 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.alpha = 1.0f; g.colscale = coef_g; g.zsplit = 1;
     g.ws = at<float>(ctx, P.ws); g.ws_floats = P.ws_floats;
     g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
+    CK(tail(g, true, Mt, P.ld_mt, d_a, d_g, P.big_lo, P.ld_mt));  // J's tails are dead: the plane is reused
+    CK(tail(g, false, Ugt, P.ld_ugt, r_g, d_g, P.ugt_lo, P.ld_ugt));
     CK(gemm_f32(g, prec, s));
   }
   {  // S = U_g T2 + M / lambda  (M read through M^T)
@@ -652,6 +715,10 @@ kfac_status precondition_run(kfac_ctx* ctx, int d_g, int d_a, const float* J, in
     g.D = S; g.ldd = lds;
     g.alpha = 1.0f; g.beta = inv_lam; g.C0 = Mt; g.ldc = P.ld_mt; g.c0_trans = 1; g.zsplit = 1;
     g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
+    if (r_g > 0) {
+      CK(tail(g, true, U_g, ld_ug, d_g, r_g, P.ug_lo, P.ld_ugp));
+      CK(tail(g, false, T2t, P.ld_t2, d_a, r_g, P.t2_lo, P.ld_t2));
+    }
     CK(gemm_f32(g, prec, s));
   }
   return KFAC_OK;
@@ -862,6 +929,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       if (v != 16 && v != 32) return KFAC_ERR_INVALID_ARG;
       ctx->chol_panel = (int)v;
       return KFAC_OK;
+    case KFAC_OPT_TAIL_PLANES:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->tail_planes = (int)v;
+      return KFAC_OK;
     case KFAC_OPT_CHOL_CLUSTER:
       if (v < 0 || v > 16) return KFAC_ERR_INVALID_ARG;
       ctx->chol_cluster = (int)v;
@@ -888,13 +959,16 @@ KFAC_API kfac_status kfac_reserve(kfac_ctx* ctx, int d_max, int k_max, int64_t m
   size_t need = 0;
   if (d_max > 0 && k_max > 0) {
     InvertLayout a = invert_layout(d_max, std::min(k_max, d_max - 1 > 0 ? d_max - 1 : 1), k_max, true, true);
+    InvertLayout a2 = invert_layout(d_max, std::min(k_max, d_max - 1 > 0 ? d_max - 1 : 1), k_max, true, false, true);
     InvertLayout b = invert_layout(std::min(d_max, k_max), k_max, k_max, true);
+    a.total = std::max(a.total, a2.total);
     need = std::max(a.total, b.total);
   }
-  if (mn_max > 0) {  // preconditioner apply: M^T (and a padded copy of J) plus thin intermediates and split-K partials
+  if (mn_max > 0) {  // preconditioner apply: M^T (and a padded copy of J, a tail plane) plus thin intermediates
+                     // (and their tails) and split-K partials
     const size_t dk = (size_t)std::max(d_max, 1) * (std::max(k_max, 1) + 4);
     const size_t mn_pad = (size_t)mn_max + 4 * (size_t)std::max(d_max, 1);
-    size_t p = sizeof(float) * (2 * mn_pad + (6 + kApplyMaxSplit) * dk) + 12 * 256;
+    size_t p = sizeof(float) * (3 * mn_pad + (12 + kApplyMaxSplit) * dk) + 20 * 256;
     need = std::max(need, p);
   }
   return ensure_ws(ctx, need);
@@ -963,24 +1037,36 @@ KFAC_API kfac_status kfac_get_status(kfac_ctx* ctx, int* flags) {
 }
 
 // Workspace bytes of one EA update: a padded copy of X when TMA cannot read its rows.
-static size_t ea_ws_bytes(int d, int n, const float* X, int ldx) {
-  if (n == 0 || tma_rows_ok(X, ldx)) return 0;
-  return sizeof(float) * (size_t)d * (size_t)round_up(n, 4) + 256;
+static bool ea_tails(const kfac_ctx* ctx, int n, kfac_precision prec) {
+  return ctx->tail_planes != 0 && n > 0 && prec == KFAC_PREC_FP32;
 }
 
-// One EA update on ctx->stream; a ragged X is first packed at byte offset `base`
-// of the workspace.
+static size_t ea_ws_bytes(const kfac_ctx* ctx, int d, int n, const float* X, int ldx, kfac_precision prec) {
+  const size_t plane = sizeof(float) * (size_t)d * (size_t)round_up(std::max(n, 1), 4) + 256;
+  return (n > 0 && !tma_rows_ok(X, ldx) ? plane : 0) + (ea_tails(ctx, n, prec) ? plane : 0);
+}
+
+// One EA update on ctx->stream; from byte offset `base` of the workspace a
+// ragged X is first packed and its 3xTF32 tails formed.
 static kfac_status ea_run(kfac_ctx* ctx, int d, int n, const float* X, int ldx, float rho, kfac_precision prec,
                           float* F, int ldf, size_t base) {
   STAGE(ctx, ST_EA);
+  const long long ldp = round_up(std::max(n, 1), 4);
+  const size_t plane = sizeof(float) * (size_t)d * (size_t)ldp + 256;
+  size_t off = (base + 255) & ~size_t(255);
   if (n > 0 && !tma_rows_ok(X, ldx)) {
-    float* Xp = at<float>(ctx, (base + 255) & ~size_t(255));
-    const long long ldp = round_up(n, 4);
+    float* Xp = at<float>(ctx, off);
     CK(pack_rows_f32(X, ldx, d, n, Xp, ldp, ctx->stream));
     X = Xp;
     ldx = (int)ldp;
+    off = (off + plane + 255) & ~size_t(255);
   }
-  CK(ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags, ctx->wait_cycles));
+  float* lo = nullptr;
+  if (ea_tails(ctx, n, prec)) {
+    lo = at<float>(ctx, off);
+    CK(tails_f32(X, ldx, d, n, lo, ldp, ctx->stream));
+  }
+  CK(ea_syrk(ctx->stream, d, n, X, ldx, rho, prec, F, ldf, ctx->dflags, ctx->wait_cycles, lo, ldp));
   return KFAC_OK;
 }
 
@@ -1003,7 +1089,7 @@ KFAC_API kfac_status kfac_ea_update(kfac_ctx* ctx, int d, int n, const float* X,
   if (d == 0) return KFAC_OK;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  kfac_status st = ensure_ws(ctx, ea_ws_bytes(d, n, X, ldx));
+  kfac_status st = ensure_ws(ctx, ea_ws_bytes(ctx, d, n, X, ldx, prec));
   if (st != KFAC_OK) return st;
   return ea_run(ctx, d, n, X, ldx, rho, prec, F, ldf, 0);
 }
@@ -1018,14 +1104,15 @@ KFAC_API kfac_status kfac_ea_update_rows(kfac_ctx* ctx, int n, int cols, const f
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
   const long long ldx = round_up(std::max(n, 1), 4);
-  kfac_status st = ensure_ws(ctx, sizeof(float) * (size_t)d * (size_t)ldx);
+  const size_t xbytes = (sizeof(float) * (size_t)d * (size_t)ldx + 255) & ~size_t(255);
+  kfac_status st = ensure_ws(ctx, xbytes + ea_ws_bytes(ctx, d, n, nullptr, (int)ldx, prec));
   if (st != KFAC_OK) return st;
   float* X = at<float>(ctx, 0);
   {
     STAGE(ctx, ST_TRANSPOSE);
     CK(rows_to_cols_f32(A, lda, n, cols, append_one ? 1 : 0, scale, X, ldx, ctx->stream));
   }
-  return ea_run(ctx, d, n, X, (int)ldx, rho, prec, F, ldf, 0);
+  return ea_run(ctx, d, n, X, (int)ldx, rho, prec, F, ldf, xbytes);
 }
 
 KFAC_API kfac_status kfac_ea_update_conv(kfac_ctx* ctx, int n, int c, int h, int w, const float* x, int kh, int kw,
@@ -1049,9 +1136,12 @@ KFAC_API kfac_status kfac_ea_update_conv(kfac_ctx* ctx, int n, int c, int h, int
   per = std::min<long long>(per, std::max(n, 1));
   while (per > 1 && per * pos > (1LL << 30)) per /= 2;
   const long long ldx = round_up(per * pos, 4);
-  kfac_status st = ensure_ws(ctx, sizeof(float) * (size_t)d * (size_t)ldx);
+  const size_t xbytes = (sizeof(float) * (size_t)d * (size_t)ldx + 255) & ~size_t(255);
+  const bool tails = ea_tails(ctx, n, prec);
+  kfac_status st = ensure_ws(ctx, xbytes * (tails ? 2 : 1));
   if (st != KFAC_OK) return st;
   float* X = at<float>(ctx, 0);
+  float* Xlo = tails ? at<float>(ctx, xbytes) : nullptr;
   const float alpha = n > 0 ? (1.0f - rho) / (float)((double)n * pos) : 0.0f;
   STAGE(ctx, ST_EA);
   if (n == 0) {
@@ -1062,8 +1152,9 @@ KFAC_API kfac_status kfac_ea_update_conv(kfac_ctx* ctx, int n, int c, int h, int
     const int ns = (int)std::min<long long>(per, n - i0);
     CK(im2col_f32(x, c, h, w, kh, kw, stride_h, stride_w, pad_h, pad_w, i0, ns, append_one ? 1 : 0, scale, X, ldx,
                   ctx->stream));
+    if (Xlo) CK(tails_f32(X, ldx, d, (int)(ns * pos), Xlo, ldx, ctx->stream));
     CK(syrk_update(ctx->stream, d, (int)(ns * pos), X, (int)ldx, alpha, i0 == 0 ? rho : 1.0f, prec, F, ldf,
-                   ctx->dflags, ctx->wait_cycles));
+                   ctx->dflags, ctx->wait_cycles, Xlo, ldx));
   }
   return KFAC_OK;
 }
@@ -1091,7 +1182,7 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
   for (int f = 0; f < count; ++f) {
     const kfac_ea_desc& a = descs[f];
     cost[f] = (double)a.d * a.d * (a.n + 8);
-    need[f] = ea_ws_bytes(a.d, a.n, a.X, a.ldx);
+    need[f] = ea_ws_bytes(ctx, a.d, a.n, a.X, a.ldx, a.prec);
   }
   std::vector<int> order, slot;
   lpt_schedule(cost, ns, order, slot);
@@ -1135,7 +1226,7 @@ KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int 
   if (st != KFAC_OK) return st;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  InvertLayout L = invert_layout(d, k, r, !tma_rows_ok(F, ldf), prec == KFAC_PREC_BF16);
+  InvertLayout L = invert_layout(d, k, r, !tma_rows_ok(F, ldf), prec == KFAC_PREC_BF16, ctx->tail_planes != 0);
   if ((st = ensure_ws(ctx, L.total)) != KFAC_OK) return st;
   return invert_run(ctx, a, L, 0);
 }
@@ -1148,7 +1239,8 @@ KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kf
     int r = 0, k = 0;
     kfac_status st = check_invert(descs[f], &r, &k);
     if (st != KFAC_OK) return st;
-    lay[f] = invert_layout(descs[f].d, k, r, !tma_rows_ok(descs[f].F, descs[f].ldf), descs[f].prec == KFAC_PREC_BF16);
+    lay[f] = invert_layout(descs[f].d, k, r, !tma_rows_ok(descs[f].F, descs[f].ldf), descs[f].prec == KFAC_PREC_BF16,
+                           ctx->tail_planes != 0);
   }
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
@@ -1331,7 +1423,7 @@ KFAC_API kfac_status kfac_precondition(kfac_ctx* ctx, int d_g, int d_a, const fl
   if (r_g > 0 && (!U_g || ld_ug < r_g || !coef_g)) return KFAC_ERR_INVALID_ARG;
   DeviceGuard dg(ctx->device);
   if (!dg.ok) return KFAC_ERR_CUDA;
-  PrecLayout P = prec_layout_for(d_g, d_a, J, ldj, U_a, ld_ua, r_a, U_g, ld_ug, r_g);
+  PrecLayout P = prec_layout_for(d_g, d_a, J, ldj, U_a, ld_ua, r_a, U_g, ld_ug, r_g, ctx->tail_planes != 0);
   kfac_status st = ensure_ws(ctx, P.total);
   if (st != KFAC_OK) return st;
   return precondition_run(ctx, d_g, d_a, J, ldj, U_a, ld_ua, coef_a, r_a, U_g, ld_ug, coef_g, r_g, lambda, prec, S,
@@ -1360,7 +1452,8 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
   std::vector<PrecLayout> lay(count);
   for (int f = 0; f < count; ++f) {
     const kfac_precond_desc& a = descs[f];
-    lay[f] = prec_layout_for(a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.r_a, a.U_g, a.ld_ug, a.r_g);
+    lay[f] = prec_layout_for(a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.r_a, a.U_g, a.ld_ug, a.r_g,
+                             ctx->tail_planes != 0);
   }
   const int ns = std::min(count, ctx->group_streams);
   std::vector<double> cost(count);
@@ -1426,8 +1519,44 @@ KFAC_API kfac_status kfac_stats_read(kfac_ctx* ctx, int64_t* out, int n) {
 
 KFAC_API kfac_status kfac_profile_enable(kfac_ctx* ctx, int on) {
   if (!ctx) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
   ctx->prof.on = on != 0;
   for (auto& u : ctx->prof.used) u = 0;
+  if (ctx->prof.on) {
+    if (!ctx->prof.base && cudaEventCreate(&ctx->prof.base) != cudaSuccess) return KFAC_ERR_CUDA;
+    if (cudaEventRecord(ctx->prof.base, ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  }
+  return KFAC_OK;
+}
+
+KFAC_API const char* kfac_stage_name(int stage) {
+  return stage >= 0 && stage < ST_COUNT ? kStageNames[stage] : nullptr;
+}
+
+KFAC_API kfac_status kfac_profile_timeline(kfac_ctx* ctx, int max_events, int* stage, int* item, double* start_ms,
+                                           double* end_ms, int* n_events) {
+  if (!ctx || max_events < 0 || !ctx->prof.base) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
+  struct Iv { double a, b; int st, it; };
+  std::vector<Iv> all;
+  for (int i = 0; i < ST_COUNT; ++i)
+    for (size_t j = 0; j < ctx->prof.used[i]; ++j) {
+      float a = 0.0f, b = 0.0f;
+      if (cudaEventElapsedTime(&a, ctx->prof.base, ctx->prof.ev[i][j].first) != cudaSuccess ||
+          cudaEventElapsedTime(&b, ctx->prof.base, ctx->prof.ev[i][j].second) != cudaSuccess)
+        return KFAC_ERR_CUDA;
+      all.push_back({a, b, i, ctx->prof.item[i][j]});
+    }
+  std::stable_sort(all.begin(), all.end(), [](const Iv& x, const Iv& y) { return x.a < y.a; });
+  const int n = std::min(max_events, (int)all.size());
+  for (int e = 0; e < n; ++e) {
+    if (stage) stage[e] = all[e].st;
+    if (item) item[e] = all[e].it;
+    if (start_ms) start_ms[e] = all[e].a;
+    if (end_ms) end_ms[e] = all[e].b;
+  }
+  if (n_events) *n_events = (int)all.size();
   return KFAC_OK;
 }
 

@@ -104,6 +104,9 @@ struct GemmDesc {
   long long wait_cycles;  // limit of the tensor-core kernels' waits on each other's progress (0: default)
   int split_target;       // split K of a product with few tiles up to this many CTAs (0: 152, < 0: never)
   int ab_bf16;            // A and B point to BF16 data (K-major, strides in elements; tensor cores only)
+  const T* A_lo;          // FP32 tensor-core products: precomputed 3xTF32 tails of A / B (row strides
+  const T* B_lo;          //   ld_alo / ld_blo, 0 = the operand's), or null (the kernel forms them per tile)
+  long long ld_alo, ld_blo;
 };
 
 // Default limit of a tensor-core kernel's wait for another role's progress:

@@ -50,7 +50,10 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
     return gemm_simt_f32(g, round_of(prec), s);
   }
   auto launch = [&](const tc::TcArgs& a, int zsplit) {
-    return bf16d ? tc::gemm_bf16(a, g.A, g.sam, g.B, g.sbn, zsplit, s) : tc::gemm(a, g.A, g.sam, g.B, g.sbn, zsplit, mode, s);
+    if (bf16d) return tc::gemm_bf16(a, g.A, g.sam, g.B, g.sbn, zsplit, s);
+    const bool tails = mode == tc::Mode::Fp32;
+    return tc::gemm(a, g.A, g.sam, g.B, g.sbn, zsplit, mode, s, tails ? g.A_lo : nullptr, g.ld_alo ? g.ld_alo : g.sam,
+                    tails ? g.B_lo : nullptr, g.ld_blo ? g.ld_blo : g.sbn);
   };
 
   tc::TcArgs a = {};
@@ -92,8 +95,10 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
 }
 
 cudaError_t syrk_update(cudaStream_t s, int d, int K, const float* X, int ldx, float alpha, float beta,
-                        kfac_precision prec, float* F, int ldf, int* flags, long long wait_cycles) {
+                        kfac_precision prec, float* F, int ldf, int* flags, long long wait_cycles, const float* Xlo,
+                        long long ldlo) {
   GemmDesc<float> g = {};
+  g.A_lo = g.B_lo = Xlo; g.ld_alo = g.ld_blo = ldlo;
   g.M = d; g.N = d; g.K = K;
   g.A = X; g.sam = ldx; g.sak = 1;
   g.B = X; g.sbn = ldx; g.sbk = 1;
@@ -109,8 +114,9 @@ cudaError_t syrk_update(cudaStream_t s, int d, int K, const float* X, int ldx, f
 }
 
 cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float rho, kfac_precision prec, float* F,
-                    int ldf, int* flags, long long wait_cycles) {
+                    int ldf, int* flags, long long wait_cycles, const float* Xlo, long long ldlo) {
   GemmDesc<float> g = {};
+  g.A_lo = g.B_lo = Xlo; g.ld_alo = g.ld_blo = ldlo;
   g.M = d; g.N = d; g.K = n;
   g.A = X; g.sam = ldx; g.sak = 1;
   g.B = X; g.sbn = ldx; g.sbk = 1;
@@ -124,6 +130,10 @@ cudaError_t ea_syrk(cudaStream_t s, int d, int n, const float* X, int ldx, float
   g.wait_cycles = wait_cycles;
   if (rho == 0.0f) g.beta = 0.0f;
   return gemm_f32(g, prec, s);
+}
+
+cudaError_t tails_f32(const float* X, long long ldx, int rows, int cols, float* lo, long long ldlo, cudaStream_t s) {
+  return tc::tf32_tails(X, ldx, rows, cols, lo, ldlo, s);
 }
 
 }  // namespace kfac

@@ -427,8 +427,17 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, in
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_gemm3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p) {
+    k_tc_gemm3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcArgs p) {
   using C = Cfg3;
+  // Operands whose tails come precomputed from global memory (p.lo_a / p.lo_b)
+  // are loaded by TMA beside the raw tile; the split warps form the others'.
+  // With both precomputed no split runs: the MMA issuer takes a stage as soon
+  // as its copies have landed.
+  const bool need_split = !(p.lo_a && p.lo_b);
+  const uint32_t stage_tx = (uint32_t)(C::RAW + (p.lo_a ? C::A_BYTES : 0) + (p.lo_b ? C::B_BYTES : 0));
+  const int split_e0 = p.lo_a ? C::A_BYTES / 16 : 0;             // float4 range of the stage to split
+  const int split_e1 = p.lo_b ? C::A_BYTES / 16 : C::RAW / 16;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
@@ -477,22 +486,25 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
       if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) break;
       const uint32_t st = smem_u32(smem + s * C::STAGE);
-      mbar_expect_tx(full0 + 8 * s, C::RAW);
+      mbar_expect_tx(full0 + 8 * s, stage_tx);
       tma_load_2d(st, &tmA, kb0 + kb * BK, m0, full0 + 8 * s);
       tma_load_2d(st + C::A_BYTES, &tmB, kb0 + kb * BK, n0, full0 + 8 * s);
+      if (p.lo_a) tma_load_2d(st + C::RAW, &tmAlo, kb0 + kb * BK, m0, full0 + 8 * s);
+      if (p.lo_b) tma_load_2d(st + C::RAW + C::A_BYTES, &tmBlo, kb0 + kb * BK, n0, full0 + 8 * s);
       ++issued;
     }
     for (int kb = (issued > C::STAGES ? issued - C::STAGES : 0); kb < issued; ++kb)
       mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags, kDrainCycles);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: stages 2m, 2m+1 -> TMEM pair m & 1 ------------------------
+    const uint32_t ready0 = need_split ? split0 : full0;
     constexpr uint32_t idesc = idesc_tf32(BM, BN3);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES, m = kb >> 1, b = m & 1;
       const bool first = (kb & 1) == 0, last = (kb & 1) == 1 || kb == nk - 1;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
       if (first && m >= 2 && !mbar_wait(tempty0 + 8 * b, (uint32_t)((m >> 1) - 1) & 1u, p.flags, p.wait_cycles)) break;
-      if (!mbar_wait(split0 + 8 * s, ph, p.flags, p.wait_cycles)) break;
+      if (!mbar_wait(ready0 + 8 * s, ph, p.flags, p.wait_cycles)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
@@ -524,14 +536,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int j = 0; j < BN3; ++j) acc[j] = 0.0f;
     }
     for (int kb = 0; kb <= nk; ++kb) {
-      if (kb < nk) {
+      if (kb < nk && need_split) {
         const int s = kb % C::STAGES;
         const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
         if (!mbar_wait_warp(full0 + 8 * s, ph, p.flags, lane, p.wait_cycles)) { drained = false; break; }
         const float4* raw = reinterpret_cast<const float4*>(smem + s * C::STAGE);
         float4* lo = reinterpret_cast<float4*>(smem + s * C::STAGE + C::RAW);
 #pragma unroll 2
-        for (int e = t; e < C::RAW / 16; e += kSplitThreads) {
+        for (int e = split_e0 + t; e < split_e1; e += kSplitThreads) {
           const float4 x = raw[e];  // read as hi by the tensor core (its TF32 truncation)
           lo[e] = make_float4(tf32_tail(x.x), tf32_tail(x.y), tf32_tail(x.z), tf32_tail(x.w));
         }
@@ -781,7 +793,35 @@ cudaError_t launch_kernel(Kern kern, int smem, int bn, const TcArgs& a, const vo
   return cudaGetLastError();
 }
 
+// lo[r][c] = tail of X[r][c] below its TF32 truncation (as the 3xTF32 kernel
+// forms in shared memory), four columns per thread.
+__global__ void k_tf32_tails(const float* __restrict__ X, long long ldx, int rows, int cols, int cols4,
+                             float* __restrict__ lo, long long ldlo) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)rows * cols4) return;
+  const int r = (int)(idx / cols4), c = (int)(idx % cols4) * 4;
+  const float* x = X + (long long)r * ldx + c;
+  float* y = lo + (long long)r * ldlo + c;
+  if (c + 4 <= cols) {
+    const float4 v = *reinterpret_cast<const float4*>(x);
+    *reinterpret_cast<float4*>(y) = make_float4(tf32_tail(v.x), tf32_tail(v.y), tf32_tail(v.z), tf32_tail(v.w));
+  } else {  // ragged row end: only the row's own columns are read
+    for (int j = 0; c + j < cols; ++j) y[j] = tf32_tail(x[j]);
+  }
+}
+
 }  // namespace
+
+cudaError_t tf32_tails(const float* X, long long ldx, int rows, int cols, float* lo, long long ldlo, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if ((ldx & 3) || (ldlo & 3) || ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(lo)) & 15u))
+    return cudaErrorInvalidValue;
+  const int cols4 = (cols + 3) / 4;
+  const long long n = (long long)rows * cols4;
+  k_tf32_tails<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, ldx, rows, cols, cols4, lo, ldlo);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t gemm_bf16(const TcArgs& a, const void* A, long long lda, const void* B, long long ldb, int zsplit,
                       cudaStream_t s) {
@@ -795,12 +835,31 @@ bool eligible(const float* A, long long lda, const float* B, long long ldb, int 
          encode_fn() != nullptr;
 }
 
-cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
-                 Mode mode, cudaStream_t s) {
-  if (mode == Mode::Fp32) return launch_kernel(k_tc_gemm3, Cfg3::SMEM, BN3, a, A, lda, B, ldb, zsplit, s);
-  if (mode == Mode::Bf16) return launch_kernel(k_tc_gemm16, Cfg16::SMEM, BN16, a, A, lda, B, ldb, zsplit, s);
-  if (a.N > 128) return launch_kernel(k_tc_gemm<256>, Cfg<256>::SMEM, 256, a, A, lda, B, ldb, zsplit, s);
-  return launch_kernel(k_tc_gemm<128>, Cfg<128>::SMEM, 128, a, A, lda, B, ldb, zsplit, s);
+cudaError_t gemm(const TcArgs& a0, const float* A, long long lda, const float* B, long long ldb, int zsplit,
+                 Mode mode, cudaStream_t s, const float* Alo, long long ldalo, const float* Blo, long long ldblo) {
+  if (mode == Mode::Fp32) {
+    {
+      cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_tc_gemm3), Cfg3::SMEM, false);
+      if (e != cudaSuccess) return e;
+    }
+    TcArgs a = a0;
+    a.lo_a = Alo != nullptr;
+    a.lo_b = Blo != nullptr;
+    // Tail planes share their operand's shape; an absent one gets its
+    // operand's map (never read).
+    CUtensorMap ma, mb, mal, mbl;
+    if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, BN3) ||
+        !make_map(&mal, Alo ? Alo : A, a.M, a.K, Alo ? ldalo : lda, BM) ||
+        !make_map(&mbl, Blo ? Blo : B, a.N, a.K, Blo ? ldblo : ldb, BN3))
+      return cudaErrorInvalidValue;
+    dim3 grid((a.N + BN3 - 1) / BN3, (a.M + BM - 1) / BM, zsplit);
+    k_tc_gemm3<<<grid, THREADS, Cfg3::SMEM, s>>>(ma, mb, mal, mbl, a);
+    note_launch();
+    return cudaGetLastError();
+  }
+  if (mode == Mode::Bf16) return launch_kernel(k_tc_gemm16, Cfg16::SMEM, BN16, a0, A, lda, B, ldb, zsplit, s);
+  if (a0.N > 128) return launch_kernel(k_tc_gemm<256>, Cfg<256>::SMEM, 256, a0, A, lda, B, ldb, zsplit, s);
+  return launch_kernel(k_tc_gemm<128>, Cfg<128>::SMEM, 128, a0, A, lda, B, ldb, zsplit, s);
 }
 
 }  // namespace tc

@@ -24,6 +24,7 @@ struct TcArgs {
   int sym;       // write only m <= n, plus the mirror (n, m); tiles below the diagonal exit
   int* flags;
   long long wait_cycles;  // limit (clock cycles, > 0) of each wait for another role's progress
+  int lo_a, lo_b;         // 3xTF32: the operand's tails come from global memory (set by gemm())
 };
 
 // True when A (M x K, row stride lda) and B (N x K, row stride ldb) can be read
@@ -40,9 +41,15 @@ inline int tile_n(int N, Mode mode) { return (mode != Mode::Tf32 || N <= 128) ? 
 // K-columns one pipeline stage of the launch consumes.
 inline int k_step(Mode mode) { return mode == Mode::Bf16 ? 64 : 32; }
 
-// Launch one GEMM.
+// Launch one GEMM. Mode::Fp32 may take precomputed tail planes Alo / Blo
+// (tf32_tails of A / B, same shape, row strides ldalo / ldblo): TMA then loads
+// them beside the operands instead of the kernel forming them per tile.
 cudaError_t gemm(const TcArgs& a, const float* A, long long lda, const float* B, long long ldb, int zsplit,
-                 Mode mode, cudaStream_t s);
+                 Mode mode, cudaStream_t s, const float* Alo = nullptr, long long ldalo = 0,
+                 const float* Blo = nullptr, long long ldblo = 0);
+// lo = the 3xTF32 tail of X (rows x cols, row strides multiples of 4 floats,
+// 16-byte aligned bases).
+cudaError_t tf32_tails(const float* X, long long ldx, int rows, int cols, float* lo, long long ldlo, cudaStream_t s);
 // The same with A and B already BF16 in global memory (row strides lda, ldb in
 // elements, multiples of 8; 16-byte aligned bases): TMA loads the BF16 tiles
 // directly and tcgen05.mma.kind::f16 multiplies them; a.kchunk a multiple of 64.

@@ -11,7 +11,15 @@ from __future__ import annotations
 import ctypes
 import os
 
-import torch
+# The forked streams of a grouped call run concurrently only as far as the
+# CUDA runtime has hardware work queues for them: CUDA_DEVICE_MAX_CONNECTIONS,
+# 8 by default, beyond which streams share a queue and one stream's pending
+# chain blocks the next. Raise it to the maximum (32) unless the caller chose a
+# value; it is read when the process creates its CUDA context, so it takes
+# effect when this module is imported before any CUDA work.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+import torch  # noqa: E402
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libkfac.so")
 _lib = None
@@ -22,7 +30,7 @@ OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_swee
            "basis_polish": 7, "cholqr_inner_fp32": 8, "eig_stop_tol": 9, "eig_refine_fp64": 10, "wait_cycles": 11,
            "group_streams": 12, "invert_method": 13,
            "chol_cluster": 14, "split_target": 15, "warm_start": 16,
-           "conv_chunk": 17, "chol_panel": 18}
+           "conv_chunk": 17, "chol_panel": 18, "tail_planes": 19}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
@@ -87,6 +95,11 @@ def lib():
         L.kfac_profile_enable.argtypes = [vp, i]
         L.kfac_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d), ctypes.POINTER(i), i,
                                         ctypes.POINTER(i)]
+        L.kfac_profile_timeline.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d),
+                                            ctypes.POINTER(d), ctypes.POINTER(i)]
+        L.kfac_profile_timeline.restype = i
+        L.kfac_stage_name.argtypes = [i]
+        L.kfac_stage_name.restype = ctypes.c_char_p
         L.kfac_kernel_launch_count.restype = ctypes.c_uint64
         L.kfac_simt_gemm_count.restype = ctypes.c_uint64
         L.kfac_rsvd_invert_grouped.argtypes = [vp, i, ctypes.POINTER(InvertDesc)]
@@ -289,6 +302,19 @@ def kfac_profile_read(ctx: Context) -> dict:
     got = ctypes.c_int(0)
     _check(lib().kfac_profile_read(ctx.handle, names, ms, cnt, n, ctypes.byref(got)), "kfac_profile_read")
     return {names[i].decode(): (ms[i], cnt[i]) for i in range(got.value)}
+
+
+def kfac_profile_timeline(ctx: Context) -> list:
+    """Recorded stage intervals [(stage name, item or -1, start ms, end ms)] in
+    order of start (call before kfac_profile_read, which clears them)."""
+    total = ctypes.c_int(0)
+    _check(lib().kfac_profile_timeline(ctx.handle, 0, None, None, None, None, ctypes.byref(total)),
+           "kfac_profile_timeline")
+    n = total.value
+    st, it = (ctypes.c_int * max(n, 1))(), (ctypes.c_int * max(n, 1))()
+    a, b = (ctypes.c_double * max(n, 1))(), (ctypes.c_double * max(n, 1))()
+    _check(lib().kfac_profile_timeline(ctx.handle, n, st, it, a, b, ctypes.byref(total)), "kfac_profile_timeline")
+    return [(lib().kfac_stage_name(st[e]).decode(), it[e], a[e], b[e]) for e in range(min(n, total.value))]
 
 
 def kfac_kernel_launch_count() -> int:

@@ -72,3 +72,33 @@ def test_step_captures_and_replays_bitwise(kf):
     for a, b in zip(ref, got):
         assert torch.equal(a, b)
     ctx.close()
+
+
+def test_stage_profile_and_timeline(kf):
+    """The stage profiler: per-stage totals equal the sum of the timeline's
+    intervals, grouped items are tagged with their index, and every interval
+    lies inside the host-measured span of the call."""
+    cases = [(257, 30), (300, 20), (140, 40)]
+    items = []
+    for i, (d, r) in enumerate(cases):
+        f = inputs.spectrum_factor(80 + i, d, inputs.power_spectrum(d, 1.0) ** 2).astype(np.float32)
+        items.append(dict(F=cuda(f), rank=r, oversample=10, power_iters=1, lam=0.1,
+                          omega=cuda(inputs.omega(80 + i, d, r + 10))))
+    with kf.Context(0) as ctx:
+        kf.kfac_rsvd_invert_grouped(ctx, items)    # sizes the workspace, creates the side streams
+        torch.cuda.synchronize()
+        kf.kfac_profile_enable(ctx, True)
+        kf.kfac_rsvd_invert_grouped(ctx, items)
+        tl = kf.kfac_profile_timeline(ctx)
+        tot = kf.kfac_profile_read(ctx)
+        kf.kfac_profile_enable(ctx, False)
+        assert kf.kfac_get_status(ctx)[0] == 0
+    assert tl and {it for _, it, _, _ in tl} == {0, 1, 2}
+    assert all(0.0 <= a <= b for _, _, a, b in tl)
+    assert [a for _, _, a, _ in tl] == sorted(a for _, _, a, _ in tl)
+    for name, (ms, n) in tot.items():
+        iv = [(a, b) for s, _, a, b in tl if s == name]
+        assert len(iv) == n
+        assert abs(sum(b - a for a, b in iv) - ms) <= 1e-3 * max(ms, 1.0)
+    for stage in ("sketch_gemm", "cholqr_chol", "eig_jacobi", "lift_gemm"):
+        assert {it for s, it, _, _ in tl if s == stage} == {0, 1, 2}, stage
