@@ -288,20 +288,21 @@ KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, c
                                                float lambda, kfac_precision prec, float* S, int lds);
 
 /* Autotuner of a grouped inversion's schedule on this GPU: the number of
- * streams a grouped call forks (KFAC_OPT_GROUP_STREAMS), the cluster size of
- * the multi-CTA Cholesky and its panel width (KFAC_OPT_CHOL_CLUSTER and
- * KFAC_OPT_CHOL_PANEL; only when a sketch width exceeds the one-CTA kernel's
- * 236) and the CTA count split-K products may fill (KFAC_OPT_SPLIT_TARGET). Runs kfac_rsvd_invert_grouped(ctx, count,
- * descs) once plus twice timed (CUDA events on the context stream) per
- * candidate of a coordinate descent from the current settings, writing the
- * descriptors' outputs as a call would, and keeps the fastest settings in the
- * context. cache_path (may be NULL): a text file of earlier results, one line
- * per device name and shape signature (the factors' d, k, power iterations
- * and precision, and the inversion method); a hit is applied without timing,
- * a new result is appended. chosen (may be NULL, 5 ints) receives the streams,
- * cluster size, split target, panel width and 1 if the result came from the
- * cache. Not
- * during stream capture (it synchronises). */
+ * streams a grouped call forks (KFAC_OPT_GROUP_STREAMS), the CTA count split-K
+ * products may fill (KFAC_OPT_SPLIT_TARGET) and, when a sketch width exceeds
+ * the one-CTA Cholesky's 236, the large-order Cholesky: blocked or on a
+ * cluster (KFAC_OPT_CHOL_BLOCKED) and, for the cluster kernel, its size and
+ * panel width (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL). Runs
+ * kfac_rsvd_invert_grouped(ctx, count, descs) once plus twice timed (CUDA
+ * events on the context stream) per candidate of a coordinate descent from the
+ * current settings, writing the descriptors' outputs as a call would, and
+ * keeps the fastest settings in the context. cache_path (may be NULL): a text
+ * file of earlier results, one line per device name and shape signature (the
+ * factors' d, k, power iterations and precision, and the inversion method); a
+ * hit is applied without timing, a new result is appended. chosen (may be
+ * NULL, 6 ints) receives the streams, cluster size, split target, panel width,
+ * blocked flag and 1 if the result came from the cache. Not during stream
+ * capture (it synchronises). */
 KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_invert_desc* descs,
                                           const char* cache_path, int* chosen);
 
@@ -382,6 +383,12 @@ typedef enum {
                                        instead of every CTA forming them in shared memory;
                                        0 = form them in the kernel (less workspace). Results
                                        are bitwise the same either way */
+  KFAC_OPT_CHOL_BLOCKED = 20,       /* [1]: FP32 Cholesky factors of order above 236 (CholeskyQR
+                                       Grams and the eigensolver's C + sI) are computed blocked:
+                                       one-CTA factorisations of diagonal blocks of at most 236,
+                                       triangular solves and tensor-core (3xTF32) rank updates
+                                       between them; 0 = on one thread-block cluster
+                                       (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL) */
   KFAC_OPT_CHOL_PANEL = 18,         /* [16]: panel width of the multi-CTA Cholesky, 16 or 32
                                        (halved while its shared memory overflows); wider panels
                                        take half the cluster barriers and broadcasts */

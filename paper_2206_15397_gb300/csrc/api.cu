@@ -75,6 +75,7 @@ struct kfac_ctx {
   int warm_start = 0;      // KFAC_OPT_WARM_START: previous U seeds the sketch
   long long conv_chunk = 32LL << 20;  // KFAC_OPT_CONV_CHUNK: floats of one patch-matrix chunk
   int tail_planes = 1;                // KFAC_OPT_TAIL_PLANES: precomputed 3xTF32 tails of the large operands
+  int chol_blocked = 1;               // KFAC_OPT_CHOL_BLOCKED: blocked FP32 Cholesky above the one-CTA limit
 };
 
 namespace {
@@ -164,7 +165,7 @@ struct StageScope {
 
 struct InvertLayout {
   size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, flo, xlo, xlo2,
-      total;
+      cb, total;
   long long dp, kp, dpb, skws_floats;
   int nsplit, kchunk;
   bool pack_f, bf16, tails;
@@ -210,6 +211,7 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
   L.g = b.take<double>((size_t)k * k);
   L.g32 = b.take<float>((size_t)k * k);
   L.l32 = b.take<float>((size_t)k * k);
+  L.cb = b.take<char>(chol_blocked_ws_bytes(k));
   L.dinv = b.take<float>(trsm_ws_floats(k));
   L.c = b.take<double>((size_t)k * k);
   L.c32 = b.take<float>((size_t)k * k);
@@ -315,8 +317,12 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       const double shift = pass == 0 ? ctx->cholqr_shift : (pass + 1 < passes ? -1e-5 : 0.0);
       const bool fp64 = (final_basis || !ctx->cholqr_inner_fp32) &&
                         (pass >= ctx->cholqr_fp32_passes || (pass + 1 == passes && ctx->cholqr_fp32_passes < passes));
-      CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
-                      ctx->stream, nullptr, at<float>(ctx, L.g32), k, ctx->chol_cluster, ctx->chol_panel));
+      if (!fp64 && ctx->chol_blocked && chol_blocked_ws_bytes(k) > 0)
+        CK(chol_blocked(at<double>(ctx, L.g), at<float>(ctx, L.g32), k, k, shift, at<float>(ctx, L.l32), ctx->dflags,
+                        ctx->dstats, ctx->stream, nullptr, at<char>(ctx, L.cb), ctx->wait_cycles));
+      else
+        CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
+                        ctx->stream, nullptr, at<float>(ctx, L.g32), k, ctx->chol_cluster, ctx->chol_panel));
     }
     {
       STAGE(ctx, ST_TRSM);
@@ -332,7 +338,8 @@ kfac_status eigensolve(kfac_ctx* ctx, const double* C, const float* C32, long lo
   {
     STAGE(ctx, ST_EIG);
     CK(eig_jacobi_f32(C, n, 1e-6, ctx->eig_max_sweeps, (float)ctx->eig_tol, (float)ctx->eig_stop_tol, X, lam, jac,
-                      ctx->dflags, ctx->dstats, ctx->stream, C32, ld32, ctx->chol_cluster, ctx->chol_panel));
+                      ctx->dflags, ctx->dstats, ctx->stream, C32, ld32, ctx->chol_cluster, ctx->chol_panel,
+                      ctx->chol_blocked, ctx->wait_cycles));
   }
   STAGE(ctx, ST_REFINE);
   for (int it = 0; it < ctx->eig_refine; ++it) {
@@ -448,7 +455,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const float* F = a.F;
   int ldf = a.ldf;
   for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
-                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2})
+                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2, &L.cb})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;
@@ -933,6 +940,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->tail_planes = (int)v;
       return KFAC_OK;
+    case KFAC_OPT_CHOL_BLOCKED:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->chol_blocked = (int)v;
+      return KFAC_OK;
     case KFAC_OPT_CHOL_CLUSTER:
       if (v < 0 || v > 16) return KFAC_ERR_INVALID_ARG;
       ctx->chol_cluster = (int)v;
@@ -988,6 +999,9 @@ KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const floa
   const size_t o_ws = b.take<float>((size_t)ws_floats);
   const size_t o_a = pack_a ? b.take<float>((size_t)M * kp) : 0;
   const size_t o_b = pack_b ? b.take<float>((size_t)N * kp) : 0;
+  const bool tails = ctx->tail_planes != 0 && prec == KFAC_PREC_FP32 && K > 0;
+  const size_t o_alo = tails ? b.take<float>((size_t)M * kp) : 0;
+  const size_t o_blo = tails ? b.take<float>((size_t)N * kp) : 0;
   kfac_status st = ensure_ws(ctx, b.off);
   if (st != KFAC_OK) return st;
   if (pack_a) {  // rows TMA cannot read: the tensor-core kernel reads padded copies
@@ -1008,6 +1022,12 @@ KFAC_API kfac_status kfac_gemm_nt(kfac_ctx* ctx, int M, int N, int K, const floa
   g.alpha = alpha; g.beta = beta; g.C0 = D; g.ldc = ldd;
   g.zsplit = 1; g.ws = at<float>(ctx, o_ws); g.ws_floats = ws_floats;
   g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
+  if (tails && tma_rows_ok(A, lda) && tma_rows_ok(B, ldb)) {
+    CK(tails_f32(A, lda, M, K, at<float>(ctx, o_alo), kp, ctx->stream));
+    CK(tails_f32(B, ldb, N, K, at<float>(ctx, o_blo), kp, ctx->stream));
+    g.A_lo = at<float>(ctx, o_alo); g.ld_alo = kp;
+    g.B_lo = at<float>(ctx, o_blo); g.ld_blo = kp;
+  }
   CK(gemm_f32(g, prec, ctx->stream));
   return KFAC_OK;
 }
@@ -1316,11 +1336,11 @@ static bool cache_lookup(const char* path, const char* dev, unsigned long long s
   while (fgets(line, sizeof line, fp)) {
     char name[256];
     unsigned long long s = 0;
-    int a = 0, b = 0, c = 0, e = 0;
+    int a = 0, b = 0, c = 0, e = 0, f = 0;
     double ms = 0.0;
-    if (sscanf(line, "%255[^|]|%llx %d %d %d %d %lf", name, &s, &a, &b, &c, &e, &ms) == 7 && s == sig &&
+    if (sscanf(line, "%255[^|]|%llx %d %d %d %d %d %lf", name, &s, &a, &b, &c, &e, &f, &ms) == 8 && s == sig &&
         strcmp(name, dev) == 0) {
-      cfg[0] = a; cfg[1] = b; cfg[2] = c; cfg[3] = e;
+      cfg[0] = a; cfg[1] = b; cfg[2] = c; cfg[3] = e; cfg[4] = f;
       found = true;  // the last entry for this key wins
     }
   }
@@ -1343,7 +1363,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
   for (char* c = prop.name; *c; ++c)
     if (*c == '|' || *c == '\n') *c = ' ';
   const unsigned long long sig = invert_signature(ctx, count, descs);
-  int cfg[4] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target, ctx->chol_panel};
+  int cfg[5] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target, ctx->chol_panel, ctx->chol_blocked};
   bool cached = cache_path && cache_lookup(cache_path, prop.name, sig, cfg);
   double best_ms = 0.0;
   if (!cached) {
@@ -1358,6 +1378,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     // One warm-up and two timed grouped inversions per candidate.
     auto run = [&](const int* c, double* ms) -> kfac_status {
       ctx->group_streams = c[0]; ctx->chol_cluster = c[1]; ctx->split_target = c[2]; ctx->chol_panel = c[3];
+      ctx->chol_blocked = c[4];
       kfac_status st = kfac_rsvd_invert_grouped(ctx, count, descs);
       if (st != KFAC_OK) return st;
       if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
@@ -1370,19 +1391,26 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
       *ms = t / 2.0;
       return KFAC_OK;
     };
-    // Coordinate descent over the four knobs, from the current settings.
+    // Coordinate descent over the knobs, from the current settings: streams,
+    // blocked or cluster Cholesky, split target, then the cluster kernel's
+    // size and panel width if it is in use.
     const int streams_c[] = {4, 8, 16, 32};
     const int chol_c[] = {0, 8, 12};
     const int split_c[] = {0, 304, -1};
     const int panel_c[] = {16, 32};
+    const int blocked_c[] = {1, 0};
+    const int order[5] = {0, 4, 2, 1, 3};
     kfac_status st = run(cfg, &best_ms);
-    for (int dim = 0; dim < 4 && st == KFAC_OK; ++dim) {
-      const int* cand = dim == 0 ? streams_c : (dim == 1 ? chol_c : (dim == 2 ? split_c : panel_c));
-      const int n = dim == 0 ? 4 : (dim == 3 ? 2 : 3);
-      if ((dim == 1 || dim == 3) && !big_k) continue;  // no factor uses the multi-CTA Cholesky
+    for (int oi = 0; oi < 5 && st == KFAC_OK; ++oi) {
+      const int dim = order[oi];
+      const int* cand = dim == 0 ? streams_c
+                                 : (dim == 1 ? chol_c : (dim == 2 ? split_c : (dim == 3 ? panel_c : blocked_c)));
+      const int n = dim == 0 ? 4 : ((dim == 3 || dim == 4) ? 2 : 3);
+      if ((dim == 1 || dim == 3 || dim == 4) && !big_k) continue;  // no factor uses a large-order Cholesky
+      if ((dim == 1 || dim == 3) && cfg[4]) continue;            // the cluster kernel is not in use
       for (int i = 0; i < n && st == KFAC_OK; ++i) {
         if (cand[i] == cfg[dim]) continue;
-        int trial[4] = {cfg[0], cfg[1], cfg[2], cfg[3]};
+        int trial[5] = {cfg[0], cfg[1], cfg[2], cfg[3], cfg[4]};
         trial[dim] = cand[i];
         double ms = 0.0;
         st = run(trial, &ms);
@@ -1398,7 +1426,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     if (cache_path) {
       FILE* fp = fopen(cache_path, "a");
       if (fp) {
-        fprintf(fp, "%s|%llx %d %d %d %d %.4f\n", prop.name, sig, cfg[0], cfg[1], cfg[2], cfg[3], best_ms);
+        fprintf(fp, "%s|%llx %d %d %d %d %d %.4f\n", prop.name, sig, cfg[0], cfg[1], cfg[2], cfg[3], cfg[4], best_ms);
         fclose(fp);
       }
     }
@@ -1407,7 +1435,11 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
   ctx->chol_cluster = cfg[1];
   ctx->split_target = cfg[2];
   ctx->chol_panel = cfg[3];
-  if (chosen) { chosen[0] = cfg[0]; chosen[1] = cfg[1]; chosen[2] = cfg[2]; chosen[3] = cfg[3]; chosen[4] = cached ? 1 : 0; }
+  ctx->chol_blocked = cfg[4];
+  if (chosen) {
+    for (int i = 0; i < 5; ++i) chosen[i] = cfg[i];
+    chosen[5] = cached ? 1 : 0;
+  }
   return KFAC_OK;
 }
 

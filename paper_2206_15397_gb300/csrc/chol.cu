@@ -22,6 +22,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "gemm.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -412,7 +413,7 @@ __host__ __device__ inline size_t cta_smem_bytes(int k) {
 // raised one.
 __device__ __forceinline__ void cta_factor_diag(float* A, int ks, int j0, int jb, float* rinv, float* Xi,
                                                 const double* G, int k, double shift, float pfloor, int* sflag,
-                                                int lane) {
+                                                int lane, int goff = 0) {
   float x[PW], w[PW];
   const int r = lane;
 #pragma unroll
@@ -422,7 +423,7 @@ __device__ __forceinline__ void cta_factor_diag(float* A, int ks, int j0, int jb
   }
   // The replacement for a pivot below the floor, one FP64 operation per lane
   // up front (the FP64 pipe is slow, and the compiler may hoist the rare path).
-  const float rp = r < jb ? raised_pivot(G, k, j0 + r, shift, pfloor) : 1.0f;
+  const float rp = r < jb ? raised_pivot(G, k, goff + j0 + r, shift, pfloor) : 1.0f;
   int bad = 0, clamped = 0;
 #pragma unroll
   for (int t = 0; t < PW; ++t) {
@@ -557,12 +558,28 @@ __device__ __forceinline__ void cta_rank_update(float* A, int ks, int k, int j0,
   }
 }
 
+// Block mode (blk.scal non-null): the kernel factors one diagonal block
+// (k x k, rows and columns goff..goff+k of a kfull x kfull matrix) of a
+// blocked factorisation. G32 is the block of the working matrix, already
+// shifted and updated by the previous blocks; trace, shift and pivot floor come
+// from blk.scal (the whole matrix's); raised pivots read the whole G's
+// diagonal; one attempt, a non-finite pivot sets *blk.fail; L (k x k, row
+// stride blk.ldl) is written without flags, stats or shift_out.
+struct CtaBlock {
+  const double* scal;  // [trace, shift, pivot floor] of the whole matrix, or null
+  int goff, kfull;
+  int* fail;
+  long long ldl;
+};
+
 __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* __restrict__ G,
                                                                 const float* __restrict__ G32, long long ld32,
                                                                 int k, double shift_rel, float* __restrict__ L32,
                                                                 int* flags, unsigned long long* stats,
-                                                                double* shift_out) {
+                                                                double* shift_out, CtaBlock blk) {
   extern __shared__ __align__(16) float csm[];
+  const bool block_mode = blk.scal != nullptr;
+  if (block_mode && *blk.fail) return;  // an earlier block (or the input) failed: the finish step writes L
   const int ks = cta_ks(k);
   float* A = csm;                        // k x ks, row-major, lower part used
   float* rinv = A + (size_t)k * ks;      // PW reciprocal pivots of the current diagonal block
@@ -571,7 +588,9 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
   __shared__ double s_trace;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  if (warp == 0) {  // fixed-order trace
+  if (block_mode) {
+    if (tid == 0) s_trace = blk.scal[0];
+  } else if (warp == 0) {  // fixed-order trace
     double t = 0.0;
     for (int i = lane; i < k; i += 32) t += fabs(G[(size_t)i * k + i]);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -579,16 +598,19 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
   }
   __syncthreads();
   const double trace = s_trace;
+  const int kg = block_mode ? blk.kfull : k;  // order of the whole matrix (floor, raised pivots)
+  const int goff = block_mode ? blk.goff : 0;
   // trace: sum of |G_ii| (the trace of a PSD matrix; a scale for the shifts and
   // the floor of any symmetric one). A zero diagonal means the zero matrix
   // (the Gram of a zero sketch, or a zero projected matrix): it is factored
   // exactly as G + 1 I = I I^T (L = I, shift 1).
   const bool finite_in = isfinite(trace) && trace > 0.0;
   const bool zero_in = trace == 0.0;
-  const float pfloor = (float)fmax(1e-9 * trace, 1e-6 * trace / k);
-  double shift = shift_rel > 0.0 ? shift_rel * trace : (shift_rel < 0.0 ? -shift_rel * trace / k : 0.0);
+  const float pfloor = block_mode ? (float)blk.scal[2] : (float)fmax(1e-9 * trace, 1e-6 * trace / k);
+  double shift = block_mode ? blk.scal[1]
+                            : (shift_rel > 0.0 ? shift_rel * trace : (shift_rel < 0.0 ? -shift_rel * trace / k : 0.0));
   int ok = 0;
-  for (int attempt = 0; attempt < CHOL_ATTEMPTS && finite_in; ++attempt) {
+  for (int attempt = 0; attempt < (block_mode ? 1 : CHOL_ATTEMPTS) && finite_in; ++attempt) {
     if (attempt > 0) {
       shift = fmax(shift, 1e-7 * trace) * 100.0;
       if (tid == 0) {
@@ -596,7 +618,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
         if (stats) atomicAdd(stats + STAT_CHOL_RETRY, 1ull);
       }
     }
-    const float shf = (float)shift;
+    const float shf = block_mode ? 0.0f : (float)shift;  // a block of the working matrix is shifted already
     if (G32) {  // lower triangle by asynchronous copies (no registers, all in flight), then the shift
       for (int i = warp; i < k; i += CTA_WARPS) {
 #pragma unroll 1
@@ -611,7 +633,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
     }
     if (tid == 0) { sflag[0] = 0; sflag[1] = 0; }
     __syncthreads();
-    if (warp == 0) cta_factor_diag(A, ks, 0, min(PW, k), rinv, Xi, G, k, shift, pfloor, sflag, lane);
+    if (warp == 0) cta_factor_diag(A, ks, 0, min(PW, k), rinv, Xi, G, kg, shift, pfloor, sflag, lane, goff);
     __syncthreads();
     for (int j0 = 0; j0 < k && !sflag[0]; j0 += PW) {
       const int jb = min(PW, k - j0);
@@ -625,7 +647,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
       // row below it, from the next block column to the diagonal.
       if (warp == 0) {
         asm volatile("bar.sync 1, %0;" ::"n"(CTA_THREADS) : "memory");
-        cta_factor_diag(A, ks, first, jb1, rinv, Xi, G, k, shift, pfloor, sflag, lane);
+        cta_factor_diag(A, ks, first, jb1, rinv, Xi, G, kg, shift, pfloor, sflag, lane, goff);
       } else {
         cta_rank_update(A, ks, k, j0, jb, first, first + jb1, first, first + jb1, 1, 1, warp, lane);
         asm volatile("bar.arrive 1, %0;" ::"n"(CTA_THREADS) : "memory");
@@ -636,12 +658,21 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
     if (!sflag[0]) {
       if (tid == 0) {
         if (sflag[1]) raise_flag(flags, KFAC_FLAG_CHOL_SHIFTED);
-        if (shift_out) *shift_out = shift;
+        if (shift_out && !block_mode) *shift_out = shift;
       }
       ok = 1;
       break;
     }
     __syncthreads();
+  }
+  if (block_mode) {
+    if (!ok) {
+      if (tid == 0) *blk.fail = 1;
+      return;
+    }
+    for (int i = warp; i < k; i += CTA_WARPS)
+      for (int j = lane; j < k; j += 32) L32[(size_t)i * blk.ldl + j] = (j <= i) ? A[(size_t)i * ks + j] : 0.0f;
+    return;
   }
   if (!ok) {
     if (tid == 0) {
@@ -672,12 +703,164 @@ cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, fl
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cta_f32), kSmemOptin, false);
     if (e != cudaSuccess) return e;
     k_chol_cta_f32<<<1, CTA_THREADS, cta_smem_bytes(k), s>>>(G, G32, ld32, k, shift_rel, L32, flags, stats,
-                                                               shift_out);
+                                                               shift_out, CtaBlock{});
     note_launch();
     return cudaGetLastError();
   }
   return fp64 ? launch_chol<double>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref, panel)
               : launch_chol<float>(G, k, shift_rel, L32, flags, stats, s, shift_out, nc_pref, panel);
+}
+
+// ---------------------------------------------------------------------------
+// Blocked FP32 Cholesky for k > CTA_KMAX: right-looking over nb diagonal
+// blocks of at most CTA_KMAX rows (sizes multiples of 4, so every block starts
+// on a 16-byte boundary of the working matrix W = G + shift I):
+//   L_bb = chol(W_bb)                        one-CTA kernel, block mode
+//   L_rb^T = L_bb^-1 W_br                     the triangular solve below
+//   W_rr <- W_rr - L_rb L_rb^T                symmetric tensor-core product (3xTF32)
+// The pivots are those of the unblocked factorisation (up to rounding), so the
+// floor, the raised pivots and the shift follow the one-CTA kernel; a
+// non-finite pivot, or a zero or non-finite input, ends in the finish step's
+// fallback factor as the other kernels' failure paths do.
+namespace {
+struct CbLayout {
+  size_t scal, W, Lb, Xb, Xt, dinv, total;
+  int nb, kb;
+  long long kp, np, kbp;
+};
+
+CbLayout cb_layout(int k) {
+  CbLayout c = {};
+  c.nb = (k + CTA_KMAX - 1) / CTA_KMAX;
+  for (;; ++c.nb) {
+    c.kb = ((k + c.nb - 1) / c.nb + 3) / 4 * 4;
+    if (c.kb <= CTA_KMAX) break;
+  }
+  c.kp = (k + 3) / 4 * 4;
+  c.np = c.kp;
+  c.kbp = c.kb;  // a multiple of 4
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = (off + 255) & ~size_t(255);
+    off = o + bytes;
+    return o;
+  };
+  c.scal = take(64);
+  c.W = take(sizeof(float) * (size_t)k * c.kp);
+  c.Lb = take(sizeof(float) * (size_t)c.kb * c.kb);
+  c.Xb = take(sizeof(float) * (size_t)c.kb * c.np);
+  c.Xt = take(sizeof(float) * (size_t)k * c.kbp);
+  c.dinv = take(sizeof(float) * trsm_ws_floats(c.kb));
+  c.total = off;
+  return c;
+}
+
+// Trace, shift and pivot floor of the whole matrix (as the one-CTA kernel
+// forms them), the failure marker (2: zero input, 3: non-finite input).
+__global__ void k_cb_prep(const double* __restrict__ G, int k, double shift_rel, double* scal, int* fail) {
+  const int lane = threadIdx.x;
+  double t = 0.0;
+  for (int i = lane; i < k; i += 32) t += fabs(G[(size_t)i * k + i]);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) {
+    scal[0] = t;
+    scal[1] = shift_rel > 0.0 ? shift_rel * t : (shift_rel < 0.0 ? -shift_rel * t / k : 0.0);
+    scal[2] = (double)(float)fmax(1e-9 * t, 1e-6 * t / k);
+    *fail = (t == 0.0) ? 2 : (isfinite(t) ? 0 : 3);
+  }
+}
+
+// W = G32 + shift I (whole symmetric matrix, row stride kp), L32 = 0.
+__global__ void k_cb_init(const float* __restrict__ G32, long long ld32, int k, const double* scal, float* W,
+                          long long kp, float* L32) {
+  const long long n = (long long)k * k;
+  const float shf = (float)scal[1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    W[(size_t)i * kp + j] = G32[(size_t)i * ld32 + j] + (i == j ? shf : 0.0f);
+    L32[e] = 0.0f;
+  }
+}
+
+// dst[r][c] = src[r][c] for r < rows, c < cols (dst row stride ldd).
+__global__ void k_cb_place(const float* __restrict__ src, long long lds, int rows, int cols, float* dst,
+                           long long ldd) {
+  const long long n = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+    dst[(size_t)r * ldd + c] = src[(size_t)r * lds + c];
+  }
+}
+
+// Flags, statistics and shift_out of the blocked factorisation; on failure the
+// fallback factor diag(sqrt(G_ii)) (1 where G_ii is not positive and finite;
+// I for the zero matrix) replaces L.
+__global__ void k_cb_finish(const double* __restrict__ G, int k, const double* scal, const int* fail, float* L32,
+                            int* flags, unsigned long long* stats, double* shift_out) {
+  const int f = *fail;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (f) raise_flag(flags, f == 2 ? KFAC_FLAG_CHOL_SHIFTED : (f == 3 ? KFAC_FLAG_NONFINITE : KFAC_FLAG_CHOL_FAILED));
+    if (shift_out) *shift_out = f == 0 ? scal[1] : (f == 2 ? 1.0 : 0.0);
+    if (stats) atomicAdd(stats + STAT_CHOL, 1ull);
+  }
+  if (!f) return;
+  const long long n = (long long)k * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    const double g = G[(size_t)i * k + i];
+    L32[e] = (i == j) ? (float)sqrt(isfinite(g) && g > 1e-30 ? g : 1.0) : 0.0f;
+  }
+}
+
+int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>(1216, (n + 255) / 256)); }
+}  // namespace
+
+size_t chol_blocked_ws_bytes(int k) { return k > CTA_KMAX ? cb_layout(k).total : 0; }
+
+cudaError_t chol_blocked(const double* G, const float* G32, long long ld32, int k, double shift_rel, float* L32,
+                         int* flags, unsigned long long* stats, cudaStream_t s, double* shift_out, void* ws,
+                         long long wait_cycles) {
+  if (k <= CTA_KMAX) return chol_cluster(G, k, shift_rel, false, L32, flags, stats, s, shift_out, G32, ld32);
+  const CbLayout c = cb_layout(k);
+  char* base = static_cast<char*>(ws);
+  double* scal = reinterpret_cast<double*>(base + c.scal);
+  int* fail = reinterpret_cast<int*>(scal + 4);
+  float* W = reinterpret_cast<float*>(base + c.W);
+  float* Lb = reinterpret_cast<float*>(base + c.Lb);
+  float* Xb = reinterpret_cast<float*>(base + c.Xb);
+  float* Xt = reinterpret_cast<float*>(base + c.Xt);
+  float* dinv = reinterpret_cast<float*>(base + c.dinv);
+  {
+    cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(k_chol_cta_f32), kSmemOptin, false);
+    if (e != cudaSuccess) return e;
+  }
+  k_cb_prep<<<1, 32, 0, s>>>(G, k, shift_rel, scal, fail);
+  note_launch();
+  k_cb_init<<<grid_for((long long)k * k), 256, 0, s>>>(G32, ld32, k, scal, W, c.kp, L32);
+  note_launch();
+  for (int o = 0; o < k; o += c.kb) {
+    const int kb = std::min(c.kb, k - o), n = k - o - kb;
+    float* Wbb = W + (size_t)o * c.kp + o;
+    CtaBlock blk{scal, o, k, fail, kb};
+    k_chol_cta_f32<<<1, CTA_THREADS, cta_smem_bytes(kb), s>>>(G, Wbb, c.kp, kb, 0.0, Lb, flags, nullptr, nullptr,
+                                                                blk);
+    note_launch();
+    k_cb_place<<<grid_for((long long)kb * kb), 256, 0, s>>>(Lb, kb, kb, kb, L32 + (size_t)o * k + o, k);
+    note_launch();
+    if (n == 0) break;
+    cudaError_t e = trsm_lower_f32(Lb, kb, Wbb + kb, c.kp, Xb, c.np, n, dinv, s);  // L_rb^T (kb x n)
+    if (e != cudaSuccess) return e;
+    if ((e = transpose_f32(Xb, c.np, kb, n, Xt, c.kbp, s)) != cudaSuccess) return e;  // L_rb (n x kb)
+    k_cb_place<<<grid_for((long long)n * kb), 256, 0, s>>>(Xt, c.kbp, n, kb, L32 + (size_t)(o + kb) * k + o, k);
+    note_launch();
+    float* Wrr = W + (size_t)(o + kb) * c.kp + o + kb;
+    if ((e = syrk_update(s, n, kb, Xt, (int)c.kbp, -1.0f, 1.0f, KFAC_PREC_FP32, Wrr, (int)c.kp, flags,
+                         wait_cycles)) != cudaSuccess)
+      return e;
+  }
+  k_cb_finish<<<grid_for((long long)k * k), 256, 0, s>>>(G, k, scal, fail, L32, flags, stats, shift_out);
+  note_launch();
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

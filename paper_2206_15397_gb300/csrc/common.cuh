@@ -172,6 +172,16 @@ cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, fl
                          unsigned long long* stats, cudaStream_t s, double* shift_out = nullptr,
                          const float* G32 = nullptr, long long ld32 = 0, int nc_pref = 0, int panel = 16);
 
+// Blocked FP32 Cholesky (the same contract as chol_cluster's FP32 path) for
+// k above the one-CTA kernel's limit: one-CTA factorisations of diagonal
+// blocks, triangular solves and tensor-core rank updates between them. G32 (row
+// stride ld32) is required; ws: chol_blocked_ws_bytes(k) bytes of device
+// workspace. k within the one-CTA limit goes to chol_cluster.
+size_t chol_blocked_ws_bytes(int k);
+cudaError_t chol_blocked(const double* G, const float* G32, long long ld32, int k, double shift_rel, float* L32,
+                         int* flags, unsigned long long* stats, cudaStream_t s, double* shift_out, void* ws,
+                         long long wait_cycles);
+
 // Qt = L^-1 Yt for lower-triangular FP32 L (k x k) and Yt (k x d, row stride ldy).
 // dinv_ws: trsm_ws_floats(k) floats of workspace (L packed by 32-row block rows
 // with inverted diagonal blocks, or the block inverses alone for large k).
@@ -185,12 +195,16 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
 // FP32 one-sided Jacobi on chol(C + s I) over a thread-block cluster: writes X
 // (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:
 // eig_scratch_floats(k) floats (the Cholesky factor and the shift it used).
-inline size_t eig_scratch_floats(int k) { return (((size_t)k * k + 1) & ~(size_t)1) + 4; }
+// (the factor, the shift, then the blocked Cholesky's workspace 256-byte aligned)
+inline size_t eig_scratch_head_floats(int k) { return ((((size_t)k * k + 1) & ~(size_t)1) + 4 + 63) & ~(size_t)63; }
+inline size_t eig_scratch_floats(int k) { return eig_scratch_head_floats(k) + (chol_blocked_ws_bytes(k) + 3) / 4; }
 // stop_tol > 0 ends the sweeps after one whose largest pair cosine was below it.
+// chol_blocked: factor C + sI by chol_blocked (k above the one-CTA limit, C32
+// given) instead of the cluster kernel.
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, float stop_tol,
                            double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
                            cudaStream_t s, const float* C32 = nullptr, long long ld32 = 0, int chol_nc = 0,
-                           int chol_panel = 16);
+                           int chol_panel = 16, int chol_blocked = 0, long long wait_cycles = 0);
 
 // One-sided Jacobi on the columns of the k x k FP32 matrix held in gscratch
 // (row-major; the factor eig_jacobi_f32 writes there), with the device scalar

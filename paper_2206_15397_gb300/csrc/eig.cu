@@ -544,13 +544,17 @@ static cudaError_t launch_eig(const EigArgs& a, int nc, size_t smem, cudaStream_
 
 cudaError_t eig_jacobi_f32(const double* C, int k, double shift_rel, int max_sweeps, float tol, float stop_tol,
                            double* X, double* lam, float* gscratch, int* flags, unsigned long long* stats,
-                           cudaStream_t s, const float* C32, long long ld32, int chol_nc, int chol_panel) {
+                           cudaStream_t s, const float* C32, long long ld32, int chol_nc, int chol_panel,
+                           int chol_blocked_on, long long wait_cycles) {
   if (k <= 0) return cudaSuccess;
-  // W = L with L L^T = C + sI, factorised on a cluster in FP32; the shift it
-  // used (grown on breakdown) is stored after the factor.
+  // W = L with L L^T = C + sI, factorised in FP32; the shift it used (grown on
+  // breakdown) is stored after the factor.
   double* shift = reinterpret_cast<double*>(gscratch + (((size_t)k * k + 1) & ~(size_t)1));
-  cudaError_t e = chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift, C32, ld32, chol_nc,
-                               chol_panel);
+  cudaError_t e = (chol_blocked_on && C32 && chol_blocked_ws_bytes(k) > 0)
+                      ? chol_blocked(C, C32, ld32, k, shift_rel, gscratch, flags, stats, s, shift,
+                                     gscratch + eig_scratch_head_floats(k), wait_cycles)
+                      : chol_cluster(C, k, shift_rel, /*fp64=*/false, gscratch, flags, stats, s, shift, C32, ld32,
+                                     chol_nc, chol_panel);
   if (e != cudaSuccess) return e;
   return jacobi_columns(k, max_sweeps, tol, stop_tol, X, lam, gscratch, shift, flags, stats, s, 0);
 }

@@ -58,6 +58,7 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
 
   tc::TcArgs a = {};
   a.M = g.M; a.N = g.N; a.K = g.K;
+  a.tn = tc::tile_n(g.N, mode, g.sym != 0, bf16d);
   a.alpha = g.alpha; a.beta = g.beta;
   a.rowscale = g.rowscale; a.colscale = g.colscale;
   a.C0 = g.C0; a.ldc = g.ldc; a.c0_trans = g.c0_trans;
@@ -68,7 +69,7 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
     a.partial = 1; a.kchunk = g.kchunk; a.zstride = g.zstride;
     return launch(a, g.zsplit);
   }
-  const int bn = bf16d ? (g.N > 128 ? 256 : 128) : tc::tile_n(g.N, mode);
+  const int bn = a.tn;
   long long tiles = cdiv(g.M, 128) * cdiv(g.N, bn);
   if (g.sym) tiles = (tiles + 1) / 2;
   const long long rows = g.d_trans ? g.N : g.M, cols = g.d_trans ? g.M : g.N;

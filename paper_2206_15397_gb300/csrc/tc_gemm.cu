@@ -251,7 +251,7 @@ struct Cfg16 {
 // (v[j] = raw sum for column nb + j): scaling, beta * C0, store (row-major via
 // the warp's staging tile, or transposed), the symmetric mirror.
 __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int m, int mrow0, int nb, int lane,
-                                            float rs, float* stage_tile, float* Dz) {
+                                            float rs, float* stage_tile, float* Dz, int nend) {
   if (!p.partial) {
     float cin[32];
     if (p.beta != 0.0f && p.C0) {
@@ -259,14 +259,14 @@ __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = nb + j;
-          cin[j] = (m < p.M && n < p.N) ? p.C0[(long long)n * p.ldc + m] : 0.0f;
+          cin[j] = (m < p.M && n < nend) ? p.C0[(long long)n * p.ldc + m] : 0.0f;
         }
       } else {  // rows of C0 through the staging tile: all 32 row loads in flight, then the stores
         float rowv[32];
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
           const int mr = mrow0 + r, n = nb + lane;
-          rowv[r] = (mr < p.M && n < p.N) ? __ldg(p.C0 + (long long)mr * p.ldc + n) : 0.0f;
+          rowv[r] = (mr < p.M && n < nend) ? __ldg(p.C0 + (long long)mr * p.ldc + n) : 0.0f;
         }
         __syncwarp();
 #pragma unroll
@@ -280,7 +280,7 @@ __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int
     for (int j = 0; j < 32; ++j) {
       const int n = nb + j;
       float x = v[j] * p.alpha * rs;
-      if (p.colscale && n < p.N) x *= p.colscale[n];
+      if (p.colscale && n < nend) x *= p.colscale[n];
       if (p.beta != 0.0f && p.C0) x = fmaf(p.beta, cin[j], x);
       v[j] = x;
     }
@@ -289,7 +289,7 @@ __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int n = nb + j;
-      if (m < p.M && n < p.N) Dz[(long long)n * p.ldd + m] = v[j];
+      if (m < p.M && n < nend) Dz[(long long)n * p.ldd + m] = v[j];
     }
   } else {
     __syncwarp();
@@ -298,13 +298,13 @@ __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int
     __syncwarp();
     for (int r = 0; r < 32; ++r) {
       const int mr = mrow0 + r, n = nb + lane;
-      if (mr < p.M && n < p.N && (!p.sym || mr <= n)) Dz[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
+      if (mr < p.M && n < nend && (!p.sym || mr <= n)) Dz[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
     }
     if (p.sym) {  // mirror: D[n][m] for m < n, consecutive lanes -> consecutive m
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int n = nb + j;
-        if (m < p.M && n < p.N && m < n) Dz[(long long)n * p.ldd + m] = v[j];
+        if (m < p.M && n < nend && m < n) Dz[(long long)n * p.ldd + m] = v[j];
       }
     }
   }
@@ -325,13 +325,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 1);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::STAGES;
   const uint32_t accb = empty0 + 8 * C::STAGES;
+  __shared__ int s_abort;  // a wait of this CTA gave up: the accumulator is not a result
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  if (p.sym && m0 > n0 + BN - 1) return;  // whole tile below the diagonal (uniform exit, nothing started)
+  const int tn = p.tn;  // this launch's tile width: a multiple of 16, at most BN
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * tn;
+  const int nend = min(p.N, n0 + tn);
+  if (p.sym && m0 > n0 + tn - 1) return;  // whole tile below the diagonal (uniform exit, nothing started)
   const int kb0 = blockIdx.z * p.kchunk;
   const int ke = min(p.K, kb0 + p.kchunk);
   const int nk = ke > kb0 ? (ke - kb0 + BK - 1) / BK : 0;
+  const uint32_t stage_tx = (uint32_t)(C::A_BYTES + tn * (C::B_BYTES / BN));
 
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -339,6 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(accb, 1);
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -358,9 +363,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) break;
+      if (kb >= C::STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) { s_abort = 1; break; }
       const uint32_t st = smem_u32(smem + s * C::STAGE);
-      mbar_expect_tx(full0 + 8 * s, C::RAW);
+      mbar_expect_tx(full0 + 8 * s, stage_tx);
       tma_load_2d(st, &tmA, kb0 + kb * BK, m0, full0 + 8 * s);
       tma_load_2d(st + C::A_BYTES, &tmB, kb0 + kb * BK, n0, full0 + 8 * s);
       ++issued;
@@ -371,11 +376,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(full0 + 8 * (kb % C::STAGES), (uint32_t)(kb / C::STAGES) & 1u, p.flags, kDrainCycles);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----------------------------------------------------------
-    constexpr uint32_t idesc = BF16D ? idesc_bf16(BM, BN) : idesc_tf32(BM, BN);
+    const uint32_t idesc = BF16D ? idesc_bf16(BM, tn) : idesc_tf32(BM, tn);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-      if (!mbar_wait(full0 + 8 * s, ph, p.flags, p.wait_cycles)) break;
+      if (!mbar_wait(full0 + 8 * s, ph, p.flags, p.wait_cycles)) { s_abort = 1; break; }
       tc_fence_after();
       const uint32_t st = smem_u32(smem + s * C::STAGE);
       const uint64_t ad = sdesc_k128(st), bd = sdesc_k128(st + C::A_BYTES);
@@ -389,10 +394,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     mma_commit(accb);  // accumulator ready (also completes when nothing was issued)
   }
-  __syncwarp();
+  __syncthreads();  // s_abort is final
 
   // ---- epilogue ----------------------------------------------------------------
-  const bool acc_ok = mbar_wait(accb, 0, p.flags, kDrainCycles);  // every issued MMA has completed
+  const bool acc_ok = mbar_wait(accb, 0, p.flags, kDrainCycles) && !s_abort;  // every issued MMA has completed
   tc_fence_after();
   float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // per-warp 32 x 33 staging
   float* const Dz = p.D + (p.partial ? (long long)blockIdx.z * p.zstride : 0LL);  // split-K slice
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const float rs = (p.rowscale && m < p.M) ? p.rowscale[m] : 1.0f;
   for (int c0 = cbeg; c0 < cbeg + BN / 2; c0 += 32) {
     const int nb = n0 + c0;
-    if (nb >= p.N) break;  // uniform across the warp
+    if (nb >= nend) break;  // uniform across the warp
     float v[32];
     if (nk > 0 && acc_ok) {
       tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = 0.0f;
     }
-    store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz);
+    store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz, nend);
   }
   tc_fence_before();
   __syncthreads();
@@ -435,9 +440,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   // With both precomputed no split runs: the MMA issuer takes a stage as soon
   // as its copies have landed.
   const bool need_split = !(p.lo_a && p.lo_b);
-  const uint32_t stage_tx = (uint32_t)(C::RAW + (p.lo_a ? C::A_BYTES : 0) + (p.lo_b ? C::B_BYTES : 0));
+  const int b_bytes = p.tn * (C::B_BYTES / BN3);  // the B tile's rows that TMA fills
+  const uint32_t stage_tx = (uint32_t)(C::A_BYTES + b_bytes + (p.lo_a ? C::A_BYTES : 0) + (p.lo_b ? b_bytes : 0));
   const int split_e0 = p.lo_a ? C::A_BYTES / 16 : 0;             // float4 range of the stage to split
-  const int split_e1 = p.lo_b ? C::A_BYTES / 16 : C::RAW / 16;
+  const int split_e1 = p.lo_b ? C::A_BYTES / 16 : (C::A_BYTES + b_bytes) / 16;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
@@ -446,8 +452,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tfull0 = empty0 + 8 * C::STAGES, tempty0 = tfull0 + 16, accb = tempty0 + 16;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN3;
-  if (p.sym && m0 > n0 + BN3 - 1) return;  // whole tile below the diagonal (uniform exit, nothing started)
+  const int tn = p.tn;  // this launch's tile width: a multiple of 16, at most BN3
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * tn;
+  const int nend = min(p.N, n0 + tn);
+  if (p.sym && m0 > n0 + tn - 1) return;  // whole tile below the diagonal (uniform exit, nothing started)
   const int kb0 = blockIdx.z * p.kchunk;
   const int ke = min(p.K, kb0 + p.kchunk);
   const int nk = ke > kb0 ? (ke - kb0 + BK - 1) / BK : 0;
@@ -498,7 +506,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: stages 2m, 2m+1 -> TMEM pair m & 1 ------------------------
     const uint32_t ready0 = need_split ? split0 : full0;
-    constexpr uint32_t idesc = idesc_tf32(BM, BN3);
+    const uint32_t idesc = idesc_tf32(BM, tn);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES, m = kb >> 1, b = m & 1;
       const bool first = (kb & 1) == 0, last = (kb & 1) == 1 || kb == nk - 1;
@@ -556,6 +564,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc_fence_after();
 #pragma unroll
         for (int c = 0; c < BN3 / 32; ++c) {
+          if (32 * c >= tn) break;  // columns this tile's MMAs never wrote (warp-uniform)
           uint32_t v[32], w[32];
           tmem_ld32_async(taddr + lrow + (uint32_t)(b * BN3 + 32 * c), v);
           tmem_ld32_async(taddr + lrow + (uint32_t)(2 * BN3 + b * BN3 + 32 * c), w);
@@ -584,11 +593,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
     for (int c = 0; c < BN3 / 32; ++c) {
       const int nb = n0 + 32 * c;
-      if (nb < p.N) {  // uniform across the warp
+      if (nb < nend) {  // uniform across the warp
         float v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = ok ? acc[32 * c + j] : 0.0f;
-        store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz);
+        store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz, nend);
       }
     }
   }
@@ -612,6 +621,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t rfull0 = smem_u32(bars), rempty0 = rfull0 + 8 * C::RAW_STAGES;
   const uint32_t hfull0 = rempty0 + 8 * C::RAW_STAGES, hempty0 = hfull0 + 8 * C::H_STAGES;
   const uint32_t accb = hempty0 + 8 * C::H_STAGES;
+  __shared__ int s_abort;  // a wait of this CTA gave up: the accumulator is not a result
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN16;
@@ -630,6 +640,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(hempty0 + 8 * h, 1);
     }
     mbar_init(accb, 1);
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -649,7 +660,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::RAW_STAGES;
       const uint32_t ph = (uint32_t)(kb / C::RAW_STAGES) & 1u;
-      if (kb >= C::RAW_STAGES && !mbar_wait(rempty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) break;
+      if (kb >= C::RAW_STAGES && !mbar_wait(rempty0 + 8 * s, ph ^ 1u, p.flags, p.wait_cycles)) { s_abort = 1; break; }
       const uint32_t st = smem_u32(raw0 + s * C::RAW);
       const int kx = kb0 + kb * BK16;
       mbar_expect_tx(rfull0 + 8 * s, C::RAW);
@@ -667,7 +678,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int h = kb % C::H_STAGES;
       const uint32_t ph = (uint32_t)(kb / C::H_STAGES) & 1u;
-      if (!mbar_wait(hfull0 + 8 * h, ph, p.flags, p.wait_cycles)) break;
+      if (!mbar_wait(hfull0 + 8 * h, ph, p.flags, p.wait_cycles)) { s_abort = 1; break; }
       tc_fence_after();
       const uint32_t hb = smem_u32(half0 + h * C::HALF);
       const uint64_t ad = sdesc_k128(hb), bd = sdesc_k128(hb + C::A_H);
@@ -687,10 +698,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int t = tid - 64;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::RAW_STAGES, h = kb % C::H_STAGES;
-      if (!mbar_wait_warp(rfull0 + 8 * s, (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags, lane, p.wait_cycles)) break;
+      if (!mbar_wait_warp(rfull0 + 8 * s, (uint32_t)(kb / C::RAW_STAGES) & 1u, p.flags, lane, p.wait_cycles)) { s_abort = 1; break; }
       if (kb >= C::H_STAGES &&
           !mbar_wait_warp(hempty0 + 8 * h, ((uint32_t)(kb / C::H_STAGES) & 1u) ^ 1u, p.flags, lane, p.wait_cycles))
-        break;
+        { s_abort = 1; break; }
       const uint8_t* rs = raw0 + s * C::RAW;
       uint8_t* hs = half0 + h * C::HALF;
       for (int q = t; q < (BM + BN16) * 8; q += kConvThreads) {
@@ -713,10 +724,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_arrive(rempty0 + 8 * s);
     }
   }
-  __syncwarp();
+  __syncthreads();  // s_abort is final
 
   // ---- epilogue (all 8 warps, as the TF32 kernel) --------------------------------
-  const bool acc_ok = mbar_wait(accb, 0, p.flags, kDrainCycles);  // every issued MMA has completed
+  const bool acc_ok = mbar_wait(accb, 0, p.flags, kDrainCycles) && !s_abort;  // every issued MMA has completed
   tc_fence_after();
   float* stage_tile = reinterpret_cast<float*>(smem) + warp * (32 * 33);
   float* const Dz = p.D + (p.partial ? (long long)blockIdx.z * p.zstride : 0LL);
@@ -734,7 +745,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = 0.0f;
     }
-    store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz);
+    store_chunk(p, v, m, m0 + 32 * q, nb, lane, rs, stage_tile, Dz, p.N);
   }
   tc_fence_before();
   __syncthreads();
@@ -777,17 +788,21 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, long long l
   return r == CUDA_SUCCESS;
 }
 
+// `bn` is the kernel's largest tile width; the launch uses a.tn (set here to
+// bn unless the caller chose a narrower multiple of 16 that fits N better).
 template <typename Kern>
-cudaError_t launch_kernel(Kern kern, int smem, int bn, const TcArgs& a, const void* A, long long lda,
+cudaError_t launch_kernel(Kern kern, int smem, int bn, const TcArgs& a0, const void* A, long long lda,
                           const void* B, long long ldb, int zsplit, cudaStream_t s, bool bf16 = false) {
   {
     cudaError_t e = set_kernel_attrs_once(reinterpret_cast<const void*>(kern), smem, false);
     if (e != cudaSuccess) return e;
   }
+  TcArgs a = a0;
+  if (a.tn <= 0 || a.tn > bn || (a.tn & 15)) a.tn = bn;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, a.M, a.K, lda, BM, bf16) || !make_map(&mb, B, a.N, a.K, ldb, bn, bf16))
+  if (!make_map(&ma, A, a.M, a.K, lda, BM, bf16) || !make_map(&mb, B, a.N, a.K, ldb, a.tn, bf16))
     return cudaErrorInvalidValue;
-  dim3 grid((a.N + bn - 1) / bn, (a.M + BM - 1) / BM, zsplit);
+  dim3 grid((a.N + a.tn - 1) / a.tn, (a.M + BM - 1) / BM, zsplit);
   kern<<<grid, THREADS, smem, s>>>(ma, mb, a);
   note_launch();
   return cudaGetLastError();
@@ -845,19 +860,24 @@ cudaError_t gemm(const TcArgs& a0, const float* A, long long lda, const float* B
     TcArgs a = a0;
     a.lo_a = Alo != nullptr;
     a.lo_b = Blo != nullptr;
+    if (a.tn <= 0 || a.tn > BN3 || (a.tn & 15)) a.tn = BN3;
     // Tail planes share their operand's shape; an absent one gets its
     // operand's map (never read).
     CUtensorMap ma, mb, mal, mbl;
-    if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, BN3) ||
+    if (!make_map(&ma, A, a.M, a.K, lda, BM) || !make_map(&mb, B, a.N, a.K, ldb, a.tn) ||
         !make_map(&mal, Alo ? Alo : A, a.M, a.K, Alo ? ldalo : lda, BM) ||
-        !make_map(&mbl, Blo ? Blo : B, a.N, a.K, Blo ? ldblo : ldb, BN3))
+        !make_map(&mbl, Blo ? Blo : B, a.N, a.K, Blo ? ldblo : ldb, a.tn))
       return cudaErrorInvalidValue;
-    dim3 grid((a.N + BN3 - 1) / BN3, (a.M + BM - 1) / BM, zsplit);
+    dim3 grid((a.N + a.tn - 1) / a.tn, (a.M + BM - 1) / BM, zsplit);
     k_tc_gemm3<<<grid, THREADS, Cfg3::SMEM, s>>>(ma, mb, mal, mbl, a);
     note_launch();
     return cudaGetLastError();
   }
-  if (mode == Mode::Bf16) return launch_kernel(k_tc_gemm16, Cfg16::SMEM, BN16, a0, A, lda, B, ldb, zsplit, s);
+  if (mode == Mode::Bf16) {  // the converting kernel keeps its full tile width
+    TcArgs a = a0;
+    a.tn = BN16;
+    return launch_kernel(k_tc_gemm16, Cfg16::SMEM, BN16, a, A, lda, B, ldb, zsplit, s);
+  }
   if (a0.N > 128) return launch_kernel(k_tc_gemm<256>, Cfg<256>::SMEM, 256, a0, A, lda, B, ldb, zsplit, s);
   return launch_kernel(k_tc_gemm<128>, Cfg<128>::SMEM, 128, a0, A, lda, B, ldb, zsplit, s);
 }

@@ -25,6 +25,7 @@ struct TcArgs {
   int* flags;
   long long wait_cycles;  // limit (clock cycles, > 0) of each wait for another role's progress
   int lo_a, lo_b;         // 3xTF32: the operand's tails come from global memory (set by gemm())
+  int tn;                 // tile width (columns of D per CTA): a multiple of 16 up to the kernel's; 0 = widest
 };
 
 // True when A (M x K, row stride lda) and B (N x K, row stride ldb) can be read
@@ -35,8 +36,17 @@ bool eligible(const float* A, long long lda, const float* B, long long ldb, int 
 // BF16 (round to nearest) operands; FP32 accumulation in tensor memory.
 enum class Mode { Fp32, Tf32, Bf16 };
 
-// Tile width (columns of D per CTA) the launch below uses.
-inline int tile_n(int N, Mode mode) { return (mode != Mode::Tf32 || N <= 128) ? 128 : 256; }
+// Tile width (columns of D per CTA) for N columns: the fewest tiles of the
+// kernel's widest (128, or 256 for TF32 and direct-BF16 products with N > 128),
+// each narrowed to the multiple of 16 that covers N evenly (k = 522 takes 5
+// tiles of 112 instead of 5 of 128). Symmetric products keep square tiles.
+inline int tile_n(int N, Mode mode, bool sym = false, bool bf16_direct = false) {
+  const int widest = ((mode == Mode::Tf32 || bf16_direct) && N > 128) ? 256 : 128;
+  if (sym || mode == Mode::Bf16 && !bf16_direct) return widest;
+  const int nt = (N + widest - 1) / widest;
+  const int tn = ((N + nt - 1) / nt + 15) / 16 * 16;
+  return tn < widest ? tn : widest;
+}
 
 // K-columns one pipeline stage of the launch consumes.
 inline int k_step(Mode mode) { return mode == Mode::Bf16 ? 64 : 32; }

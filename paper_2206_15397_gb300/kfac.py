@@ -30,7 +30,8 @@ OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_swee
            "basis_polish": 7, "cholqr_inner_fp32": 8, "eig_stop_tol": 9, "eig_refine_fp64": 10, "wait_cycles": 11,
            "group_streams": 12, "invert_method": 13,
            "chol_cluster": 14, "split_target": 15, "warm_start": 16,
-           "conv_chunk": 17, "chol_panel": 18, "tail_planes": 19}
+           "conv_chunk": 17, "chol_panel": 18, "tail_planes": 19,
+           "chol_blocked": 20}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
@@ -197,11 +198,11 @@ def kfac_get_status(ctx: Context):
 def kfac_autotune_invert(ctx: Context, descs, cache_path: str | None = None) -> dict:
     """Tune the grouped inversion's schedule for a prepared descriptor array
     (invert_descs); returns the chosen settings."""
-    out = (ctypes.c_int * 5)()
+    out = (ctypes.c_int * 6)()
     _check(lib().kfac_autotune_invert(ctx.handle, len(descs), descs,
                                       cache_path.encode() if cache_path else None, out), "kfac_autotune_invert")
     return {"group_streams": out[0], "chol_cluster": out[1], "split_target": out[2], "chol_panel": out[3],
-            "cached": bool(out[4])}
+            "chol_blocked": out[4], "cached": bool(out[5])}
 
 
 def kfac_get_item_status(ctx: Context, count: int):

@@ -87,3 +87,10 @@ def test_apply_bitwise(kf):
     cg = -torch.linspace(3, 0.2, rg, device="cuda")
     on, off = both(kf, lambda ctx: [kf.kfac_precondition(ctx, j, Ua, ca, Ug, cg, 0.1)])
     assert torch.equal(on[0], off[0])
+
+
+def test_gemm_nt_bitwise(kf):
+    A = cuda(inputs.gaussian(103, (333, 1029)))
+    B = cuda(inputs.gaussian(104, (522, 1029)))
+    on, off = both(kf, lambda ctx: [kf.kfac_gemm_nt(ctx, A, B, torch.zeros(333, 522, device="cuda"))])
+    assert torch.equal(on[0], off[0])
