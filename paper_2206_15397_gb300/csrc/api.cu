@@ -219,7 +219,7 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
   L.lam = b.take<double>(k);
   L.work = b.take<double>(eig_refine_doubles(k));
   L.jac = b.take<float>(eig_scratch_floats(k));
-  L.r32 = b.take<float>(eig_refine_floats(k) + 3 * (size_t)k * k);  // refinement, then the polish's E, P, Q
+  L.r32 = b.take<float>(eig_refine_floats(k) + polish_floats(k));  // refinement, then the polish's E, P, Q
   L.kp = round_up(k, 4);
   L.pt = b.take<float>((size_t)r * L.kp);  // P[:, :r]^T, the lift's B operand
   L.qn = b.take<float>((size_t)d * L.kp);  // Q (d x k), the lift's A operand

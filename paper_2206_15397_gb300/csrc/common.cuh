@@ -232,16 +232,22 @@ cudaError_t eig_refine_f64(const double* C, int k, double* X, double* lam, doubl
                            cudaStream_t s);
 // The same step with FP32 k x k products (C32 = FP32 copy of C, row stride
 // ldc32): their rounding (~6e-8 of ||C||) is at the accuracy C itself carries.
-// w32: eig_refine_floats(k) floats; part: 3 * 128 doubles.
-inline size_t eig_refine_floats(int k) { return 7 * (size_t)k * k; }
+// w32: eig_refine_floats(k) floats; part: 3 * 128 doubles. The FP32 work
+// matrices have the row stride ref_ld(k), so their products (from k = 128 up)
+// run on the tensor cores.
+inline long long ref_ld(int k) { return ((long long)k + 3) / 4 * 4; }
+inline size_t eig_refine_floats(int k) { return 8 * (size_t)k * ref_ld(k); }
+// Floats of w32 the basis polish uses (E, P, Q and a padded copy of C32).
+inline size_t polish_floats(int k) { return 4 * (size_t)k * ref_ld(k); }
 cudaError_t eig_refine_f32(const float* C32, long long ldc32, int k, double* X, double* lam, float* w32, double* part,
                            int* flags, cudaStream_t s);
 // Basis polish in FP32 products: with E = G - I (G = Q^T Q, FP64) and
-// M = I - E/2 = (3I - G)/2, C <- M C M (C32 updated too) keeps E in the first
-// 3 k^2 floats of w32 for polish_vectors_f32, which applies X <- M X.
+// M = I - E/2 = (3I - G)/2, C <- M C M (C32, row stride k, updated too) keeps
+// E (row stride ref_ld(k)) at the start of w32 (polish_floats(k) floats) for
+// polish_vectors_f32, which applies X <- M X.
 cudaError_t polish_projected_f32(const double* G, double* C, float* C32, int k, float* w32, cudaStream_t s);
 cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s);
-// E = G - I (FP32, k x k) into the first k^2 floats of w32, for polish_vectors_f32.
+// E = G - I (FP32, k x k, row stride ref_ld(k)) at the start of w32, for polish_vectors_f32.
 cudaError_t polish_E_f32(const double* G, int k, float* w32, cudaStream_t s);
 
 // Sort eigenpairs descending (stable by index), emit the r leading ones:

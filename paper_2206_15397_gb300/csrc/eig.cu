@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "gemm.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -658,9 +659,12 @@ __global__ void k_f64_to_f32(const double* __restrict__ in, long long n, float* 
 }
 
 // ---- FP32 refinement and polish (k x k) ------------------------------------
-// X (FP64) -> X32 = X and Xt32 = X^T in FP32, 32 x 32 tiles through shared
-// memory (both stores coalesced).
-__global__ void k_split_f32_t(const double* __restrict__ X, int k, float* __restrict__ X32, float* __restrict__ Xt32) {
+// The FP32 work matrices have the row stride ld = ref_ld(k) (a multiple of 4
+// floats), so their products qualify for the tensor cores.
+// X (FP64, row stride k) -> X32 = X and Xt32 = X^T in FP32, 32 x 32 tiles
+// through shared memory (both stores coalesced).
+__global__ void k_split_f32_t(const double* __restrict__ X, int k, float* __restrict__ X32, float* __restrict__ Xt32,
+                              long long ld) {
   __shared__ float tile[32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -668,14 +672,23 @@ __global__ void k_split_f32_t(const double* __restrict__ X, int k, float* __rest
     float v = 0.0f;
     if (r < k && c < k) {
       v = (float)X[(size_t)r * k + c];
-      if (X32) X32[(size_t)r * k + c] = v;
+      if (X32) X32[(size_t)r * ld + c] = v;
     }
     tile[y][tx] = v;
   }
   __syncthreads();
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     const int c = c0 + y, r = r0 + tx;  // Xt32[c][r] = X[r][c]
-    if (r < k && c < k) Xt32[(size_t)c * k + r] = tile[tx][y];
+    if (r < k && c < k) Xt32[(size_t)c * ld + r] = tile[tx][y];
+  }
+}
+
+// dst (k x k, row stride ldd) = src (row stride lds).
+__global__ void k_copy_f32(const float* __restrict__ src, long long lds, int k, float* __restrict__ dst, long long ldd) {
+  const long long n = (long long)k * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    dst[(size_t)i * ldd + j] = src[(size_t)i * lds + j];
   }
 }
 
@@ -683,13 +696,13 @@ __global__ void k_split_f32_t(const double* __restrict__ X, int k, float* __rest
 // ||C||^2, ||I - G||^2; a CTA takes whole rows.
 __global__ void __launch_bounds__(REF_THREADS) k_refine_norms32(const float* __restrict__ C32, long long ldc32,
                                                                  const float* __restrict__ G,
-                                                                 const float* __restrict__ S, int k,
+                                                                 const float* __restrict__ S, int k, long long ld,
                                                                  double* __restrict__ lam, double* __restrict__ part) {
   __shared__ double red[REF_THREADS / 32];
   double a = 0.0, b = 0.0, c = 0.0;
   for (int i = blockIdx.x; i < k; i += gridDim.x) {
-    const float* Si = S + (size_t)i * k;
-    const float* Gi = G + (size_t)i * k;
+    const float* Si = S + (size_t)i * ld;
+    const float* Gi = G + (size_t)i * ld;
     const float* Ci = C32 + (size_t)i * ldc32;
     if (threadIdx.x == 0) lam[i] = (double)Si[i] / (double)Gi[i];
     for (int j = threadIdx.x; j < k; j += REF_THREADS) {
@@ -713,7 +726,7 @@ __global__ void __launch_bounds__(REF_THREADS) k_refine_norms32(const float* __r
 // E^T (FP32): E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) for separated
 // pairs, R_ij / 2 otherwise (R = I - G); the threshold as k_refine_E.
 __global__ void __launch_bounds__(REF_THREADS) k_refine_Et32(const float* __restrict__ G, const float* __restrict__ S,
-                                                              int k, const double* __restrict__ lam,
+                                                              int k, long long ld, const double* __restrict__ lam,
                                                               const double* __restrict__ part, int nparts,
                                                               float* __restrict__ Et, int* flags) {
   __shared__ double s_delta;
@@ -739,42 +752,46 @@ __global__ void __launch_bounds__(REF_THREADS) k_refine_Et32(const float* __rest
   for (int j = blockIdx.x; j < k; j += gridDim.x) {  // row j of E^T = column j of E
     const float lj = (float)lam[j];
     for (int i = threadIdx.x; i < k; i += REF_THREADS) {
-      const float rij = (i == j ? 1.0f : 0.0f) - G[(size_t)i * k + j];
+      const float rij = (i == j ? 1.0f : 0.0f) - G[(size_t)i * ld + j];
       float v;
       if (i == j) {
         v = 0.5f * rij;
       } else {
         const float gap = (float)(lam[j] - lam[i]);
-        v = (fabsf(gap) > delta) ? __fdiv_rn(fmaf(lj, rij, S[(size_t)i * k + j]), gap) : 0.5f * rij;
+        v = (fabsf(gap) > delta) ? __fdiv_rn(fmaf(lj, rij, S[(size_t)i * ld + j]), gap) : 0.5f * rij;
       }
-      Et[(size_t)j * k + i] = v;
+      Et[(size_t)j * ld + i] = v;
     }
   }
 }
 
-// X += alpha * D (FP64 += FP32), k x k.
-__global__ void k_axpy_f64_f32(double* __restrict__ X, const float* __restrict__ D, long long n, double alpha) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    X[e] = fma(alpha, (double)D[e], X[e]);
+// X += alpha * D (FP64 X with row stride k, FP32 D with row stride ld), k x k.
+__global__ void k_axpy_f64_f32(double* __restrict__ X, const float* __restrict__ D, int k, long long ld, double alpha) {
+  const long long n = (long long)k * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e - (long long)i * k);
+    X[e] = fma(alpha, (double)D[(size_t)i * ld + j], X[e]);
+  }
 }
 
 // E32 = G - I in FP32 (from the FP64 Gram, so the diagonal keeps its small part).
-__global__ void k_polish_E32(const double* __restrict__ G, int k, float* __restrict__ E32) {
+__global__ void k_polish_E32(const double* __restrict__ G, int k, float* __restrict__ E32, long long ld) {
   for (int i = blockIdx.x; i < k; i += gridDim.x)
     for (int j = threadIdx.x; j < k; j += blockDim.x)
-      E32[(size_t)i * k + j] = (float)(G[(size_t)i * k + j] - (i == j ? 1.0 : 0.0));
+      E32[(size_t)i * ld + j] = (float)(G[(size_t)i * k + j] - (i == j ? 1.0 : 0.0));
 }
 
 // C <- C - (P + P^T)/2 + (Q + Q^T)/8 with P = E C and Q = E C E: the same
-// symmetric result as M C M for M = I - E/2, and C32 = C.
+// symmetric result as M C M for M = I - E/2, and C32 = C (row stride k).
 __global__ void k_polish_apply(double* __restrict__ C, const float* __restrict__ P, const float* __restrict__ Q,
-                               int k, float* __restrict__ C32) {
+                               int k, long long ld, float* __restrict__ C32) {
   for (int i = blockIdx.x; i < k; i += gridDim.x)
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
-      const size_t ij = (size_t)i * k + j, ji = (size_t)j * k + i;
-      const double v = C[ij] - 0.5 * ((double)P[ij] + (double)P[ji]) + 0.125 * ((double)Q[ij] + (double)Q[ji]);
-      C[ij] = v;
-      C32[ij] = (float)v;
+      const size_t ij = (size_t)i * ld + j, ji = (size_t)j * ld + i;
+      const double v = C[(size_t)i * k + j] - 0.5 * ((double)P[ij] + (double)P[ji]) +
+                       0.125 * ((double)Q[ij] + (double)Q[ji]);
+      C[(size_t)i * k + j] = v;
+      C32[(size_t)i * k + j] = (float)v;
     }
 }
 }  // namespace
@@ -810,86 +827,97 @@ cudaError_t eig_select(const double* X, const double* lam, int k, int r, float l
 
 
 namespace {
-// D (k x k, row stride k) = A B^T for row-major A (row stride lda) and B in FP32.
-cudaError_t small_nt(const float* A, const float* B, float* D, int k, bool d_trans, cudaStream_t s,
-                     long long lda = 0) {
+// D (k x k) = A B^T for row-major FP32 A and B, all with row stride ld: FP32-
+// accurate tensor-core products (3xTF32) from k = 128 up, the SIMT kernel below.
+cudaError_t small_nt(const float* A, const float* B, float* D, int k, long long ld, bool d_trans, int* flags,
+                     cudaStream_t s) {
   GemmDesc<float> g = {};
   g.M = k; g.N = k; g.K = k; g.alpha = 1.0f; g.beta = 0.0f; g.zsplit = 1;
-  g.A = A; g.sam = lda > 0 ? lda : k; g.sak = 1;
-  g.B = B; g.sbn = k; g.sbk = 1;
-  g.D = D; g.ldd = k; g.d_trans = d_trans ? 1 : 0;
+  g.A = A; g.sam = ld; g.sak = 1;
+  g.B = B; g.sbn = ld; g.sbk = 1;
+  g.D = D; g.ldd = ld; g.d_trans = d_trans ? 1 : 0;
+  g.flags = flags;
+  if (k >= 128) return gemm_f32(g, KFAC_PREC_FP32, s);
   return gemm_small_f32(g, s);
 }
 int row_grid(int k) { return k < 1 ? 1 : (k > REF_MAX_BLOCKS ? REF_MAX_BLOCKS : k); }
+int elem_grid(long long n) { return (int)std::min<long long>(304, std::max<long long>(1, (n + 255) / 256)); }
 }  // namespace
 
 cudaError_t eig_refine_f32(const float* C32, long long ldc32, int k, double* X, double* lam, float* w32, double* part,
                            int* flags, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  const size_t kk = (size_t)k * k;
+  const long long ld = ref_ld(k);
+  const size_t kl = (size_t)k * ld;
   float* X32 = w32;
-  float* Xt = w32 + kk;
-  float* G = w32 + 2 * kk;
-  float* CXt = w32 + 3 * kk;
-  float* S = w32 + 4 * kk;
-  float* Et = w32 + 5 * kk;
-  float* XE = w32 + 6 * kk;
+  float* Xt = w32 + kl;
+  float* G = w32 + 2 * kl;
+  float* CXt = w32 + 3 * kl;
+  float* S = w32 + 4 * kl;
+  float* Et = w32 + 5 * kl;
+  float* XE = w32 + 6 * kl;
+  float* Cp = w32 + 7 * kl;  // C32 with the padded row stride
   const dim3 tg((k + 31) / 32, (k + 31) / 32);
-  k_split_f32_t<<<tg, dim3(32, 8), 0, s>>>(X, k, X32, Xt);
+  k_split_f32_t<<<tg, dim3(32, 8), 0, s>>>(X, k, X32, Xt, ld);
+  note_launch();
+  k_copy_f32<<<elem_grid((long long)k * k), 256, 0, s>>>(C32, ldc32, k, Cp, ld);
   note_launch();
   cudaError_t e;
-  if ((e = small_nt(Xt, Xt, G, k, false, s)) != cudaSuccess) return e;   // G = X^T X
-  if ((e = small_nt(C32, Xt, CXt, k, true, s, ldc32)) != cudaSuccess) return e; // (C X)^T
-  if ((e = small_nt(Xt, CXt, S, k, false, s)) != cudaSuccess) return e;  // S = X^T C X
+  if ((e = small_nt(Xt, Xt, G, k, ld, false, flags, s)) != cudaSuccess) return e;   // G = X^T X
+  if ((e = small_nt(Cp, Xt, CXt, k, ld, true, flags, s)) != cudaSuccess) return e;  // (C X)^T
+  if ((e = small_nt(Xt, CXt, S, k, ld, false, flags, s)) != cudaSuccess) return e;  // S = X^T C X
   const int nb = row_grid(k);
-  k_refine_norms32<<<nb, REF_THREADS, 0, s>>>(C32, ldc32, G, S, k, lam, part);
+  k_refine_norms32<<<nb, REF_THREADS, 0, s>>>(Cp, ld, G, S, k, ld, lam, part);
   note_launch();
-  k_refine_Et32<<<nb, REF_THREADS, 0, s>>>(G, S, k, lam, part, nb, Et, flags);
+  k_refine_Et32<<<nb, REF_THREADS, 0, s>>>(G, S, k, ld, lam, part, nb, Et, flags);
   note_launch();
-  if ((e = small_nt(X32, Et, XE, k, false, s)) != cudaSuccess) return e;  // X E
-  const int ag = (int)std::min<long long>(304, ((long long)kk + 255) / 256);
-  k_axpy_f64_f32<<<ag, 256, 0, s>>>(X, XE, (long long)kk, 1.0);
+  if ((e = small_nt(X32, Et, XE, k, ld, false, flags, s)) != cudaSuccess) return e;  // X E
+  k_axpy_f64_f32<<<elem_grid((long long)k * k), 256, 0, s>>>(X, XE, k, ld, 1.0);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t polish_projected_f32(const double* G, double* C, float* C32, int k, float* w32, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  const size_t kk = (size_t)k * k;
+  const long long ld = ref_ld(k);
+  const size_t kl = (size_t)k * ld;
   float* E = w32;  // kept for polish_vectors_f32
-  float* P = w32 + kk;
-  float* Q = w32 + 2 * kk;
+  float* P = w32 + kl;
+  float* Q = w32 + 2 * kl;
+  float* Cp = w32 + 3 * kl;
   const int nb = row_grid(k);
-  k_polish_E32<<<nb, 256, 0, s>>>(G, k, E);
+  k_polish_E32<<<nb, 256, 0, s>>>(G, k, E, ld);
+  note_launch();
+  k_copy_f32<<<elem_grid((long long)k * k), 256, 0, s>>>(C32, k, k, Cp, ld);
   note_launch();
   cudaError_t e;
-  if ((e = small_nt(E, C32, P, k, false, s)) != cudaSuccess) return e;  // P = E C (C symmetric)
-  if ((e = small_nt(P, E, Q, k, false, s)) != cudaSuccess) return e;    // Q = P E (E symmetric)
-  k_polish_apply<<<nb, 256, 0, s>>>(C, P, Q, k, C32);
+  if ((e = small_nt(E, Cp, P, k, ld, false, nullptr, s)) != cudaSuccess) return e;  // P = E C (C symmetric)
+  if ((e = small_nt(P, E, Q, k, ld, false, nullptr, s)) != cudaSuccess) return e;   // Q = P E (E symmetric)
+  k_polish_apply<<<nb, 256, 0, s>>>(C, P, Q, k, ld, C32);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t polish_E_f32(const double* G, int k, float* w32, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  k_polish_E32<<<row_grid(k), 256, 0, s>>>(G, k, w32);
+  k_polish_E32<<<row_grid(k), 256, 0, s>>>(G, k, w32, ref_ld(k));
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t polish_vectors_f32(double* X, int k, float* w32, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  const size_t kk = (size_t)k * k;
+  const long long ld = ref_ld(k);
+  const size_t kl = (size_t)k * ld;
   const float* E = w32;
-  float* Xt = w32 + kk;
-  float* EX = w32 + 2 * kk;
+  float* Xt = w32 + kl;
+  float* EX = w32 + 2 * kl;
   const dim3 tg((k + 31) / 32, (k + 31) / 32);
-  k_split_f32_t<<<tg, dim3(32, 8), 0, s>>>(X, k, nullptr, Xt);
+  k_split_f32_t<<<tg, dim3(32, 8), 0, s>>>(X, k, nullptr, Xt, ld);
   note_launch();
   cudaError_t e;
-  if ((e = small_nt(E, Xt, EX, k, false, s)) != cudaSuccess) return e;  // E X
-  const int ag = (int)std::min<long long>(304, ((long long)kk + 255) / 256);
-  k_axpy_f64_f32<<<ag, 256, 0, s>>>(X, EX, (long long)kk, -0.5);
+  if ((e = small_nt(E, Xt, EX, k, ld, false, nullptr, s)) != cudaSuccess) return e;  // E X
+  k_axpy_f64_f32<<<elem_grid((long long)k * k), 256, 0, s>>>(X, EX, k, ld, -0.5);
   note_launch();
   return cudaGetLastError();
 }
