@@ -317,7 +317,11 @@ def stage_roofline(stage: str, ms: float, launches: int, spec: dict, prec: str, 
 
 class DeviceWorkload:
     """Tensors of one workload on the device: factors (EA-consistent synthetic
-    spectra), EA batches, test matrices, gradients and every output buffer."""
+    spectra), EA batches, test matrices, gradients and every output buffer.
+    The per-step inputs and outputs (EA batches, test matrices, gradients,
+    preconditioned gradients) come in nb sets, so that the end-to-end
+    measurement can copy one step's inputs in while another step computes; the
+    factors and the inverses are the optimiser's state and exist once."""
 
     def __init__(self, spec: dict, dev, nb: int = 2):
         import torch
@@ -359,7 +363,18 @@ class DeviceWorkload:
             J.copy_(spec["j_std"] * torch.randn(dg, da, generator=gen, device=dev))
             self.J.append(J)
             self.S.append(self.padded(dg, da))
+        # the input/output sets: set 0 is the lists above, the others copies
+        self.Om_b, self.J_b, self.S_b = [self.Om], [self.J], [self.S]
+        for _ in range(1, nb):
+            self.Om_b.append([o.clone() if o is not None else None for o in self.Om])
+            self.J_b.append([self.copy_padded(j) for j in self.J])
+            self.S_b.append([self.padded(*t.shape) for t in self.S])
         torch.cuda.synchronize(dev)
+
+    def copy_padded(self, t):
+        c = self.padded(*t.shape)
+        c.copy_(t)
+        return c
 
     def padded(self, rows, cols):
         """rows x cols view of a rows x round_up(cols, 4) tensor (16-byte row stride)."""
@@ -367,23 +382,26 @@ class DeviceWorkload:
         return torch.empty((rows, (cols + 3) // 4 * 4), device=self.dev)[:, :cols]
 
     def descriptors(self, kfac, prec: str):
+        """Descriptor arrays of every input/output set b: (ea[b], inv[b], pre[b])."""
         spec = self.spec
         ea = [kfac.ea_descs([dict(X=self.X[i][b], F=self.F[i], rho=spec["rho"], prec=prec)
                              for i in range(len(self.F))]) for b in range(self.nb)]
-        inv, _ = kfac.invert_descs([dict(F=self.F[i], rank=f["r"], oversample=spec["p"], power_iters=spec["q"],
-                                         lam=spec["lam"], omega=self.Om[i], prec=prec, out=self.out[i])
-                                    for i, f in enumerate(spec["factors"])])
-        pre, _ = kfac.precond_descs([dict(J=self.J[li], U_a=self.out[a][0], coef_a=self.out[a][2],
-                                          U_g=self.out[g][0], coef_g=self.out[g][2], lam=spec["lam"], prec=prec,
-                                          out=self.S[li]) for li, (a, g) in enumerate(spec["layers"])])
+        inv = [kfac.invert_descs([dict(F=self.F[i], rank=f["r"], oversample=spec["p"], power_iters=spec["q"],
+                                       lam=spec["lam"], omega=self.Om_b[b][i], prec=prec, out=self.out[i])
+                                  for i, f in enumerate(spec["factors"])])[0] for b in range(self.nb)]
+        pre = [kfac.precond_descs([dict(J=self.J_b[b][li], U_a=self.out[a][0], coef_a=self.out[a][2],
+                                        U_g=self.out[g][0], coef_g=self.out[g][2], lam=spec["lam"], prec=prec,
+                                        out=self.S_b[b][li]) for li, (a, g) in enumerate(spec["layers"])])[0]
+               for b in range(self.nb)]
         return ea, inv, pre
 
 
 def run_step(kfac, ctx, descs, b):
+    """One step on input/output set b."""
     ea, inv, pre = descs
     kfac.call_grouped(ctx, "ea", ea[b])
-    kfac.call_grouped(ctx, "invert", inv)
-    kfac.call_grouped(ctx, "precondition", pre)
+    kfac.call_grouped(ctx, "invert", inv[b])
+    kfac.call_grouped(ctx, "precondition", pre[b])
 
 
 def capture_graphs(kfac, ctx, wl, descs, stream):
@@ -425,8 +443,8 @@ def profile_stages(kfac, ctx, descs, stream, steps, streams):
         kfac.kfac_stats_read(ctx)
         kfac.kfac_profile_enable(ctx, True)
         n_simt = kfac.kfac_simt_gemm_count()
-        for i in range(steps):
-            run_step(kfac, ctx, descs, i % len(descs[0]))
+        for i in range(steps):   # the last step uses set 0 (the error checks read set 0)
+            run_step(kfac, ctx, descs, (steps - 1 - i) % len(descs[0]))
         prof = kfac.kfac_profile_read(ctx)
         kfac.kfac_profile_enable(ctx, False)
         kfac.kfac_set_option(ctx, "group_streams", streams)
@@ -508,8 +526,8 @@ def phase_times(kfac, ctx, descs, stream, reps=5):
     ea, inv, pre = descs
     out = {}
     for name, fn in (("ea", lambda: kfac.call_grouped(ctx, "ea", ea[0])),
-                     ("invert", lambda: kfac.call_grouped(ctx, "invert", inv)),
-                     ("apply", lambda: kfac.call_grouped(ctx, "precondition", pre))):
+                     ("invert", lambda: kfac.call_grouped(ctx, "invert", inv[0])),
+                     ("apply", lambda: kfac.call_grouped(ctx, "precondition", pre[0]))):
         with torch.cuda.stream(stream):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
@@ -527,36 +545,63 @@ def phase_times(kfac, ctx, descs, stream, reps=5):
 
 
 def e2e_measure(kfac, ctx, wl, graphs, stream, steps):
-    """The captured step end to end with host buffers: per step, pinned H2D of
-    every factor's EA batch and test matrix and every layer's gradient, the
-    graph replay, and D2H of every preconditioned gradient."""
+    """The captured step end to end with host buffers, pipelined over the
+    workload's input/output sets: step i (set b = i % nb) copies its inputs
+    from pinned host memory (every factor's EA batch and test matrix, every
+    layer's gradient) on a copy stream, replays its graph on the compute stream
+    once they have landed, and copies its preconditioned gradients back on a
+    second copy stream. Step i's input copy waits only for step i - nb's
+    compute (the set's previous user), so copies overlap other steps' compute;
+    every byte of every step is inside the timed region. Returns (ms per step,
+    H2D bytes per step, D2H bytes per step)."""
     import torch
     base = lambda t: t._base if t._base is not None else t
-    dev_in = [base(wl.X[i][0]) for i in range(len(wl.F))] + [o for o in wl.Om if o is not None] + \
-             [base(j) for j in wl.J]
-    dev_out = [base(s) for s in wl.S]
-    host_in = [t.cpu().pin_memory() for t in dev_in]
-    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in dev_out]
-    h2d = sum(t.numel() * 4 for t in host_in)
-    d2h = sum(t.numel() * 4 for t in host_out)
+    nb = len(graphs)
+    dev_in = [[base(wl.X[i][b]) for i in range(len(wl.F))] + [o for o in wl.Om_b[b] if o is not None] +
+              [base(j) for j in wl.J_b[b]] for b in range(nb)]
+    dev_out = [[base(s_) for s_ in wl.S_b[b]] for b in range(nb)]
+    host_in = [[t.cpu().pin_memory() for t in dev_in[0]] for _ in range(nb)]
+    host_out = [[torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in dev_out[0]] for _ in range(nb)]
+    h2d = sum(t.numel() * 4 for t in host_in[0])
+    d2h = sum(t.numel() * 4 for t in host_out[0])
+    hs, ds = torch.cuda.Stream(stream.device), torch.cuda.Stream(stream.device)
+    ev = lambda: torch.cuda.Event()
+    comp_done = [ev() for _ in range(nb)]
+    out_done = [ev() for _ in range(nb)]
 
-    def one():
-        for h, d in zip(host_in, dev_in):
-            d.copy_(h, non_blocking=True)
-        graphs[0].replay()
-        for d, h in zip(dev_out, host_out):
-            h.copy_(d, non_blocking=True)
+    def run(n):
+        in_done = [ev() for _ in range(nb)]
+        for i in range(n):
+            b = i % nb
+            with torch.cuda.stream(hs):
+                if i >= nb:
+                    hs.wait_event(comp_done[b])      # the set's previous step has read its inputs
+                for h, d in zip(host_in[b], dev_in[b]):
+                    d.copy_(h, non_blocking=True)
+                in_done[b].record(hs)
+            stream.wait_event(in_done[b])
+            if i >= nb:
+                stream.wait_event(out_done[b])       # the set's previous outputs have been read back
+            with torch.cuda.stream(stream):
+                graphs[b].replay()
+                comp_done[b].record(stream)
+            with torch.cuda.stream(ds):
+                ds.wait_event(comp_done[b])
+                for d, h in zip(dev_out[b], host_out[b]):
+                    h.copy_(d, non_blocking=True)
+                out_done[b].record(ds)
+        stream.wait_stream(hs)
+        stream.wait_stream(ds)
 
-    with torch.cuda.stream(stream):
-        for _ in range(2):
-            one()
-        stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            one()
-        e1.record(stream)
-        e1.synchronize()
+    run(nb)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hs.wait_stream(stream)
+    ds.wait_stream(stream)
+    run(steps)
+    e1.record(stream)
+    e1.synchronize()
     return e0.elapsed_time(e1) / steps, h2d, d2h
 
 
@@ -734,7 +779,7 @@ def bench_workload(kfac, ctx, wl, stream, prec, steps, warmup, streams, clocks=N
     if tune:  # the library's autotuner picks the grouped inversion's schedule (outside the timed region)
         with torch.cuda.stream(stream):
             t0 = time.perf_counter()
-            tuned = kfac.kfac_autotune_invert(ctx, descs[1])
+            tuned = kfac.kfac_autotune_invert(ctx, descs[1][0])
             tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
         streams = tuned["group_streams"]
         log(f"autotuned schedule: {tuned}")
@@ -824,7 +869,9 @@ def main(argv=None):
                              "l2": "no flush: %.1f GB of factors, batches, gradients and outputs per step (L2 129 MB)"
                                    % (bytes_touched(spec) / 1e9),
                              "parallelism": "replicas" if world > 1 else "single GPU"},
-                  "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                  "e2e": {"value": e2e_ms, "unit": "ms/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                          "pipeline": "two input/output sets: a step's pinned H2D copies and D2H read-back run on "
+                                      "copy streams beside the neighbouring steps' compute"},
                   "gpu_launches": res["launches"] * args.steps, "clocks": res["clocks"],
                   "status": {"code": st, "flags": flags},
                   "stage_ms_per_step": {k: round(v[0], 4) for k, v in sorted(stages.items())},
@@ -850,6 +897,9 @@ def main(argv=None):
     # ---- full-EVD comparator on the same GPU, accuracy at equal rank -------------
     if rank == 0 and not args.no_evd:
         log("full-EVD comparator")
+        with torch.cuda.stream(stream):   # S of set 0 from the current factors (the checks read set 0)
+            run_step(kfac, ctx, res["descs"], 0)
+            stream.synchronize()
         cmp_ = evd_comparison(kfac, ctx, wl, stream, args.prec, 3)
         ea_ms = result["stage_ms_per_step"].get("ea_syrk", 0.0)
         cmp_["ms_per_step"] = cmp_["ms_per_step_excl_ea"] + ea_ms
