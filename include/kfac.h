@@ -388,7 +388,10 @@ typedef enum {
                                        one-CTA factorisations of diagonal blocks of at most 236,
                                        triangular solves and tensor-core (3xTF32) rank updates
                                        between them; 0 = on one thread-block cluster
-                                       (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL) */
+                                       (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL). With 1 the
+                                       CholeskyQR solves Q^T = L^-1 Y^T of order above 288 are
+                                       blocked the same way (the off-diagonal work as
+                                       tensor-core products) */
   KFAC_OPT_CHOL_PANEL = 18,         /* [16]: panel width of the multi-CTA Cholesky, 16 or 32
                                        (halved while its shared memory overflows); wider panels
                                        take half the cluster barriers and broadcasts */

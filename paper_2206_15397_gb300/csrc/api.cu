@@ -165,7 +165,7 @@ struct StageScope {
 
 struct InvertLayout {
   size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, flo, xlo, xlo2,
-      cb, total;
+      cb, tb, total;
   long long dp, kp, dpb, skws_floats;
   int nsplit, kchunk;
   bool pack_f, bf16, tails;
@@ -212,6 +212,7 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
   L.g32 = b.take<float>((size_t)k * k);
   L.l32 = b.take<float>((size_t)k * k);
   L.cb = b.take<char>(chol_blocked_ws_bytes(k));
+  L.tb = b.take<char>(trsm_blocked_ws_bytes(k, d));
   L.dinv = b.take<float>(trsm_ws_floats(k));
   L.c = b.take<double>((size_t)k * k);
   L.c32 = b.take<float>((size_t)k * k);
@@ -326,7 +327,11 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
     }
     {
       STAGE(ctx, ST_TRSM);
-      CK(trsm_lower_f32(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<float>(ctx, L.dinv), ctx->stream));
+      if (ctx->chol_blocked && trsm_blocked_used(k))
+        CK(trsm_blocked(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<char>(ctx, L.tb), ctx->dflags,
+                        ctx->wait_cycles, ctx->stream));
+      else
+        CK(trsm_lower_f32(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<float>(ctx, L.dinv), ctx->stream));
     }
     std::swap(cur, other);
   }
@@ -455,7 +460,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const float* F = a.F;
   int ldf = a.ldf;
   for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
-                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2, &L.cb})
+                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2, &L.cb, &L.tb})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;

@@ -1130,4 +1130,83 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Blocked triangular solve Qt = L^-1 Yt for k above the shared-memory solve's
+// range, over the diagonal blocks of the blocked Cholesky (at most CTA_KMAX
+// rows, multiples of 4). Block row I: the residual R_I = Y_I - L_I,<I X_<I is
+// one FP32-accurate tensor-core product (A = L's rows of block I with a padded
+// stride, B = the solved rows so far, kept transposed in XT: d x k), then
+// X_I = L_II^-1 R_I by the shared-memory solve, then X_I is transposed into XT.
+namespace {
+struct TbLayout {
+  size_t Lp, Lbb, dinv, XT, R, total;
+  int kb;
+  long long kp, ldr;
+};
+
+TbLayout tb_layout(int k, int d) {
+  TbLayout t = {};
+  const CbLayout c = cb_layout(k);
+  t.kb = c.kb;
+  t.kp = c.kp;
+  t.ldr = (d + 3) / 4 * 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = (off + 255) & ~size_t(255);
+    off = o + bytes;
+    return o;
+  };
+  t.Lp = take(sizeof(float) * (size_t)k * t.kp);
+  t.Lbb = take(sizeof(float) * (size_t)t.kb * t.kb);
+  t.dinv = take(sizeof(float) * trsm_ws_floats(t.kb));
+  t.XT = take(sizeof(float) * (size_t)d * t.kp);
+  t.R = take(sizeof(float) * (size_t)t.kb * t.ldr);
+  t.total = off;
+  return t;
+}
+}  // namespace
+
+bool trsm_blocked_used(int k) { return k > TS_MAXT * TR_RB; }
+
+size_t trsm_blocked_ws_bytes(int k, int d) { return trsm_blocked_used(k) ? tb_layout(k, d).total : 0; }
+
+cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
+                         void* ws, int* flags, long long wait_cycles, cudaStream_t s) {
+  if (k <= 0 || d <= 0) return cudaSuccess;
+  const TbLayout t = tb_layout(k, d);
+  char* base = static_cast<char*>(ws);
+  float* Lp = reinterpret_cast<float*>(base + t.Lp);
+  float* Lbb = reinterpret_cast<float*>(base + t.Lbb);
+  float* dinv = reinterpret_cast<float*>(base + t.dinv);
+  float* XT = reinterpret_cast<float*>(base + t.XT);
+  float* R = reinterpret_cast<float*>(base + t.R);
+  k_cb_place<<<grid_for((long long)k * k), 256, 0, s>>>(L, k, k, k, Lp, t.kp);
+  note_launch();
+  cudaError_t e;
+  for (int o = 0; o < k; o += t.kb) {
+    const int kb = std::min(t.kb, k - o);
+    const float* src = Yt + (size_t)o * ldy;
+    long long lds = ldy;
+    if (o > 0) {  // R = Y_I - L_I,<I X_<I
+      GemmDesc<float> g = {};
+      g.M = kb; g.N = d; g.K = o;
+      g.A = Lp + (size_t)o * t.kp; g.sam = t.kp; g.sak = 1;
+      g.B = XT; g.sbn = t.kp; g.sbk = 1;
+      g.D = R; g.ldd = t.ldr;
+      g.C0 = Yt + (size_t)o * ldy; g.ldc = ldy;
+      g.alpha = -1.0f; g.beta = 1.0f; g.zsplit = 1;
+      g.flags = flags; g.wait_cycles = wait_cycles;
+      if ((e = gemm_f32(g, KFAC_PREC_FP32, s)) != cudaSuccess) return e;
+      src = R;
+      lds = t.ldr;
+    }
+    k_cb_place<<<grid_for((long long)kb * kb), 256, 0, s>>>(Lp + (size_t)o * t.kp + o, t.kp, kb, kb, Lbb, kb);
+    note_launch();
+    if ((e = trsm_lower_f32(Lbb, kb, src, lds, Qt + (size_t)o * ldq, ldq, d, dinv, s)) != cudaSuccess) return e;
+    if (o + kb < k && (e = transpose_f32(Qt + (size_t)o * ldq, ldq, kb, d, XT + o, t.kp, s)) != cudaSuccess)
+      return e;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace kfac

@@ -191,6 +191,14 @@ inline size_t trsm_ws_floats(int k) {
 }
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
                            float* dinv_ws, cudaStream_t s);
+// The same solve blocked over the blocked Cholesky's diagonal blocks, the
+// off-diagonal work as FP32-accurate tensor-core products (for k above the
+// shared-memory solve's range: trsm_blocked_used(k)). ws: trsm_blocked_ws_bytes
+// (k, d) bytes of device workspace; Yt and Qt must not overlap.
+bool trsm_blocked_used(int k);
+size_t trsm_blocked_ws_bytes(int k, int d);
+cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
+                         void* ws, int* flags, long long wait_cycles, cudaStream_t s);
 
 // FP32 one-sided Jacobi on chol(C + s I) over a thread-block cluster: writes X
 // (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:
