@@ -1,6 +1,6 @@
 """Small single-call cases of the hot path for kernel profilers.
 
-    python -m paper_2206_15397_gb300.profile_cases <case>
+    python -m paper_2206_15397_gb300.profile_cases <case> [--chol-cluster]
 
 Each case builds its inputs on the device with torch (seeded), makes a few
 library calls and checks that the library reported no error, so that a
@@ -16,6 +16,9 @@ footprint (well under 1 GB):
   ea_apply  the EA update of a 4096 x 4096 factor from a 4096 x 256 batch,
             then the damped Kronecker apply (Eq. 13 on both sides) of a
             4096 x 4097 gradient with r = 220 bases.
+
+--chol-cluster factors orders above 236 on the thread-block cluster (and
+solves them with the tiled kernel) instead of the blocked forms.
 
 The factors are F = V diag(i^-2 alpha) V^T with V the Q factor of a Gaussian
 matrix with min(d, m) columns (the fast-decaying spectra of Sec. 3)."""
@@ -34,12 +37,14 @@ def _spectral(g, dev, d, alpha, m=640):
     return ((v * lam) @ v.T).float().contiguous()
 
 
-def run(case: str) -> None:
+def run(case: str, chol_cluster: bool = False) -> None:
     build.build()
     dev = torch.device("cuda", 0)
     g = torch.Generator(device=dev)
     g.manual_seed(0)
     ctx = kfac.Context(0)
+    if chol_cluster:
+        kfac.kfac_set_option(ctx, "chol_blocked", 0)
     if case == "big_k":
         F = _spectral(g, dev, 2048, 1.0)
         om = torch.randn(2048, 522, generator=g, device=dev)
@@ -69,4 +74,5 @@ def run(case: str) -> None:
 
 
 if __name__ == "__main__":
-    run(sys.argv[1] if len(sys.argv) > 1 else "big_k")
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    run(args[0] if args else "big_k", chol_cluster="--chol-cluster" in sys.argv[1:])
