@@ -199,9 +199,15 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
     return L;
   }
   L.dp = round_up(d, 4);
-  // Grams (k x k, K = d): ~128-deep K-chunks so that the few output tiles
-  // still spread over most SMs (the pipeline of one CTA is then short).
-  L.nsplit = (int)std::min<long long>(32, std::max<long long>(1, d / 128));
+  // Grams (k x k, K = d): symmetric ones are computed on the upper tiles only
+  // (t (t + 1) / 2 of 128 x 128, t = ceil(k / 128)); K is split so that about
+  // one CTA per SM works on a Gram, each over at least 256 of K (a CTA's
+  // pipeline fill and epilogue then stay small against its main loop).
+  {
+    const long long t = (k + 127) / 128, tiles = t * (t + 1) / 2;
+    const long long cap = std::max<long long>(1, std::min<long long>(32, d / 256));
+    L.nsplit = (int)std::min<long long>(cap, std::max<long long>(1, (152 + tiles / 2) / tiles));
+  }
   L.kchunk = (int)round_up((d + L.nsplit - 1) / L.nsplit, 64);
   L.nsplit = (d + L.kchunk - 1) / L.kchunk;
   L.om = b.take<float>((size_t)k * L.dp);
@@ -253,6 +259,9 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.D = at<float>(ctx, L.part); g.ldd = k;
   g.alpha = 1.0f;
   g.zsplit = L.nsplit; g.kchunk = L.kchunk; g.zstride = (long long)k * k;
+  // A A^T: only the tiles at and above the diagonal, the reduce mirrors them
+  const bool upper = A == Bm && symmetrize == 1;
+  g.sym = upper ? 1 : 0;
   g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   StageScope sc(ctx, stage);
   if (L.tails && prec == KFAC_PREC_FP32) {
@@ -262,8 +271,8 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
     g.B_lo = at<float>(ctx, Bm != A ? L.xlo2 : L.xlo); g.ld_blo = L.dp;
   }
   CK(gemm_f32(g, prec, ctx->stream));
-  CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, symmetrize, ctx->dflags,
-                       ctx->stream, out32));
+  CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, upper ? 2 : symmetrize,
+                       ctx->dflags, ctx->stream, out32));
   return KFAC_OK;
 }
 

@@ -123,8 +123,9 @@ cudaError_t set_kernel_attrs_once(const void* fn, int max_dyn_smem, bool nonport
 
 // FP32 product with 16 x 16 output tiles (plain FP32 FMA), for k x k matrices.
 cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s);
-// out[i, j] = sum_z part[z][i, j] in FP64 (n x n), optionally symmetrised as
-// (S + S^T) / 2. part has row stride ldp and z stride zstride.
+// out[i, j] = sum_z part[z][i, j] in FP64 (n x n), symmetrised as (S + S^T) / 2
+// with symmetrize = 1, or (symmetrize = 2) from partials that hold only the
+// upper triangle i <= j, mirrored. part has row stride ldp and z stride zstride.
 // out32 (optional): an FP32 copy of the result, n x n dense.
 cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out,
                               int ldo, int symmetrize, int* flags, cudaStream_t s, float* out32 = nullptr);

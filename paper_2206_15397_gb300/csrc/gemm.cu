@@ -44,7 +44,7 @@ cudaError_t gemm_f32(const GemmDesc<float>& g, kfac_precision prec, cudaStream_t
     return cudaErrorInvalidValue;
   const bool tc_ok = bf16d || (kmajor && g.K > 0 &&
                      tc::eligible(g.A, g.sam, g.B, g.sbn, g.M, g.N, g.K) &&
-                     (g.zsplit <= 1 || g.kchunk % kalign == 0) && !(g.sym && g.zsplit > 1));
+                     (g.zsplit <= 1 || g.kchunk % kalign == 0));
   if (!tc_ok) {
     if (g.K > 0) note_simt_gemm();
     return gemm_simt_f32(g, round_of(prec), s);

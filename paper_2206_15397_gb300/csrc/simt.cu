@@ -217,10 +217,14 @@ __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // n * n < 2^31
   if (idx >= n * n) return;
   const int i = idx / n, j = idx - i * n;
-  const double s = sum_partials(part + (long long)i * ldp + j, nsplit, zstride);
+  // symmetrize == 2: the partials hold the upper triangle only (a symmetric
+  // product computed on the tiles at and above the diagonal); both halves of
+  // the result read it, so the sum is exactly symmetric.
+  const int a = symmetrize == 2 ? min(i, j) : i, b = symmetrize == 2 ? max(i, j) : j;
+  const double s = sum_partials(part + (long long)a * ldp + b, nsplit, zstride);
   if (!isfinite(s)) raise_flag(flags, KFAC_FLAG_NONFINITE);
   out[(long long)i * ldo + j] = s;
-  if (out32 && !symmetrize) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
+  if (out32 && symmetrize != 1) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
 }
 
 // out <- (out + out^T) / 2 in place, one thread per pair i <= j (the summed
@@ -414,7 +418,7 @@ cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, 
   k_reduce_splitk<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, zstride, n, ldp, out, ldo, symmetrize,
                                                                   out32, flags);
   note_launch();
-  if (symmetrize) {
+  if (symmetrize == 1) {
     k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(out, n, ldo, out32);
     note_launch();
   }

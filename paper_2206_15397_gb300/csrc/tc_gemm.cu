@@ -300,7 +300,7 @@ __device__ __forceinline__ void store_chunk(const TcArgs& p, float (&v)[32], int
       const int mr = mrow0 + r, n = nb + lane;
       if (mr < p.M && n < nend && (!p.sym || mr <= n)) Dz[(long long)mr * p.ldd + n] = stage_tile[r * 33 + lane];
     }
-    if (p.sym) {  // mirror: D[n][m] for m < n, consecutive lanes -> consecutive m
+    if (p.sym && !p.partial) {  // mirror: D[n][m] for m < n (raw split-K partials keep the upper triangle only)
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int n = nb + j;
