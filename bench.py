@@ -393,15 +393,21 @@ class DeviceWorkload:
                                         U_g=self.out[g][0], coef_g=self.out[g][2], lam=spec["lam"], prec=prec,
                                         out=self.S_b[b][li]) for li, (a, g) in enumerate(spec["layers"])])[0]
                for b in range(self.nb)]
-        return ea, inv, pre
+        return ea, inv, pre, kfac.step_descs(spec["layers"])
+
+
+FUSED = {"on": False}   # kfac_step_grouped (per-item dependencies) or the three grouped calls in turn
 
 
 def run_step(kfac, ctx, descs, b):
     """One step on input/output set b."""
-    ea, inv, pre = descs
-    kfac.call_grouped(ctx, "ea", ea[b])
-    kfac.call_grouped(ctx, "invert", inv[b])
-    kfac.call_grouped(ctx, "precondition", pre[b])
+    ea, inv, pre, lf = descs
+    if FUSED["on"]:
+        kfac.kfac_step_grouped(ctx, ea[b], inv[b], pre[b], lf)
+    else:
+        kfac.call_grouped(ctx, "ea", ea[b])
+        kfac.call_grouped(ctx, "invert", inv[b])
+        kfac.call_grouped(ctx, "precondition", pre[b])
 
 
 def capture_graphs(kfac, ctx, wl, descs, stream):
@@ -523,7 +529,7 @@ def phase_times(kfac, ctx, descs, stream, reps=5):
     """Device ms of the step's three phases, each captured in a graph of its own
     and replayed: the grouped EA update, the grouped inversion, the grouped apply."""
     import torch
-    ea, inv, pre = descs
+    ea, inv, pre, _ = descs
     out = {}
     for name, fn in (("ea", lambda: kfac.call_grouped(ctx, "ea", ea[0])),
                      ("invert", lambda: kfac.call_grouped(ctx, "invert", inv[0])),
@@ -815,7 +821,10 @@ def main(argv=None):
     ap.add_argument("--streams", type=int, default=16, help="streams a grouped call forks (1..32)")
     ap.add_argument("--profile-steps", type=int, default=3, help="eager steps of the per-stage pass (0: none)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (no autotuner)")
+    ap.add_argument("--fused", action="store_true",
+                    help="kfac_step_grouped (per-item dependencies) instead of the three grouped calls in turn")
     args = ap.parse_args(argv)
+    FUSED["on"] = args.fused
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:
@@ -862,7 +871,9 @@ def main(argv=None):
                   "data": "synthetic (seeded device draws: orthonormal directions, power-law spectra, Gaussian "
                           "batches, gradients and test matrices)",
                   "config": {"workload": spec["workload"], "steps_per_layer": 1, "precision": args.prec,
-                             "graph": "one CUDA graph per step (grouped EA, inversion on forked streams, apply)",
+                             "graph": ("one CUDA graph per step: kfac_step_grouped (per factor EA then inversion on "
+                                       "forked streams, each layer's apply after its two factors)" if FUSED["on"] else
+                                       "one CUDA graph per step (grouped EA, grouped inversion, grouped apply)"),
                              "streams": (res["tuned"] or {}).get("group_streams", args.streams),
                              "autotuned": res["tuned"],
                              "layout": "row strides rounded up to 16 bytes",

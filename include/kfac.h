@@ -250,6 +250,26 @@ typedef struct {
  * call has sized the workspace). All descriptors are checked first. */
 KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const kfac_precond_desc* descs);
 
+/* One K-FAC step of a set of layers (Alg. 1: the EA updates of the factors,
+ * their inversions by Alg. 3 or Alg. 2, and Alg. 4's apply for every layer),
+ * with per-item dependencies instead of a join between the phases. Factor f
+ * (0 <= f < n_factors) takes ea[f] (skipped when ea is NULL) and then the
+ * inversion inv[f], in turn, on one of up to KFAC_OPT_GROUP_STREAMS streams
+ * forked from the context stream (the costliest factors first, each on the
+ * least-loaded stream). Layer l (0 <= l < n_layers) takes the apply pre[l] as
+ * soon as the inversions of factors layer_factors[2l] and layer_factors[2l+1]
+ * (-1: none) have finished, on the stream of the later of the two, so the
+ * applies of early layers overlap the inversions still running. pre[l]'s U and
+ * coefficient pointers should be those inversions' outputs; the call orders
+ * the work, it does not check that. The results are those of
+ * kfac_ea_update_grouped + kfac_rsvd_invert_grouped + kfac_precondition_grouped
+ * on the same descriptors. All descriptors are checked before anything is
+ * enqueued; per-item flags (kfac_get_item_status) are factors 0..n_factors-1
+ * then layers. Graph-capturable once an earlier call has sized the workspace. */
+KFAC_API kfac_status kfac_step_grouped(kfac_ctx* ctx, int n_factors, const kfac_ea_desc* ea,
+                                       const kfac_invert_desc* inv, int n_layers, const kfac_precond_desc* pre,
+                                       const int* layer_factors);
+
 /* Allocation-free variant of kfac_precondition (the paper has no counterpart:
  * this is a deployment interface). It is for callers that cannot allocate GPU
  * memory at call time: code that runs while a CUDA graph is being captured,
@@ -292,7 +312,8 @@ KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, c
  * products may fill (KFAC_OPT_SPLIT_TARGET) and, when a sketch width exceeds
  * the one-CTA Cholesky's 236, the large-order Cholesky: blocked or on a
  * cluster (KFAC_OPT_CHOL_BLOCKED) and, for the cluster kernel, its size and
- * panel width (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL). Runs
+ * panel width (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL); and the form of the
+ * CholeskyQR solves (KFAC_OPT_TRSM_INVERSE). Runs
  * kfac_rsvd_invert_grouped(ctx, count, descs) once plus twice timed (CUDA
  * events on the context stream) per candidate of a coordinate descent from the
  * current settings, writing the descriptors' outputs as a call would, and
@@ -300,9 +321,9 @@ KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, c
  * file of earlier results, one line per device name and shape signature (the
  * factors' d, k, power iterations and precision, and the inversion method); a
  * hit is applied without timing, a new result is appended. chosen (may be
- * NULL, 6 ints) receives the streams, cluster size, split target, panel width,
- * blocked flag and 1 if the result came from the cache. Not during stream
- * capture (it synchronises). */
+ * NULL, 7 ints) receives the streams, cluster size, split target, panel width,
+ * blocked flag, solve form and 1 if the result came from the cache. Not during
+ * stream capture (it synchronises). */
 KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_invert_desc* descs,
                                           const char* cache_path, int* chosen);
 
@@ -392,6 +413,12 @@ typedef enum {
                                        CholeskyQR solves Q^T = L^-1 Y^T of order above 288 are
                                        blocked the same way (the off-diagonal work as
                                        tensor-core products) */
+  KFAC_OPT_TRSM_INVERSE = 21,       /* [1]: the CholeskyQR solves Q^T = L^-1 Y^T (Alg. 3's QR
+                                       step) form L^-1 once by solving the k x k identity, then
+                                       Q^T as one FP32-accurate tensor-core product with the
+                                       transposed basis (2 k^2 d flops on the tensor cores);
+                                       0 = block substitution on the SIMT pipes (shared-memory
+                                       solve, blocked above order 288) */
   KFAC_OPT_CHOL_PANEL = 18,         /* [16]: panel width of the multi-CTA Cholesky, 16 or 32
                                        (halved while its shared memory overflows); wider panels
                                        take half the cluster barriers and broadcasts */

@@ -45,6 +45,7 @@ struct kfac_ctx {
   cudaStream_t side[kMaxSideStreams] = {};  // forked streams for grouped calls
   cudaEvent_t join_ev[kMaxSideStreams] = {};
   cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> item_ev;  // kfac_step_grouped: one per factor (its inversion done)
   int device = 0;
   cudaStream_t stream = nullptr;
   void* ws = nullptr;
@@ -76,6 +77,7 @@ struct kfac_ctx {
   long long conv_chunk = 32LL << 20;  // KFAC_OPT_CONV_CHUNK: floats of one patch-matrix chunk
   int tail_planes = 1;                // KFAC_OPT_TAIL_PLANES: precomputed 3xTF32 tails of the large operands
   int chol_blocked = 1;               // KFAC_OPT_CHOL_BLOCKED: blocked FP32 Cholesky above the one-CTA limit
+  int trsm_inverse = 1;               // KFAC_OPT_TRSM_INVERSE: CholeskyQR solves through L^-1 and one product
 };
 
 namespace {
@@ -165,7 +167,7 @@ struct StageScope {
 
 struct InvertLayout {
   size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, flo, xlo, xlo2,
-      cb, tb, total;
+      cb, tb, ti, total;
   long long dp, kp, dpb, skws_floats;
   int nsplit, kchunk;
   bool pack_f, bf16, tails;
@@ -219,6 +221,7 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
   L.l32 = b.take<float>((size_t)k * k);
   L.cb = b.take<char>(chol_blocked_ws_bytes(k));
   L.tb = b.take<char>(trsm_blocked_ws_bytes(k, d));
+  L.ti = b.take<char>(trsm_inverse_ws_bytes(k, d));
   L.dinv = b.take<float>(trsm_ws_floats(k));
   L.c = b.take<double>((size_t)k * k);
   L.c32 = b.take<float>((size_t)k * k);
@@ -336,7 +339,10 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
     }
     {
       STAGE(ctx, ST_TRSM);
-      if (ctx->chol_blocked && trsm_blocked_used(k))
+      if (ctx->trsm_inverse)
+        CK(trsm_inverse(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<char>(ctx, L.ti), ctx->dflags,
+                        ctx->wait_cycles, ctx->stream));
+      else if (ctx->chol_blocked && trsm_blocked_used(k))
         CK(trsm_blocked(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<char>(ctx, L.tb), ctx->dflags,
                         ctx->wait_cycles, ctx->stream));
       else
@@ -469,7 +475,7 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const float* F = a.F;
   int ldf = a.ldf;
   for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
-                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2, &L.cb, &L.tb})
+                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2, &L.cb, &L.tb, &L.ti})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;
@@ -874,6 +880,7 @@ KFAC_API kfac_status kfac_destroy(kfac_ctx* ctx) {
     if (ctx->join_ev[q]) cudaEventDestroy(ctx->join_ev[q]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (cudaEvent_t e : ctx->item_ev) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->ditems) cudaFree(ctx->ditems);
   if (ctx->dglobal) cudaFree(ctx->dglobal);
@@ -957,6 +964,10 @@ KFAC_API kfac_status kfac_set_option(kfac_ctx* ctx, kfac_option opt, double v) {
     case KFAC_OPT_CHOL_BLOCKED:
       if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
       ctx->chol_blocked = (int)v;
+      return KFAC_OK;
+    case KFAC_OPT_TRSM_INVERSE:
+      if (v != 0 && v != 1) return KFAC_ERR_INVALID_ARG;
+      ctx->trsm_inverse = (int)v;
       return KFAC_OK;
     case KFAC_OPT_CHOL_CLUSTER:
       if (v < 0 || v > 16) return KFAC_ERR_INVALID_ARG;
@@ -1350,11 +1361,11 @@ static bool cache_lookup(const char* path, const char* dev, unsigned long long s
   while (fgets(line, sizeof line, fp)) {
     char name[256];
     unsigned long long s = 0;
-    int a = 0, b = 0, c = 0, e = 0, f = 0;
+    int a = 0, b = 0, c = 0, e = 0, f = 0, h = 0;
     double ms = 0.0;
-    if (sscanf(line, "%255[^|]|%llx %d %d %d %d %d %lf", name, &s, &a, &b, &c, &e, &f, &ms) == 8 && s == sig &&
-        strcmp(name, dev) == 0) {
-      cfg[0] = a; cfg[1] = b; cfg[2] = c; cfg[3] = e; cfg[4] = f;
+    if (sscanf(line, "%255[^|]|%llx %d %d %d %d %d %d %lf", name, &s, &a, &b, &c, &e, &f, &h, &ms) == 9 &&
+        s == sig && strcmp(name, dev) == 0) {
+      cfg[0] = a; cfg[1] = b; cfg[2] = c; cfg[3] = e; cfg[4] = f; cfg[5] = h;
       found = true;  // the last entry for this key wins
     }
   }
@@ -1377,7 +1388,8 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
   for (char* c = prop.name; *c; ++c)
     if (*c == '|' || *c == '\n') *c = ' ';
   const unsigned long long sig = invert_signature(ctx, count, descs);
-  int cfg[5] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target, ctx->chol_panel, ctx->chol_blocked};
+  int cfg[6] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target, ctx->chol_panel, ctx->chol_blocked,
+                ctx->trsm_inverse};
   bool cached = cache_path && cache_lookup(cache_path, prop.name, sig, cfg);
   double best_ms = 0.0;
   if (!cached) {
@@ -1392,7 +1404,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     // One warm-up and two timed grouped inversions per candidate.
     auto run = [&](const int* c, double* ms) -> kfac_status {
       ctx->group_streams = c[0]; ctx->chol_cluster = c[1]; ctx->split_target = c[2]; ctx->chol_panel = c[3];
-      ctx->chol_blocked = c[4];
+      ctx->chol_blocked = c[4]; ctx->trsm_inverse = c[5];
       kfac_status st = kfac_rsvd_invert_grouped(ctx, count, descs);
       if (st != KFAC_OK) return st;
       if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) return KFAC_ERR_CUDA;
@@ -1413,18 +1425,21 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     const int split_c[] = {0, 304, -1};
     const int panel_c[] = {16, 32};
     const int blocked_c[] = {1, 0};
-    const int order[5] = {0, 4, 2, 1, 3};
+    const int inverse_c[] = {1, 0};
+    const int order[6] = {0, 5, 4, 2, 1, 3};
     kfac_status st = run(cfg, &best_ms);
-    for (int oi = 0; oi < 5 && st == KFAC_OK; ++oi) {
+    for (int oi = 0; oi < 6 && st == KFAC_OK; ++oi) {
       const int dim = order[oi];
       const int* cand = dim == 0 ? streams_c
-                                 : (dim == 1 ? chol_c : (dim == 2 ? split_c : (dim == 3 ? panel_c : blocked_c)));
-      const int n = dim == 0 ? 4 : ((dim == 3 || dim == 4) ? 2 : 3);
+                                 : (dim == 1 ? chol_c
+                                             : (dim == 2 ? split_c : (dim == 3 ? panel_c : (dim == 4 ? blocked_c
+                                                                                                     : inverse_c))));
+      const int n = dim == 0 ? 4 : ((dim == 3 || dim == 4 || dim == 5) ? 2 : 3);
       if ((dim == 1 || dim == 3 || dim == 4) && !big_k) continue;  // no factor uses a large-order Cholesky
       if ((dim == 1 || dim == 3) && cfg[4]) continue;            // the cluster kernel is not in use
       for (int i = 0; i < n && st == KFAC_OK; ++i) {
         if (cand[i] == cfg[dim]) continue;
-        int trial[5] = {cfg[0], cfg[1], cfg[2], cfg[3], cfg[4]};
+        int trial[6] = {cfg[0], cfg[1], cfg[2], cfg[3], cfg[4], cfg[5]};
         trial[dim] = cand[i];
         double ms = 0.0;
         st = run(trial, &ms);
@@ -1440,7 +1455,8 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     if (cache_path) {
       FILE* fp = fopen(cache_path, "a");
       if (fp) {
-        fprintf(fp, "%s|%llx %d %d %d %d %d %.4f\n", prop.name, sig, cfg[0], cfg[1], cfg[2], cfg[3], cfg[4], best_ms);
+        fprintf(fp, "%s|%llx %d %d %d %d %d %d %.4f\n", prop.name, sig, cfg[0], cfg[1], cfg[2], cfg[3], cfg[4], cfg[5],
+                best_ms);
         fclose(fp);
       }
     }
@@ -1450,9 +1466,10 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
   ctx->split_target = cfg[2];
   ctx->chol_panel = cfg[3];
   ctx->chol_blocked = cfg[4];
+  ctx->trsm_inverse = cfg[5];
   if (chosen) {
-    for (int i = 0; i < 5; ++i) chosen[i] = cfg[i];
-    chosen[5] = cached ? 1 : 0;
+    for (int i = 0; i < 6; ++i) chosen[i] = cfg[i];
+    chosen[6] = cached ? 1 : 0;
   }
   return KFAC_OK;
 }
@@ -1537,6 +1554,122 @@ KFAC_API kfac_status kfac_precondition_grouped(kfac_ctx* ctx, int count, const k
     ctx->stream = ctx->side[slot[f]];
     ctx->dflags = ctx->ditems + f;
     first_err = run(f, base[slot[f]]);
+  }
+  ctx->dflags = ctx->dglobal;
+  ctx->stream = main_s;
+  for (int q = 0; q < ns; ++q) {
+    CK(cudaEventRecord(ctx->join_ev[q], ctx->side[q]));
+    CK(cudaStreamWaitEvent(main_s, ctx->join_ev[q], 0));
+  }
+  return first_err;
+}
+
+// One K-FAC step of a set of layers (Alg. 1 EA updates, Alg. 3 / Alg. 2
+// inversions, Alg. 4 applies) with per-item dependencies instead of a join
+// between the phases: factor f's EA update and inversion run in turn on its
+// forked stream, and layer l's apply starts as soon as its two factors are
+// inverted, on the stream of the later of them (an event from the other), so
+// applies overlap the inversions still running.
+KFAC_API kfac_status kfac_step_grouped(kfac_ctx* ctx, int n_factors, const kfac_ea_desc* ea,
+                                       const kfac_invert_desc* inv, int n_layers, const kfac_precond_desc* pre,
+                                       const int* layer_factors) {
+  if (!ctx || n_factors < 0 || n_layers < 0 || (n_factors > 0 && !inv) || (n_layers > 0 && (!pre || !layer_factors)))
+    return KFAC_ERR_INVALID_ARG;
+  std::vector<InvertLayout> il(n_factors);
+  for (int f = 0; f < n_factors; ++f) {
+    int r = 0, k = 0;
+    kfac_status st = check_invert(inv[f], &r, &k);
+    if (st != KFAC_OK) return st;
+    if (ea && (st = check_ea(ea[f])) != KFAC_OK) return st;
+    il[f] = invert_layout(inv[f].d, k, r, !tma_rows_ok(inv[f].F, inv[f].ldf), inv[f].prec == KFAC_PREC_BF16,
+                          ctx->tail_planes != 0);
+  }
+  std::vector<PrecLayout> pl(n_layers);
+  for (int l = 0; l < n_layers; ++l) {
+    kfac_status st = check_precond(pre[l]);
+    if (st != KFAC_OK) return st;
+    for (int q = 0; q < 2; ++q)
+      if (layer_factors[2 * l + q] < -1 || layer_factors[2 * l + q] >= n_factors) return KFAC_ERR_INVALID_ARG;
+    const kfac_precond_desc& a = pre[l];
+    pl[l] = prec_layout_for(a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.r_a, a.U_g, a.ld_ug, a.r_g,
+                            ctx->tail_planes != 0);
+  }
+  if (n_factors + n_layers == 0) return KFAC_OK;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  const int ns = std::max(1, std::min(std::max(n_factors, n_layers), ctx->group_streams));
+  std::vector<double> cost(n_factors);
+  for (int f = 0; f < n_factors; ++f)
+    cost[f] = invert_cost(inv[f]) + (ea ? 2.0 * ea[f].d * (double)ea[f].d * ea[f].n / 1e14 : 0.0);
+  std::vector<int> order, slot;
+  lpt_schedule(cost, ns, order, slot);
+  std::vector<int> pos(n_factors, 0);
+  for (int i = 0; i < n_factors; ++i) pos[order[i]] = i;
+  // Each layer runs after the later (in issue order) of its factors, on that
+  // factor's stream; a layer without factors runs first, spread over the streams.
+  std::vector<std::vector<int>> after(n_factors);
+  std::vector<int> free_layers;
+  std::vector<size_t> need(n_factors + n_layers);
+  std::vector<int> slot_all(n_factors + n_layers);
+  for (int f = 0; f < n_factors; ++f) {
+    need[f] = std::max(il[f].total, ea ? ea_ws_bytes(ctx, ea[f].d, ea[f].n, ea[f].X, ea[f].ldx, ea[f].prec) : 0);
+    slot_all[f] = slot[f];
+  }
+  for (int l = 0; l < n_layers; ++l) {
+    const int a = layer_factors[2 * l], g = layer_factors[2 * l + 1];
+    const int host = a < 0 ? g : (g < 0 ? a : (pos[a] > pos[g] ? a : g));
+    need[n_factors + l] = pl[l].total;
+    if (host < 0) {
+      free_layers.push_back(l);
+      slot_all[n_factors + l] = l % ns;
+    } else {
+      after[host].push_back(l);
+      slot_all[n_factors + l] = slot[host];
+    }
+  }
+  const std::vector<size_t> base = stream_bases(need, slot_all, ns);
+  kfac_status st = ensure_ws(ctx, base[ns]);
+  if (st != KFAC_OK) return st;
+  if ((st = ensure_items(ctx, n_factors + n_layers)) != KFAC_OK) return st;
+  if ((st = ensure_side_streams(ctx, ns)) != KFAC_OK) return st;
+  while ((int)ctx->item_ev.size() < n_factors) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return KFAC_ERR_CUDA;
+    ctx->item_ev.push_back(e);
+  }
+  auto apply = [&](int l, int q) -> kfac_status {
+    const kfac_precond_desc& a = pre[l];
+    if ((long long)a.d_g * a.d_a == 0) return KFAC_OK;
+    ctx->dflags = ctx->ditems + n_factors + l;
+    return precondition_run(ctx, a.d_g, a.d_a, a.J, a.ldj, a.U_a, a.ld_ua, a.coef_a, a.r_a, a.U_g, a.ld_ug,
+                            a.coef_g, a.r_g, a.lambda, a.prec, a.S, a.lds, pl[l], base[q]);
+  };
+  cudaStream_t main_s = ctx->stream;
+  CK(cudaEventRecord(ctx->fork_ev, main_s));
+  for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(ctx->side[q], ctx->fork_ev, 0));
+  kfac_status first_err = KFAC_OK;
+  for (int l : free_layers) {
+    if (first_err != KFAC_OK) break;
+    ctx->stream = ctx->side[l % ns];
+    first_err = apply(l, l % ns);
+  }
+  for (int i = 0; i < n_factors && first_err == KFAC_OK; ++i) {
+    const int f = order[i], q = slot[f];
+    ctx->stream = ctx->side[q];
+    ctx->dflags = ctx->ditems + f;
+    if (ea && ea[f].d > 0) first_err = ea_run(ctx, ea[f].d, ea[f].n, ea[f].X, ea[f].ldx, ea[f].rho, ea[f].prec,
+                                              ea[f].F, ea[f].ldf, base[q]);
+    if (first_err == KFAC_OK) first_err = invert_run(ctx, inv[f], il[f], base[q]);
+    if (first_err != KFAC_OK) break;
+    if (cudaEventRecord(ctx->item_ev[f], ctx->stream) != cudaSuccess) { first_err = KFAC_ERR_CUDA; break; }
+    for (int l : after[f]) {
+      const int a = layer_factors[2 * l], g = layer_factors[2 * l + 1];
+      for (int o : {a, g})
+        if (o >= 0 && o != f && cudaStreamWaitEvent(ctx->stream, ctx->item_ev[o], 0) != cudaSuccess)
+          first_err = KFAC_ERR_CUDA;
+      if (first_err == KFAC_OK) first_err = apply(l, q);
+      if (first_err != KFAC_OK) break;
+    }
   }
   ctx->dflags = ctx->dglobal;
   ctx->stream = main_s;

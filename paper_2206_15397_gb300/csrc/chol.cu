@@ -1209,4 +1209,71 @@ cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Qt = L^-1 Yt through the explicit inverse: Linv = L^-1 by the triangular
+// solve of the k x k identity (the shared-memory or the blocked form), Y = Yt^T
+// by a transpose, then one FP32-accurate tensor-core product Qt = (Y Linv^T)^T
+// (both operands K-major, transposed store). The k x k inverse is small; the
+// k^2 d product, which the substitution spends on the SIMT pipes, runs on the
+// tensor cores.
+namespace {
+__global__ void k_identity(float* __restrict__ E, int k, long long ld) {
+  const long long n = (long long)k * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / ld, j = e - i * ld;
+    E[e] = (i == j) ? 1.0f : 0.0f;
+  }
+}
+
+struct TiLayout {
+  size_t E, Linv, Y, dinv, inner, total;
+  long long kp;
+};
+
+TiLayout ti_layout(int k, int d) {
+  TiLayout t = {};
+  t.kp = (k + 3) / 4 * 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = (off + 255) & ~size_t(255);
+    off = o + bytes;
+    return o;
+  };
+  t.E = take(sizeof(float) * (size_t)k * t.kp);
+  t.Linv = take(sizeof(float) * (size_t)k * t.kp);
+  t.Y = take(sizeof(float) * (size_t)d * t.kp);
+  t.dinv = take(sizeof(float) * trsm_ws_floats(k));
+  t.inner = take(trsm_blocked_ws_bytes(k, k));
+  t.total = off;
+  return t;
+}
+}  // namespace
+
+size_t trsm_inverse_ws_bytes(int k, int d) { return k > 0 && d > 0 ? ti_layout(k, d).total : 0; }
+
+cudaError_t trsm_inverse(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
+                         void* ws, int* flags, long long wait_cycles, cudaStream_t s) {
+  if (k <= 0 || d <= 0) return cudaSuccess;
+  const TiLayout t = ti_layout(k, d);
+  char* base = static_cast<char*>(ws);
+  float* E = reinterpret_cast<float*>(base + t.E);
+  float* Linv = reinterpret_cast<float*>(base + t.Linv);
+  float* Y = reinterpret_cast<float*>(base + t.Y);
+  k_identity<<<grid_for((long long)k * t.kp), 256, 0, s>>>(E, k, t.kp);
+  note_launch();
+  cudaError_t e = trsm_blocked_used(k)
+                      ? trsm_blocked(L, k, E, t.kp, Linv, t.kp, k, base + t.inner, flags, wait_cycles, s)
+                      : trsm_lower_f32(L, k, E, t.kp, Linv, t.kp, k, reinterpret_cast<float*>(base + t.dinv), s);
+  if (e != cudaSuccess) return e;
+  if ((e = transpose_f32(Yt, ldy, k, d, Y, t.kp, s)) != cudaSuccess) return e;
+  GemmDesc<float> g = {};
+  g.M = d; g.N = k; g.K = k;
+  g.A = Y; g.sam = t.kp; g.sak = 1;
+  g.B = Linv; g.sbn = t.kp; g.sbk = 1;
+  g.D = Qt; g.ldd = ldq; g.d_trans = 1;
+  g.alpha = 1.0f; g.zsplit = 1;
+  g.flags = flags; g.wait_cycles = wait_cycles;
+  return gemm_f32(g, KFAC_PREC_FP32, s);
+}
+
 }  // namespace kfac

@@ -200,6 +200,12 @@ bool trsm_blocked_used(int k);
 size_t trsm_blocked_ws_bytes(int k, int d);
 cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
                          void* ws, int* flags, long long wait_cycles, cudaStream_t s);
+// The same solve through the explicit inverse: L^-1 by solving the identity,
+// then Qt = (Yt^T L^-T)^T as one FP32-accurate tensor-core product. ws:
+// trsm_inverse_ws_bytes(k, d) bytes of device workspace.
+size_t trsm_inverse_ws_bytes(int k, int d);
+cudaError_t trsm_inverse(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
+                         void* ws, int* flags, long long wait_cycles, cudaStream_t s);
 
 // FP32 one-sided Jacobi on chol(C + s I) over a thread-block cluster: writes X
 // (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:

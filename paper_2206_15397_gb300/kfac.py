@@ -31,7 +31,7 @@ OPTIONS = {"cholqr_passes": 0, "cholqr_shift": 1, "eig_refine": 2, "eig_max_swee
            "group_streams": 12, "invert_method": 13,
            "chol_cluster": 14, "split_target": 15, "warm_start": 16,
            "conv_chunk": 17, "chol_panel": 18, "tail_planes": 19,
-           "chol_blocked": 20}
+           "chol_blocked": 20, "trsm_inverse": 21}
 FLAGS = {1: "CHOL_SHIFTED", 2: "CHOL_FAILED", 4: "EIG_NOCONV", 8: "NONFINITE", 16: "EIG_SHIFTED", 32: "TIMEOUT"}
 
 
@@ -108,6 +108,9 @@ def lib():
         L.kfac_ea_update_grouped.restype = i
         L.kfac_precondition_grouped.argtypes = [vp, i, ctypes.POINTER(PrecondDesc)]
         L.kfac_precondition_grouped.restype = i
+        L.kfac_step_grouped.argtypes = [vp, i, ctypes.POINTER(EaDesc), ctypes.POINTER(InvertDesc), i,
+                                        ctypes.POINTER(PrecondDesc), ctypes.POINTER(i)]
+        L.kfac_step_grouped.restype = i
         L.kfac_gemm_nt.argtypes = [vp, i, i, i, vp, i, vp, i, f, f, vp, i, i]
         L.kfac_gemm_nt.restype = i
         L.kfac_rsvd_invert_grouped.restype = i
@@ -198,11 +201,11 @@ def kfac_get_status(ctx: Context):
 def kfac_autotune_invert(ctx: Context, descs, cache_path: str | None = None) -> dict:
     """Tune the grouped inversion's schedule for a prepared descriptor array
     (invert_descs); returns the chosen settings."""
-    out = (ctypes.c_int * 6)()
+    out = (ctypes.c_int * 7)()
     _check(lib().kfac_autotune_invert(ctx.handle, len(descs), descs,
                                       cache_path.encode() if cache_path else None, out), "kfac_autotune_invert")
     return {"group_streams": out[0], "chol_cluster": out[1], "split_target": out[2], "chol_panel": out[3],
-            "chol_blocked": out[4], "cached": bool(out[5])}
+            "chol_blocked": out[4], "trsm_inverse": out[5], "cached": bool(out[6])}
 
 
 def kfac_get_item_status(ctx: Context, count: int):
@@ -430,6 +433,19 @@ def precond_descs(items):
 
 _GROUPED = {"ea": "kfac_ea_update_grouped", "invert": "kfac_rsvd_invert_grouped",
             "precondition": "kfac_precondition_grouped"}
+
+
+def step_descs(layer_factors):
+    """int array of (A factor, G factor) per layer for kfac_step_grouped (-1: none)."""
+    flat = [int(v) for pair in layer_factors for v in pair]
+    return (ctypes.c_int * max(len(flat), 1))(*flat)
+
+
+def kfac_step_grouped(ctx: Context, ea, inv, pre, layer_factors):
+    """One step on prepared descriptor arrays (ea_descs or None, invert_descs,
+    precond_descs) and a step_descs array of each layer's two factor indices."""
+    n_l = len(pre)
+    _check(lib().kfac_step_grouped(ctx.handle, len(inv), ea, inv, n_l, pre, layer_factors), "kfac_step_grouped")
 
 
 def call_grouped(ctx: Context, kind: str, descs):

@@ -37,7 +37,7 @@ def test_autotune_then_cache(kf, tmp_path):
         got = kf.kfac_autotune_invert(ctx, descs, cache)
         assert got["group_streams"] in (4, 8, 16, 32) and got["chol_cluster"] in (0, 8, 12)
         assert got["split_target"] in (0, 304, -1) and got["chol_panel"] in (16, 32) and not got["cached"]
-        assert got["chol_blocked"] in (0, 1)
+        assert got["chol_blocked"] in (0, 1) and got["trsm_inverse"] in (0, 1)
         assert kf.kfac_get_status(ctx)[0] == 0
         kf.call_grouped(ctx, "invert", descs)
         assert kf.kfac_get_status(ctx)[0] == 0
@@ -46,6 +46,6 @@ def test_autotune_then_cache(kf, tmp_path):
             assert np.abs(D.double().cpu().numpy() - d_o).max() <= 1e-5 * d_o[0]
     with kf.Context(0) as ctx2:
         again = kf.kfac_autotune_invert(ctx2, descs, cache)
-        keys = ("group_streams", "chol_cluster", "split_target", "chol_panel", "chol_blocked")
+        keys = ("group_streams", "chol_cluster", "split_target", "chol_panel", "chol_blocked", "trsm_inverse")
         assert again["cached"] and {k: again[k] for k in keys} == {k: got[k] for k in keys}
     assert len(open(cache).read().strip().splitlines()) == 1

@@ -1,6 +1,8 @@
 """Large-order Cholesky factorisations (sketch widths k above the one-CTA
-kernel's 236): the blocked form (KFAC_OPT_CHOL_BLOCKED = 1, the default) and
-the cluster kernel (= 0) each give inversions that match the FP64 oracle
+kernel's 236) and the CholeskyQR solves: the blocked factorisation
+(KFAC_OPT_CHOL_BLOCKED = 1, the default) or the cluster kernel (= 0), with the
+solves through the explicit inverse (KFAC_OPT_TRSM_INVERSE = 1, the default)
+or by substitution (= 0), each give inversions that match the FP64 oracle
 (Alg. 3: eigenvalues to 1e-5 of the largest, orthonormal U, Alg. 4's
 preconditioned gradient), for the CholeskyQR Grams and the eigensolver's
 factor alike; degenerate inputs (zero, non-finite) take the failure paths."""
@@ -30,9 +32,9 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("blocked", [1, 0])
+@pytest.mark.parametrize("blocked,inverse", [(1, 1), (1, 0), (0, 0)])
 @pytest.mark.parametrize("d,r,alpha", [(700, 256, 1.0), (1100, 512, 1.5), (560, 560, 1.0)])
-def test_large_k_inversion_matches_oracle(kf, blocked, d, r, alpha):
+def test_large_k_inversion_matches_oracle(kf, blocked, inverse, d, r, alpha):
     """k = 266, 522 (sketched) and d = 560 <= k (exact path: the eigensolver
     factors the whole factor)."""
     p, lam = 10, 0.1
@@ -42,6 +44,7 @@ def test_large_k_inversion_matches_oracle(kf, blocked, d, r, alpha):
         om = None
     with kf.Context(0) as ctx:
         kf.kfac_set_option(ctx, "chol_blocked", blocked)
+        kf.kfac_set_option(ctx, "trsm_inverse", inverse)
         U, D, c = kf.kfac_rsvd_invert(ctx, cuda(f), r, p, 1, lam, om_t)
         st, flags = kf.kfac_get_status(ctx)
         assert st == 0 and set(flags) <= {"CHOL_SHIFTED", "EIG_SHIFTED"}, (st, flags)
@@ -62,12 +65,13 @@ def test_large_k_inversion_matches_oracle(kf, blocked, d, r, alpha):
         assert np.linalg.norm(host(S) - want) <= 1e-4 * np.linalg.norm(want)
 
 
-@pytest.mark.parametrize("blocked", [1, 0])
-def test_large_k_zero_and_nonfinite_factors(kf, blocked):
+@pytest.mark.parametrize("blocked,inverse", [(1, 1), (0, 0)])
+def test_large_k_zero_and_nonfinite_factors(kf, blocked, inverse):
     d, r, p = 600, 300, 10
     om = cuda(inputs.omega(112, d, r + p))
     with kf.Context(0) as ctx:
         kf.kfac_set_option(ctx, "chol_blocked", blocked)
+        kf.kfac_set_option(ctx, "trsm_inverse", inverse)
         U, D, c = kf.kfac_rsvd_invert(ctx, torch.zeros(d, d, device="cuda"), r, p, 1, 0.1, om)
         st, flags = kf.kfac_get_status(ctx)
         assert st == 0 and set(flags) <= {"CHOL_SHIFTED", "EIG_SHIFTED"}, (st, flags)

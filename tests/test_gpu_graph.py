@@ -102,3 +102,73 @@ def test_stage_profile_and_timeline(kf):
         assert abs(sum(b - a for a, b in iv) - ms) <= 1e-3 * max(ms, 1.0)
     for stage in ("sketch_gemm", "cholqr_chol", "eig_jacobi", "lift_gemm"):
         assert {it for s, it, _, _ in tl if s == stage} == {0, 1, 2}, stage
+
+
+def test_fused_step_matches_the_three_grouped_calls(kf):
+    """kfac_step_grouped (per-item dependencies, applies overlapping the
+    inversions) gives bitwise the results of the grouped EA, inversion and
+    apply calls in turn, eagerly and replayed from a CUDA graph."""
+    dims = [(513, 40), (300, 30), (257, 50), (120, 20), (700, 60), (64, 70)]   # (d, r); the last is exact
+    layers = [(0, 1), (2, 3), (4, 5)]
+    n = 48
+
+    def state():
+        st = dict(F=[], X=[], O=[], out=[], J=[], S=[])
+        for i, (d, r) in enumerate(dims):
+            st["F"].append(cuda(inputs.spectrum_factor(90 + i, d, inputs.power_spectrum(d, 1.0) ** 2)))
+            st["X"].append(cuda(inputs.gaussian(120 + i, (d, n))))
+            k = r + 10
+            st["O"].append(cuda(inputs.omega(90 + i, d, k)) if k < d else None)
+            st["out"].append((torch.empty(d, min(r, d), device="cuda"), torch.empty(min(r, d), device="cuda"),
+                              torch.empty(min(r, d), device="cuda")))
+        for a, g in layers:
+            st["J"].append(cuda(inputs.gradient(95 + a, dims[g][0], dims[a][0], std=0.1)))
+            st["S"].append(torch.empty(dims[g][0], dims[a][0], device="cuda"))
+        return st
+
+    def descs(st):
+        ea = kf.ea_descs([dict(X=st["X"][i], F=st["F"][i], rho=0.9) for i in range(len(dims))])
+        inv, _ = kf.invert_descs([dict(F=st["F"][i], rank=r, oversample=10, power_iters=1, lam=0.1,
+                                       omega=st["O"][i], out=st["out"][i]) for i, (d, r) in enumerate(dims)])
+        pre, _ = kf.precond_descs([dict(J=st["J"][li], U_a=st["out"][a][0], coef_a=st["out"][a][2],
+                                        U_g=st["out"][g][0], coef_g=st["out"][g][2], lam=0.1, out=st["S"][li])
+                                   for li, (a, g) in enumerate(layers)])
+        return ea, inv, pre
+
+    def outputs(st):
+        return [t.clone() for t in st["F"] + [u for o in st["out"] for u in o] + st["S"]]
+
+    ref_st = state()
+    ea, inv, pre = descs(ref_st)
+    with kf.Context(0) as ctx:
+        kf.call_grouped(ctx, "ea", ea)
+        kf.call_grouped(ctx, "invert", inv)
+        kf.call_grouped(ctx, "precondition", pre)
+        assert kf.kfac_get_status(ctx)[0] == 0
+    ref = outputs(ref_st)
+    lf = kf.step_descs(layers)
+    st = state()
+    ea, inv, pre = descs(st)
+    F0 = [f.clone() for f in st["F"]]
+    stream = torch.cuda.Stream()
+    with kf.Context(0, stream) as ctx:
+        with torch.cuda.stream(stream):
+            kf.kfac_step_grouped(ctx, ea, inv, pre, lf)
+            stream.synchronize()
+        assert kf.kfac_get_status(ctx)[0] == 0
+        got = outputs(st)
+        for a, b in zip(ref, got):
+            assert torch.equal(a, b)
+        for f, f0 in zip(st["F"], F0):
+            f.copy_(f0)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            kf.kfac_step_grouped(ctx, ea, inv, pre, lf)
+        for f, f0 in zip(st["F"], F0):
+            f.copy_(f0)
+        with torch.cuda.stream(stream):
+            g.replay()
+            stream.synchronize()
+        assert kf.kfac_get_status(ctx)[0] == 0
+        for a, b in zip(ref, outputs(st)):
+            assert torch.equal(a, b)
