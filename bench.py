@@ -250,7 +250,10 @@ def bytes_touched(spec: dict) -> float:
 # dominant kernels from ncu captures of this bench's kernels on a GB300 (the
 # summaries under profiles/), keyed by (workload, stage); None where no capture
 # of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = {}
+NCU_TRAFFIC_PER_LAUNCH = {
+    # the 64 one-sided Jacobi solves of one 64-factor step, averaged (profiles/eig_jacobi_c5_step_dram.md)
+    ("c5", "eig_jacobi"): 350684,
+}
 
 
 def load_peaks():
