@@ -356,7 +356,8 @@ class DeviceWorkload:
                 xs.append(X)
             self.X.append(xs)
             k = f["r"] + p
-            self.Om.append(torch.randn(d, k, generator=gen, device=dev, dtype=torch.float32) if k < d else None)
+            self.Om.append(torch.randn(d, k, generator=gen, device=dev, dtype=torch.float32)
+                           if k < d and OMEGA["mode"] == "input" else None)
             r = min(f["r"], d)
             self.out.append((self.padded(d, r), torch.empty(r, device=dev), torch.empty(r, device=dev)))
         self.J, self.S = [], []
@@ -390,7 +391,8 @@ class DeviceWorkload:
         ea = [kfac.ea_descs([dict(X=self.X[i][b], F=self.F[i], rho=spec["rho"], prec=prec)
                              for i in range(len(self.F))]) for b in range(self.nb)]
         inv = [kfac.invert_descs([dict(F=self.F[i], rank=f["r"], oversample=spec["p"], power_iters=spec["q"],
-                                       lam=spec["lam"], omega=self.Om_b[b][i], prec=prec, out=self.out[i])
+                                       lam=spec["lam"], omega=self.Om_b[b][i], seed=1000 * (b + 1) + i, prec=prec,
+                                       out=self.out[i])
                                   for i, f in enumerate(spec["factors"])])[0] for b in range(self.nb)]
         pre = [kfac.precond_descs([dict(J=self.J_b[b][li], U_a=self.out[a][0], coef_a=self.out[a][2],
                                         U_g=self.out[g][0], coef_g=self.out[g][2], lam=spec["lam"], prec=prec,
@@ -400,6 +402,10 @@ class DeviceWorkload:
 
 
 FUSED = {"on": False}   # kfac_step_grouped (per-item dependencies) or the three grouped calls in turn
+# "input": every factor's test matrix is an input tensor (drawn with torch.randn,
+# copied in with the step's inputs end to end); "seed": the library draws it on
+# the device from a per-factor seed (omega NULL), so it is neither stored nor copied.
+OMEGA = {"mode": "input"}
 
 
 def run_step(kfac, ctx, descs, b):
@@ -826,8 +832,11 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (no autotuner)")
     ap.add_argument("--fused", action="store_true",
                     help="kfac_step_grouped (per-item dependencies) instead of the three grouped calls in turn")
+    ap.add_argument("--omega", choices=["input", "seed"], default="input",
+                    help="test matrices as input tensors, or drawn on the device from seeds (omega NULL)")
     args = ap.parse_args(argv)
     FUSED["on"] = args.fused
+    OMEGA["mode"] = args.omega
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:
@@ -860,7 +869,7 @@ def main(argv=None):
     barrier(world, dev)
     ms_step = reduce_max(res["ms"], world, dev)
     log("end to end with host buffers")
-    e2e_ms, h2d, d2h = e2e_measure(kfac, ctx, wl, res["graphs"], stream, max(3, min(args.steps, 10)))
+    e2e_ms, h2d, d2h = e2e_measure(kfac, ctx, wl, res["graphs"], stream, max(3, args.steps))
     e2e_ms = reduce_max(e2e_ms, world, dev)
 
     result = None
@@ -879,6 +888,10 @@ def main(argv=None):
                                        "one CUDA graph per step (grouped EA, grouped inversion, grouped apply)"),
                              "streams": (res["tuned"] or {}).get("group_streams", args.streams),
                              "autotuned": res["tuned"],
+                             "omega": ("input tensors (torch.randn on the device; copied in with the step's inputs "
+                                       "end to end)" if OMEGA["mode"] == "input" else
+                                       "drawn by the library on the device from per-factor seeds (Philox4x32-10 + "
+                                       "Box-Muller), inside the step"),
                              "layout": "row strides rounded up to 16 bytes",
                              "l2": "no flush: %.1f GB of factors, batches, gradients and outputs per step (L2 129 MB)"
                                    % (bytes_touched(spec) / 1e9),

@@ -176,15 +176,36 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
  * When k >= d the factor is diagonalised directly (Q = I). The sketch width
  * (or d on that direct path) is limited to 576: larger requests return
  * KFAC_ERR_UNSUPPORTED.
- * omega: d x k Gaussian test matrix (row stride ldo >= k), caller-drawn (the
- *        library draws no random numbers). Ignored when k >= d (may be NULL).
+ * omega: d x k Gaussian test matrix (row stride ldo >= k), drawn by the caller;
+ *        or NULL: the library draws the matrix kfac_draw_omega gives for `seed`
+ *        on the device, straight into the transposed layout the sketch reads
+ *        (no copy in, no transpose). Ignored when k >= d (may be NULL).
+ * seed:  the generator key when omega is NULL (ignored otherwise).
  * U: d x r output (row stride ldu >= r); D, coef: r outputs.
  * F must hold the full symmetric matrix (both triangles are read; F is not
  * modified). power_iters counts extra products F Q, each followed by a fresh
  * orthonormalisation, so the basis spans F^(power_iters + 1) Omega. */
 KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
                                       int power_iters, float lambda, const float* omega, int ldo,
-                                      kfac_precision prec, float* U, int ldu, float* D, float* coef);
+                                      unsigned long long seed, kfac_precision prec, float* U, int ldu, float* D,
+                                      float* coef);
+
+/* The library's Gaussian test matrix for a seed (Omega of Alg. 2 / Alg. 3,
+ * i.i.d. N(0, 1) entries), written to omega (d x k, row stride ldo >= k) on the
+ * context stream. Element (i, j) is value e = i*k + j of one counter-based
+ * stream, Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11) keyed by the seed's low and high
+ * 32-bit halves:
+ *   block b = floor(e / 4) has the counter (b mod 2^32, floor(b / 2^32), 0, 1)
+ *   and gives the words w0..w3; a word w maps to (floor(w / 512) + 1/2) / 2^23
+ *   in (0, 1) (exact in FP32); values 4b and 4b+1 are rho cos(2 pi v) and rho sin(2 pi v) with
+ *   rho = sqrt(-2 ln u), u from w0 and v from w1 (Box-Muller); values 4b+2 and
+ *   4b+3 the same from w2 and w3.
+ * Evaluated in FP32 (logf, sqrtf, sincospif): each value is within a few units
+ * in the last place of the same formula evaluated exactly. kfac_rsvd_invert and
+ * the grouped inversion draw this matrix when their omega is NULL. Returns
+ * KFAC_ERR_INVALID_ARG for d or k < 1, a NULL omega or ldo < k. */
+KFAC_API kfac_status kfac_draw_omega(kfac_ctx* ctx, int d, int k, unsigned long long seed, float* omega, int ldo);
 
 /* One factor of a grouped inversion: the arguments of kfac_rsvd_invert. */
 typedef struct {
@@ -200,6 +221,7 @@ typedef struct {
   int ldu;
   float* D;
   float* coef;
+  unsigned long long seed; /* generator key when omega is NULL (kfac_draw_omega) */
 } kfac_invert_desc;
 
 /* kfac_rsvd_invert for `count` independent factors (the per-layer loop of
@@ -388,7 +410,8 @@ typedef enum {
                                        beyond the paper): the sketch matrix is [U_prev | omega'],
                                        U_prev being what the call's U buffer holds on entry (the
                                        previous inversion of the same factor, same d and r) and
-                                       omega' the first k - r columns of omega. The EA factor moves
+                                       omega' the first k - r columns of omega (of the seeded
+                                       matrix when omega is NULL). The EA factor moves
                                        little between inversions, so C = Q^T F Q starts nearly
                                        diagonal and the Jacobi solve stops after fewer sweeps; one
                                        power iteration or none may then do. Only for calls whose U

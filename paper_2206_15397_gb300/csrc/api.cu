@@ -388,7 +388,7 @@ kfac_status check_invert(const kfac_invert_desc& a, int* r_out, int* k_out) {
   const long long kl = (long long)a.rank + a.oversample;
   if (!a.U || a.ldu < r || !a.D || !a.coef) return KFAC_ERR_INVALID_ARG;
   const bool exact = kl >= a.d;
-  if (!exact && (!a.omega || a.ldo < kl)) return KFAC_ERR_INVALID_ARG;
+  if (!exact && a.omega && a.ldo < kl) return KFAC_ERR_INVALID_ARG;  // NULL omega: drawn from a.seed
   if ((exact ? (long long)a.d : kl) > kMaxSketch) return KFAC_ERR_UNSUPPORTED;
   const int k = (int)kl;
   *r_out = r;
@@ -511,15 +511,13 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   float* other = at<float>(ctx, L.q);
   {
     STAGE(ctx, ST_TRANSPOSE);
-    if (ctx->warm_start) {
-      // Subspace iteration across inversions: the previous inversion's U (the
-      // caller's U buffer, read before this call overwrites it) seeds the
-      // first r sketch columns, omega's first k - r columns the rest.
-      CK(transpose_f32(a.U, a.ldu, d, r, Om, L.dp, s));
-      CK(transpose_f32(a.omega, a.ldo, d, k - r, Om + (size_t)r * L.dp, L.dp, s));
-    } else {
-      CK(transpose_f32(a.omega, a.ldo, d, k, Om, L.dp, s));
-    }
+    // Subspace iteration across inversions (warm start): the previous
+    // inversion's U (the caller's U buffer, read before this call overwrites
+    // it) seeds the first r sketch columns, omega's first k - r columns the rest.
+    const int r0 = ctx->warm_start ? r : 0;
+    if (r0 > 0) CK(transpose_f32(a.U, a.ldu, d, r, Om, L.dp, s));
+    if (a.omega) CK(transpose_f32(a.omega, a.ldo, d, k - r0, Om + (size_t)r0 * L.dp, L.dp, s));
+    else CK(draw_omega_f32(d, k, a.seed, 0, k - r0, Om + (size_t)r0 * L.dp, L.dp, true, s));
   }
   st = sketch_product(ctx, L, Om, L.dp, F, ldf, k, d, a.prec, cur, L.dp);  // Y^T = Omega^T F
   if (st != KFAC_OK) return st;
@@ -1263,9 +1261,10 @@ KFAC_API kfac_status kfac_ea_update_grouped(kfac_ctx* ctx, int count, const kfac
 
 KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int ldf, int rank, int oversample,
                                       int power_iters, float lambda, const float* omega, int ldo,
-                                      kfac_precision prec, float* U, int ldu, float* D, float* coef) {
+                                      unsigned long long seed, kfac_precision prec, float* U, int ldu, float* D,
+                                      float* coef) {
   if (!ctx) return KFAC_ERR_INVALID_ARG;
-  kfac_invert_desc a = {d, F, ldf, rank, oversample, power_iters, lambda, omega, ldo, prec, U, ldu, D, coef};
+  kfac_invert_desc a = {d, F, ldf, rank, oversample, power_iters, lambda, omega, ldo, prec, U, ldu, D, coef, seed};
   int r = 0, k = 0;
   kfac_status st = check_invert(a, &r, &k);
   if (st != KFAC_OK) return st;
@@ -1274,6 +1273,13 @@ KFAC_API kfac_status kfac_rsvd_invert(kfac_ctx* ctx, int d, const float* F, int 
   InvertLayout L = invert_layout(d, k, r, !tma_rows_ok(F, ldf), prec == KFAC_PREC_BF16, ctx->tail_planes != 0);
   if ((st = ensure_ws(ctx, L.total)) != KFAC_OK) return st;
   return invert_run(ctx, a, L, 0);
+}
+
+KFAC_API kfac_status kfac_draw_omega(kfac_ctx* ctx, int d, int k, unsigned long long seed, float* omega, int ldo) {
+  if (!ctx || d < 1 || k < 1 || !omega || ldo < k) return KFAC_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) return KFAC_ERR_CUDA;
+  return draw_omega_f32(d, k, seed, 0, k, omega, ldo, false, ctx->stream) == cudaSuccess ? KFAC_OK : KFAC_ERR_CUDA;
 }
 
 KFAC_API kfac_status kfac_rsvd_invert_grouped(kfac_ctx* ctx, int count, const kfac_invert_desc* descs) {

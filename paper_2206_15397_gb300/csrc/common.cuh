@@ -131,6 +131,11 @@ cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, 
                               int ldo, int symmetrize, int* flags, cudaStream_t s, float* out32 = nullptr);
 cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, float* out, long long ldo,
                           cudaStream_t s);
+// Columns j0 .. j0 + ncols - 1 of the seeded d x k Gaussian test matrix (the
+// generator kfac_draw_omega documents): out (d x ncols, row stride ld) or, with
+// trans, its transpose (ncols x d, row stride ld).
+cudaError_t draw_omega_f32(int d, int k, unsigned long long seed, int j0, int ncols, float* out, long long ld,
+                           bool trans, cudaStream_t s);
 cudaError_t convert_f32_to_f64(const float* in, long long ldi, int rows, int cols, double* out, long long ldo,
                                int* flags, cudaStream_t s);
 // dst (rows x cols, row stride ldd: a multiple of 4 floats, 16-byte aligned

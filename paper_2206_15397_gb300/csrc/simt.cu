@@ -355,7 +355,65 @@ __global__ void k_convert(const float* __restrict__ in, long long ldi, int rows,
   out[(long long)r * ldo + c] = (double)v;
 }
 
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, SC'11): each round
+// forms the two 32x32 -> 64-bit products of words 0 and 2 with the round
+// multipliers, crosses their high halves with words 1 and 3 and the key, and
+// steps the key by the Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Value e of the test-matrix stream: block e / 4 of Philox (counter (block, 0, 1)),
+// two Box-Muller pairs per block, each word mapped to (floor(w / 512) + 1/2) / 2^23.
+__device__ __forceinline__ float omega_value(unsigned long long e, uint32_t k0, uint32_t k1) {
+  const unsigned long long b = e >> 2;
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0u, 1u), k0, k1);
+  const int t = (int)(e & 3);
+  const uint32_t wu = t < 2 ? w.x : w.z, wv = t < 2 ? w.y : w.w;
+  const float u = ((float)(wu >> 9) + 0.5f) * 0x1p-23f;  // exact in FP32: a 23-bit integer + 1/2, times 2^-23
+  const float v = ((float)(wv >> 9) + 0.5f) * 0x1p-23f;
+  const float rho = sqrtf(-2.0f * logf(u));
+  float sn, cs;
+  sincospif(2.0f * v, &sn, &cs);
+  return rho * ((t & 1) ? sn : cs);
+}
+
+// Columns j0 .. j0 + ncols - 1 of the d x k seeded test matrix: out[i][j - j0], or
+// with trans out[j - j0][i] (consecutive threads take consecutive i, so the
+// transposed rows are written contiguously).
+__global__ void k_draw_omega(int d, int k, int j0, int ncols, uint32_t k0, uint32_t k1, float* __restrict__ out,
+                             long long ld, int trans) {
+  const long long n = (long long)d * ncols;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    long long i, j;
+    if (trans) { j = x / d; i = x - j * d; }
+    else { i = x / ncols; j = x - i * ncols; }
+    const float z = omega_value((unsigned long long)i * (unsigned long long)k + (unsigned long long)(j0 + j), k0, k1);
+    if (trans) out[j * ld + i] = z;
+    else out[i * ld + j] = z;
+  }
+}
+
 }  // namespace
+
+cudaError_t draw_omega_f32(int d, int k, unsigned long long seed, int j0, int ncols, float* out, long long ld,
+                           bool trans, cudaStream_t s) {
+  if (d <= 0 || ncols <= 0) return cudaSuccess;
+  const long long total = (long long)d * ncols;
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
+  k_draw_omega<<<(unsigned)blocks, 256, 0, s>>>(d, k, j0, ncols, (uint32_t)seed, (uint32_t)(seed >> 32), out, ld,
+                                                trans ? 1 : 0);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t set_kernel_attrs_once(const void* fn, int max_dyn_smem, bool nonportable_cluster) {
   static std::mutex mu;

@@ -122,6 +122,35 @@ def omega(seed: int, d: int, k: int, salt: int = 0) -> np.ndarray:
     return z.astype(np.float32)
 
 
+def seeded_omega(seed: int, d: int, k: int) -> np.ndarray:
+    """The d x k Gaussian test matrix the library draws on the device for `seed`
+    (its seed path): value e = i*k + j of element (i, j) comes from Philox block
+    e // 4 with the counter (block mod 2^32, block // 2^32, 0, 1); a word w maps
+    to u = (floor(w / 512) + 1/2) / 2^23 (exact in FP32); words 0, 1 give the Box-Muller pair
+    sqrt(-2 ln u0) (cos, sin)(2 pi u1) (values 4b, 4b+1), words 2, 3 the next
+    pair. Evaluated here in FP64 and rounded to FP32 (the device evaluates the
+    same formula in FP32)."""
+    n = int(d) * int(k)
+    nblk = (n + 3) // 4
+    idx = np.arange(nblk, dtype=np.uint64)
+    ctr = np.zeros((nblk, 4), dtype=np.uint32)
+    ctr[:, 0] = (idx & _MASK32).astype(np.uint32)
+    ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
+    ctr[:, 3] = np.uint32(1)
+    key = np.empty((nblk, 2), dtype=np.uint32)
+    key[:, 0] = np.uint32(seed & 0xFFFFFFFF)
+    key[:, 1] = np.uint32((seed >> 32) & 0xFFFFFFFF)
+    w = philox4x32_10(ctr, key)
+    u = ((w >> np.uint32(9)).astype(np.float64) + 0.5) / 8388608.0
+    z = np.empty((nblk, 4))
+    for a in (0, 2):
+        rho = np.sqrt(-2.0 * np.log(u[:, a]))
+        ang = 2.0 * math.pi * u[:, a + 1]
+        z[:, a] = rho * np.cos(ang)
+        z[:, a + 1] = rho * np.sin(ang)
+    return z.reshape(-1)[:n].reshape(int(d), int(k)).astype(np.float32)
+
+
 def haar(seed: int, d: int, salt: int = 0) -> np.ndarray:
     """Haar-distributed orthogonal d x d matrix: QR of a Gaussian matrix with the
     signs of diag(R) moved into Q (Mezzadri 2007)."""

@@ -44,7 +44,7 @@ class InvertDesc(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("F", ctypes.c_void_p), ("ldf", ctypes.c_int), ("rank", ctypes.c_int),
                 ("oversample", ctypes.c_int), ("power_iters", ctypes.c_int), ("lam", ctypes.c_float),
                 ("omega", ctypes.c_void_p), ("ldo", ctypes.c_int), ("prec", ctypes.c_int), ("U", ctypes.c_void_p),
-                ("ldu", ctypes.c_int), ("D", ctypes.c_void_p), ("coef", ctypes.c_void_p)]
+                ("ldu", ctypes.c_int), ("D", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
 
 
 class EaDesc(ctypes.Structure):
@@ -91,7 +91,8 @@ def lib():
         L.kfac_get_item_status.argtypes = [vp, i, ctypes.POINTER(i)]
         L.kfac_get_item_status.restype = i
         L.kfac_ea_update.argtypes = [vp, i, i, vp, i, f, i, vp, i]
-        L.kfac_rsvd_invert.argtypes = [vp, i, vp, i, i, i, i, f, vp, i, i, vp, i, vp, vp]
+        L.kfac_rsvd_invert.argtypes = [vp, i, vp, i, i, i, i, f, vp, i, ctypes.c_uint64, i, vp, i, vp, vp]
+        L.kfac_draw_omega.argtypes = [vp, i, i, ctypes.c_uint64, vp, i]
         L.kfac_precondition.argtypes = [vp, i, i, vp, i, vp, i, vp, i, vp, i, vp, i, f, i, vp, i]
         L.kfac_profile_enable.argtypes = [vp, i]
         L.kfac_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d), ctypes.POINTER(i), i,
@@ -253,9 +254,10 @@ def kfac_ea_update_conv(ctx: Context, x: torch.Tensor, F: torch.Tensor, kernel, 
 
 
 def kfac_rsvd_invert(ctx: Context, F: torch.Tensor, rank: int, oversample: int, power_iters: int, lam: float,
-                     omega: torch.Tensor | None, prec: str = "fp32", out=None):
+                     omega: torch.Tensor | None, prec: str = "fp32", out=None, seed: int = 0):
     """Randomized low-rank eigendecomposition of F and the damping coefficients.
-    Returns (U (d x r), D (r), coef (r)) with r = min(rank, d)."""
+    Returns (U (d x r), D (r), coef (r)) with r = min(rank, d). omega None: the
+    library draws the test matrix of `seed` on the device (kfac_draw_omega)."""
     d = F.shape[0]
     r = min(rank, d)
     pf, ldf = _mat(F, "F", d, d)
@@ -272,9 +274,19 @@ def kfac_rsvd_invert(ctx: Context, F: torch.Tensor, rank: int, oversample: int, 
         U, D, coef = out
     pu, ldu = _mat(U, "U", d, r)
     _check(lib().kfac_rsvd_invert(ctx.handle, d, pf, ldf, int(rank), int(oversample), int(power_iters), float(lam),
-                                  po, ldo, PRECISION[prec], pu, ldu, _vec(D, "D", r), _vec(coef, "coef", r)),
+                                  po, ldo, int(seed) & 0xFFFFFFFFFFFFFFFF, PRECISION[prec], pu, ldu,
+                                  _vec(D, "D", r), _vec(coef, "coef", r)),
            "kfac_rsvd_invert")
     return U, D, coef
+
+
+def kfac_draw_omega(ctx: Context, d: int, k: int, seed: int, out: torch.Tensor | None = None) -> torch.Tensor:
+    """The library's seeded Gaussian test matrix (d x k), drawn on the device."""
+    om = torch.empty((d, k), device=ctx.device, dtype=torch.float32) if out is None else out
+    po, ldo = _mat(om, "omega", d, k)
+    _check(lib().kfac_draw_omega(ctx.handle, int(d), int(k), int(seed) & 0xFFFFFFFFFFFFFFFF, po, ldo),
+           "kfac_draw_omega")
+    return om
 
 
 def kfac_precondition(ctx: Context, J: torch.Tensor, U_a: torch.Tensor, coef_a: torch.Tensor, U_g: torch.Tensor,
@@ -364,8 +376,8 @@ def kfac_precondition_noalloc(J: torch.Tensor, U_a: torch.Tensor, coef_a: torch.
 
 def invert_descs(items):
     """kfac_invert_desc array for a grouped inversion. items: sequence of dicts
-    with keys F, rank, oversample, power_iters, lam, omega, prec (optional) and
-    out (optional (U, D, coef)). Returns (descs, [(U, D, coef), ...]); the array
+    with keys F, rank, oversample, power_iters, lam, omega (None: drawn from the
+    key seed on the device), prec (optional) and out (optional (U, D, coef)). Returns (descs, [(U, D, coef), ...]); the array
     can be passed to call_grouped() any number of times."""
     descs = (InvertDesc * len(items))()
     outs = []
@@ -387,6 +399,7 @@ def invert_descs(items):
         dsc.d, dsc.F, dsc.ldf = d, pf.value, ldf
         dsc.rank, dsc.oversample, dsc.power_iters = int(it["rank"]), int(it["oversample"]), int(it["power_iters"])
         dsc.lam, dsc.omega, dsc.ldo = float(it["lam"]), po.value, ldo
+        dsc.seed = int(it.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
         dsc.prec = PRECISION[it.get("prec", "fp32")]
         dsc.U, dsc.ldu = pu.value, ldu
         dsc.D, dsc.coef = _vec(D, "D", r).value, _vec(coef, "coef", r).value

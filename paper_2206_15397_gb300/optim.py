@@ -8,8 +8,9 @@ updates of both K-factors from the layer inputs and output gradients
 SREVD, Alg. 3 / SRE-KFAC, or RSVD's V~, Alg. 2 / RS-KFAC) and the damped
 Kronecker apply to every layer's gradient (kfac_precondition_grouped). This
 module only captures tensors with autograd hooks, keeps the per-layer state,
-draws the Gaussian test matrices (torch.randn on the device) and copies the
-gradient in and out of the Mat(g) = [dW | db] layout.
+picks the seeds of the Gaussian test matrices (the library draws them on the
+device, omega_seed below) and copies the gradient in and out of the
+Mat(g) = [dW | db] layout.
 
 Schedule (Sec. 5): the factors are updated every `t_update` steps (T_KU) and
 inverted every `t_invert` steps (T_KI); the preconditioner is applied every
@@ -20,6 +21,14 @@ from __future__ import annotations
 import torch
 
 from . import kfac
+
+
+def omega_seed(seed: int, inversion: int, factor: int) -> int:
+    """Generator key of one factor's test matrix: the optimiser's seed in the
+    high 32 bits, then the inversion count (20 bits) and the factor's position in
+    the grouped call (12 bits), so every inversion of every factor draws a fresh
+    matrix (up to 2^20 inversions of 4096 factors)."""
+    return ((seed & 0xFFFFFFFF) << 32) | ((inversion & 0xFFFFF) << 12) | (factor & 0xFFF)
 
 
 def _value(v, step):
@@ -69,8 +78,8 @@ class RandomizedKFAC:
         self.rank, self.oversample, self.power_iters = rank, oversample, power_iters
         self.damping, self.rho, self.prec, self.grad_scale = damping, rho, prec, grad_scale
         self.t_update, self.t_invert = int(t_update), int(t_invert)
-        self.gen = torch.Generator(device=dev)
-        self.gen.manual_seed(seed)
+        self.seed = int(seed)
+        self.inversions = 0
         self.steps = 0
         self._hooks = []
         for L in self.layers:
@@ -119,11 +128,11 @@ class RandomizedKFAC:
             for L in self.layers:
                 for F in (L.FA, L.FG):
                     d = F.shape[0]
-                    k = min(r, d) + p
-                    om = torch.randn(d, k, generator=self.gen, device=F.device) if k < d else None
                     items.append(dict(F=F, rank=min(r, d), oversample=p, power_iters=self.power_iters, lam=lam,
-                                      omega=om, prec=self.prec))
+                                      omega=None, seed=omega_seed(self.seed, self.inversions, len(items)),
+                                      prec=self.prec))
             outs = kfac.kfac_rsvd_invert_grouped(self.ctx, items)
+            self.inversions += 1
             for i, L in enumerate(self.layers):
                 L.inv = (outs[2 * i], outs[2 * i + 1])
                 L.lam = lam

@@ -53,6 +53,7 @@ def test_null_arguments_rejected_without_device(libkfac):
     assert libkfac.kfac_ea_update_grouped(None, 1, None) == 1
     assert libkfac.kfac_precondition_grouped(None, 1, None) == 1
     assert libkfac.kfac_rsvd_invert_grouped(None, 1, None) == 1
+    assert libkfac.kfac_draw_omega(None, 4, 4, ctypes.c_uint64(1), None, 4) == 1
 
 
 def test_create_without_gpu_fails_loudly(libkfac):
@@ -62,3 +63,48 @@ def test_create_without_gpu_fails_loudly(libkfac):
     h = ctypes.c_void_p()
     st = libkfac.kfac_create(ctypes.byref(h), 0, None)
     assert st != 0 and not h.value
+
+
+def _param_class(decl: str) -> str:
+    decl = " ".join(decl.split())
+    if "*" in decl:
+        return "ptr"
+    if "unsigned long long" in decl or "uint64_t" in decl:
+        return "u64"
+    if "long long" in decl or "int64_t" in decl or "size_t" in decl:
+        return "i64"
+    if decl.startswith("float") or decl.startswith("const float"):
+        return "f32"
+    if decl.startswith("double") or decl.startswith("const double"):
+        return "f64"
+    return "i32"
+
+
+def _ctype_class(t) -> str:
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"
+    if t is ctypes.c_float:
+        return "f32"
+    if t is ctypes.c_double:
+        return "f64"
+    size = ctypes.sizeof(t)
+    unsigned = t(-1).value > 0
+    return {(8, True): "u64", (8, False): "i64", (4, False): "i32"}.get((size, unsigned), "?")
+
+
+def test_binding_argtypes_match_the_header(libkfac):
+    """Every argtypes list the binding declares has the header prototype's
+    parameter count and kinds (a mismatch would pass wrong values silently)."""
+    text = open(os.path.join(ROOT, "include", "kfac.h")).read()
+    protos = dict(re.findall(r"KFAC_API\s+[\w\s\*]+?\b(kfac_\w+)\s*\(([^)]*)\)", text))
+    checked = 0
+    for name, params in protos.items():
+        fn = getattr(libkfac, name)
+        if fn.argtypes is None:
+            continue
+        decls = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        want = [_param_class(p) for p in decls]
+        got = [_ctype_class(t) for t in fn.argtypes]
+        assert got == want, (name, got, want)
+        checked += 1
+    assert checked >= 20, checked

@@ -3,11 +3,13 @@ hooks feed the layers' inputs and output gradients to the library's EA
 update, the factors are inverted on the T_KI schedule and every step's
 gradients come back preconditioned. Checked against the FP64 oracle built from
 the same captured tensors (torch's forward/backward, not the library) and the
-same Gaussian test matrices (re-drawn from the optimizer's seed)."""
+same Gaussian test matrices (the library draws them on the device from the
+optimizer's per-factor seeds; the host generator evaluates the same definition)."""
 import numpy as np
 import pytest
 
 import oracle
+from paper_2206_15397_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,19 +52,18 @@ def test_one_step_matches_oracle(optim, method):
     for h in hs:
         h.remove()
     assert pre.status()[0] == 0
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(5)
     invert = oracle.invert if method == "srevd" else oracle.invert_rsvd
     n = x.shape[0]
-    for m, a, g, j in zip(lins, acts, gouts, grads):
+    for li, (m, a, g, j) in enumerate(zip(lins, acts, gouts, grads)):
         abar = np.hstack([a, np.ones((n, 1))]) if m.bias is not None else a
         fa = oracle.ea_update(np.zeros((abar.shape[1],) * 2), abar.T, rho)
         fg = oracle.ea_update(np.zeros((g.shape[1],) * 2), (n * g).T, rho)
         inv = []
-        for f in (fa, fg):
+        for side, f in enumerate((fa, fg)):
             d = f.shape[0]
             k = min(r, d) + p
-            om = torch.randn(d, k, generator=gen, device="cuda").double().cpu().numpy() if k < d else np.zeros((d, k))
+            om = (inputs.seeded_omega(optim.omega_seed(5, 0, 2 * li + side), d, k).astype(np.float64) if k < d
+                  else np.zeros((d, k)))
             inv.append(invert(f.astype(np.float32).astype(np.float64), om, min(r, d), q, lam))
         (ua, _, ca), (ug, _, cg) = inv
         want = oracle.precondition(j, ua, ca, ug, cg, lam)
