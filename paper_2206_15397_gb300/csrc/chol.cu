@@ -563,8 +563,11 @@ __device__ __forceinline__ void cta_rank_update(float* A, int ks, int k, int j0,
 // blocked factorisation. G32 is the block of the working matrix, already
 // shifted and updated by the previous blocks; trace, shift and pivot floor come
 // from blk.scal (the whole matrix's); raised pivots read the whole G's
-// diagonal; one attempt, a non-finite pivot sets *blk.fail; L (k x k, row
-// stride blk.ldl) is written without flags, stats or shift_out.
+// diagonal. A non-finite pivot retries the block with a growing shift of its
+// own diagonal (the blocked factorisation then factors G + shift I plus a
+// block-diagonal extra shift: R stays invertible and span(Y R^-1) = span(Y));
+// if every attempt fails, *blk.fail is set. L (k x k, row stride blk.ldl) is
+// written without stats or shift_out.
 struct CtaBlock {
   const double* scal;  // [trace, shift, pivot floor] of the whole matrix, or null
   int goff, kfull;
@@ -610,7 +613,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
   double shift = block_mode ? blk.scal[1]
                             : (shift_rel > 0.0 ? shift_rel * trace : (shift_rel < 0.0 ? -shift_rel * trace / k : 0.0));
   int ok = 0;
-  for (int attempt = 0; attempt < (block_mode ? 1 : CHOL_ATTEMPTS) && finite_in; ++attempt) {
+  for (int attempt = 0; attempt < CHOL_ATTEMPTS && finite_in; ++attempt) {
     if (attempt > 0) {
       shift = fmax(shift, 1e-7 * trace) * 100.0;
       if (tid == 0) {
@@ -618,7 +621,9 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
         if (stats) atomicAdd(stats + STAT_CHOL_RETRY, 1ull);
       }
     }
-    const float shf = block_mode ? 0.0f : (float)shift;  // a block of the working matrix is shifted already
+    // a block of the working matrix carries the whole matrix's shift already:
+    // only a retry's increase is added to its diagonal
+    const float shf = block_mode ? (float)(shift - blk.scal[1]) : (float)shift;
     if (G32) {  // lower triangle by asynchronous copies (no registers, all in flight), then the shift
       for (int i = warp; i < k; i += CTA_WARPS) {
 #pragma unroll 1
