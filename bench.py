@@ -26,8 +26,10 @@ used. Per-stage device times come from a separate eager pass with the
 library's stage events on, outside the timed region.
 
 Also reported: the same step end to end through the public API with host
-buffers (pinned H2D of the step's batches, gradients and test matrices, D2H of
-the preconditioned gradients, inside the timed region); the full-eigendecomposition
+buffers (pinned H2D of the step's batches and gradients, and of the test
+matrices when they are inputs (--omega input; by default the library draws them
+on the device from seeds), D2H of the preconditioned gradients, inside the timed
+region); the full-eigendecomposition
 path on the same GPU (torch.linalg.eigh + the same apply) with both paths'
 errors against the exact damped inverse on sampled layers; the roofline of the
 dominant kernel group and of the sketch products; extra lines for the other
@@ -405,7 +407,7 @@ FUSED = {"on": False}   # kfac_step_grouped (per-item dependencies) or the three
 # "input": every factor's test matrix is an input tensor (drawn with torch.randn,
 # copied in with the step's inputs end to end); "seed": the library draws it on
 # the device from a per-factor seed (omega NULL), so it is neither stored nor copied.
-OMEGA = {"mode": "input"}
+OMEGA = {"mode": "seed"}
 
 
 def run_step(kfac, ctx, descs, b):
@@ -562,8 +564,8 @@ def phase_times(kfac, ctx, descs, stream, reps=5):
 def e2e_measure(kfac, ctx, wl, graphs, stream, steps):
     """The captured step end to end with host buffers, pipelined over the
     workload's input/output sets: step i (set b = i % nb) copies its inputs
-    from pinned host memory (every factor's EA batch and test matrix, every
-    layer's gradient) on a copy stream, replays its graph on the compute stream
+    from pinned host memory (every factor's EA batch and, when test matrices
+    are inputs, its test matrix; every layer's gradient) on a copy stream, replays its graph on the compute stream
     once they have landed, and copies its preconditioned gradients back on a
     second copy stream. Step i's input copy waits only for step i - nb's
     compute (the set's previous user), so copies overlap other steps' compute;
@@ -832,8 +834,9 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (no autotuner)")
     ap.add_argument("--fused", action="store_true",
                     help="kfac_step_grouped (per-item dependencies) instead of the three grouped calls in turn")
-    ap.add_argument("--omega", choices=["input", "seed"], default="input",
-                    help="test matrices as input tensors, or drawn on the device from seeds (omega NULL)")
+    ap.add_argument("--omega", choices=["input", "seed"], default="seed",
+                    help="test matrices drawn by the library on the device from seeds (omega NULL), or passed in "
+                         "as input tensors")
     args = ap.parse_args(argv)
     FUSED["on"] = args.fused
     OMEGA["mode"] = args.omega

@@ -166,8 +166,8 @@ struct StageScope {
 // ---- invert ------------------------------------------------------------------
 
 struct InvertLayout {
-  size_t om, y, q, part, g, g32, l32, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, flo, xlo, xlo2,
-      cb, tb, ti, total;
+  size_t om, y, q, part, g, g32, l32, gd, dinv, c, c32, x, lam, work, jac, r32, pt, qn, fp, fb, xb, skws, flo, xlo,
+      xlo2, cb, tb, ti, total;
   long long dp, kp, dpb, skws_floats;
   int nsplit, kchunk;
   bool pack_f, bf16, tails;
@@ -219,6 +219,7 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
   L.g = b.take<double>((size_t)k * k);
   L.g32 = b.take<float>((size_t)k * k);
   L.l32 = b.take<float>((size_t)k * k);
+  L.gd = b.take<double>((size_t)k);
   L.cb = b.take<char>(chol_blocked_ws_bytes(k));
   L.tb = b.take<char>(trsm_blocked_ws_bytes(k, d));
   L.ti = b.take<char>(trsm_inverse_ws_bytes(k, d));
@@ -254,7 +255,8 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
 // operands, split over K with FP32 partials summed with compensation (and
 // symmetrised) into FP64.
 kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const float* Bm, long long ld, int k,
-                     int d, kfac_precision prec, double* out, int stage, float* out32, int symmetrize = 1) {
+                     int d, kfac_precision prec, double* out, int stage, float* out32, int symmetrize = 1,
+                     double* dscale = nullptr) {
   GemmDesc<float> g = {};
   g.M = k; g.N = k; g.K = d;
   g.A = A; g.sam = ld; g.sak = 1;
@@ -275,7 +277,7 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   }
   CK(gemm_f32(g, prec, ctx->stream));
   CK(reduce_splitk_f64(at<float>(ctx, L.part), L.nsplit, g.zstride, k, k, out, k, upper ? 2 : symmetrize,
-                       ctx->dflags, ctx->stream, out32));
+                       ctx->dflags, ctx->stream, out32, dscale));
   return KFAC_OK;
 }
 
@@ -316,8 +318,15 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
 kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, float*& other, int k, int d,
                            int passes, bool final_basis) {
   for (int pass = 0; pass < passes; ++pass) {
-    kfac_status st =
-        gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM, at<float>(ctx, L.g32));
+    // Passes after the first factor the column-scaled Gram D^-1 G D^-1 (unit
+    // diagonal, D = diag(G)^1/2) and solve with D chol(D^-1 G D^-1 + s I): a
+    // column that the shifted pass before left far below unit length (the
+    // directions of a numerically rank-deficient sketch) is normalised instead
+    // of staying short, and the shifts and the pivot floor act relative to
+    // each column's own length.
+    double* dscale = pass > 0 ? at<double>(ctx, L.gd) : nullptr;
+    kfac_status st = gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM,
+                              at<float>(ctx, L.g32), 1, dscale);
     if (st != KFAC_OK) return st;
     {
       STAGE(ctx, ST_CHOL);
@@ -336,12 +345,13 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
       else
         CK(chol_cluster(at<double>(ctx, L.g), k, shift, fp64, at<float>(ctx, L.l32), ctx->dflags, ctx->dstats,
                         ctx->stream, nullptr, at<float>(ctx, L.g32), k, ctx->chol_cluster, ctx->chol_panel));
+      if (dscale && !ctx->trsm_inverse) CK(factor_unscale(at<float>(ctx, L.l32), k, dscale, ctx->stream));
     }
     {
       STAGE(ctx, ST_TRSM);
       if (ctx->trsm_inverse)
         CK(trsm_inverse(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<char>(ctx, L.ti), ctx->dflags,
-                        ctx->wait_cycles, ctx->stream));
+                        ctx->wait_cycles, ctx->stream, dscale));
       else if (ctx->chol_blocked && trsm_blocked_used(k))
         CK(trsm_blocked(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<char>(ctx, L.tb), ctx->dflags,
                         ctx->wait_cycles, ctx->stream));
@@ -474,8 +484,9 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   const int d = a.d, r = std::min(a.rank, a.d), k = a.rank + a.oversample;
   const float* F = a.F;
   int ldf = a.ldf;
-  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work, &L.jac,
-                    &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2, &L.cb, &L.tb, &L.ti})
+  for (size_t* o : {&L.om, &L.y, &L.q, &L.part, &L.g, &L.g32, &L.l32, &L.gd, &L.dinv, &L.c, &L.c32, &L.x, &L.lam, &L.work,
+                    &L.jac, &L.r32, &L.pt, &L.qn, &L.fp, &L.fb, &L.xb, &L.skws, &L.flo, &L.xlo, &L.xlo2, &L.cb, &L.tb,
+                    &L.ti})
     *o += base;
   cudaStream_t s = ctx->stream;
   kfac_status st;

@@ -822,6 +822,23 @@ int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long lon
 
 size_t chol_blocked_ws_bytes(int k) { return k > CTA_KMAX ? cb_layout(k).total : 0; }
 
+namespace {
+__global__ void k_factor_unscale(float* __restrict__ L32, int k, const double* __restrict__ dscale) {
+  const long long n = (long long)k * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k);
+    L32[e] = (float)((double)L32[e] * dscale[i]);
+  }
+}
+}  // namespace
+
+cudaError_t factor_unscale(float* L32, int k, const double* dscale, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_factor_unscale<<<grid_for((long long)k * k), 256, 0, s>>>(L32, k, dscale);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t chol_blocked(const double* G, const float* G32, long long ld32, int k, double shift_rel, float* L32,
                          int* flags, unsigned long long* stats, cudaStream_t s, double* shift_out, void* ws,
                          long long wait_cycles) {
@@ -1222,11 +1239,13 @@ cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, 
 // k^2 d product, which the substitution spends on the SIMT pipes, runs on the
 // tensor cores.
 namespace {
-__global__ void k_identity(float* __restrict__ E, int k, long long ld) {
+// E = I, or diag(1 / dscale) (the right-hand side whose solve with L gives
+// (D L)^-1 = L^-1 D^-1)
+__global__ void k_identity(float* __restrict__ E, int k, long long ld, const double* __restrict__ dscale) {
   const long long n = (long long)k * ld;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / ld, j = e - i * ld;
-    E[e] = (i == j) ? 1.0f : 0.0f;
+    E[e] = (i == j) ? (dscale ? (float)(1.0 / dscale[i]) : 1.0f) : 0.0f;
   }
 }
 
@@ -1257,14 +1276,14 @@ TiLayout ti_layout(int k, int d) {
 size_t trsm_inverse_ws_bytes(int k, int d) { return k > 0 && d > 0 ? ti_layout(k, d).total : 0; }
 
 cudaError_t trsm_inverse(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
-                         void* ws, int* flags, long long wait_cycles, cudaStream_t s) {
+                         void* ws, int* flags, long long wait_cycles, cudaStream_t s, const double* dscale) {
   if (k <= 0 || d <= 0) return cudaSuccess;
   const TiLayout t = ti_layout(k, d);
   char* base = static_cast<char*>(ws);
   float* E = reinterpret_cast<float*>(base + t.E);
   float* Linv = reinterpret_cast<float*>(base + t.Linv);
   float* Y = reinterpret_cast<float*>(base + t.Y);
-  k_identity<<<grid_for((long long)k * t.kp), 256, 0, s>>>(E, k, t.kp);
+  k_identity<<<grid_for((long long)k * t.kp), 256, 0, s>>>(E, k, t.kp, dscale);
   note_launch();
   cudaError_t e = trsm_blocked_used(k)
                       ? trsm_blocked(L, k, E, t.kp, Linv, t.kp, k, base + t.inner, flags, wait_cycles, s)

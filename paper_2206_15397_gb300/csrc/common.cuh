@@ -126,9 +126,13 @@ cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s);
 // out[i, j] = sum_z part[z][i, j] in FP64 (n x n), symmetrised as (S + S^T) / 2
 // with symmetrize = 1, or (symmetrize = 2) from partials that hold only the
 // upper triangle i <= j, mirrored. part has row stride ldp and z stride zstride.
-// out32 (optional): an FP32 copy of the result, n x n dense.
+// out32 (optional): an FP32 copy of the result, n x n dense. dscale (optional,
+// symmetrize 0 or 2): the result is column-scaled, out_ij = S_ij / (d_i d_j)
+// with d_i = sqrt(S_ii) (1 where S_ii is not positive and finite), and
+// dscale[i] = d_i.
 cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out,
-                              int ldo, int symmetrize, int* flags, cudaStream_t s, float* out32 = nullptr);
+                              int ldo, int symmetrize, int* flags, cudaStream_t s, float* out32 = nullptr,
+                              double* dscale = nullptr);
 cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, float* out, long long ldo,
                           cudaStream_t s);
 // Columns j0 .. j0 + ncols - 1 of the seeded d x k Gaussian test matrix (the
@@ -183,6 +187,9 @@ cudaError_t chol_cluster(const double* G, int k, double shift_rel, bool fp64, fl
 // blocks, triangular solves and tensor-core rank updates between them. G32 (row
 // stride ld32) is required; ws: chol_blocked_ws_bytes(k) bytes of device
 // workspace. k within the one-CTA limit goes to chol_cluster.
+// Row i of the lower factor L32 (k x k, dense) times dscale[i]: the factor of
+// a column-scaled Gram (reduce_splitk_f64's dscale) back to the Gram's scale.
+cudaError_t factor_unscale(float* L32, int k, const double* dscale, cudaStream_t s);
 size_t chol_blocked_ws_bytes(int k);
 cudaError_t chol_blocked(const double* G, const float* G32, long long ld32, int k, double shift_rel, float* L32,
                          int* flags, unsigned long long* stats, cudaStream_t s, double* shift_out, void* ws,
@@ -207,10 +214,12 @@ cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, 
                          void* ws, int* flags, long long wait_cycles, cudaStream_t s);
 // The same solve through the explicit inverse: L^-1 by solving the identity,
 // then Qt = (Yt^T L^-T)^T as one FP32-accurate tensor-core product. ws:
-// trsm_inverse_ws_bytes(k, d) bytes of device workspace.
+// trsm_inverse_ws_bytes(k, d) bytes of device workspace. dscale (optional):
+// L is the factor of a column-scaled Gram and the solve uses D L (row i of L
+// times dscale[i]): the inverse solves diag(1 / dscale) instead of I.
 size_t trsm_inverse_ws_bytes(int k, int d);
 cudaError_t trsm_inverse(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
-                         void* ws, int* flags, long long wait_cycles, cudaStream_t s);
+                         void* ws, int* flags, long long wait_cycles, cudaStream_t s, const double* dscale = nullptr);
 
 // FP32 one-sided Jacobi on chol(C + s I) over a thread-block cluster: writes X
 // (k x k FP64, column j = unit eigenvector) and lam (k, unsorted). gscratch:

@@ -211,9 +211,11 @@ __global__ void __launch_bounds__(256) k_gemm_t16_wholek(GemmDesc<float> g) {
   }
 }
 
+__device__ __forceinline__ double column_scale(double g) { return (isfinite(g) && g > 0.0) ? sqrt(g) : 1.0; }
+
 __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
                                 double* __restrict__ out, int ldo, int symmetrize, float* __restrict__ out32,
-                                int* flags) {
+                                int* flags, double* __restrict__ dscale) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // n * n < 2^31
   if (idx >= n * n) return;
   const int i = idx / n, j = idx - i * n;
@@ -221,8 +223,14 @@ __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long
   // product computed on the tiles at and above the diagonal); both halves of
   // the result read it, so the sum is exactly symmetric.
   const int a = symmetrize == 2 ? min(i, j) : i, b = symmetrize == 2 ? max(i, j) : j;
-  const double s = sum_partials(part + (long long)a * ldp + b, nsplit, zstride);
+  double s = sum_partials(part + (long long)a * ldp + b, nsplit, zstride);
   if (!isfinite(s)) raise_flag(flags, KFAC_FLAG_NONFINITE);
+  if (dscale) {  // column scaling: every thread sums the two diagonal entries it needs in the same order
+    const double di = column_scale(sum_partials(part + (long long)i * ldp + i, nsplit, zstride));
+    const double dj = column_scale(sum_partials(part + (long long)j * ldp + j, nsplit, zstride));
+    s /= di * dj;
+    if (i == j) dscale[i] = di;
+  }
   out[(long long)i * ldo + j] = s;
   if (out32 && symmetrize != 1) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
 }
@@ -470,11 +478,12 @@ cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s) {
 }
 
 cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out, int ldo,
-                              int symmetrize, int* flags, cudaStream_t s, float* out32) {
+                              int symmetrize, int* flags, cudaStream_t s, float* out32, double* dscale) {
   long long tot = (long long)n * n;
   if (tot == 0) return cudaSuccess;
+  if (dscale && symmetrize == 1) return cudaErrorInvalidValue;  // scaling reads the reduced diagonal: modes 0 and 2
   k_reduce_splitk<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, zstride, n, ldp, out, ldo, symmetrize,
-                                                                  out32, flags);
+                                                                  out32, flags, dscale);
   note_launch();
   if (symmetrize == 1) {
     k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(out, n, ldo, out32);

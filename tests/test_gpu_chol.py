@@ -81,3 +81,30 @@ def test_large_k_zero_and_nonfinite_factors(kf, blocked, inverse):
         kf.kfac_rsvd_invert(ctx, cuda(f), r, p, 1, 0.1, om)
         st, flags = kf.kfac_get_status(ctx)
         assert st != 0 and "NONFINITE" in flags, (st, flags)
+
+
+@pytest.mark.parametrize("inverse", [1, 0])
+def test_steep_spectrum_blocked_factorisations_do_not_break_down(kf, inverse):
+    """A k = 522 sketch of a factor whose eigenvalues fall as i^-3.6 over 640
+    directions (the steepest of the batching-stress set): the sketch is
+    numerically rank-deficient from about the 80th column, and the blocked
+    Cholesky of the CholeskyQR Grams once overflowed in a diagonal block on some
+    test matrices. Over many seeded draws every inversion must succeed (a block
+    that overflows is retried with a shift of its own), with orthonormal U and
+    the leading eigenvalues of the factor."""
+    d, m, r, p, lam = 3238, 640, 512, 10, 0.1
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(19)
+    v, _ = torch.linalg.qr(torch.randn(d, m, generator=gen, device="cuda", dtype=torch.float64))
+    s2 = torch.arange(1, m + 1, device="cuda", dtype=torch.float64) ** (-3.63)
+    F = ((v * s2) @ v.T).float()
+    lam_ref = s2[:r].cpu().numpy()
+    with kf.Context(0) as ctx:
+        kf.kfac_set_option(ctx, "trsm_inverse", inverse)
+        for seed in range(12):
+            U, D, _ = kf.kfac_rsvd_invert(ctx, F, r, p, 1, lam, None, seed=1000 + seed)
+            st, flags = kf.kfac_get_status(ctx)
+            assert st == 0 and set(flags) <= {"CHOL_SHIFTED", "EIG_SHIFTED"}, (seed, st, flags)
+            u = U.double()
+            assert (u.T @ u - torch.eye(r, device="cuda", dtype=torch.float64)).abs().max().item() <= 1e-4, seed
+            assert np.abs(host(D) - lam_ref).max() <= 1e-5 * lam_ref[0], seed
