@@ -334,8 +334,8 @@ KFAC_API kfac_status kfac_precondition_noalloc(void* stream, int d_g, int d_a, c
  * products may fill (KFAC_OPT_SPLIT_TARGET) and, when a sketch width exceeds
  * the one-CTA Cholesky's 236, the large-order Cholesky: blocked or on a
  * cluster (KFAC_OPT_CHOL_BLOCKED) and, for the cluster kernel, its size and
- * panel width (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL); and the form of the
- * CholeskyQR solves (KFAC_OPT_TRSM_INVERSE). Runs
+ * panel width (KFAC_OPT_CHOL_CLUSTER, KFAC_OPT_CHOL_PANEL); the form of the
+ * CholeskyQR solves (KFAC_OPT_TRSM_INVERSE) is reported as set. Runs
  * kfac_rsvd_invert_grouped(ctx, count, descs) once plus twice timed (CUDA
  * events on the context stream) per candidate of a coordinate descent from the
  * current settings, writing the descriptors' outputs as a call would, and
@@ -436,12 +436,15 @@ typedef enum {
                                        CholeskyQR solves Q^T = L^-1 Y^T of order above 288 are
                                        blocked the same way (the off-diagonal work as
                                        tensor-core products) */
-  KFAC_OPT_TRSM_INVERSE = 21,       /* [1]: the CholeskyQR solves Q^T = L^-1 Y^T (Alg. 3's QR
-                                       step) form L^-1 once by solving the k x k identity, then
-                                       Q^T as one FP32-accurate tensor-core product with the
-                                       transposed basis (2 k^2 d flops on the tensor cores);
-                                       0 = block substitution on the SIMT pipes (shared-memory
-                                       solve, blocked above order 288) */
+  KFAC_OPT_TRSM_INVERSE = 21,       /* [0]: 1 = the CholeskyQR solves Q^T = L^-1 Y^T (Alg. 3's
+                                       QR step) form L^-1 once by solving the k x k identity,
+                                       then Q^T as one FP32-accurate tensor-core product with
+                                       the transposed basis (2 k^2 d flops on the tensor cores):
+                                       faster on some GPUs, but the explicit inverse of a nearly
+                                       singular factor (a numerically rank-deficient sketch of
+                                       a steep spectrum) can overflow; 0 = block substitution
+                                       on the SIMT pipes (shared-memory solve, blocked above
+                                       order 288). The autotuner leaves it as set */
   KFAC_OPT_CHOL_PANEL = 18,         /* [16]: panel width of the multi-CTA Cholesky, 16 or 32
                                        (halved while its shared memory overflows); wider panels
                                        take half the cluster barriers and broadcasts */

@@ -77,7 +77,7 @@ struct kfac_ctx {
   long long conv_chunk = 32LL << 20;  // KFAC_OPT_CONV_CHUNK: floats of one patch-matrix chunk
   int tail_planes = 1;                // KFAC_OPT_TAIL_PLANES: precomputed 3xTF32 tails of the large operands
   int chol_blocked = 1;               // KFAC_OPT_CHOL_BLOCKED: blocked FP32 Cholesky above the one-CTA limit
-  int trsm_inverse = 1;               // KFAC_OPT_TRSM_INVERSE: CholeskyQR solves through L^-1 and one product
+  int trsm_inverse = 0;               // KFAC_OPT_TRSM_INVERSE: CholeskyQR solves through L^-1 and one product
 };
 
 namespace {
@@ -1436,16 +1436,18 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
     };
     // Coordinate descent over the knobs, from the current settings: streams,
     // blocked or cluster Cholesky, split target, then the cluster kernel's
-    // size and panel width if it is in use.
+    // size and panel width if it is in use. The solve form is left as set: the
+    // explicit inverse is faster on some GPUs but less robust (its inverse of
+    // a nearly singular factor can overflow), a choice for the caller.
     const int streams_c[] = {4, 8, 16, 32};
     const int chol_c[] = {0, 8, 12};
     const int split_c[] = {0, 304, -1};
     const int panel_c[] = {16, 32};
     const int blocked_c[] = {1, 0};
     const int inverse_c[] = {1, 0};
-    const int order[6] = {0, 5, 4, 2, 1, 3};
+    const int order[5] = {0, 4, 2, 1, 3};
     kfac_status st = run(cfg, &best_ms);
-    for (int oi = 0; oi < 6 && st == KFAC_OK; ++oi) {
+    for (int oi = 0; oi < 5 && st == KFAC_OK; ++oi) {
       const int dim = order[oi];
       const int* cand = dim == 0 ? streams_c
                                  : (dim == 1 ? chol_c

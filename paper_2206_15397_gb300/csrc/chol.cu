@@ -563,16 +563,18 @@ __device__ __forceinline__ void cta_rank_update(float* A, int ks, int k, int j0,
 // blocked factorisation. G32 is the block of the working matrix, already
 // shifted and updated by the previous blocks; trace, shift and pivot floor come
 // from blk.scal (the whole matrix's); raised pivots read the whole G's
-// diagonal. A non-finite pivot retries the block with a growing shift of its
-// own diagonal (the blocked factorisation then factors G + shift I plus a
-// block-diagonal extra shift: R stays invertible and span(Y R^-1) = span(Y));
-// if every attempt fails, *blk.fail is set. L (k x k, row stride blk.ldl) is
+// diagonal. With blk.retry, a non-finite pivot retries the block with a
+// growing shift of its own diagonal (the blocked factorisation then factors
+// G + shift I plus a block-diagonal extra shift: R stays invertible and
+// span(Y R^-1) = span(Y), all a CholeskyQR pass needs); if every attempt
+// fails, *blk.fail is set. L (k x k, row stride blk.ldl) is
 // written without stats or shift_out.
 struct CtaBlock {
   const double* scal;  // [trace, shift, pivot floor] of the whole matrix, or null
   int goff, kfull;
   int* fail;
   long long ldl;
+  int retry;  // a block that overflows may be refactored with a shift of its own
 };
 
 __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* __restrict__ G,
@@ -613,7 +615,8 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_chol_cta_f32(const double* _
   double shift = block_mode ? blk.scal[1]
                             : (shift_rel > 0.0 ? shift_rel * trace : (shift_rel < 0.0 ? -shift_rel * trace / k : 0.0));
   int ok = 0;
-  for (int attempt = 0; attempt < CHOL_ATTEMPTS && finite_in; ++attempt) {
+  const int attempts = (block_mode && !blk.retry) ? 1 : CHOL_ATTEMPTS;
+  for (int attempt = 0; attempt < attempts && finite_in; ++attempt) {
     if (attempt > 0) {
       shift = fmax(shift, 1e-7 * trace) * 100.0;
       if (tid == 0) {
@@ -863,7 +866,9 @@ cudaError_t chol_blocked(const double* G, const float* G32, long long ld32, int 
   for (int o = 0; o < k; o += c.kb) {
     const int kb = std::min(c.kb, k - o), n = k - o - kb;
     float* Wbb = W + (size_t)o * c.kp + o;
-    CtaBlock blk{scal, o, k, fail, kb};
+    // shift_out asks for one shift of the whole matrix (the eigensolver
+    // subtracts it): no block may add its own
+    CtaBlock blk{scal, o, k, fail, kb, shift_out ? 0 : 1};
     k_chol_cta_f32<<<1, CTA_THREADS, cta_smem_bytes(kb), s>>>(G, Wbb, c.kp, kb, 0.0, Lb, flags, nullptr, nullptr,
                                                                 blk);
     note_launch();
@@ -1239,13 +1244,11 @@ cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, 
 // k^2 d product, which the substitution spends on the SIMT pipes, runs on the
 // tensor cores.
 namespace {
-// E = I, or diag(1 / dscale) (the right-hand side whose solve with L gives
-// (D L)^-1 = L^-1 D^-1)
-__global__ void k_identity(float* __restrict__ E, int k, long long ld, const double* __restrict__ dscale) {
+__global__ void k_identity(float* __restrict__ E, int k, long long ld) {
   const long long n = (long long)k * ld;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / ld, j = e - i * ld;
-    E[e] = (i == j) ? (dscale ? (float)(1.0 / dscale[i]) : 1.0f) : 0.0f;
+    E[e] = (i == j) ? 1.0f : 0.0f;
   }
 }
 
@@ -1283,13 +1286,13 @@ cudaError_t trsm_inverse(const float* L, int k, const float* Yt, long long ldy, 
   float* E = reinterpret_cast<float*>(base + t.E);
   float* Linv = reinterpret_cast<float*>(base + t.Linv);
   float* Y = reinterpret_cast<float*>(base + t.Y);
-  k_identity<<<grid_for((long long)k * t.kp), 256, 0, s>>>(E, k, t.kp, dscale);
+  k_identity<<<grid_for((long long)k * t.kp), 256, 0, s>>>(E, k, t.kp);
   note_launch();
   cudaError_t e = trsm_blocked_used(k)
                       ? trsm_blocked(L, k, E, t.kp, Linv, t.kp, k, base + t.inner, flags, wait_cycles, s)
                       : trsm_lower_f32(L, k, E, t.kp, Linv, t.kp, k, reinterpret_cast<float*>(base + t.dinv), s);
   if (e != cudaSuccess) return e;
-  if ((e = transpose_f32(Yt, ldy, k, d, Y, t.kp, s)) != cudaSuccess) return e;
+  if ((e = transpose_f32(Yt, ldy, k, d, Y, t.kp, s, dscale)) != cudaSuccess) return e;
   GemmDesc<float> g = {};
   g.M = d; g.N = k; g.K = k;
   g.A = Y; g.sam = t.kp; g.sak = 1;

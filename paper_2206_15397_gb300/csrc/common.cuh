@@ -133,8 +133,9 @@ cudaError_t gemm_small_f32(const GemmDesc<float>& g, cudaStream_t s);
 cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, int n, int ldp, double* out,
                               int ldo, int symmetrize, int* flags, cudaStream_t s, float* out32 = nullptr,
                               double* dscale = nullptr);
+// out (cols x rows) = in^T; with rdiv, row r of in is divided by rdiv[r] first.
 cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, float* out, long long ldo,
-                          cudaStream_t s);
+                          cudaStream_t s, const double* rdiv = nullptr);
 // Columns j0 .. j0 + ncols - 1 of the seeded d x k Gaussian test matrix (the
 // generator kfac_draw_omega documents): out (d x ncols, row stride ld) or, with
 // trans, its transpose (ncols x d, row stride ld).
@@ -216,7 +217,9 @@ cudaError_t trsm_blocked(const float* L, int k, const float* Yt, long long ldy, 
 // then Qt = (Yt^T L^-T)^T as one FP32-accurate tensor-core product. ws:
 // trsm_inverse_ws_bytes(k, d) bytes of device workspace. dscale (optional):
 // L is the factor of a column-scaled Gram and the solve uses D L (row i of L
-// times dscale[i]): the inverse solves diag(1 / dscale) instead of I.
+// times dscale[i]): Qt = L^-1 (D^-1 Yt), the rows of Yt divided by dscale as
+// they are transposed for the product (L^-1 itself is not scaled, so it keeps
+// the magnitude it has without the scaling).
 size_t trsm_inverse_ws_bytes(int k, int d);
 cudaError_t trsm_inverse(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
                          void* ws, int* flags, long long wait_cycles, cudaStream_t s, const double* dscale = nullptr);

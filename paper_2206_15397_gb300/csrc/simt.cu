@@ -251,13 +251,17 @@ __global__ void k_symmetrize(double* __restrict__ out, int n, int ldo, float* __
   }
 }
 
+// out[c][r] = in[r][c], or in[r][c] / rdiv[r] when rdiv is given
 __global__ void k_transpose(const float* __restrict__ in, long long ldi, int rows, int cols, float* __restrict__ out,
-                            long long ldo) {
+                            long long ldo, const double* __restrict__ rdiv) {
   __shared__ float tile[32][33];
   int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     int r = r0 + y, c = c0 + threadIdx.x;
-    if (r < rows && c < cols) tile[y][threadIdx.x] = in[(long long)r * ldi + c];
+    if (r < rows && c < cols) {
+      const float v = in[(long long)r * ldi + c];
+      tile[y][threadIdx.x] = rdiv ? (float)((double)v / rdiv[r]) : v;
+    }
   }
   __syncthreads();
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -493,10 +497,10 @@ cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, 
 }
 
 cudaError_t transpose_f32(const float* in, long long ldi, int rows, int cols, float* out, long long ldo,
-                          cudaStream_t s) {
+                          cudaStream_t s, const double* rdiv) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   dim3 grid((cols + 31) / 32, (rows + 31) / 32);
-  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, ldi, rows, cols, out, ldo);
+  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, ldi, rows, cols, out, ldo, rdiv);
   note_launch();
   return cudaGetLastError();
 }
