@@ -213,9 +213,17 @@ __global__ void __launch_bounds__(256) k_gemm_t16_wholek(GemmDesc<float> g) {
 
 __device__ __forceinline__ double column_scale(double g) { return (isfinite(g) && g > 0.0) ? sqrt(g) : 1.0; }
 
+// dscale[i] = sqrt(S_ii) of the summed partials (1 where S_ii is not positive
+// and finite), summed in the same order as the reduce below sums S_ii
+__global__ void k_diag_scale(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
+                             double* __restrict__ dscale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dscale[i] = column_scale(sum_partials(part + (long long)i * ldp + i, nsplit, zstride));
+}
+
 __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long long zstride, int n, int ldp,
                                 double* __restrict__ out, int ldo, int symmetrize, float* __restrict__ out32,
-                                int* flags, double* __restrict__ dscale) {
+                                int* flags, const double* __restrict__ dscale) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // n * n < 2^31
   if (idx >= n * n) return;
   const int i = idx / n, j = idx - i * n;
@@ -225,12 +233,7 @@ __global__ void k_reduce_splitk(const float* __restrict__ part, int nsplit, long
   const int a = symmetrize == 2 ? min(i, j) : i, b = symmetrize == 2 ? max(i, j) : j;
   double s = sum_partials(part + (long long)a * ldp + b, nsplit, zstride);
   if (!isfinite(s)) raise_flag(flags, KFAC_FLAG_NONFINITE);
-  if (dscale) {  // column scaling: every thread sums the two diagonal entries it needs in the same order
-    const double di = column_scale(sum_partials(part + (long long)i * ldp + i, nsplit, zstride));
-    const double dj = column_scale(sum_partials(part + (long long)j * ldp + j, nsplit, zstride));
-    s /= di * dj;
-    if (i == j) dscale[i] = di;
-  }
+  if (dscale) s /= dscale[i] * dscale[j];  // column scaling (k_diag_scale ran first)
   out[(long long)i * ldo + j] = s;
   if (out32 && symmetrize != 1) out32[(long long)i * n + j] = (float)s;  // FP32 copy for FP32 consumers (n x n, dense)
 }
@@ -486,6 +489,10 @@ cudaError_t reduce_splitk_f64(const float* part, int nsplit, long long zstride, 
   long long tot = (long long)n * n;
   if (tot == 0) return cudaSuccess;
   if (dscale && symmetrize == 1) return cudaErrorInvalidValue;  // scaling reads the reduced diagonal: modes 0 and 2
+  if (dscale) {
+    k_diag_scale<<<(n + 127) / 128, 128, 0, s>>>(part, nsplit, zstride, n, ldp, dscale);
+    note_launch();
+  }
   k_reduce_splitk<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, zstride, n, ldp, out, ldo, symmetrize,
                                                                   out32, flags, dscale);
   note_launch();
