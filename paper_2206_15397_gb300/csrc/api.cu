@@ -1408,6 +1408,7 @@ KFAC_API kfac_status kfac_autotune_invert(kfac_ctx* ctx, int count, const kfac_i
   int cfg[6] = {ctx->group_streams, ctx->chol_cluster, ctx->split_target, ctx->chol_panel, ctx->chol_blocked,
                 ctx->trsm_inverse};
   bool cached = cache_path && cache_lookup(cache_path, prop.name, sig, cfg);
+  cfg[5] = ctx->trsm_inverse;  // the solve form stays as set, whatever a cached line holds
   double best_ms = 0.0;
   if (!cached) {
     bool big_k = false;
