@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// Warp-uniform bounded wait: lane 0 polls, the verdict is broadcast.
+// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast.
 __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* flags, int lane, long long limit) {
   int ok = 1;
   if (lane == 0) ok = mbar_wait(bar, parity, flags, limit) ? 1 : 0;
