@@ -89,3 +89,14 @@ def test_seeded_omega_moments():
     # columns of a sketch are uncorrelated
     c = np.corrcoef(inputs.seeded_omega(6, 4000, 8).T.astype(np.float64))
     assert np.abs(c - np.eye(8)).max() < 0.06
+
+
+def test_training_layer_omega_seeds_are_distinct():
+    """The training layer keys every factor's test matrix by (optimiser seed,
+    inversion count, factor position): no two inversions or factors of one
+    optimiser share a seed, and two optimisers with different seeds differ."""
+    from paper_2206_15397_gb300.optim import omega_seed
+    seeds = {omega_seed(5, inv, f) for inv in range(200) for f in range(64)}
+    assert len(seeds) == 200 * 64
+    assert omega_seed(5, 0, 0) != omega_seed(6, 0, 0)
+    assert all(0 <= s < 2 ** 64 for s in seeds)
