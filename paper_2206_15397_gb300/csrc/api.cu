@@ -254,9 +254,10 @@ InvertLayout invert_layout(int d, int k, int r, bool pack_f, bool bf16 = false, 
 // Gram-type product out = A A'^T (k x k, K = d) for two k x d row-major
 // operands, split over K with FP32 partials summed with compensation (and
 // symmetrised) into FP64.
+// a_tails_ready: L.xlo already holds A's TF32 tails (stored by the solve that produced A).
 kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const float* Bm, long long ld, int k,
                      int d, kfac_precision prec, double* out, int stage, float* out32, int symmetrize = 1,
-                     double* dscale = nullptr) {
+                     double* dscale = nullptr, bool a_tails_ready = false) {
   GemmDesc<float> g = {};
   g.M = k; g.N = k; g.K = d;
   g.A = A; g.sam = ld; g.sak = 1;
@@ -270,7 +271,7 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
   g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   StageScope sc(ctx, stage);
   if (L.tails && prec == KFAC_PREC_FP32) {
-    CK(tails_f32(A, ld, k, d, at<float>(ctx, L.xlo), L.dp, ctx->stream));
+    if (!a_tails_ready) CK(tails_f32(A, ld, k, d, at<float>(ctx, L.xlo), L.dp, ctx->stream));
     g.A_lo = at<float>(ctx, L.xlo); g.ld_alo = L.dp;
     if (Bm != A) CK(tails_f32(Bm, ld, k, d, at<float>(ctx, L.xlo2), L.dp, ctx->stream));
     g.B_lo = at<float>(ctx, Bm != A ? L.xlo2 : L.xlo); g.ld_blo = L.dp;
@@ -286,7 +287,8 @@ kfac_status gram_f64(kfac_ctx* ctx, const InvertLayout& L, const float* A, const
 // Xt the small one (B, N = k); the transposed store of the d x k product lands
 // row-major in Yt. F is symmetric, so A(m, kk) = F[m][kk] reads F row-major.
 kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt, long long ldx, const float* F,
-                           int ldf, int k, int d, kfac_precision prec, float* out, long long ldo) {
+                           int ldf, int k, int d, kfac_precision prec, float* out, long long ldo,
+                           bool x_tails_ready = false) {
   GemmDesc<float> g = {};
   g.M = d; g.N = k; g.K = d;
   g.A = F; g.sam = ldf; g.sak = 1;
@@ -304,7 +306,7 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
   g.flags = ctx->dflags; g.wait_cycles = ctx->wait_cycles; g.split_target = ctx->split_target;
   STAGE(ctx, ST_SKETCH);
   if (L.tails && prec == KFAC_PREC_FP32) {  // F's tails were formed once per inversion
-    CK(tails_f32(Xt, ldx, k, d, at<float>(ctx, L.xlo), L.dp, ctx->stream));
+    if (!x_tails_ready) CK(tails_f32(Xt, ldx, k, d, at<float>(ctx, L.xlo), L.dp, ctx->stream));
     g.A_lo = at<float>(ctx, L.flo); g.ld_alo = L.dp;
     g.B_lo = at<float>(ctx, L.xlo); g.ld_blo = L.dp;
   }
@@ -315,8 +317,11 @@ kfac_status sketch_product(kfac_ctx* ctx, const InvertLayout& L, const float* Xt
 // `final_basis`: the basis the eigenpairs are taken in (the last one of Alg. 3);
 // a basis that only feeds the next power iteration may factor every pass in
 // FP32 (KFAC_OPT_CHOLQR_INNER_FP32).
+// *tails_ready (optional): on return, whether L.xlo holds the TF32 tails of the
+// basis in cur (the shared-memory substitution solve stores them beside it).
 kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, float*& other, int k, int d,
-                           int passes, bool final_basis) {
+                           int passes, bool final_basis, bool* tails_ready = nullptr) {
+  bool ready = false;  // L.xlo holds the tails of cur
   for (int pass = 0; pass < passes; ++pass) {
     // Passes after the first factor the column-scaled Gram D^-1 G D^-1 (unit
     // diagonal, D = diag(G)^1/2) and solve with D chol(D^-1 G D^-1 + s I): a
@@ -326,7 +331,7 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
     // each column's own length.
     double* dscale = pass > 0 ? at<double>(ctx, L.gd) : nullptr;
     kfac_status st = gram_f64(ctx, L, cur, cur, L.dp, k, d, KFAC_PREC_FP32, at<double>(ctx, L.g), ST_GRAM,
-                              at<float>(ctx, L.g32), 1, dscale);
+                              at<float>(ctx, L.g32), 1, dscale, ready);
     if (st != KFAC_OK) return st;
     {
       STAGE(ctx, ST_CHOL);
@@ -347,19 +352,25 @@ kfac_status orthonormalise(kfac_ctx* ctx, const InvertLayout& L, float*& cur, fl
                         ctx->stream, nullptr, at<float>(ctx, L.g32), k, ctx->chol_cluster, ctx->chol_panel));
       if (dscale && !ctx->trsm_inverse) CK(factor_unscale(at<float>(ctx, L.l32), k, dscale, ctx->stream));
     }
+    ready = false;
     {
       STAGE(ctx, ST_TRSM);
-      if (ctx->trsm_inverse)
+      if (ctx->trsm_inverse) {
         CK(trsm_inverse(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<char>(ctx, L.ti), ctx->dflags,
                         ctx->wait_cycles, ctx->stream, dscale));
-      else if (ctx->chol_blocked && trsm_blocked_used(k))
+      } else if (ctx->chol_blocked && trsm_blocked_used(k)) {
         CK(trsm_blocked(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<char>(ctx, L.tb), ctx->dflags,
                         ctx->wait_cycles, ctx->stream));
-      else
-        CK(trsm_lower_f32(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<float>(ctx, L.dinv), ctx->stream));
+      } else {  // the solve stores the new basis's tails beside it: no tails pass before its next product
+        float* qlo = L.tails ? at<float>(ctx, L.xlo) : nullptr;
+        CK(trsm_lower_f32(at<float>(ctx, L.l32), k, cur, L.dp, other, L.dp, d, at<float>(ctx, L.dinv), ctx->stream,
+                          qlo, L.dp));
+        ready = qlo != nullptr;
+      }
     }
     std::swap(cur, other);
   }
+  if (tails_ready) *tails_ready = ready;
   return KFAC_OK;
 }
 
@@ -533,12 +544,13 @@ kfac_status invert_run(kfac_ctx* ctx, const kfac_invert_desc& a, InvertLayout L,
   st = sketch_product(ctx, L, Om, L.dp, F, ldf, k, d, a.prec, cur, L.dp);  // Y^T = Omega^T F
   if (st != KFAC_OK) return st;
   for (int it = 0;; ++it) {
+    bool q_tails = false;
     st = orthonormalise(ctx, L, cur, other, k, d,
                         it == a.power_iters ? ctx->cholqr_passes : ctx->cholqr_inner_passes,
-                        it == a.power_iters);  // Q^T in cur
+                        it == a.power_iters, &q_tails);  // Q^T in cur
     if (st != KFAC_OK) return st;
     if (it == a.power_iters) break;
-    st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp);  // Y^T = Q^T F
+    st = sketch_product(ctx, L, cur, L.dp, F, ldf, k, d, a.prec, other, L.dp, q_tails);  // Y^T = Q^T F
     if (st != KFAC_OK) return st;
     std::swap(cur, other);
   }

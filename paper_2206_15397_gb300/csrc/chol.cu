@@ -946,7 +946,8 @@ __device__ __forceinline__ void trsm_tile_async(float* dst, const float* __restr
 
 __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restrict__ L, const float* __restrict__ Dinv,
                                                             int k, const float* __restrict__ Yt, long long ldy,
-                                                            float* __restrict__ Qt, long long ldq, int d) {
+                                                            float* __restrict__ Qt, long long ldq, int d,
+                                                            float* __restrict__ Qlo, long long ldlo) {
   extern __shared__ __align__(16) float tsm[];
   float* X = tsm;                          // kpad x TR_COLS
   const int kpad = (k + TR_RB - 1) / TR_RB * TR_RB;
@@ -1001,7 +1002,10 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower(const float* __restri
           const int ri = r0 + 8 * v;
           if (ri < ib) {
             X[(size_t)(i0 + ri) * TR_COLS + c] = out[v];
-            if (col < d) Qt[(long long)(i0 + ri) * ldq + col] = out[v];
+            if (col < d) {
+              Qt[(long long)(i0 + ri) * ldq + col] = out[v];
+              if (Qlo) Qlo[(long long)(i0 + ri) * ldlo + col] = tf32_tail(out[v]);
+            }
           }
         }
       }
@@ -1069,7 +1073,8 @@ __host__ __device__ inline size_t trsm_smem_floats(int T) {
 
 __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower_smem(const float* __restrict__ Lpk, int k, int T,
                                                                  const float* __restrict__ Yt, long long ldy,
-                                                                 float* __restrict__ Qt, long long ldq, int d) {
+                                                                 float* __restrict__ Qt, long long ldq, int d,
+                                                                 float* __restrict__ Qlo, long long ldlo) {
   extern __shared__ __align__(16) float tsm[];
   const int kpad = 32 * T, xs = kpad + 4;
   float* Lp = tsm;                                     // block row I at 1024 I (I+1) / 2: [32][32 (I+1)]
@@ -1119,7 +1124,10 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower_smem(const float* __r
     for (int u = 0; u < 4; ++u) {
       const int row = 32 * I + 4 * w + u;
       Xc[(size_t)c * xs + row] = out[u];
-      if (row < k && col < d) Qt[(long long)row * ldq + col] = out[u];
+      if (row < k && col < d) {
+        Qt[(long long)row * ldq + col] = out[u];
+        if (Qlo) Qlo[(long long)row * ldlo + col] = tf32_tail(out[u]);
+      }
     }
     __syncthreads();
   }
@@ -1127,7 +1135,7 @@ __global__ void __launch_bounds__(TR_THREADS) k_trsm_lower_smem(const float* __r
 }  // namespace
 
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
-                           float* dinv_ws, cudaStream_t s) {
+                           float* dinv_ws, cudaStream_t s, float* qlo, long long ldlo) {
   if (k <= 0 || d <= 0) return cudaSuccess;
   const int kpad = (k + TR_RB - 1) / TR_RB * TR_RB;  // X rows incl. the padded tail block
   size_t smem = sizeof(float) * ((size_t)kpad * TR_COLS + 2 * TR_RB * (TR_RB + 1));
@@ -1145,14 +1153,14 @@ cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy
       k_trsm_pack<<<T, 256, 0, s>>>(L, k, dinv_ws);
       note_launch();
       k_trsm_lower_smem<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem_all, s>>>(dinv_ws, k, T, Yt, ldy, Qt, ldq,
-                                                                                  d);
+                                                                                  d, qlo, ldlo);
       note_launch();
       return cudaGetLastError();
     }
   }
   k_diag_block_inv<<<(k + TR_RB - 1) / TR_RB, 32, 0, s>>>(L, k, dinv_ws);
   note_launch();
-  k_trsm_lower<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem, s>>>(L, dinv_ws, k, Yt, ldy, Qt, ldq, d);
+  k_trsm_lower<<<(d + TR_COLS - 1) / TR_COLS, TR_THREADS, smem, s>>>(L, dinv_ws, k, Yt, ldy, Qt, ldq, d, qlo, ldlo);
   note_launch();
   return cudaGetLastError();
 }

@@ -203,8 +203,10 @@ inline size_t trsm_ws_floats(int k) {
   const size_t T = (size_t)(k + 31) / 32;
   return T * 1024 > 512 * T * (T + 1) ? T * 1024 : 512 * T * (T + 1);
 }
+// qlo (optional, row stride ldlo): the TF32 tails of Qt (tf32_tail) stored
+// beside it, the tail plane the next 3xTF32 product of Qt reads.
 cudaError_t trsm_lower_f32(const float* L, int k, const float* Yt, long long ldy, float* Qt, long long ldq, int d,
-                           float* dinv_ws, cudaStream_t s);
+                           float* dinv_ws, cudaStream_t s, float* qlo = nullptr, long long ldlo = 0);
 // The same solve blocked over the blocked Cholesky's diagonal blocks, the
 // off-diagonal work as FP32-accurate tensor-core products (for k above the
 // shared-memory solve's range: trsm_blocked_used(k)). ws: trsm_blocked_ws_bytes
@@ -289,5 +291,20 @@ cudaError_t polish_E_f32(const double* G, int k, float* w32, cudaStream_t s);
 // singular != 0: lam holds squared singular values; D = sqrt(max(lam, 0)).
 cudaError_t eig_select(const double* X, const double* lam, int k, int r, float lambda, float* Pt, long long ldpt,
                        float* D, float* coef, float* Uout, long long ldu, cudaStream_t s, int singular = 0);
+
+// FP32 rounded to TF32 (to nearest, ties away).
+__device__ __forceinline__ float tf32_head(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// The tail of x below the TF32 the tensor core reads from an FP32 operand (it
+// drops the 13 low mantissa bits), rounded to nearest TF32: x - trunc(x) is
+// exact in FP32 and below 2^-10 |x|, so x ~ trunc(x) + tail to 2^-21 |x|,
+// without a sign bias. The 3xTF32 products' tail planes hold these values.
+__device__ __forceinline__ float tf32_tail(float x) {
+  return tf32_head(x - __uint_as_float(__float_as_uint(x) & 0xffffe000u));
+}
 
 }  // namespace kfac

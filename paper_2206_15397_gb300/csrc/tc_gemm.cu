@@ -193,19 +193,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // truncation) keeps the tail |x - hi| <= 2^-11 |x| and unbiased: truncated heads
 // leave tails of one sign that the tensor core truncates again, biasing every
 // product low by ~1e-6, which chained products accumulate.
-__device__ __forceinline__ float tf32_head(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// The tail of x below the TF32 the tensor core reads from an FP32 operand (it
-// drops the 13 low mantissa bits), rounded to nearest TF32: x - trunc(x) is
-// exact in FP32 and below 2^-10 |x|, so x ~ trunc(x) + tail to 2^-21 |x|,
-// without a sign bias.
-__device__ __forceinline__ float tf32_tail(float x) {
-  return tf32_head(x - __uint_as_float(__float_as_uint(x) & 0xffffe000u));
-}
 
 template <int BN>
 struct Cfg {
